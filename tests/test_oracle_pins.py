@@ -1,0 +1,326 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test names the fact it checks: a textbook stencil, a closed form, an
+identity of the model, or an independent brute-force solver.  The cases are
+chosen so that a dropped term, a wrong sign or index, or a transposed
+operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import fem
+from oracle import periodic as P
+
+
+def _uniform(n, N=4, *, sigma=1.0, nonlinear=True, nu_linear=100.0, amp=50.0):
+    prob = W.unit_square_problem(n, N, amps=(amp,))
+    ne = prob.n_tri
+    return prob.replace(sigma_e=np.full(ne, sigma),
+                        nonlinear_e=np.full(ne, 1 if nonlinear else 0, np.uint8),
+                        nu_linear=nu_linear)
+
+
+# --------------------------------------------------------------------------
+# Assembly: textbook stencils of P1 on the right-triangle grid
+# --------------------------------------------------------------------------
+
+def test_stiffness_is_five_point_laplacian():
+    """P1 stiffness on the uniform right-triangle grid is the classical
+    5-point stencil (4, -1, -1, -1, -1); the diagonal edges carry 0 because
+    the angle opposite them is a right angle."""
+    n = 7
+    prob = _uniform(n)
+    A = fem.stiffness(prob.xy, prob.tri, np.ones(prob.n_tri)).toarray()
+    free = prob.interior
+    ref = np.zeros((n * n, n * n))
+    for j in range(1, n - 1):
+        for i in range(1, n - 1):
+            k = j * n + i
+            ref[k, k] = 4.0
+            for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                ref[k, (j + dj) * n + (i + di)] = -1.0
+    np.testing.assert_allclose(A[np.ix_(free, free)], ref[np.ix_(free, free)], atol=1e-13)
+
+
+def test_mass_stencil_and_total():
+    """Consistent P1 mass with sigma = 1: row of an interior node has
+    h^2/2 on the diagonal and h^2/12 to the six neighbours sharing an edge
+    ((+-1,0), (0,+-1), (1,1), (-1,-1)); the sum of all entries is the area."""
+    n = 9
+    h = 1.0 / (n - 1)
+    prob = _uniform(n, sigma=1.0)
+    M = fem.mass(prob.xy, prob.tri, prob.sigma_e).toarray()
+    assert abs(M.sum() - 1.0) < 1e-13
+    j = i = 4
+    k = j * n + i
+    row = np.zeros(n * n)
+    row[k] = h * h / 2
+    for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1)):
+        row[(j + dj) * n + (i + di)] = h * h / 12
+    np.testing.assert_allclose(M[k], row, atol=1e-15)
+
+
+def test_stiffness_kernel_and_symmetry():
+    """The full-node stiffness annihilates constants (rows sum to zero) and
+    is symmetric."""
+    prob = W.transformer_problem(17, 9, 4)
+    A = fem.stiffness(prob.xy, prob.tri, np.linspace(1, 3, prob.n_tri))
+    assert abs(A - A.T).max() < 1e-13
+    assert np.abs(A @ np.ones(prob.n_nodes)).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Nonlinear operator K
+# --------------------------------------------------------------------------
+
+def test_K_vanishes_on_linear_field():
+    """For u = a x + b y the gradient is constant, so nu is constant and
+    K(u)_i = nu g . sum_T |T| grad(phi_i) = 0 at every interior node."""
+    prob = _uniform(9)
+    u = 0.3 * prob.xy[:, 0] - 0.7 * prob.xy[:, 1]
+    Ku = fem.K_apply(prob, u)
+    assert np.abs(Ku[prob.interior]).max() < 1e-12
+
+
+def test_K_is_gradient_of_coenergy():
+    """K(u) = grad E(u) with E = sum_T |T|/2 W(|g_T|^2), W' = nu, where W is
+    the closed-form antiderivative of the reluctivity law (log form).
+    Checked by central differences on a random field, mixed materials."""
+    prob = W.unit_square_problem(9, 4)
+    rng = np.random.default_rng(3)
+    u = np.zeros(prob.n_nodes)
+    u[prob.interior] = rng.normal(scale=0.8, size=prob.n_free)
+    Ku = fem.K_apply(prob, u)
+    h = 1e-6
+    for i in prob.interior[::5]:
+        e = np.zeros_like(u)
+        e[i] = h
+        fd = (fem.energy(prob, u + e) - fem.energy(prob, u - e)) / (2 * h)
+        assert abs(fd - Ku[i]) <= 1e-7 * max(1.0, abs(Ku[i]))
+
+
+def test_K_one_node_closed_form():
+    """3x3 grid, h = 1/2, single free node c, all elements iron.  Four of the
+    six elements at c have |grad phi_c|^2 = 1/h^2 and two (right angle at c)
+    have 2/h^2, each of area h^2/2, hence
+    K(u_c) = [2 nu(u^2/h^2) + 2 nu(2u^2/h^2)] u_c."""
+    prob = W.one_node_problem(4)
+    h = 0.5
+    for uc in (0.0, 0.1, 0.37, -1.3):
+        u = np.zeros(prob.n_nodes)
+        u[4] = uc
+        nu = lambda s2: fem.nu_law(s2, prob.nu_min, prob.nu_max, prob.s_sat)
+        ref = (2 * nu(uc**2 / h**2) + 2 * nu(2 * uc**2 / h**2)) * uc
+        assert abs(fem.K_apply(prob, u)[4] - ref) < 1e-12 * max(1, abs(ref))
+
+
+def test_nu_law_limits():
+    """nu(0) = nu_min, nu(s_sat) = (nu_min+nu_max)/2, nu(inf) -> nu_max."""
+    assert fem.nu_law(0.0, 1.0, 100.0, 1.0) == 1.0
+    assert abs(fem.nu_law(4.0, 1.0, 100.0, 2.0) - 50.5) < 1e-13
+    assert abs(fem.nu_law(1e12, 1.0, 100.0, 1.0) - 100.0) < 1e-8
+
+
+def test_K_jacobian_matches_differences():
+    """DK(u) v equals the central difference of K along v."""
+    prob = W.unit_square_problem(9, 4)
+    rng = np.random.default_rng(5)
+    u = np.zeros(prob.n_nodes)
+    v = np.zeros(prob.n_nodes)
+    u[prob.interior] = rng.normal(scale=0.7, size=prob.n_free)
+    v[prob.interior] = rng.normal(size=prob.n_free)
+    J = fem.K_jacobian(prob, u)
+    h = 1e-6
+    fd = (fem.K_apply(prob, u + h * v) - fem.K_apply(prob, u - h * v)) / (2 * h)
+    np.testing.assert_allclose(J @ v, fd, rtol=1e-6, atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# Source
+# --------------------------------------------------------------------------
+
+def test_coil_load_total_is_coil_area():
+    """sum_i b_c,i = integral of chi_c = (number of coil elements) * h^2/2
+    on the uniform grid (each element gives |T|/3 to three vertices)."""
+    prob = W.config_plain_fp64()
+    b = fem.coil_load(prob)
+    h = 1.0 / 32
+    count = int((prob.coil_of_elem == 0).sum())
+    assert count > 0
+    assert abs(b.sum() - count * h * h / 2) < 1e-14
+
+
+def test_source_sampling_times():
+    """f^n is sampled at t^n = n tau, n = 1..N: for one coil with phase 0,
+    column N-1 (t = T) is sin(2 pi) b = 0 and column N/4 - 1 is b."""
+    prob = W.config_plain_fp64()
+    d = P.assemble(prob)
+    F = P.source(prob, d)
+    b = d.b[0] * prob.amp[0]
+    assert np.abs(F[:, -1]).max() < 1e-12 * np.abs(b).max()
+    np.testing.assert_allclose(F[:, prob.N // 4 - 1], b, rtol=1e-14, atol=1e-16)
+
+
+# --------------------------------------------------------------------------
+# Exact periodic linear solvers
+# --------------------------------------------------------------------------
+
+def test_periodic_solvers_agree_with_dense():
+    """Space-time sparse LU, time-DFT and a dense solve of the same
+    block-cyclic system agree (odd and even N)."""
+    prob = W.unit_square_problem(6, 5)
+    d = P.assemble(prob)
+    rng = np.random.default_rng(0)
+    for N in (5, 6):
+        B = rng.normal(size=(d.n, N))
+        X0 = P.dense_periodic_solve(d.M, d.L, 0.1, B)
+        X1 = P.SpaceTimeLU(d.M, d.L, 0.1, N).solve(B)
+        X2 = P.DFTSolver(d.M, d.L, 0.1, N).solve(B)
+        np.testing.assert_allclose(X1, X0, rtol=1e-11, atol=1e-13)
+        np.testing.assert_allclose(X2, X0, rtol=1e-11, atol=1e-13)
+
+
+def test_periodic_matrix_structure():
+    """The space-time matrix applied to X gives M(x^n - x^{n-1})/tau + K x^n
+    with x^0 = x^N, written out column by column."""
+    prob = W.unit_square_problem(6, 4)
+    d = P.assemble(prob)
+    rng = np.random.default_rng(1)
+    N, tau = 4, 0.25
+    X = rng.normal(size=(d.n, N))
+    Y = (P.periodic_matrix(d.M, d.L, tau, N) @ X.ravel()).reshape(X.shape)
+    for j in range(N):
+        prev = X[:, N - 1] if j == 0 else X[:, j - 1]
+        ref = d.M @ (X[:, j] - prev) / tau + d.L @ X[:, j]
+        np.testing.assert_allclose(Y[:, j], ref, rtol=1e-13, atol=1e-13)
+
+
+def test_scalar_periodic_closed_form():
+    """One free node, linear material with nu = nu_max (so K = L and the
+    fixed point is exact after one step), f^n = a b sin(2 pi n/N).
+    Closed form: u^n = Im(c e^{i theta n}), theta = 2 pi/N,
+    c = a b / (m (1 - e^{-i theta})/tau + l), m = sigma h^2/2, l = 4 nu_max,
+    b = 6 (h^2/2)/3 with h = 1/2."""
+    N = 8
+    prob = W.one_node_problem(N, nonlinear=False, sigma=10.0, amp=3.0)
+    res = P.fixed_point(prob, tol=1e-14, max_it=5)
+    h = 0.5
+    m = 10.0 * h * h / 2
+    l = 4 * prob.nu_max
+    b = 6 * (h * h / 2) / 3
+    tau = prob.T / N
+    th = 2 * math.pi / N
+    c = 3.0 * b / (m * (1 - np.exp(-1j * th)) / tau + l)
+    ref = np.imag(c * np.exp(1j * th * np.arange(1, N + 1)))
+    np.testing.assert_allclose(res.U[0], ref, rtol=1e-13, atol=1e-16)
+    assert res.iterations == 1
+
+
+# --------------------------------------------------------------------------
+# Fixed-point iteration (Theorem 3) and its limit (Theorem 2)
+# --------------------------------------------------------------------------
+
+def test_one_step_convergence_when_K_is_Khat():
+    """nu = nu_max everywhere makes K = K_hat, so eq. (iter1) is the exact
+    problem and one step gives the solution."""
+    prob = W.unit_square_problem(9, 8)
+    prob = prob.replace(nonlinear_e=np.zeros(prob.n_tri, np.uint8), nu_linear=prob.nu_max)
+    res = P.fixed_point(prob, tol=1e-13, max_it=3)
+    assert res.iterations == 1 and res.converged
+
+
+def test_fixed_point_matches_newton_tiny():
+    """The fixed-point limit equals the solution of A(U) = F obtained by an
+    independent Newton solver (unique by Theorem 2); strong nonlinearity
+    (large source) so that nu varies across the iron."""
+    prob = W.unit_square_problem(7, 6, amps=(4000.0,), coil_boxes=(((0.05, 0.45), (0.2, 0.8)),))
+    d = P.assemble(prob)
+    Un, rel = P.newton(prob, d, tol=1e-14)
+    assert rel < 1e-13
+    res = P.fixed_point(prob, d, tol=1e-14, max_it=20000)
+    assert res.converged
+    err = np.linalg.norm(res.U - Un) / np.linalg.norm(Un)
+    assert err < 1e-11
+    full = P.lift(prob, d, Un)
+    s = np.sqrt((fem.element_gradients(prob, full) ** 2).sum(axis=1))
+    iron = prob.nonlinear_e.astype(bool)
+    # the solution visits both sides of s_sat in the iron, so nu is nonlinear
+    assert s[iron].max() > prob.s_sat > s[iron].min()
+
+
+def test_manufactured_periodic_solution():
+    """Choose U*, set F := A(U*); the iteration recovers U*."""
+    prob = W.unit_square_problem(9, 8)
+    d = P.assemble(prob)
+    x, y = prob.xy[d.free, 0], prob.xy[d.free, 1]
+    t = d.tau * np.arange(1, d.N + 1)
+    U = np.outer(np.sin(math.pi * x) * np.sin(math.pi * y),
+                 np.cos(2 * math.pi * t) + 0.5 * np.sin(4 * math.pi * t)) * 0.8
+    F = P.A_apply(prob, d, U)
+    res = P.fixed_point(prob, d, F=F, tol=1e-13, max_it=20000)
+    assert res.converged
+    assert np.linalg.norm(res.U - U) / np.linalg.norm(U) < 1e-11
+
+
+def test_half_period_antisymmetry_and_contraction():
+    """K is odd and f(t + T/2) = -f(t), so the unique solution satisfies
+    u^{n+N/2} = -u^n.  Theorem 3 with K_hat = nu_max A: the observed ratio
+    ||U^{k+1}-U^k||_Khat / ||U^k-U^{k-1}||_Khat stays below 1 - nu_min/nu_max
+    (the derivative of s nu(s) lies in [nu_min, 2 nu_max - nu_min])."""
+    prob = W.unit_square_problem(9, 8, amps=(3000.0,))
+    d = P.assemble(prob)
+    res = P.fixed_point(prob, d, tol=1e-12, max_it=20000)
+    assert res.converged
+    U = res.U
+    N = d.N
+    assert np.abs(U[:, N // 2:] + U[:, :N // 2]).max() <= 1e-12 * np.abs(U).max()
+    s = np.array(res.step_knorms)
+    ratios = s[1:] / s[:-1]
+    q = 1 - prob.nu_min / prob.nu_max
+    assert ratios.max() <= q + 1e-9
+
+
+def test_linear_rate_closed_form():
+    """Linear material nu = c < nu_max on every element, zero source: the
+    error propagator is P^{-1}(nu_max - c)A.  On the time-mean (k = 0) mode
+    the periodic operator P reduces to nu_max A, so a time-constant start
+    contracts by exactly 1 - c/nu_max per step; a start with zero time mean
+    contracts strictly faster (Re of the discrete symbol > 0 for k != 0)."""
+    c = 40.0
+    prob = W.unit_square_problem(7, 4, amps=(0.0,))
+    prob = prob.replace(nonlinear_e=np.zeros(prob.n_tri, np.uint8), nu_linear=c)
+    d = P.assemble(prob)
+    rng = np.random.default_rng(2)
+    U0 = np.repeat(rng.normal(size=(d.n, 1)), d.N, axis=1)
+    res = P.fixed_point(prob, d, U0=U0, tol=1e-8, max_it=60)
+    s = np.array(res.step_knorms)
+    np.testing.assert_allclose(s[1:] / s[:-1], 1 - c / prob.nu_max, rtol=1e-10)
+    V0 = rng.normal(size=(d.n, d.N))
+    V0 -= V0.mean(axis=1, keepdims=True)
+    res = P.fixed_point(prob, d, U0=V0, tol=1e-8, max_it=60)
+    s = np.array(res.step_knorms)
+    assert (s[1:] / s[:-1]).max() < 1 - c / prob.nu_max - 1e-6
+
+
+def test_zero_source_gives_zero():
+    prob = W.unit_square_problem(7, 4, amps=(0.0,))
+    res = P.fixed_point(prob, tol=1e-10, max_it=3)
+    assert np.abs(res.U).max() == 0.0
+
+
+def test_newton_jacobian_matches_differences():
+    """The space-time Jacobian of A (used by Newton and the adjoint) is the
+    derivative of A: J v = (A(U + h v) - A(U - h v)) / 2h."""
+    prob = W.unit_square_problem(6, 4, amps=(2000.0,))
+    d = P.assemble(prob)
+    rng = np.random.default_rng(4)
+    U = rng.normal(scale=0.05, size=(d.n, d.N))
+    V = rng.normal(size=(d.n, d.N))
+    J = P.jacobian(prob, d, U)
+    h = 1e-7
+    fd = (P.A_apply(prob, d, U + h * V) - P.A_apply(prob, d, U - h * V)) / (2 * h)
+    np.testing.assert_allclose((J @ V.ravel()).reshape(V.shape), fd, rtol=1e-6, atol=1e-7)
