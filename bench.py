@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark: space-time DOF/s of the time-periodic fixed-point solve to tolerance.
+
+One step = one complete solve of the 257x257-node, N = 256 unit-square
+workload (65 025 free nodes x 256 steps = 16.6 M space-time DOFs; iron block
+with the saturating reluctivity law, strip coil with J0 ~ U[20, 80] drawn
+from the rank's seed) from U = 0 until ||F - A(U)|| <= 1e-8 ||F||, in the
+mixed-precision form (float multigrid in time / PCG / SpMM, double outer
+residual and update).  Inputs are resident in HBM when the timed region
+starts; the working set (~1.5 GB) is far larger than L2.
+
+Also reported on the same line:
+  fp64      the same solve with every kernel in double (ALU-bound on GB300)
+  e2e       the same metric through the host-pointer C-ABI call ptp_solve,
+            copies of U0 (in) and U (out) from/to pinned host memory inside
+            the timed region
+  roofline  the level-0 SpMM (M + tau L) X over N right-hand sides in float
+            (K2), timed alone on the context stream with CUDA events,
+            algorithmic bytes / duration against the measured HBM copy peak;
+            roofline_k1: the double outer residual against the FP64 FMA peak
+  cpu_baseline  the CPU oracle on a bounded sample (see `sample`)
+
+Multi-GPU: every rank solves its own seeded instance (independent replicas,
+weak scaling); the only collectives are the timing barriers and a max.
+
+--impl reference times the CPU oracle (the reference arm) on the same
+workload, metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "space-time DOF/s to fixed-point tol 1e-8 (FP64 vs mixed) and % HBM roofline"
+UNIT = "DOF/s"
+TOL = 1e-8
+WORKLOAD = "square257_N256"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 FMA peak of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz
+# (an FMA loop measured 1.20 TFLOP/s on this machine's GB300).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[4] not in ("", "[N/A]") and float(r[4]) > 10] or rows
+        sm = [float(r[1]) for r in loaded]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in loaded for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(loaded)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(prob, iterations_to_tol, repeats=1):
+    """Times the oracle's own pieces on the full workload and extrapolates one
+    solve: setup = (N/2+1) mode factorizations, each outer iteration =
+    two K evaluations (right-hand side and residual) + (N/2+1) mode solves +
+    the forward/backward FFTs.  Iterations to tolerance are those of the
+    method (identical iterates up to rounding)."""
+    from oracle import periodic as P
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    d = P.assemble(prob)
+    F = P.source(prob, d)
+    U = np.zeros((d.n, d.N))
+    t_assemble = time.perf_counter() - t0
+    t_res, t_fac, t_sol, t_fft = [], [], [], []
+    solver = P.DFTSolver(d.M, d.L, d.tau, d.N, keep_factors=False)
+    for _ in range(repeats):
+        t = time.perf_counter(); R = P.residual(prob, d, U, F); t_res.append(time.perf_counter() - t)
+        t = time.perf_counter(); lu = solver._factor(1); t_fac.append(time.perf_counter() - t)
+        t = time.perf_counter(); lu.solve(np.ascontiguousarray(R[:, 0], dtype=np.complex128)); t_sol.append(time.perf_counter() - t)
+        t = time.perf_counter(); np.fft.irfft(np.fft.rfft(R, axis=1), n=d.N, axis=1); t_fft.append(time.perf_counter() - t)
+    modes = d.N // 2 + 1
+    res = min(t_res); fac = min(t_fac); sol = min(t_sol); fft = min(t_fft)
+    per_iter = 2 * res + modes * sol + fft
+    setup = t_assemble + modes * fac
+    total = setup + iterations_to_tol * per_iter
+    wall = time.perf_counter() - t0
+    return {
+        "value": d.n * d.N / total,
+        "unit": UNIT,
+        "cores": cpu_threads() if "OMP_NUM_THREADS" not in os.environ else threads,
+        "kind": "oracle",
+        "sample": (f"{WORKLOAD}: timed one K evaluation, one complex mode factorization and solve and the "
+                   f"time FFTs of the oracle ({wall:.1f} s of CPU work); extrapolated to {modes} modes and "
+                   f"{iterations_to_tol} outer iterations: setup {setup:.0f} s + {per_iter:.2f} s/iteration"),
+        "extrapolated_solve_s": total,
+    }
+
+
+def reduce_scalar(x, op, device, world):
+    """All-reduce of one float over the ranks (max or sum); identity for one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(ms_local, dofs_local, device, world):
+    """Whole-job DOF/s: all ranks' DOFs over the slowest rank's time."""
+    ms = reduce_scalar(ms_local, "max", device, world)
+    dofs = reduce_scalar(dofs_local, "sum", device, world)
+    return dofs / (ms / 1e3), ms
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2502_21013_gb300 import ptp
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        return reduce_scalar(x, "max", dev, world)
+
+    def sum_over_ranks(x):
+        return reduce_scalar(x, "sum", dev, world)
+
+    prob = W.config_mixed(seed=rank)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make(precision):
+        c = ptp.Context(local)
+        c.set_stream(stream.cuda_stream)
+        ptp.load_problem(c, prob)
+        o = ptp.default_opts(precision=precision, tol=TOL, max_outer=args.max_outer)
+        c.setup(o)
+        return c, o
+
+    ctx, opts = make(ptp.PTP_MIXED)
+    info = ctx.info()
+    n, N = info["n_free"], info["N"]
+    dofs = n * N
+    U = torch.zeros((n, N), dtype=torch.float64, device=dev)
+
+    def solve_once(c, o):
+        st, rc = c.solve_dev(U, o)
+        if rc != ptp.PTP_OK and not (args.allow_unconverged and rc == ptp.PTP_ENOTCONV):
+            raise RuntimeError(f"solve did not converge (rc {rc}, {st.outer_iterations} iterations)")
+        return st
+
+    for _ in range(args.warmup):
+        solve_once(ctx, opts)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    iters = []
+    for _ in range(args.steps):
+        st = solve_once(ctx, opts)
+        launches += st.kernel_launches
+        iters.append(st.outer_iterations)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    value, ms = job_throughput(e0.elapsed_time(e1) / args.steps, dofs, dev, world)
+    res_rel = st.res_final / st.res0
+
+    # ---- end to end through the host-pointer C ABI (pinned host buffers) ----
+    U0h = torch.zeros((n, N), dtype=torch.float64).pin_memory()
+    Uh = torch.empty((n, N), dtype=torch.float64).pin_memory()
+    import ctypes
+    barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        s2 = ptp.Stats()
+        rc = ptp.lib.ptp_solve(ctx._h, ctypes.byref(opts), ctypes.c_void_p(U0h.data_ptr()),
+                               ctypes.c_void_p(Uh.data_ptr()), ctypes.byref(s2))
+        if rc != ptp.PTP_OK and not (args.allow_unconverged and rc == ptp.PTP_ENOTCONV):
+            raise RuntimeError(f"host-pointer solve failed: {rc}")
+    e2e_s = max_over_ranks((time.perf_counter() - t) / max(1, args.e2e_steps))
+    e2e_val = sum_over_ranks(dofs) / e2e_s
+
+    # ---- K2 roofline: level-0 SpMM over N right-hand sides in float ----
+    hbm_peak, peak_kind = load_peaks()
+    X = torch.randn((n, N), dtype=torch.float32, device=dev)
+    Y = torch.empty_like(X)
+    for _ in range(5):
+        ctx.apply_shifted_dev(0, X, Y)
+    reps = 50
+    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ka.record(stream)
+    for _ in range(reps):
+        ctx.apply_shifted_dev(0, X, Y)
+    kb.record(stream)
+    torch.cuda.synchronize()
+    k2_s = ka.elapsed_time(kb) / reps / 1e3
+    nnz = info["op_nnz"]
+    k2_bytes = 2 * 4 * n * N + 4 * (n + 1) + 12 * nnz   # X in, Y out, CSR (idx, M, L)
+    k2_gbs = k2_bytes / k2_s / 1e9
+
+    # ---- K1 roofline: outer residual in double, FP64 FMA bound ----
+    Rt = torch.empty((n, N), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        ctx.residual_dev(U, Rt, want_norm=False)
+    ka.record(stream)
+    kreps = 10
+    for _ in range(kreps):
+        ctx.residual_dev(U, Rt, want_norm=False)
+    kb.record(stream)
+    torch.cuda.synchronize()
+    k1_s = ka.elapsed_time(kb) / kreps / 1e3
+    # flops per time step: 24 per iron element (gradient, |g|^2, Newton reciprocal,
+    # nu |T|, flux), 4 per iron incidence, 2 per linear-stiffness and 3 per mass
+    # nonzero, 4 + 2 n_coils per node (source, combination, norm)
+    k1_flops = (24 * info["n_iron"] + 4 * info["iron_incidences"] + 2 * info["lin_nnz"]
+                + 3 * info["mass_nnz"] + (4 + 2 * info["n_coils"]) * n) * N
+    k1_tflops = k1_flops / k1_s / 1e12
+
+    # ---- FP64 leg (same workload, every kernel in double) ----
+    fp64 = None
+    if args.fp64_steps > 0:
+        c64, o64 = make(ptp.PTP_FP64)
+        c64.solve_dev(U, ptp.default_opts(precision=ptp.PTP_FP64, tol=TOL, max_outer=3))  # graph capture
+        barrier()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            s64 = solve_once(c64, o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(f0.elapsed_time(f1) / args.fp64_steps)
+        fp64 = {"value": sum_over_ranks(dofs) / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "outer_iterations": s64.outer_iterations, "dtype": "f64"}
+        del c64
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(prob, iterations_to_tol=iters[-1])
+        cpu.pop("extrapolated_solve_s", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "257x257 nodes, 131072 triangles", "free_nodes": n,
+                       "time_steps": N, "space_time_dofs": dofs, "tol": TOL, "precision": "mixed",
+                       "outer_iterations": iters, "final_rel_residual": res_rel,
+                       "l2": "inputs larger than L2 (U alone is 133 MB)", "parallelism": f"replicas{world}"},
+            "fp64": fp64,
+            "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dofs, "d2h_bytes_per_step": 8 * dofs},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": "K2 level-0 SpMM (M + tau L) X, float, N columns",
+                         "achieved": k2_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": k2_gbs / hbm_peak,
+                         "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes": k2_bytes,
+                         "duration_us": k2_s * 1e6},
+            "roofline_k1": {"bound": "alu", "kernel": "K1 outer residual, double",
+                            "achieved": k1_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": k1_tflops / FP64_PEAK_TFLOPS, "algorithmic_flops": k1_flops,
+                            "duration_us": k1_s * 1e6},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = W.config_mixed(seed=0)
+    iters = args.ref_iterations
+    for _ in range(args.warmup):
+        oracle_sample(prob, iters)
+    t = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        s = oracle_sample(prob, iters)
+        vals.append(s["extrapolated_solve_s"])
+    elapsed = (time.perf_counter() - t) / args.steps
+    solve_s = statistics.median(vals)
+    value = prob.n_free * prob.N / solve_s
+    cpu = {"value": value, "unit": UNIT, "kind": "oracle", "cores": cpu_threads(), "sample": s["sample"]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tol": TOL, "outer_iterations": iters,
+                       "sample_wall_s_per_step": elapsed},
+            "impl": "reference", "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--max-outer", type=int, default=6000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--allow-unconverged", action="store_true",
+                    help="profiling only: accept solves cut short by --max-outer")
+    ap.add_argument("--ref-iterations", type=int, default=1800,
+                    help="outer iterations to 1e-8 used to extrapolate the oracle (measured by the GPU arm)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

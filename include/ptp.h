@@ -1,0 +1,230 @@
+/*
+ * ptp.h -- C ABI of the GB300 time-periodic parabolic solver.
+ *
+ * The library solves the implicit-Euler, time-periodic problem of Problem 1
+ * (Section 2, eq. disc1-disc2):
+ *
+ *     M (u^n - u^{n-1}) / tau + K(u^n) = f^n,   n = 1..N,   u^0 = u^N,
+ *
+ * for P1 finite elements on triangles (Section 4), with
+ *     K(u)_i = sum_T nu(|grad u|_T) |T| grad(u)_T . grad(phi_i),
+ *     nu(s)  = nu_min + (nu_max - nu_min) s^2 / (s^2 + s_sat^2) on iron
+ *              elements and nu_linear elsewhere,
+ *     M      = sigma-weighted consistent P1 mass (degenerate where sigma = 0),
+ *     f^n_i  = sum_c amp_c sin(2 pi t^n / T + phase_c) int(chi_c phi_i),
+ *              t^n = n tau, tau = T / N,
+ * by the fixed-point iteration of eq. (iter1)-(iter2) with
+ * K_hat = L = nu_max * (unit-coefficient stiffness), in correction form
+ *     (M + tau L) d^n - M d^{n-1} = tau (f^n - A(U)^n),  U <- U + d,
+ * each periodic linear system being solved by multigrid in time
+ * (Remark on parallel solvers, Section 3; method (M1), Section 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: PTP_OK (0) or a negative PTP_E* code.  No C++ exception
+ *    crosses this boundary.  ptp_last_error() gives a message.
+ *  - Space-time vectors ("[n_free][N]") hold the free (non-Dirichlet) nodes
+ *    in ascending node id, node-major with the time index fastest:
+ *    X[i * N + (n - 1)] is the value at free node i and time step n.
+ *  - Functions without suffix take HOST pointers; the library copies in and
+ *    out on its stream and returns after the result is on the host.
+ *    Functions with suffix _dev take DEVICE pointers (on the context's
+ *    device), enqueue on the context's stream and return without waiting
+ *    unless stated otherwise.
+ *  - The caller owns every buffer it passes; the library owns its internal
+ *    device state, which lives until ptp_destroy().
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef PTP_H
+#define PTP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PTP_OK        0
+#define PTP_EINVAL   -1   /* invalid argument or inconsistent sizes        */
+#define PTP_ECUDA    -2   /* a CUDA runtime call failed                    */
+#define PTP_ENOTCONV -3   /* max iterations reached; outputs hold the last
+                             iterate and the statistics are filled          */
+#define PTP_ENAN     -4   /* a non-finite residual norm was detected        */
+#define PTP_ESTATE   -5   /* call order violated (e.g. solve before setup)  */
+#define PTP_ENOMEM   -6   /* device allocation failed                       */
+
+/* ---- precision of the inner (linear) solve --------------------------- */
+#define PTP_FP64  0       /* every kernel in double                         */
+#define PTP_MIXED 1       /* multigrid-in-time, smoother, PCG and SpMM in
+                             float with float accumulation; outer residual,
+                             update and coarsest periodic solve in double   */
+
+/* ---- spatial preconditioner of the batched PCG ----------------------- */
+#define PTP_PREC_JACOBI 0 /* diagonal scaling                               */
+#define PTP_PREC_GMG    1 /* geometric multigrid V-cycle on the nested
+                             structured grids (needs ptp_set_structured)    */
+
+typedef struct ptp_ctx ptp_ctx;
+
+/* Solver options; ptp_default_opts() fills sensible defaults. */
+typedef struct ptp_opts {
+    double tol;          /* stop when ||F - A(U^k)||_2 <= tol ||F - A(U^0)||_2
+                            (stopping rule of Section 4)                     */
+    int    max_outer;    /* maximum fixed-point iterations                   */
+    int    precision;    /* PTP_FP64 or PTP_MIXED                            */
+    int    time_levels;  /* multigrid-in-time levels; 0 = coarsen by 2 while
+                            N_l is even and N_l > coarse_steps               */
+    int    coarse_steps; /* N_c of the coarsest level: 1 or 2 (exact solve)  */
+    int    vcycles;      /* multigrid-in-time V-cycles per outer step        */
+    int    pre_smooth;   /* damped block-Jacobi sweeps before coarsening     */
+    int    post_smooth;  /* ... and after                                    */
+    double omega_t;      /* block-Jacobi damping                             */
+    int    pcg_iters;    /* PCG iterations per block-Jacobi spatial solve    */
+    int    spatial_prec; /* PTP_PREC_JACOBI or PTP_PREC_GMG                  */
+    int    gmg_smooth;   /* damped-Jacobi sweeps per GMG level (pre = post)  */
+    double gmg_omega;    /* damping of those sweeps                          */
+    double coarse_tol;   /* relative tolerance of the coarsest-level PCG     */
+    int    coarse_max_it;/* iteration cap of the coarsest-level PCG          */
+    int    use_graph;    /* capture one outer step in a CUDA graph           */
+    int    check_every;  /* host reads the residual every this many steps    */
+} ptp_opts;
+
+/* Statistics of the last solve. */
+typedef struct ptp_stats {
+    int    outer_iterations;  /* fixed-point steps taken                     */
+    int    converged;         /* 1 if the stopping rule was met              */
+    double res0;              /* ||F - A(U^0)||_2                            */
+    double res_final;         /* ||F - A(U^k)||_2 at the returned iterate    */
+    double setup_ms;          /* operator/hierarchy set-up time              */
+    double solve_ms;          /* wall time of the solve call                 */
+    double residual_ms;       /* device time of the last residual evaluation */
+    int64_t kernel_launches;  /* kernels launched by the solve (graph nodes
+                                 counted once per replay)                    */
+    int    time_levels;       /* levels actually used                        */
+    int    spatial_levels;    /* GMG levels actually used (1 = none)         */
+} ptp_stats;
+
+void        ptp_default_opts(ptp_opts* opts);
+const char* ptp_version(void);
+/* sizeof(ptp_opts) and sizeof(ptp_stats) as compiled into the library, so a
+   binding can check its own struct layouts.  Either pointer may be NULL. */
+void        ptp_abi_sizes(size_t* opts_bytes, size_t* stats_bytes);
+
+/* Create a context for CUDA device `device` (>= 0).  No CUDA call is made
+   here: the device is first used by ptp_setup or ptp_set_stream, which also
+   create the context's own non-blocking stream.  The set_* calls below only
+   record host data and work without a GPU. */
+int  ptp_create(ptp_ctx** out, int device);
+/* Free all device memory and the context.  Accepts NULL. */
+void ptp_destroy(ptp_ctx* ctx);
+/* Message of the last failing call on this context ("" if none). */
+const char* ptp_last_error(const ptp_ctx* ctx);
+/* Use an external CUDA stream (cudaStream_t passed as void*; NULL = the
+   context's own stream).  The caller keeps the stream alive. */
+int  ptp_set_stream(ptp_ctx* ctx, void* stream);
+
+/* ---- problem definition (host pointers, copied) ---------------------- */
+
+/* Triangle mesh: xy[2*n_nodes] coordinates, tri[3*n_tri] counter-clockwise
+   vertex ids (0-based), dirichlet[n_nodes] = 1 for homogeneous Dirichlet
+   nodes (u = 0, Section 4).  Returns PTP_EINVAL for bad ids or clockwise /
+   degenerate triangles. */
+int ptp_set_mesh(ptp_ctx* ctx, int n_nodes, const double* xy, int n_tri,
+                 const int32_t* tri, const uint8_t* dirichlet);
+
+/* Declare that the mesh is the uniform nx-by-ny grid on [x0,x1]x[y0,y1]
+   with node (i,j) = j*nx+i, cells split along (i,j)-(i+1,j+1), boundary
+   Dirichlet, and build exactly that mesh (replacing any previous mesh).
+   Enables the geometric-multigrid preconditioner when nx-1 and ny-1 are
+   divisible by 2 on at least one coarsening. */
+int ptp_set_structured(ptp_ctx* ctx, int nx, int ny, double x0, double y0,
+                       double x1, double y1);
+
+/* Materials per element (Section 4, "Test problem"): conductivity sigma_e
+   (>= 0), nonlinear_e = 1 for the iron law, else nu_linear. */
+int ptp_set_materials(ptp_ctx* ctx, const double* sigma_e,
+                      const uint8_t* nonlinear_e, double nu_min,
+                      double nu_max, double s_sat, double nu_linear);
+
+/* Coils: coil_of_elem[n_tri] in [-1, n_coils), amplitude and phase per
+   coil; the current density on coil c is amp_c sin(2 pi t/T + phase_c). */
+int ptp_set_sources(ptp_ctx* ctx, int n_coils, const int32_t* coil_of_elem,
+                    const double* amp, const double* phase);
+
+/* Period T > 0 and number of implicit-Euler steps N >= 1 (tau = T/N). */
+int ptp_set_time(ptp_ctx* ctx, double T, int N);
+
+/* Assemble every operator and hierarchy on the device for `opts`
+   (time levels, precision and preconditioner are fixed here).  Must be
+   called after the set_* calls and again after any of them. */
+int ptp_setup(ptp_ctx* ctx, const ptp_opts* opts);
+
+/* Sizes after ptp_setup: free nodes, time steps, triangles, time levels. */
+int ptp_sizes(const ptp_ctx* ctx, int* n_free, int* N, int* n_tri,
+              int* time_levels);
+
+/* Structure counts after ptp_setup, for roofline arithmetic.  counts[k] is
+   written for k < n (n <= PTP_INFO_COUNT); returns the number written.
+     0 free nodes   1 time steps N     2 triangles       3 iron triangles
+     4 iron element-node incidences    5 nonzeros of the linear-element
+     stiffness      6 nonzeros of the mass (M/tau) rows  7 nonzeros of the
+     level-0 spatial operator M + tau L                  8 spatial levels
+     9 time levels  10 coils                                              */
+#define PTP_INFO_COUNT 11
+int ptp_info(const ptp_ctx* ctx, int64_t* counts, int n);
+
+/* ---- the hot path ---------------------------------------------------- */
+
+/* Source F = (f^1..f^N), [n_free][N] (Problem 1 data, Section 4 source). */
+int ptp_source(ptp_ctx* ctx, double* F);
+int ptp_source_dev(ptp_ctx* ctx, double* F);
+
+/* Outer residual R = F - A(U), A(U)^n = M (u^n - u^{n-1})/tau + K(u^n),
+   u^0 = u^N (proof of Theorem 2), all [n_free][N] in double, and its
+   Euclidean norm (stopping rule of Section 4).  `norm` may be NULL.
+   The _dev form writes the norm to host memory after synchronising. */
+int ptp_residual(ptp_ctx* ctx, const double* U, double* R, double* norm);
+int ptp_residual_dev(ptp_ctx* ctx, const double* U, double* R, double* norm);
+
+/* Y = (M + tau_l L) X for the N_l = N / 2^l columns of time level l
+   (the diagonal blocks of the periodic system at level l), double. */
+int ptp_apply_shifted_dev(ptp_ctx* ctx, int level, const double* X, double* Y);
+/* Same in float (the operator values rounded to float), for PTP_MIXED. */
+int ptp_apply_shifted_f32_dev(ptp_ctx* ctx, int level, const float* X, float* Y);
+
+/* Periodic operator of level l: Y^n = (M + tau_l L) X^n - M X^{n-1},
+   X^0 = X^{N_l} (eq. iter1 multiplied by tau_l), double. */
+int ptp_periodic_apply_dev(ptp_ctx* ctx, int level, const double* X, double* Y);
+
+/* Batched PCG: solve (M + tau_l L) X = B column by column (N_l columns),
+   starting from X = 0, with the preconditioner chosen at setup, until every
+   column's residual is <= tol * ||b_col|| or max_it iterations.  *iters
+   receives the iterations run (may be NULL).  Synchronises. */
+int ptp_spatial_solve_dev(ptp_ctx* ctx, int level, const double* B, double* X,
+                          double tol, int max_it, int* iters);
+int ptp_spatial_solve_f32_dev(ptp_ctx* ctx, int level, const float* B, float* X,
+                              double tol, int max_it, int* iters);
+
+/* Multigrid in time for the periodic linear system of level 0,
+   (M + tau L) x^n - M x^{n-1} = b^n, x^0 = x^N: `cycles` V-cycles from
+   x = 0 in the precision chosen at setup (inputs/outputs double).
+   *relres receives ||b - P x|| / ||b|| (may be NULL).  Synchronises. */
+int ptp_periodic_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* B,
+                           double* X, int cycles, double* relres);
+
+/* Fixed-point solve of Problem 1 (eq. iter1-iter2 in correction form) from
+   U0 (NULL = zero start) to opts->tol; U receives the last iterate.
+   Returns PTP_ENOTCONV if max_outer was reached, PTP_ENAN on a non-finite
+   residual.  `stats` may be NULL.  The host form copies U0 in and U out
+   inside the call; the _dev form synchronises before returning. */
+int ptp_solve(ptp_ctx* ctx, const ptp_opts* opts, const double* U0, double* U,
+              ptp_stats* stats);
+int ptp_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* U0,
+                  double* U, ptp_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTP_H */

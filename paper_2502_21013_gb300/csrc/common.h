@@ -1,0 +1,231 @@
+// Internal declarations of the time-periodic solver library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ptp.h"
+
+namespace ptp {
+
+// Thrown inside the library, turned into a status code at the ABI boundary.
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define PTP_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            throw ::ptp::Error(PTP_ECUDA, std::string(#call) + ": " +          \
+                                              cudaGetErrorString(e_));         \
+    } while (0)
+
+#define PTP_REQUIRE(cond, msg)                                                 \
+    do {                                                                       \
+        if (!(cond)) throw ::ptp::Error(PTP_EINVAL, msg);                      \
+    } while (0)
+
+// Owning device allocation (cudaMalloc / cudaFree).
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) return;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            throw Error(PTP_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+                                        " bytes failed: " + cudaGetErrorString(e));
+        }
+        n = count;
+    }
+    void upload(const std::vector<T>& h, cudaStream_t s) {
+        alloc(h.size());
+        if (!h.empty())
+            PTP_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T),
+                                     cudaMemcpyHostToDevice, s));
+    }
+};
+
+// Host CSR matrix (sorted column indices per row).
+struct HostCSR {
+    int rows = 0, cols = 0;
+    std::vector<int> ptr, idx;
+    std::vector<double> val;
+    int nnz() const { return (int)idx.size(); }
+};
+
+// Device CSR whose values are a combination  cm * v1 + cl * v2  (v2 optional),
+// stored in double and in float.
+struct DevCSR {
+    int rows = 0, cols = 0, nnz = 0;
+    DBuf<int> ptr, idx;
+    DBuf<double> v1d, v2d;
+    DBuf<float> v1f, v2f;
+    DBuf<double> d1d, d2d;  // diagonals of v1 / v2 (rows == cols only)
+    DBuf<float> d1f, d2f;
+};
+
+// One level of the spatial (geometric) hierarchy.
+struct SpatialLevel {
+    int n = 0;          // free nodes on this level
+    int nx = 0, ny = 0; // grid nodes (structured)
+    DevCSR op;          // pattern with v1 = mass, v2 = stiffness L (Galerkin)
+    DevCSR P;           // interpolation from the next coarser level (n x n_c)
+    DevCSR R;           // restriction = P^T (n_c x n)
+    HostCSR hM, hL, hP;
+};
+
+// A spatial operator  cm * M + cl * L  used somewhere in the hierarchy.
+struct OpPair {
+    double cm = 1.0, cl = 0.0;
+    DBuf<double> inv_d;  // dense inverse on the coarsest spatial level (row-major)
+    DBuf<float> inv_f;
+};
+
+struct TimeLevel {
+    int N = 0;        // time steps on this level
+    double tau = 0.0; // T / N
+    int op = 0;       // index into Ctx::ops of (1, tau)
+};
+
+// Device-side status of a solve (one allocation, copied to pinned host).
+struct Status {
+    double res;      // ||R|| of the latest residual evaluation
+    double res0;     // ||R|| at the first evaluation
+    double tol;      // relative tolerance
+    double bscale;   // divisor of the float right-hand side of the next step
+    double bscale_used;  // divisor used by the current step (its correction is multiplied back)
+    int iteration;   // residual evaluations so far
+    int done;        // stopping rule met (1) or non-finite (2)
+};
+
+struct Ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // ---- problem definition (host copies) ----
+    int n_nodes = 0, n_tri = 0;
+    std::vector<double> xy;
+    std::vector<int> tri;
+    std::vector<uint8_t> dirichlet;
+    bool structured = false;
+    int gnx = 0, gny = 0;
+    double gx0 = 0, gy0 = 0, gx1 = 1, gy1 = 1;
+    std::vector<double> sigma;
+    std::vector<uint8_t> nonlinear;
+    double nu_min = 1, nu_max = 100, s_sat = 1, nu_linear = 100;
+    bool have_materials = false;
+    int n_coils = 0;
+    std::vector<int> coil_of_elem;
+    std::vector<double> amp, phase;
+    double T = 0;
+    int N = 0;
+
+    // ---- derived, after setup ----
+    bool ready = false;
+    ptp_opts opts{};
+    int n = 0;                  // free nodes
+    std::vector<int> free_id;   // node -> free index or -1
+    double setup_ms = 0;
+    double f_norm = 0;          // ||F||, computed at setup
+
+    // residual (K1) data
+    int n_iron = 0;             // iron (nonlinear) elements
+    DBuf<int> e_nodes;          // 3 per iron element, free index or -1
+    DBuf<double> e_geo;         // 6 per iron element: g1x g1y g2x g2y |T| nu_max, |T| dnu s_sat^2
+    DBuf<int> inc_ptr, inc_elem;// node -> incident iron elements
+    DBuf<double> inc_grad;      // 2 per incidence: grad phi_i on that element
+    DBuf<int> m_ptr, m_idx;     // mass rows (only nonzero entries), scaled 1/tau
+    DBuf<double> m_val;
+    DBuf<int> l_ptr, l_idx;     // stiffness of the linear elements (nu_linear)
+    DBuf<double> l_val;
+    DBuf<double> coil_b;        // n_coils x n
+    DBuf<double> coil_s;        // n_coils x N: amp sin(2 pi t^n/T + phase)
+    std::vector<int> coil_rows; // nodes with a nonzero coil load (host)
+    DBuf<double> Qx, Qy;        // iron element flux scratch, n_iron x N each
+
+    // spatial hierarchy (level 0 = the mesh itself)
+    std::vector<SpatialLevel> sl;
+    std::vector<OpPair> ops;
+    std::vector<TimeLevel> tl;
+    int coarse_ops[2] = {-1, -1};  // ops of the coarsest time level (N_c = 1 or 2)
+    bool coarse_ok = false;        // the coarsest time level has 1 or 2 steps
+
+    // work vectors (sized n * N on the finest level)
+    DBuf<double> U, R, F, Ud;              // double state / residual / scratch
+    // multigrid in time, per level: correction x, right-hand side b (T = float or double)
+    std::vector<DBuf<double>> mg_xd, mg_bd;
+    std::vector<DBuf<float>> mg_xf, mg_bf;
+    // PCG and GMG work (largest level size), double and float
+    DBuf<double> w_d[6];
+    DBuf<float> w_f[6];
+    std::vector<DBuf<double>> g_xd, g_bd, g_rd;  // per spatial level
+    std::vector<DBuf<float>> g_xf, g_bf, g_rf;
+    DBuf<double> scal;    // device scalars of the host-driven entry points (norms, scales)
+    DBuf<double> col_d;   // per-column PCG scalars: 8 x N
+    DBuf<float> col_f;
+    DBuf<double> part_d;  // block partials for column reductions
+    DBuf<float> part_f;
+    DBuf<unsigned> counter;  // last-block counters
+    DBuf<Status> status;
+    Status* h_status = nullptr;  // pinned
+    DBuf<int> flag;              // device early-exit flags
+    int red_blocks = 0;          // blocks of reduction kernels
+
+    // CUDA graph of one outer step
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_key = -1;
+    int64_t launches = 0;        // kernels issued (counting while capturing)
+    int64_t launches_per_step = 0;
+
+    ~Ctx();
+};
+
+// ---- setup.cpp ----
+void build_problem(Ctx& c);       // free numbering, K1 data, mass, coils
+void build_hierarchy(Ctx& c);     // spatial levels, time levels, op pairs
+void make_structured_mesh(Ctx& c, int nx, int ny, double x0, double y0, double x1, double y1);
+void upload_csr(DevCSR& d, const HostCSR& a, const HostCSR* b, bool diag, cudaStream_t s);
+
+// ---- solver.cu ----
+void alloc_work(Ctx& c);
+void residual_dev(Ctx& c, const double* U, double* R, double* b_out_d, float* b_out_f,
+                  double scale, bool outer_check);
+void source_dev(Ctx& c, double* F);
+double norm_dev(Ctx& c, const double* x, size_t count);   // ||x||_2, synchronises
+template <typename T>
+void apply_op(Ctx& c, int s, int op, int N, const T* X, T* Y);
+template <typename T>
+void periodic_apply(Ctx& c, int level, const T* X, T* Y);
+template <typename T>
+int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check);
+void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres);
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st);
+
+}  // namespace ptp

@@ -1,0 +1,825 @@
+// Sparse kernels on node-major, time-fastest column blocks X[row * N + n].
+//
+// Every kernel maps a thread to (row, chunk of VEC consecutive columns) so a
+// row's N values are read as 16/8-byte vectors and a warp covers a contiguous
+// run; the CSR row structure is shared by all threads of the row (L1
+// broadcast).  A block holds rpb = 256 / (N / VEC) rows and walks the row
+// range with a grid stride, so each thread keeps the same columns and can
+// accumulate per-column dot products in registers.  Per-column reductions
+// are deterministic: block partials, then the last block to finish (atomic
+// ticket, no waiting) sums them in a fixed order and applies the PCG scalar
+// update for every column.
+//
+// Operators are cm * v1 + cl * v2 on a CSR pattern: at time level l the
+// spatial block of the periodic system is M + tau_l L (Remark on parallel
+// solvers, Section 3), with v1 = M and v2 = L = nu_max * stiffness.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace ptp {
+
+namespace {
+
+constexpr int kMaxBlock = 256;
+
+__device__ __forceinline__ bool skip_now(const Skip& s) {
+    return (s.done && *(volatile const int*)s.done) || (s.pdone && *(volatile const int*)s.pdone);
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void ldg_vec(const T* p, T (&o)[VEC]) {
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = a.x; o[1] = a.y;
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = a.x; o[1] = a.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = __ldg(p + v);
+    }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void ld_vec(const T* p, T (&o)[VEC]) {  // coherent load
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        o[0] = a.x; o[1] = a.y;
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        o[0] = a.x; o[1] = a.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) o[v] = p[v];
+    }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void st_vec(T* p, const T (&o)[VEC]) {
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) p[v] = o[v];
+    }
+}
+
+// acc = (cm v1 + cl v2)[row, :] X[:, col0 .. col0+VEC)
+template <typename T, int VEC>
+__device__ __forceinline__ void row_apply(const Op<T>& op, int N, int row, int col0, const T* X,
+                                          T (&acc)[VEC]) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+    const int k0 = __ldg(op.ptr + row), k1 = __ldg(op.ptr + row + 1);
+    for (int k = k0; k < k1; ++k) {
+        const int j = __ldg(op.idx + k);
+        T a = op.cm * __ldg(op.v1 + k);
+        if (op.v2) a += op.cl * __ldg(op.v2 + k);
+        T x[VEC];
+        ldg_vec<T, VEC>(X + (size_t)j * N + col0, x);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += a * x[v];
+    }
+}
+
+// periodic operator of one row: (cm M + cl L) X^n - M X^{n-1}, X^0 = X^N
+template <typename T, int VEC>
+__device__ __forceinline__ void row_papply(const Op<T>& op, int N, int row, int col0, const T* X,
+                                           T (&acc)[VEC]) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+    const int k0 = __ldg(op.ptr + row), k1 = __ldg(op.ptr + row + 1);
+    const int cprev = col0 == 0 ? N - 1 : col0 - 1;
+    for (int k = k0; k < k1; ++k) {
+        const int j = __ldg(op.idx + k);
+        const T m = __ldg(op.v1 + k);
+        T a = op.cm * m;
+        if (op.v2) a += op.cl * __ldg(op.v2 + k);
+        T x[VEC];
+        const T* xr = X + (size_t)j * N;
+        ldg_vec<T, VEC>(xr + col0, x);
+        T xp = __ldg(xr + cprev);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            acc[v] += a * x[v] - m * xp;
+            xp = x[v];
+        }
+    }
+}
+
+// periodic residual of one row: B^n - [(cm M + cl L) X^n - M X^{n-1}]
+template <typename T, int VEC>
+__device__ __forceinline__ void row_presid(const Op<T>& op, int N, int row, int col0, const T* X,
+                                           const T* B, T (&r)[VEC]) {
+    T acc[VEC];
+    row_papply<T, VEC>(op, N, row, col0, X, acc);
+    T b[VEC];
+    ldg_vec<T, VEC>(B + (size_t)row * N + col0, b);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) r[v] = b[v] - acc[v];
+}
+
+template <typename T>
+__device__ __forceinline__ T diag_of(const Op<T>& op, int row) {
+    T d = op.cm * __ldg(op.d1 + row);
+    if (op.d2) d += op.cl * __ldg(op.d2 + row);
+    return d;
+}
+
+// grid-stride walk over (row, chunk); NC = N / VEC, rpb = rows per block
+#define PTP_ROW_LOOP(rows, NC, rpb)                                                    \
+    const int chunk_ = threadIdx.x % (NC);                                             \
+    const int rsub_ = threadIdx.x / (NC);                                              \
+    const int col0 = chunk_ * VEC;                                                     \
+    for (int rg_ = blockIdx.x; rg_ * (rpb) < (rows); rg_ += gridDim.x)                  \
+        for (int row = rg_ * (rpb) + rsub_; row < (rows) && rsub_ < (rpb); row = (rows))
+
+template <typename T, int VEC, int MODE>
+__global__ void __launch_bounds__(kMaxBlock)
+k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, T omega, Skip sk) {
+    if (skip_now(sk)) return;
+    const int NC = N / VEC;
+    const int rpb = blockDim.x / NC;
+    PTP_ROW_LOOP(op.rows, NC, rpb) {
+        if constexpr (MODE == SP_APPLY || MODE == SP_RESTRICT) {
+            T acc[VEC];
+            row_apply<T, VEC>(op, N, row, col0, X, acc);
+            st_vec<T, VEC>(Y + (size_t)row * N + col0, acc);
+        } else if constexpr (MODE == SP_RESID) {
+            T acc[VEC], b[VEC];
+            row_apply<T, VEC>(op, N, row, col0, X, acc);
+            ldg_vec<T, VEC>(B + (size_t)row * N + col0, b);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = b[v] - acc[v];
+            st_vec<T, VEC>(Y + (size_t)row * N + col0, acc);
+        } else if constexpr (MODE == SP_JACOBI) {
+            T b[VEC], out[VEC];
+            ldg_vec<T, VEC>(B + (size_t)row * N + col0, b);
+            const T w = omega / diag_of(op, row);
+            if (X) {
+                T acc[VEC], x[VEC];
+                row_apply<T, VEC>(op, N, row, col0, X, acc);
+                ldg_vec<T, VEC>(X + (size_t)row * N + col0, x);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) out[v] = x[v] + w * (b[v] - acc[v]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) out[v] = w * b[v];
+            }
+            st_vec<T, VEC>(Y + (size_t)row * N + col0, out);
+        } else if constexpr (MODE == SP_PAPPLY) {
+            T acc[VEC];
+            row_papply<T, VEC>(op, N, row, col0, X, acc);
+            st_vec<T, VEC>(Y + (size_t)row * N + col0, acc);
+        } else if constexpr (MODE == SP_PRESID) {
+            T r[VEC];
+            row_presid<T, VEC>(op, N, row, col0, X, B, r);
+            st_vec<T, VEC>(Y + (size_t)row * N + col0, r);
+        } else if constexpr (MODE == SP_PRESID_RESTRICT) {
+            T r[VEC];
+            row_presid<T, VEC>(op, N, row, col0, X, B, r);
+            constexpr int H = VEC / 2;
+            T o[H];
+#pragma unroll
+            for (int v = 0; v < H; ++v) o[v] = r[2 * v] + r[2 * v + 1];
+            st_vec<T, H>(Y + (size_t)row * (N / 2) + col0 / 2, o);
+        } else if constexpr (MODE == SP_INTERP_ADD) {
+            T acc[VEC], y[VEC];
+            row_apply<T, VEC>(op, N, row, col0, X, acc);
+            T* yp = Y + (size_t)row * N + col0;
+            ld_vec<T, VEC>(yp, y);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) y[v] += acc[v];
+            st_vec<T, VEC>(yp, y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-column reductions with a last-block finish
+// ---------------------------------------------------------------------------
+
+enum Fin { FIN_ALPHA = 0, FIN_UPDATE_JACOBI = 1, FIN_UPDATE_RR = 2, FIN_RZ_FIRST = 3, FIN_RZ_NEXT = 4 };
+
+// column scalar slots in ColRed::col (each N long)
+enum Slot { S_RHO = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_BB = 4 };
+
+// num / den for PCG scalars, evaluated in double; 0 when the column has
+// no (or a non-finite) search direction, so a column whose right-hand side
+// is zero or underflows stays untouched instead of propagating NaN.
+template <typename T>
+__device__ __forceinline__ T safe_ratio(T num, T den) {
+    if (!(num > T(0) && den > T(0))) return T(0);
+    const double r = (double)num / (double)den;
+    return isfinite(r) && r < 1e30 ? (T)r : T(0);
+}
+
+// Blocks are grouped by kGroup; the last block of each group to finish sums
+// its group's partials, and the last group finisher sums the group results
+// and applies FIN to every column.  Both sums run in a fixed order, so the
+// result does not depend on block scheduling.  Counters: [0] for the groups,
+// [1 + g] for group g; each is reset by the block that consumed it.
+constexpr int kGroup = 32;
+
+template <typename T, int VEC, int NQ, int FIN>
+__device__ void col_reduce_finish(T (&acc)[NQ][VEC], int N, int NC, int rpb, ColRed<T> cr) {
+    __shared__ T sm[NQ * kMaxBlock * VEC];
+    __shared__ int stage;
+    __shared__ int all_conv;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) sm[(q * blockDim.x + threadIdx.x) * VEC + v] = acc[q][v];
+    __syncthreads();
+    const int G = gridDim.x;
+    const int QN = NQ * N;
+    for (int e = threadIdx.x; e < QN; e += blockDim.x) {
+        const int q = e / N, col = e - q * N;
+        const int chunk = col / VEC, v = col - chunk * VEC;
+        T s = T(0);
+        for (int r = 0; r < rpb; ++r) s += sm[(q * blockDim.x + r * NC + chunk) * VEC + v];
+        cr.partials[(size_t)blockIdx.x * QN + e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    const int ng = (G + kGroup - 1) / kGroup;
+    const int g = blockIdx.x / kGroup;
+    const int b0 = g * kGroup;
+    const int gsz = min(kGroup, G - b0);
+    T* part2 = cr.partials + (size_t)G * QN;
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(cr.counter + 1 + g, 1u);
+        stage = ticket == (unsigned)(gsz - 1) ? 1 : 0;
+        all_conv = 1;
+    }
+    __syncthreads();
+    if (!stage) return;
+    for (int e = threadIdx.x; e < QN; e += blockDim.x) {
+        T a = T(0);
+#pragma unroll 8
+        for (int b = 0; b < gsz; ++b) a += __ldcg(cr.partials + (size_t)(b0 + b) * QN + e);
+        part2[(size_t)g * QN + e] = a;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cr.counter[1 + g] = 0u;
+        const unsigned ticket = atomicAdd(cr.counter, 1u);
+        stage = ticket == (unsigned)(ng - 1) ? 2 : 0;
+    }
+    __syncthreads();
+    if (stage != 2) return;
+    for (int col = threadIdx.x; col < N; col += blockDim.x) {
+        T s[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            T a = T(0);
+            for (int b = 0; b < ng; ++b) a += __ldcg(part2 + (size_t)b * QN + q * N + col);
+            s[q] = a;
+        }
+        T* c = cr.col;
+        if constexpr (FIN == FIN_ALPHA) {
+            c[S_ALPHA * N + col] = safe_ratio<T>(c[S_RHO * N + col], s[0]);
+        } else if constexpr (FIN == FIN_UPDATE_JACOBI) {  // s = (rz, rr)
+            c[S_BETA * N + col] = safe_ratio<T>(s[0], c[S_RHO * N + col]);
+            c[S_RHO * N + col] = s[0];
+            c[S_RR * N + col] = s[1];
+            if (!(s[1] <= cr.tol2 * c[S_BB * N + col])) all_conv = 0;
+        } else if constexpr (FIN == FIN_UPDATE_RR) {
+            c[S_RR * N + col] = s[0];
+            if (!(s[0] <= cr.tol2 * c[S_BB * N + col])) all_conv = 0;
+        } else if constexpr (FIN == FIN_RZ_FIRST) {  // s = (rz, rr)
+            c[S_RHO * N + col] = s[0];
+            c[S_BB * N + col] = s[1];
+            c[S_RR * N + col] = s[1];
+        } else if constexpr (FIN == FIN_RZ_NEXT) {
+            c[S_BETA * N + col] = safe_ratio<T>(s[0], c[S_RHO * N + col]);
+            c[S_RHO * N + col] = s[0];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if constexpr (FIN == FIN_UPDATE_JACOBI || FIN == FIN_UPDATE_RR)
+            if (cr.pdone && all_conv) *cr.pdone = 1;
+        cr.counter[0] = 0u;
+    }
+}
+
+// q = A p ; alpha = rho / (p . q)
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock)
+k_pcg_apply_alpha(Op<T> op, int N, const T* __restrict__ p, T* __restrict__ q, ColRed<T> cr, Skip sk) {
+    if (skip_now(sk)) return;
+    const int NC = N / VEC, rpb = blockDim.x / NC;
+    T acc[1][VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[0][v] = T(0);
+    PTP_ROW_LOOP(op.rows, NC, rpb) {
+        T y[VEC], x[VEC];
+        row_apply<T, VEC>(op, N, row, col0, p, y);
+        ldg_vec<T, VEC>(p + (size_t)row * N + col0, x);
+        st_vec<T, VEC>(q + (size_t)row * N + col0, y);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[0][v] += x[v] * y[v];
+    }
+    col_reduce_finish<T, VEC, 1, FIN_ALPHA>(acc, N, NC, rpb, cr);
+}
+
+// x += xscale alpha p ; r -= alpha q ; (jacobi) z = r / D ; dots (rz, rr) or (rr)
+template <typename T, int VEC, bool JAC>
+__global__ void __launch_bounds__(kMaxBlock)
+k_pcg_update(Op<T> op, int N, T xscale, int assign, T* x, const T* __restrict__ p, T* r,
+             const T* __restrict__ q, T* z, ColRed<T> cr, Skip sk) {
+    if (skip_now(sk)) return;
+    const int NC = N / VEC, rpb = blockDim.x / NC;
+    constexpr int NQ = JAC ? 2 : 1;
+    T acc[NQ][VEC];
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[qq][v] = T(0);
+    const T* alpha = cr.col + S_ALPHA * N;
+    PTP_ROW_LOOP(op.rows, NC, rpb) {
+        const size_t o = (size_t)row * N + col0;
+        T pv[VEC], qv[VEC], xv[VEC], rv[VEC], al[VEC];
+        ldg_vec<T, VEC>(p + o, pv);
+        ldg_vec<T, VEC>(q + o, qv);
+        if (assign) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) xv[v] = T(0);
+        } else {
+            ld_vec<T, VEC>(x + o, xv);
+        }
+        ld_vec<T, VEC>(r + o, rv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) al[v] = alpha[col0 + v];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            xv[v] += xscale * al[v] * pv[v];
+            rv[v] -= al[v] * qv[v];
+        }
+        st_vec<T, VEC>(x + o, xv);
+        st_vec<T, VEC>(r + o, rv);
+        if constexpr (JAC) {
+            const T dinv = T(1) / diag_of(op, row);
+            T zv[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                zv[v] = rv[v] * dinv;
+                acc[0][v] += rv[v] * zv[v];
+                acc[1][v] += rv[v] * rv[v];
+            }
+            st_vec<T, VEC>(z + o, zv);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[0][v] += rv[v] * rv[v];
+        }
+    }
+    col_reduce_finish<T, VEC, NQ, JAC ? FIN_UPDATE_JACOBI : FIN_UPDATE_RR>(acc, N, NC, rpb, cr);
+}
+
+// z = r / D ; p = z ; rho = r.z ; bb = rr = r.r
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock)
+k_pcg_init_jacobi(Op<T> op, int N, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
+                  ColRed<T> cr, Skip sk) {
+    if (skip_now(sk)) return;
+    const int NC = N / VEC, rpb = blockDim.x / NC;
+    T acc[2][VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[0][v] = acc[1][v] = T(0);
+    PTP_ROW_LOOP(op.rows, NC, rpb) {
+        const size_t o = (size_t)row * N + col0;
+        T rv[VEC], zv[VEC];
+        ldg_vec<T, VEC>(r + o, rv);
+        const T dinv = T(1) / diag_of(op, row);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            zv[v] = rv[v] * dinv;
+            acc[0][v] += rv[v] * zv[v];
+            acc[1][v] += rv[v] * rv[v];
+        }
+        st_vec<T, VEC>(z + o, zv);
+        st_vec<T, VEC>(p + o, zv);
+    }
+    col_reduce_finish<T, VEC, 2, FIN_RZ_FIRST>(acc, N, NC, rpb, cr);
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock)
+k_pcg_dot_rz(int rows, int N, const T* __restrict__ r, const T* __restrict__ z, ColRed<T> cr, int first,
+             Skip sk) {
+    if (skip_now(sk)) return;
+    const int NC = N / VEC, rpb = blockDim.x / NC;
+    T acc[2][VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[0][v] = acc[1][v] = T(0);
+    PTP_ROW_LOOP(rows, NC, rpb) {
+        const size_t o = (size_t)row * N + col0;
+        T rv[VEC], zv[VEC];
+        ldg_vec<T, VEC>(r + o, rv);
+        ldg_vec<T, VEC>(z + o, zv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            acc[0][v] += rv[v] * zv[v];
+            acc[1][v] += rv[v] * rv[v];
+        }
+    }
+    if (first)
+        col_reduce_finish<T, VEC, 2, FIN_RZ_FIRST>(acc, N, NC, rpb, cr);
+    else
+        col_reduce_finish<T, VEC, 2, FIN_RZ_NEXT>(acc, N, NC, rpb, cr);
+}
+
+// p = z + beta p
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock)
+k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Skip sk) {
+    if (skip_now(sk)) return;
+    const int NC = N / VEC, rpb = blockDim.x / NC;
+    const T* beta = cr.col + S_BETA * N;
+    PTP_ROW_LOOP(rows, NC, rpb) {
+        const size_t o = (size_t)row * N + col0;
+        T zv[VEC], pv[VEC];
+        ldg_vec<T, VEC>(z + o, zv);
+        ld_vec<T, VEC>(p + o, pv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) pv[v] = zv[v] + beta[col0 + v] * pv[v];
+        st_vec<T, VEC>(p + o, pv);
+    }
+}
+
+// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv)
+template <typename T>
+__global__ void k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Y,
+                              Skip sk) {
+    if (skip_now(sk)) return;
+    const size_t total = (size_t)n * N;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g / N), c = (int)(g - (size_t)i * N);
+        const T* a = A + (size_t)i * n;
+        T s = T(0);
+        for (int j = 0; j < n; ++j) s += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
+        Y[g] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_time_prolong_add(int rows, int Nc, const T* __restrict__ xc, T* __restrict__ x, Skip sk) {
+    if (skip_now(sk)) return;
+    const size_t total = (size_t)rows * Nc;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = g / Nc, m = g - i * Nc;
+        const T v = xc[g];
+        T* xr = x + i * (2 * (size_t)Nc) + 2 * m;
+        xr[0] += v;
+        xr[1] += v;
+    }
+}
+
+template <typename T>
+__global__ void k_axpy(size_t count, T a, const T* __restrict__ x, T* __restrict__ y, Skip sk) {
+    if (skip_now(sk)) return;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
+        y[g] += a * x[g];
+}
+
+template <typename T>
+__global__ void k_fill(size_t count, T v, T* __restrict__ y, Skip sk) {
+    if (skip_now(sk)) return;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
+        y[g] = v;
+}
+
+template <typename TI, typename TO>
+__global__ void k_cast(size_t count, const TI* __restrict__ x, TO* __restrict__ y, Skip sk) {
+    if (skip_now(sk)) return;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
+        y[g] = (TO)x[g];
+}
+
+template <typename T>
+__global__ void k_add_to_double(size_t count, const T* __restrict__ d, double* __restrict__ U,
+                                const double* __restrict__ scale, Skip sk) {
+    if (skip_now(sk)) return;
+    const double s = scale ? *scale : 1.0;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
+        U[g] += s * (double)d[g];
+}
+
+template <typename TI, typename TO>
+__global__ void k_cast_scaled(size_t count, const TI* __restrict__ x, TO* __restrict__ y,
+                              const double* __restrict__ mul, const double* __restrict__ div) {
+    const double s = (mul ? *mul : 1.0) / (div ? *div : 1.0);
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
+        y[g] = (TO)(s * (double)x[g]);
+}
+
+template <typename T>
+__global__ void k_split2(int rows, const T* __restrict__ b, double* __restrict__ bs, double* __restrict__ bd, Skip sk) {
+    if (skip_now(sk)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+        const double b0 = (double)b[2 * (size_t)i], b1 = (double)b[2 * (size_t)i + 1];
+        bs[i] = b0 + b1;
+        bd[i] = b0 - b1;
+    }
+}
+
+template <typename T>
+__global__ void k_combine2(int rows, const double* __restrict__ xs, const double* __restrict__ xd, T* __restrict__ x,
+                           Skip sk) {
+    if (skip_now(sk)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
+        x[2 * (size_t)i] = (T)(0.5 * (xs[i] + xd[i]));
+        x[2 * (size_t)i + 1] = (T)(0.5 * (xs[i] - xd[i]));
+    }
+}
+
+__global__ void k_flag(int* flag, int v, Skip sk) {
+    if (skip_now(sk)) return;
+    if (threadIdx.x == 0 && blockIdx.x == 0) *flag = v;
+}
+
+template <typename T>
+__global__ void k_norm2(size_t count, const T* __restrict__ x, double* partials, unsigned* counter, double* out) {
+    double s = 0.0;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[g];
+        s += v * v;
+    }
+    __shared__ double sm[kMaxBlock];
+    __shared__ bool last;
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = sm[0];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(partials + b);
+        *out = t;
+        *counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+
+inline bool aligned(const void* p, size_t a) { return p == nullptr || ((uintptr_t)p % a) == 0; }
+
+template <typename T>
+int pick_vec(int N, std::initializer_list<const void*> ptrs, bool need_even = false) {
+    int vmax = sizeof(T) == 4 ? 4 : 2;
+    for (int v = vmax; v >= 1; v /= 2) {
+        if (N % v) continue;
+        if (need_even && v < 2) continue;
+        bool ok = true;
+        for (const void* p : ptrs) ok = ok && aligned(p, v * sizeof(T));
+        if (need_even && v == 4 && N % 4) ok = false;
+        if (ok) return v;
+    }
+    if (need_even) throw Error(PTP_EINVAL, "time restriction needs an even number of steps and aligned buffers");
+    return 1;
+}
+
+struct Launch {
+    int grid, block;
+};
+
+Launch row_launch(int rows, int N, int vec) {
+    const int NC = N / vec;
+    if (NC > kMaxBlock) throw Error(PTP_EINVAL, "too many time steps per level for one block (N/VEC > 256)");
+    const int rpb = kMaxBlock / NC;
+    const int block = NC * rpb;
+    long groups = ((long)rows + rpb - 1) / rpb;
+    long cap = (long)num_sms() * std::min(8, 2048 / block);
+    Launch l;
+    l.grid = (int)std::max(1L, std::min(groups, cap));
+    l.block = block;
+    return l;
+}
+
+int flat_grid(size_t total) {
+    size_t want = (total + 255) / 256;
+    size_t cap = (size_t)num_sms() * 8;
+    return (int)std::max<size_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
+// max partial-buffer entries a reduction launch can need for N columns
+size_t reduction_partials(int Nmax) { return (size_t)num_sms() * 9 * 2 * (size_t)Nmax; }
+
+#define PTP_VEC_DISPATCH(vec, ...)                               \
+    switch (vec) {                                               \
+        case 4: { constexpr int VEC = 4; __VA_ARGS__; } break;   \
+        case 2: { constexpr int VEC = 2; __VA_ARGS__; } break;   \
+        default: { constexpr int VEC = 1; __VA_ARGS__; } break;  \
+    }
+
+template <typename T>
+int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* Y, T omega, Skip sk,
+                cudaStream_t s) {
+    const bool restrict_time = mode == SP_PRESID_RESTRICT;
+    int vec = pick_vec<T>(N, {X, B, Y}, restrict_time);
+    if (sizeof(T) == 8 && vec == 4) vec = 2;
+    if (restrict_time && sizeof(T) == 4 && vec == 4 && !aligned(Y, 8)) vec = 2;
+    const Launch l = row_launch(op.rows, N, vec);
+#define PTP_SPMM_CASE(M)                                                                          \
+    case M:                                                                                       \
+        if constexpr (M == SP_PRESID_RESTRICT) {                                                  \
+            if (vec == 4) {                                                                       \
+                if constexpr (sizeof(T) == 4)                                                     \
+                    k_spmm<T, 4, M><<<l.grid, l.block, 0, s>>>(op, N, X, B, Y, omega, sk);        \
+            } else                                                                                \
+                k_spmm<T, 2, M><<<l.grid, l.block, 0, s>>>(op, N, X, B, Y, omega, sk);            \
+        } else {                                                                                  \
+            PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)                       \
+                                      k_spmm<T, VEC, M><<<l.grid, l.block, 0, s>>>(op, N, X, B, Y, \
+                                                                                 omega, sk));     \
+        }                                                                                         \
+        break;
+    switch (mode) {
+        PTP_SPMM_CASE(SP_APPLY)
+        PTP_SPMM_CASE(SP_RESID)
+        PTP_SPMM_CASE(SP_JACOBI)
+        PTP_SPMM_CASE(SP_PRESID)
+        PTP_SPMM_CASE(SP_PRESID_RESTRICT)
+        PTP_SPMM_CASE(SP_INTERP_ADD)
+        PTP_SPMM_CASE(SP_RESTRICT)
+        PTP_SPMM_CASE(SP_PAPPLY)
+    }
+#undef PTP_SPMM_CASE
+    return 1;
+}
+
+template <typename T>
+int launch_pcg_init_jacobi(const Op<T>& op, int N, T* r, T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s) {
+    int vec = pick_vec<T>(N, {r, z, p});
+    if (sizeof(T) == 8 && vec == 4) vec = 2;
+    const Launch l = row_launch(op.rows, N, vec);
+    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
+                              k_pcg_init_jacobi<T, VEC><<<l.grid, l.block, 0, s>>>(op, N, r, z, p, cr, sk));
+    return 1;
+}
+
+template <typename T>
+int launch_pcg_dot_rz(int rows, int N, const T* r, const T* z, ColRed<T> cr, int first, Skip sk, cudaStream_t s) {
+    int vec = pick_vec<T>(N, {r, z});
+    if (sizeof(T) == 8 && vec == 4) vec = 2;
+    const Launch l = row_launch(rows, N, vec);
+    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
+                              k_pcg_dot_rz<T, VEC><<<l.grid, l.block, 0, s>>>(rows, N, r, z, cr, first, sk));
+    return 1;
+}
+
+template <typename T>
+int launch_pcg_apply_alpha(const Op<T>& op, int N, const T* p, T* q, ColRed<T> cr, Skip sk, cudaStream_t s) {
+    int vec = pick_vec<T>(N, {p, q});
+    if (sizeof(T) == 8 && vec == 4) vec = 2;
+    const Launch l = row_launch(op.rows, N, vec);
+    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
+                              k_pcg_apply_alpha<T, VEC><<<l.grid, l.block, 0, s>>>(op, N, p, q, cr, sk));
+    return 1;
+}
+
+template <typename T>
+int launch_pcg_update(const Op<T>& op, int N, T xscale, int assign, T* x, const T* p, T* r, const T* q, T* z,
+                      int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s) {
+    int vec = pick_vec<T>(N, {x, p, r, q, z});
+    if (sizeof(T) == 8 && vec == 4) vec = 2;
+    const Launch l = row_launch(op.rows, N, vec);
+    if (jacobi) {
+        PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
+                                  k_pcg_update<T, VEC, true><<<l.grid, l.block, 0, s>>>(op, N, xscale, assign, x, p,
+                                                                                       r, q, z, cr, sk));
+    } else {
+        PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
+                                  k_pcg_update<T, VEC, false><<<l.grid, l.block, 0, s>>>(op, N, xscale, assign, x, p,
+                                                                                        r, q, z, cr, sk));
+    }
+    return 1;
+}
+
+template <typename T>
+int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s) {
+    int vec = pick_vec<T>(N, {z, p});
+    if (sizeof(T) == 8 && vec == 4) vec = 2;
+    const Launch l = row_launch(rows, N, vec);
+    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
+                              k_pcg_direction<T, VEC><<<l.grid, l.block, 0, s>>>(rows, N, z, p, cr, sk));
+    return 1;
+}
+
+template <typename T>
+int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
+    k_dense_apply<T><<<flat_grid((size_t)n * N), 256, 0, s>>>(n, N, Ainv, B, Y, sk);
+    return 1;
+}
+
+template <typename T>
+int launch_time_prolong_add(int rows, int Nc, const T* xc, T* x, Skip sk, cudaStream_t s) {
+    k_time_prolong_add<T><<<flat_grid((size_t)rows * Nc), 256, 0, s>>>(rows, Nc, xc, x, sk);
+    return 1;
+}
+
+template <typename T>
+int launch_axpy(size_t count, T a, const T* x, T* y, Skip sk, cudaStream_t s) {
+    k_axpy<T><<<flat_grid(count), 256, 0, s>>>(count, a, x, y, sk);
+    return 1;
+}
+
+template <typename T>
+int launch_fill(size_t count, T v, T* y, Skip sk, cudaStream_t s) {
+    k_fill<T><<<flat_grid(count), 256, 0, s>>>(count, v, y, sk);
+    return 1;
+}
+
+template <typename TI, typename TO>
+int launch_cast(size_t count, const TI* x, TO* y, Skip sk, cudaStream_t s) {
+    k_cast<TI, TO><<<flat_grid(count), 256, 0, s>>>(count, x, y, sk);
+    return 1;
+}
+
+template <typename T>
+int launch_add_to_double(size_t count, const T* d, double* U, const double* scale, Skip sk, cudaStream_t s) {
+    k_add_to_double<T><<<flat_grid(count), 256, 0, s>>>(count, d, U, scale, sk);
+    return 1;
+}
+
+template <typename TI, typename TO>
+int launch_cast_scaled(size_t count, const TI* x, TO* y, const double* mul, const double* div, cudaStream_t s) {
+    k_cast_scaled<TI, TO><<<flat_grid(count), 256, 0, s>>>(count, x, y, mul, div);
+    return 1;
+}
+
+template <typename T>
+int launch_split2(int rows, const T* b, double* bs, double* bd, Skip sk, cudaStream_t s) {
+    k_split2<T><<<flat_grid(rows), 256, 0, s>>>(rows, b, bs, bd, sk);
+    return 1;
+}
+
+template <typename T>
+int launch_combine2(int rows, const double* xs, const double* xd, T* x, Skip sk, cudaStream_t s) {
+    k_combine2<T><<<flat_grid(rows), 256, 0, s>>>(rows, xs, xd, x, sk);
+    return 1;
+}
+
+int launch_flag(int* flag, int v, Skip sk, cudaStream_t s) {
+    k_flag<<<1, 32, 0, s>>>(flag, v, sk);
+    return 1;
+}
+
+template <typename T>
+int launch_norm2(size_t count, const T* x, double* partials, unsigned* counter, double* out, cudaStream_t s) {
+    k_norm2<T><<<flat_grid(count), 256, 0, s>>>(count, x, partials, counter, out);
+    return 1;
+}
+
+#define PTP_INST(T)                                                                                        \
+    template int launch_spmm<T>(SpMode, const Op<T>&, int, const T*, const T*, T*, T, Skip, cudaStream_t); \
+    template int launch_pcg_init_jacobi<T>(const Op<T>&, int, T*, T*, T*, ColRed<T>, Skip, cudaStream_t);  \
+    template int launch_pcg_dot_rz<T>(int, int, const T*, const T*, ColRed<T>, int, Skip, cudaStream_t);   \
+    template int launch_pcg_apply_alpha<T>(const Op<T>&, int, const T*, T*, ColRed<T>, Skip, cudaStream_t); \
+    template int launch_pcg_update<T>(const Op<T>&, int, T, int, T*, const T*, T*, const T*, T*, int, ColRed<T>, \
+                                      Skip, cudaStream_t);                                                 \
+    template int launch_pcg_direction<T>(int, int, const T*, T*, ColRed<T>, Skip, cudaStream_t);          \
+    template int launch_dense_apply<T>(int, int, const T*, const T*, T*, Skip, cudaStream_t);              \
+    template int launch_time_prolong_add<T>(int, int, const T*, T*, Skip, cudaStream_t);                   \
+    template int launch_axpy<T>(size_t, T, const T*, T*, Skip, cudaStream_t);                              \
+    template int launch_fill<T>(size_t, T, T*, Skip, cudaStream_t);                                        \
+    template int launch_add_to_double<T>(size_t, const T*, double*, const double*, Skip, cudaStream_t);    \
+    template int launch_split2<T>(int, const T*, double*, double*, Skip, cudaStream_t);                    \
+    template int launch_combine2<T>(int, const double*, const double*, T*, Skip, cudaStream_t);            \
+    template int launch_norm2<T>(size_t, const T*, double*, unsigned*, double*, cudaStream_t);
+
+PTP_INST(float)
+PTP_INST(double)
+template int launch_cast<double, float>(size_t, const double*, float*, Skip, cudaStream_t);
+template int launch_cast<float, double>(size_t, const float*, double*, Skip, cudaStream_t);
+template int launch_cast_scaled<double, float>(size_t, const double*, float*, const double*, const double*,
+                                               cudaStream_t);
+template int launch_cast_scaled<float, double>(size_t, const float*, double*, const double*, const double*,
+                                               cudaStream_t);
+
+}  // namespace ptp

@@ -1,0 +1,137 @@
+// Kernel launchers (host functions) shared by the solver translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace ptp {
+
+// ---------------------------------------------------------------------------
+// K1: outer residual R = F - A(U), double (fused source, mass, K(u), norm)
+// ---------------------------------------------------------------------------
+struct ResidualArgs {
+    int n, N, n_iron, n_coils;
+    const int* e_nodes;
+    const double* e_geo;
+    const int* inc_ptr;
+    const int* inc_elem;
+    const double* inc_grad;
+    const int* m_ptr;
+    const int* m_idx;
+    const double* m_val;      // mass / tau
+    const int* l_ptr;         // linear-element stiffness (nu_linear)
+    const int* l_idx;
+    const double* l_val;
+    const double* coil_b;
+    const double* coil_s;
+    double s2sat;             // s_sat^2
+    const double* U;
+    double* Qx;
+    double* Qy;
+    double* R;                // may be null
+    double* b_d;              // scale * R in double (may be null)
+    float* b_f;               // scale * R in float (may be null)
+    double scale;
+    double* partials;         // >= grid doubles
+    unsigned* counter;
+    Status* status;           // norm written to status->res (and check)
+    int* done;                // outer early-exit flag (may be null)
+    int check;                // apply the stopping rule in the last block
+};
+int launch_residual(const ResidualArgs& a, cudaStream_t s);  // returns kernels launched
+void launch_source(int n, int N, int n_coils, const double* coil_b, const double* coil_s,
+                   double* F, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Sparse kernels on [rows][N] column blocks (node-major, time fastest)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Op {             // cm * v1 + cl * v2 on a CSR pattern
+    int rows = 0, cols = 0;
+    const int* ptr = nullptr;
+    const int* idx = nullptr;
+    const T* v1 = nullptr;
+    const T* v2 = nullptr;   // may be null
+    const T* d1 = nullptr;   // diagonal of v1
+    const T* d2 = nullptr;   // diagonal of v2
+    T cm = 1, cl = 0;
+};
+
+template <typename T>
+struct ColRed {         // per-column reduction workspace
+    T* partials = nullptr;   // grid * N * 2
+    unsigned* counter = nullptr;
+    T* col = nullptr;        // per-column scalars, 8 x N: rho alpha beta rr bb . . .
+    int* pdone = nullptr;    // PCG early-exit flag
+    T tol2 = 0;              // squared relative tolerance for pdone
+};
+
+struct Skip {           // early-exit flags checked by every kernel of a step
+    const int* done = nullptr;
+    const int* pdone = nullptr;
+};
+
+enum SpMode {
+    SP_APPLY = 0,       // Y = A X
+    SP_RESID = 1,       // Y = B - A X
+    SP_JACOBI = 2,      // Y = X + w D^-1 (B - A X)   (X null: Y = w D^-1 B)
+    SP_PRESID = 3,      // Y^n = B^n - A X^n + M X^{n-1}  (periodic, M = v1)
+    SP_PRESID_RESTRICT = 4,  // Y^m = sum over the pair (2m, 2m+1) of the periodic residual
+    SP_INTERP_ADD = 5,  // Y += Op X   (interpolation, v1 only)
+    SP_RESTRICT = 6,    // Y = Op X    (restriction, v1 only)
+    SP_PAPPLY = 7,      // Y^n = A X^n - M X^{n-1}  (periodic operator)
+};
+
+template <typename T>
+int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* Y, T omega,
+                Skip sk, cudaStream_t s);
+
+// PCG pieces (batched over N independent columns)
+template <typename T>
+int launch_pcg_init_jacobi(const Op<T>& op, int N, T* r, T* z, T* p, ColRed<T> cr, Skip sk,
+                           cudaStream_t s);  // z = r/d, p = z, rho = r.z, bb = r.r
+template <typename T>
+int launch_pcg_dot_rz(int rows, int N, const T* r, const T* z, ColRed<T> cr, int first, Skip sk,
+                      cudaStream_t s);       // first: rho = r.z, bb = r.r ; else beta = rz/rho, rho = rz
+template <typename T>
+int launch_pcg_apply_alpha(const Op<T>& op, int N, const T* p, T* q, ColRed<T> cr, Skip sk,
+                           cudaStream_t s);  // q = A p, alpha = rho / p.q
+template <typename T>
+int launch_pcg_update(const Op<T>& op, int N, T xscale, int assign, T* x, const T* p, T* r,
+                      const T* q, T* z, int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s);
+// (assign = 1: x = xscale alpha p instead of x += ..., for a zero start)
+template <typename T>
+int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s);
+
+// dense coarse-level apply Y = Ainv B  (n x n, row-major)
+template <typename T>
+int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s);
+
+// time transfers and vector helpers
+template <typename T>
+int launch_time_prolong_add(int rows, int Nc, const T* xc, T* x, Skip sk, cudaStream_t s);
+template <typename T>
+int launch_axpy(size_t count, T a, const T* x, T* y, Skip sk, cudaStream_t s);   // y += a x
+template <typename T>
+int launch_fill(size_t count, T v, T* y, Skip sk, cudaStream_t s);
+template <typename TI, typename TO>
+int launch_cast(size_t count, const TI* x, TO* y, Skip sk, cudaStream_t s);
+template <typename T>   // U += s d with s = *scale (scale may be null: s = 1)
+int launch_add_to_double(size_t count, const T* d, double* U, const double* scale, Skip sk, cudaStream_t s);
+template <typename TI, typename TO>   // y = x * (*mul) / (*div)   (null pointers read as 1)
+int launch_cast_scaled(size_t count, const TI* x, TO* y, const double* mul, const double* div, cudaStream_t s);
+// coarsest level with two steps: split b into sum / difference columns, and combine
+template <typename T>
+int launch_split2(int rows, const T* b, double* bs, double* bd, Skip sk, cudaStream_t s);
+template <typename T>
+int launch_combine2(int rows, const double* xs, const double* xd, T* x, Skip sk, cudaStream_t s);
+int launch_flag(int* flag, int v, Skip sk, cudaStream_t s);   // *flag = v
+// squared norm of a column block into status-like scalar (double)
+template <typename T>
+int launch_norm2(size_t count, const T* x, double* partials, unsigned* counter, double* out,
+                 cudaStream_t s);
+
+int num_sms();
+
+}  // namespace ptp

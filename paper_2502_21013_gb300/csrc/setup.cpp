@@ -1,0 +1,464 @@
+// Host-side set-up: free-node numbering, P1 geometry, the data of the fused
+// residual kernel, sparse operators and the spatial / temporal hierarchies.
+//
+// Discretisation (Section 4, "Simulation setup"): P1 elements on triangles,
+// homogeneous Dirichlet nodes removed, implicit Euler with tau = T/N.
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+#include "common.h"
+
+namespace ptp {
+
+namespace {
+
+// Gradients of the hat functions of vertices 1 and 2 and the area of a
+// triangle: grad(phi_1) = (b11, -b01)/det, grad(phi_2) = (-b10, b00)/det with
+// B = [p1 - p0, p2 - p0] = [[b00, b01], [b10, b11]]; grad(phi_0) = -(sum).
+struct Geo {
+    double g[3][2];
+    double area;
+};
+
+Geo triangle_geo(const double* p0, const double* p1, const double* p2) {
+    double b00 = p1[0] - p0[0], b10 = p1[1] - p0[1];
+    double b01 = p2[0] - p0[0], b11 = p2[1] - p0[1];
+    double det = b00 * b11 - b01 * b10;
+    Geo G;
+    if (!(det > 0.0)) throw Error(PTP_EINVAL, "triangle is clockwise or degenerate");
+    G.g[1][0] = b11 / det;
+    G.g[1][1] = -b01 / det;
+    G.g[2][0] = -b10 / det;
+    G.g[2][1] = b00 / det;
+    G.g[0][0] = -(G.g[1][0] + G.g[2][0]);
+    G.g[0][1] = -(G.g[1][1] + G.g[2][1]);
+    G.area = 0.5 * det;
+    return G;
+}
+
+// Row-wise accumulation into a CSR matrix with sorted columns.
+struct RowAccum {
+    std::vector<std::map<int, double>> rows;
+    explicit RowAccum(int n) : rows(n) {}
+    void add(int i, int j, double v) { rows[i][j] += v; }
+    HostCSR finish(int cols, bool drop_zeros) const {
+        HostCSR A;
+        A.rows = (int)rows.size();
+        A.cols = cols;
+        A.ptr.assign(A.rows + 1, 0);
+        for (int i = 0; i < A.rows; ++i) {
+            for (auto& kv : rows[i]) {
+                if (drop_zeros && kv.second == 0.0) continue;
+                A.idx.push_back(kv.first);
+                A.val.push_back(kv.second);
+            }
+            A.ptr[i + 1] = (int)A.idx.size();
+        }
+        return A;
+    }
+};
+
+HostCSR transpose(const HostCSR& A) {
+    HostCSR T;
+    T.rows = A.cols;
+    T.cols = A.rows;
+    T.ptr.assign(T.rows + 1, 0);
+    for (int k = 0; k < A.nnz(); ++k) T.ptr[A.idx[k] + 1]++;
+    for (int i = 0; i < T.rows; ++i) T.ptr[i + 1] += T.ptr[i];
+    T.idx.resize(A.nnz());
+    T.val.resize(A.nnz());
+    std::vector<int> pos(T.ptr.begin(), T.ptr.end() - 1);
+    for (int i = 0; i < A.rows; ++i)
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+            int p = pos[A.idx[k]]++;
+            T.idx[p] = i;
+            T.val[p] = A.val[k];
+        }
+    return T;  // rows come out sorted because i increases
+}
+
+// C = A * B with a dense accumulator per row (Gustavson).
+HostCSR matmul(const HostCSR& A, const HostCSR& B) {
+    if (A.cols != B.rows) throw Error(PTP_EINVAL, "matmul size mismatch");
+    HostCSR C;
+    C.rows = A.rows;
+    C.cols = B.cols;
+    C.ptr.assign(C.rows + 1, 0);
+    std::vector<double> acc(B.cols, 0.0);
+    std::vector<int> mark(B.cols, -1), cols;
+    for (int i = 0; i < A.rows; ++i) {
+        cols.clear();
+        for (int ka = A.ptr[i]; ka < A.ptr[i + 1]; ++ka) {
+            int k = A.idx[ka];
+            double a = A.val[ka];
+            for (int kb = B.ptr[k]; kb < B.ptr[k + 1]; ++kb) {
+                int j = B.idx[kb];
+                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; cols.push_back(j); }
+                acc[j] += a * B.val[kb];
+            }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int j : cols) { C.idx.push_back(j); C.val.push_back(acc[j]); }
+        C.ptr[i + 1] = (int)C.idx.size();
+    }
+    return C;
+}
+
+// Values of A on the pattern `pat` (pat must contain A's pattern).
+std::vector<double> values_on(const HostCSR& pat, const HostCSR& A) {
+    std::vector<double> v(pat.nnz(), 0.0);
+    for (int i = 0; i < pat.rows; ++i) {
+        int kp = pat.ptr[i];
+        for (int ka = A.ptr[i]; ka < A.ptr[i + 1]; ++ka) {
+            while (kp < pat.ptr[i + 1] && pat.idx[kp] < A.idx[ka]) ++kp;
+            if (kp == pat.ptr[i + 1] || pat.idx[kp] != A.idx[ka])
+                throw Error(PTP_EINVAL, "pattern does not contain matrix");
+            v[kp] = A.val[ka];
+        }
+    }
+    return v;
+}
+
+HostCSR pattern_union(const HostCSR& A, const HostCSR& B) {
+    HostCSR U;
+    U.rows = A.rows;
+    U.cols = A.cols;
+    U.ptr.assign(U.rows + 1, 0);
+    for (int i = 0; i < A.rows; ++i) {
+        int a = A.ptr[i], b = B.ptr[i];
+        while (a < A.ptr[i + 1] || b < B.ptr[i + 1]) {
+            int ja = a < A.ptr[i + 1] ? A.idx[a] : INT32_MAX;
+            int jb = b < B.ptr[i + 1] ? B.idx[b] : INT32_MAX;
+            int j = std::min(ja, jb);
+            U.idx.push_back(j);
+            U.val.push_back(0.0);
+            if (ja == j) ++a;
+            if (jb == j) ++b;
+        }
+        U.ptr[i + 1] = (int)U.idx.size();
+    }
+    return U;
+}
+
+// Dense inverse of an SPD matrix by Gauss-Jordan with partial pivoting
+// (coarsest spatial level only, a few hundred unknowns).
+std::vector<double> dense_inverse(const HostCSR& M, const HostCSR& L, double cm, double cl) {
+    int n = M.rows;
+    std::vector<double> a((size_t)n * n, 0.0), inv((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        for (int k = M.ptr[i]; k < M.ptr[i + 1]; ++k) a[(size_t)i * n + M.idx[k]] += cm * M.val[k];
+        for (int k = L.ptr[i]; k < L.ptr[i + 1]; ++k) a[(size_t)i * n + L.idx[k]] += cl * L.val[k];
+        inv[(size_t)i * n + i] = 1.0;
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)piv * n + c])) piv = r;
+        if (std::fabs(a[(size_t)piv * n + c]) == 0.0)
+            throw Error(PTP_EINVAL, "singular coarsest spatial operator");
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(a[(size_t)piv * n + k], a[(size_t)c * n + k]);
+                std::swap(inv[(size_t)piv * n + k], inv[(size_t)c * n + k]);
+            }
+        double d = 1.0 / a[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) { a[(size_t)c * n + k] *= d; inv[(size_t)c * n + k] *= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = a[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                a[(size_t)r * n + k] -= f * a[(size_t)c * n + k];
+                inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+            }
+        }
+    }
+    return inv;
+}
+
+std::vector<float> to_float(const std::vector<double>& v) {
+    return std::vector<float>(v.begin(), v.end());
+}
+
+}  // namespace
+
+void upload_csr(DevCSR& d, const HostCSR& a, const HostCSR* b, bool diag, cudaStream_t s) {
+    d.rows = a.rows;
+    d.cols = a.cols;
+    d.nnz = a.nnz();
+    d.ptr.upload(a.ptr, s);
+    d.idx.upload(a.idx, s);
+    d.v1d.upload(a.val, s);
+    d.v1f.upload(to_float(a.val), s);
+    std::vector<double> bv;
+    if (b) {
+        bv = values_on(a, *b);
+        d.v2d.upload(bv, s);
+        d.v2f.upload(to_float(bv), s);
+    }
+    if (diag) {
+        std::vector<double> d1(a.rows, 0.0), d2(a.rows, 0.0);
+        for (int i = 0; i < a.rows; ++i)
+            for (int k = a.ptr[i]; k < a.ptr[i + 1]; ++k)
+                if (a.idx[k] == i) {
+                    d1[i] = a.val[k];
+                    if (b) d2[i] = bv[k];
+                }
+        d.d1d.upload(d1, s);
+        d.d1f.upload(to_float(d1), s);
+        d.d2d.upload(d2, s);
+        d.d2f.upload(to_float(d2), s);
+    }
+}
+
+void make_structured_mesh(Ctx& c, int nx, int ny, double x0, double y0, double x1, double y1) {
+    PTP_REQUIRE(nx >= 2 && ny >= 2, "structured grid needs nx, ny >= 2");
+    PTP_REQUIRE(x1 > x0 && y1 > y0, "structured grid needs x1 > x0 and y1 > y0");
+    c.n_nodes = nx * ny;
+    c.xy.assign(2 * (size_t)c.n_nodes, 0.0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            c.xy[2 * ((size_t)j * nx + i) + 0] = x0 + (x1 - x0) * i / (nx - 1);
+            c.xy[2 * ((size_t)j * nx + i) + 1] = y0 + (y1 - y0) * j / (ny - 1);
+        }
+    c.n_tri = 2 * (nx - 1) * (ny - 1);
+    c.tri.assign(3 * (size_t)c.n_tri, 0);
+    size_t e = 0;
+    for (int j = 0; j < ny - 1; ++j)
+        for (int i = 0; i < nx - 1; ++i) {
+            int n00 = j * nx + i, n10 = n00 + 1, n11 = n00 + nx + 1, n01 = n00 + nx;
+            int* t = &c.tri[3 * e];
+            t[0] = n00; t[1] = n10; t[2] = n11;
+            t[3] = n00; t[4] = n11; t[5] = n01;
+            e += 2;
+        }
+    c.dirichlet.assign(c.n_nodes, 0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) c.dirichlet[(size_t)j * nx + i] = 1;
+    c.structured = true;
+    c.gnx = nx; c.gny = ny; c.gx0 = x0; c.gy0 = y0; c.gx1 = x1; c.gy1 = y1;
+}
+
+void build_problem(Ctx& c) {
+    PTP_REQUIRE(c.n_nodes > 0 && c.n_tri > 0, "no mesh");
+    PTP_REQUIRE(c.have_materials, "materials not set");
+    PTP_REQUIRE(c.N >= 1 && c.T > 0, "time not set");
+    PTP_REQUIRE((int)c.sigma.size() == c.n_tri, "materials do not match the mesh");
+    PTP_REQUIRE((int)c.coil_of_elem.size() == c.n_tri || c.n_coils == 0, "sources do not match the mesh");
+    cudaStream_t s = c.stream;
+    const double tau = c.T / c.N;
+
+    c.free_id.assign(c.n_nodes, -1);
+    int n = 0;
+    for (int i = 0; i < c.n_nodes; ++i)
+        if (!c.dirichlet[i]) c.free_id[i] = n++;
+    PTP_REQUIRE(n > 0, "mesh has no free node");
+    c.n = n;
+
+    // Residual data.  K(u) splits exactly into a linear part (elements with
+    // constant nu_linear: a CSR stencil nu_linear * A_lin) and the iron
+    // elements, whose fluxes nu(|g|^2)|T| g are computed per element.
+    std::vector<int> iron_of(c.n_tri, -1);
+    int n_iron = 0;
+    for (int e = 0; e < c.n_tri; ++e)
+        if (c.nonlinear[e]) iron_of[e] = n_iron++;
+    std::vector<int> e_nodes(3 * (size_t)std::max(n_iron, 1), -1);
+    std::vector<double> e_geo(6 * (size_t)std::max(n_iron, 1), 0.0);
+    std::vector<std::vector<std::pair<int, int>>> inc(n);  // (iron element, local vertex)
+    std::vector<Geo> geo(c.n_tri);
+    RowAccum Ma(n), Aa(n), Llin(n);
+    std::vector<double> cb((size_t)std::max(c.n_coils, 1) * n, 0.0);
+    const double dnu_c = (c.nu_max - c.nu_min) * c.s_sat * c.s_sat;
+    for (int e = 0; e < c.n_tri; ++e) {
+        const int* t = &c.tri[3 * (size_t)e];
+        for (int a = 0; a < 3; ++a)
+            PTP_REQUIRE(t[a] >= 0 && t[a] < c.n_nodes, "triangle vertex id out of range");
+        Geo G = triangle_geo(&c.xy[2 * (size_t)t[0]], &c.xy[2 * (size_t)t[1]], &c.xy[2 * (size_t)t[2]]);
+        geo[e] = G;
+        const int ie = iron_of[e];
+        if (ie >= 0) {
+            for (int a = 0; a < 3; ++a) e_nodes[3 * (size_t)ie + a] = c.free_id[t[a]];
+            double* g = &e_geo[6 * (size_t)ie];
+            g[0] = G.g[1][0]; g[1] = G.g[1][1]; g[2] = G.g[2][0]; g[3] = G.g[2][1];
+            // nu |T| = |T| nu_max - |T| (nu_max - nu_min) s_sat^2 / (s^2 + s_sat^2)
+            g[4] = G.area * c.nu_max;
+            g[5] = G.area * dnu_c;
+        }
+        for (int a = 0; a < 3; ++a) {
+            int i = c.free_id[t[a]];
+            if (i < 0) continue;
+            if (ie >= 0) inc[i].push_back({ie, a});
+            for (int b = 0; b < 3; ++b) {
+                int j = c.free_id[t[b]];
+                if (j < 0) continue;
+                // consistent mass sigma |T| / 12 (1 + delta_ab); unit stiffness
+                const double k = G.area * (G.g[a][0] * G.g[b][0] + G.g[a][1] * G.g[b][1]);
+                if (c.sigma[e] != 0.0) Ma.add(i, j, c.sigma[e] * G.area * (a == b ? 2.0 : 1.0) / 12.0);
+                Aa.add(i, j, k);
+                if (ie < 0) Llin.add(i, j, c.nu_linear * k);
+            }
+            if (c.n_coils > 0 && c.coil_of_elem[e] >= 0)
+                cb[(size_t)c.coil_of_elem[e] * n + i] += G.area / 3.0;
+        }
+    }
+    c.n_iron = n_iron;
+    c.e_nodes.upload(e_nodes, s);
+    c.e_geo.upload(e_geo, s);
+
+    std::vector<int> ip(n + 1, 0), ie;
+    std::vector<double> ig;
+    for (int i = 0; i < n; ++i) {
+        for (auto& pr : inc[i]) ie.push_back(pr.first);
+        ip[i + 1] = (int)ie.size();
+    }
+    {
+        std::vector<int> iron_elem(std::max(n_iron, 1), 0);
+        for (int e = 0; e < c.n_tri; ++e)
+            if (iron_of[e] >= 0) iron_elem[iron_of[e]] = e;
+        for (int i = 0; i < n; ++i)
+            for (auto& pr : inc[i]) {
+                const Geo& G = geo[iron_elem[pr.first]];
+                ig.push_back(G.g[pr.second][0]);
+                ig.push_back(G.g[pr.second][1]);
+            }
+    }
+    c.inc_ptr.upload(ip, s);
+    c.inc_elem.upload(ie, s);
+    c.inc_grad.upload(ig, s);
+
+    HostCSR M = Ma.finish(n, true);
+    HostCSR A = Aa.finish(n, false);
+    {   // mass rows scaled by 1/tau and the linear-element stiffness, for the residual
+        std::vector<double> mv(M.val);
+        for (auto& v : mv) v /= tau;
+        c.m_ptr.upload(M.ptr, s);
+        c.m_idx.upload(M.idx, s);
+        c.m_val.upload(mv, s);
+        HostCSR Ll = Llin.finish(n, true);
+        c.l_ptr.upload(Ll.ptr, s);
+        c.l_idx.upload(Ll.idx, s);
+        c.l_val.upload(Ll.val, s);
+    }
+    HostCSR L = A;
+    for (auto& v : L.val) v *= c.nu_max;
+
+    // spatial level 0
+    c.sl.clear();
+    c.sl.emplace_back();
+    SpatialLevel& l0 = c.sl[0];
+    l0.n = n;
+    l0.nx = c.structured ? c.gnx : 0;
+    l0.ny = c.structured ? c.gny : 0;
+    l0.hM = M;
+    l0.hL = L;
+
+    // coils: loads and time factors amp sin(2 pi t^n / T + phase), t^n = n tau
+    std::vector<double> cs((size_t)std::max(c.n_coils, 1) * c.N, 0.0);
+    for (int k = 0; k < c.n_coils; ++k)
+        for (int j = 0; j < c.N; ++j)
+            cs[(size_t)k * c.N + j] =
+                c.amp[k] * std::sin(2.0 * M_PI * ((j + 1) * tau) / c.T + c.phase[k]);
+    c.coil_b.upload(cb, s);
+    c.coil_s.upload(cs, s);
+}
+
+void build_hierarchy(Ctx& c) {
+    cudaStream_t s = c.stream;
+    const ptp_opts& o = c.opts;
+    const int COARSE_MAX = 600;  // free nodes of the coarsest spatial level (dense inverse)
+
+    // ---- spatial hierarchy on nested structured grids ----
+    while (o.spatial_prec == PTP_PREC_GMG && c.structured) {
+        SpatialLevel& f = c.sl.back();
+        int nx = f.nx, ny = f.ny;
+        if (f.n <= COARSE_MAX) break;
+        if ((nx - 1) % 2 || (ny - 1) % 2 || nx < 5 || ny < 5) break;
+        int cx = (nx - 1) / 2 + 1, cy = (ny - 1) / 2 + 1;
+        // free numbering of both grids (interior nodes, row-major)
+        auto fid = [&](int i, int j) { return (j - 1) * (nx - 2) + (i - 1); };
+        auto cid = [&](int i, int j) -> int {
+            if (i <= 0 || j <= 0 || i >= cx - 1 || j >= cy - 1) return -1;
+            return (j - 1) * (cx - 2) + (i - 1);
+        };
+        int nc = (cx - 2) * (cy - 2);
+        RowAccum Pa(f.n);
+        for (int j = 1; j < ny - 1; ++j)
+            for (int i = 1; i < nx - 1; ++i) {
+                int r = fid(i, j);
+                // P1 interpolation on the nested mesh (diagonal (i,j)-(i+1,j+1)):
+                // coarse vertex, edge midpoints (horizontal, vertical, diagonal)
+                int ci[2], cj[2], m;
+                if (i % 2 == 0 && j % 2 == 0) { ci[0] = i / 2; cj[0] = j / 2; m = 1; }
+                else if (j % 2 == 0) { ci[0] = (i - 1) / 2; cj[0] = j / 2; ci[1] = (i + 1) / 2; cj[1] = j / 2; m = 2; }
+                else if (i % 2 == 0) { ci[0] = i / 2; cj[0] = (j - 1) / 2; ci[1] = i / 2; cj[1] = (j + 1) / 2; m = 2; }
+                else { ci[0] = (i - 1) / 2; cj[0] = (j - 1) / 2; ci[1] = (i + 1) / 2; cj[1] = (j + 1) / 2; m = 2; }
+                for (int k = 0; k < m; ++k) {
+                    int q = cid(ci[k], cj[k]);
+                    if (q >= 0) Pa.add(r, q, m == 1 ? 1.0 : 0.5);
+                }
+            }
+        HostCSR P = Pa.finish(nc, true);
+        HostCSR Rt = transpose(P);
+        SpatialLevel cl;
+        cl.n = nc;
+        cl.nx = cx;
+        cl.ny = cy;
+        cl.hM = matmul(Rt, matmul(f.hM, P));
+        cl.hL = matmul(Rt, matmul(f.hL, P));
+        f.hP = P;
+        c.sl.push_back(std::move(cl));
+    }
+    for (size_t k = 0; k < c.sl.size(); ++k) {
+        SpatialLevel& L = c.sl[k];
+        HostCSR pat = pattern_union(L.hM, L.hL);
+        HostCSR vm = pat;
+        vm.val = values_on(pat, L.hM);
+        upload_csr(L.op, vm, &L.hL, true, s);
+        if (k + 1 < c.sl.size()) {
+            upload_csr(L.P, L.hP, nullptr, false, s);
+            upload_csr(L.R, transpose(L.hP), nullptr, false, s);
+        }
+    }
+
+    // ---- time levels: coarsen by 2 while N_l is even and above N_c ----
+    c.tl.clear();
+    c.ops.clear();
+    int Nl = c.N;
+    int nc_target = o.coarse_steps == 2 ? 2 : 1;
+    for (;;) {
+        TimeLevel t;
+        t.N = Nl;
+        t.tau = c.T / Nl;
+        c.tl.push_back(t);
+        bool can = (Nl % 2 == 0) && (Nl / 2 >= nc_target);
+        if (o.time_levels > 0 && (int)c.tl.size() >= o.time_levels) can = false;
+        if (!can) break;
+        Nl /= 2;
+    }
+    const int Nc = c.tl.back().N;   // the exact coarse solve needs Nc in {1, 2}; checked by the solves
+    auto add_op = [&](double cm, double cl) {
+        OpPair p;
+        p.cm = cm;
+        p.cl = cl;
+        c.ops.push_back(std::move(p));
+        return (int)c.ops.size() - 1;
+    };
+    for (auto& t : c.tl) t.op = add_op(1.0, t.tau);
+    double tc = c.tl.back().tau;
+    c.coarse_ops[0] = add_op(0.0, tc);            // sum mode:        tau_c L
+    c.coarse_ops[1] = Nc == 2 ? add_op(2.0, tc) : -1;  // difference:  2M + tau_c L
+    c.coarse_ok = Nc == 1 || Nc == 2;
+    // dense inverses on the coarsest spatial level
+    const SpatialLevel& cs = c.sl.back();
+    if (cs.n <= COARSE_MAX) {
+        for (auto& p : c.ops) {
+            std::vector<double> inv = dense_inverse(cs.hM, cs.hL, p.cm, p.cl);
+            p.inv_d.upload(inv, s);
+            p.inv_f.upload(to_float(inv), s);
+        }
+    }
+}
+
+}  // namespace ptp

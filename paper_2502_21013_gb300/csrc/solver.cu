@@ -1,0 +1,644 @@
+// Host orchestration of the hot path (all work runs in the kernels of
+// k_residual.cu and k_sparse.cu):
+//
+//   outer step k (fixed point of eq. iter1-iter2 in correction form)
+//     R = F - A(U^k), ||R||, stopping rule          (K1, double)
+//     b = tau R
+//     x = V-cycle(s) of multigrid in time on  (M + tau L) x^n - M x^{n-1} = b^n,  x^0 = x^N
+//     U^{k+1} = U^k + x                             (double)
+//
+//   multigrid in time, level l (N_l steps, tau_l = T/N_l):
+//     damped block-Jacobi sweeps  x += w_t (M + tau_l L)^{-1} (b + M x^{n-1} - (M + tau_l L) x^n),
+//       each spatial solve = batched PCG over the N_l columns (Jacobi or GMG preconditioned)
+//     residual restricted to N_l/2 steps by summing pairs (2m, 2m+1)
+//     coarse correction prolongated by injection to both steps of the pair
+//     coarsest level N_c = 1: tau_c L x = b;  N_c = 2: sum / difference split into
+//       tau_c L s = b^0 + b^1 and (2M + tau_c L) d = b^0 - b^1, both SPD, PCG in double.
+//
+// With piecewise-constant prolongation P and restriction P^T the Galerkin
+// coarse operator of the level-l periodic operator is exactly the level-(l+1)
+// operator with tau_{l+1} = 2 tau_l, so coarse levels are rediscretisations.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace ptp {
+
+size_t reduction_partials(int Nmax);
+int residual_grid(size_t total);
+
+Ctx::~Ctx() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (h_status) cudaFreeHost(h_status);
+    if (own_stream) cudaStreamDestroy(own_stream);
+}
+
+namespace {
+
+template <typename T> T* wbuf(Ctx& c, int k);
+template <> double* wbuf<double>(Ctx& c, int k) { return c.w_d[k].p; }
+template <> float* wbuf<float>(Ctx& c, int k) { return c.w_f[k].p; }
+
+template <typename T> T* gx(Ctx& c, int s);
+template <typename T> T* gb(Ctx& c, int s);
+template <typename T> T* gr(Ctx& c, int s);
+template <> double* gx<double>(Ctx& c, int s) { return c.g_xd[s].p; }
+template <> double* gb<double>(Ctx& c, int s) { return c.g_bd[s].p; }
+template <> double* gr<double>(Ctx& c, int s) { return c.g_rd[s].p; }
+template <> float* gx<float>(Ctx& c, int s) { return c.g_xf[s].p; }
+template <> float* gb<float>(Ctx& c, int s) { return c.g_bf[s].p; }
+template <> float* gr<float>(Ctx& c, int s) { return c.g_rf[s].p; }
+
+template <typename T> T* mgx(Ctx& c, int l);
+template <typename T> T* mgb(Ctx& c, int l);
+template <> double* mgx<double>(Ctx& c, int l) { return c.mg_xd[l].p; }
+template <> double* mgb<double>(Ctx& c, int l) { return c.mg_bd[l].p; }
+template <> float* mgx<float>(Ctx& c, int l) { return c.mg_xf[l].p; }
+template <> float* mgb<float>(Ctx& c, int l) { return c.mg_bf[l].p; }
+
+template <typename T>
+Op<T> make_op(const DevCSR& d, double cm, double cl) {
+    Op<T> o;
+    o.rows = d.rows;
+    o.cols = d.cols;
+    o.ptr = d.ptr.p;
+    o.idx = d.idx.p;
+    if constexpr (sizeof(T) == 8) {
+        o.v1 = d.v1d.p; o.v2 = d.v2d.p; o.d1 = d.d1d.p; o.d2 = d.d2d.p;
+    } else {
+        o.v1 = d.v1f.p; o.v2 = d.v2f.p; o.d1 = d.d1f.p; o.d2 = d.d2f.p;
+    }
+    o.cm = (T)cm;
+    o.cl = (T)cl;
+    return o;
+}
+
+template <typename T>
+ColRed<T> make_cr(Ctx& c) {
+    ColRed<T> r;
+    if constexpr (sizeof(T) == 8) {
+        r.partials = c.part_d.p;
+        r.col = c.col_d.p;
+    } else {
+        r.partials = c.part_f.p;
+        r.col = c.col_f.p;
+    }
+    r.counter = c.counter.p;
+    return r;
+}
+
+bool use_gmg(const Ctx& c) {
+    return c.opts.spatial_prec == PTP_PREC_GMG &&
+           (c.sl.size() > 1 || c.ops[0].inv_d.p != nullptr);
+}
+
+// Spatial geometric-multigrid V-cycle for (cm M + cl L) on N columns:
+// z = V(b).  Damped-Jacobi pre/post sweeps (symmetric), Galerkin coarse
+// operators, dense inverse on the coarsest level.  Returns the buffer that
+// holds z (xa or xb).
+template <typename T>
+T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk) {
+    const int S = (int)c.sl.size();
+    const double cm = c.ops[opi].cm, cl = c.ops[opi].cl;
+    const int nu = std::max(1, c.opts.gmg_smooth);
+    const T w = (T)c.opts.gmg_omega;
+    cudaStream_t st = c.stream;
+    std::vector<const T*> b(S);
+    std::vector<T*> cur(S), oth(S);
+    b[0] = b0;
+    cur[0] = xa;
+    oth[0] = xb;
+    for (int s = 1; s < S; ++s) {
+        b[s] = gb<T>(c, s);
+        cur[s] = gx<T>(c, s);
+        oth[s] = gr<T>(c, s);
+    }
+    for (int s = 0; s < S - 1; ++s) {
+        Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
+        c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
+        for (int k = 1; k < nu; ++k) {
+            c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
+            std::swap(cur[s], oth[s]);
+        }
+        c.launches += launch_spmm<T>(SP_RESID, A, N, cur[s], b[s], oth[s], T(0), sk, st);
+        Op<T> R = make_op<T>(c.sl[s].R, 1.0, 0.0);
+        c.launches += launch_spmm<T>(SP_RESTRICT, R, N, oth[s], nullptr, const_cast<T*>(b[s + 1]), T(0), sk, st);
+    }
+    {
+        const int s = S - 1;
+        const OpPair& p = c.ops[opi];
+        const T* inv = nullptr;
+        if constexpr (sizeof(T) == 8) inv = p.inv_d.p; else inv = p.inv_f.p;
+        if (inv) {
+            c.launches += launch_dense_apply<T>(c.sl[s].n, N, inv, b[s], cur[s], sk, st);
+        } else {
+            Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
+            c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
+            for (int k = 1; k < 4 * nu; ++k) {
+                c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
+                std::swap(cur[s], oth[s]);
+            }
+        }
+    }
+    for (int s = S - 2; s >= 0; --s) {
+        Op<T> P = make_op<T>(c.sl[s].P, 1.0, 0.0);
+        c.launches += launch_spmm<T>(SP_INTERP_ADD, P, N, cur[s + 1], nullptr, cur[s], T(0), sk, st);
+        Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
+        for (int k = 0; k < nu; ++k) {
+            c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
+            std::swap(cur[s], oth[s]);
+        }
+    }
+    return cur[0];
+}
+
+// Batched PCG on (cm M + cl L) X = B over N columns, X accumulated as
+// X += xscale * (solution from zero).  `r` holds B on entry and is
+// destroyed.  Work buffers: w[1..5] of the precision.  With tol > 0 the
+// iteration stops early on the device once every column has
+// ||r|| <= tol ||b|| (later kernels of the solve see the flag and return).
+template <typename T>
+struct PCG {
+    Ctx& c;
+    int opi, N;
+    T* r;
+    T* x;
+    T xscale;
+    bool gmg;
+    Skip sk, sk2;
+    ColRed<T> cr;
+    T *p = nullptr, *q = nullptr, *z = nullptr, *pa = nullptr, *pb = nullptr;
+    Op<T> A;
+
+    bool assign_first;   // x is not initialised: the first update assigns
+    int iter = 0;
+
+    PCG(Ctx& c_, int opi_, int N_, T* r_, T* x_, T xscale_, double tol, Skip sk_, bool x_uninit)
+        : c(c_), opi(opi_), N(N_), r(r_), x(x_), xscale(xscale_), sk(sk_), assign_first(x_uninit) {
+        gmg = use_gmg(c);
+        cr = make_cr<T>(c);
+        sk2 = sk;
+        if (tol > 0) {
+            cr.pdone = c.flag.p + 1;
+            cr.tol2 = (T)(tol * tol);
+            sk2.pdone = c.flag.p + 1;
+        }
+        A = make_op<T>(c.sl[0].op, c.ops[opi].cm, c.ops[opi].cl);
+        q = wbuf<T>(c, 3);
+    }
+
+    void init() {
+        cudaStream_t st = c.stream;
+        if (cr.pdone) c.launches += launch_flag(c.flag.p + 1, 0, sk, st);
+        if (!gmg) {
+            z = wbuf<T>(c, 1);
+            p = wbuf<T>(c, 2);
+            c.launches += launch_pcg_init_jacobi<T>(A, N, r, z, p, cr, sk2, st);
+        } else {
+            T* zr = gmg_vcycle<T>(c, opi, N, r, wbuf<T>(c, 1), wbuf<T>(c, 4), sk2);
+            c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, zr, cr, 1, sk2, st);
+            p = zr;
+            pa = zr == wbuf<T>(c, 1) ? wbuf<T>(c, 4) : wbuf<T>(c, 1);
+            pb = wbuf<T>(c, 5);
+        }
+    }
+
+    void iterate(bool last) {
+        cudaStream_t st = c.stream;
+        c.launches += launch_pcg_apply_alpha<T>(A, N, p, q, cr, sk2, st);
+        const int assign = (assign_first && iter == 0) ? 1 : 0;
+        ++iter;
+        c.launches += launch_pcg_update<T>(A, N, xscale, assign, x, p, r, q, gmg ? nullptr : z, gmg ? 0 : 1, cr,
+                                           sk2, st);
+        if (last) return;
+        if (gmg) {
+            z = gmg_vcycle<T>(c, opi, N, r, pa, pb, sk2);
+            c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, z, cr, 0, sk2, st);
+        }
+        c.launches += launch_pcg_direction<T>(A.rows, N, z, p, cr, sk2, st);
+    }
+};
+
+// one damped block-Jacobi sweep at time level l on x (in place)
+template <typename T>
+void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
+    const TimeLevel& t = c.tl[l];
+    T* r = wbuf<T>(c, 0);
+    const size_t cnt = (size_t)c.n * t.N;
+    if (x_zero) {
+        PTP_CUDA(cudaMemcpyAsync(r, b, cnt * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+        Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+        c.launches += launch_spmm<T>(SP_PRESID, A, t.N, x, b, r, T(0), sk, c.stream);
+    }
+    // a zero start means x holds stale data: the first PCG update assigns it
+    PCG<T> pcg(c, t.op, t.N, r, x, (T)c.opts.omega_t, 0.0, sk, x_zero);
+    pcg.init();
+    const int it = std::max(1, c.opts.pcg_iters);
+    for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
+}
+
+// exact (to coarse_tol) solve on the coarsest time level, in double
+template <typename T>
+void coarse_solve(Ctx& c, Skip sk) {
+    const int L = (int)c.tl.size();
+    const int Nc = c.tl[L - 1].N;
+    const int n = c.n;
+    cudaStream_t st = c.stream;
+    T* xc = mgx<T>(c, L - 1);
+    const T* bc = mgb<T>(c, L - 1);
+    double* cb = c.w_d[0].p;   // rhs (destroyed by PCG)
+    double* cx = c.Ud.p;       // solution columns
+    const double tol = c.opts.coarse_tol;
+    const int maxit = std::max(1, c.opts.coarse_max_it);
+    auto run = [&](int opi, double* rhs, double* sol) {
+        // the fill is kept: with early exit the assigning update may be skipped
+        c.launches += launch_fill<double>((size_t)n, 0.0, sol, sk, st);
+        PCG<double> pcg(c, opi, 1, rhs, sol, 1.0, tol, sk, false);
+        pcg.init();
+        for (int k = 0; k < maxit; ++k) pcg.iterate(k == maxit - 1);
+    };
+    if (Nc == 1) {
+        if constexpr (sizeof(T) == 8)
+            PTP_CUDA(cudaMemcpyAsync(cb, bc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        else
+            c.launches += launch_cast<float, double>((size_t)n, bc, cb, sk, st);
+        run(c.coarse_ops[0], cb, cx);
+        if constexpr (sizeof(T) == 8)
+            PTP_CUDA(cudaMemcpyAsync(xc, cx, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        else
+            c.launches += launch_cast<double, float>((size_t)n, cx, xc, sk, st);
+    } else {
+        double* bs = cb;
+        double* bd = cb + n;
+        double* xs = cx;
+        double* xd = cx + n;
+        c.launches += launch_split2<T>(n, bc, bs, bd, sk, st);
+        run(c.coarse_ops[0], bs, xs);
+        run(c.coarse_ops[1], bd, xd);
+        c.launches += launch_combine2<T>(n, xs, xd, xc, sk, st);
+    }
+}
+
+// multigrid-in-time V-cycle at level l: improves x_l for P_l x_l = b_l
+template <typename T>
+void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk) {
+    const int L = (int)c.tl.size();
+    T* x = mgx<T>(c, l);
+    const T* b = mgb<T>(c, l);
+    const TimeLevel& t = c.tl[l];
+    cudaStream_t st = c.stream;
+    if (l == L - 1) {
+        coarse_solve<T>(c, sk);  // x_zero is implied: exact solve
+        return;
+    }
+    const int pre = c.opts.pre_smooth, post = c.opts.post_smooth;
+    bool zero = x_zero;
+    if (pre == 0 && zero) {
+        c.launches += launch_fill<T>((size_t)c.n * t.N, T(0), x, sk, st);
+        zero = false;
+    }
+    for (int k = 0; k < pre; ++k) {
+        bj_sweep<T>(c, l, x, b, zero, sk);
+        zero = false;
+    }
+    Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+    c.launches += launch_spmm<T>(SP_PRESID_RESTRICT, A, t.N, x, b, mgb<T>(c, l + 1), T(0), sk, st);
+    mgt_vcycle<T>(c, l + 1, true, sk);
+    c.launches += launch_time_prolong_add<T>(c.n, c.tl[l + 1].N, mgx<T>(c, l + 1), x, sk, st);
+    for (int k = 0; k < post; ++k) bj_sweep<T>(c, l, x, b, false, sk);
+}
+
+ResidualArgs residual_args(Ctx& c, const double* U, double* R) {
+    ResidualArgs a{};
+    a.n = c.n;
+    a.N = c.N;
+    a.n_iron = c.n_iron;
+    a.n_coils = c.n_coils;
+    a.e_nodes = c.e_nodes.p;
+    a.e_geo = c.e_geo.p;
+    a.inc_ptr = c.inc_ptr.p;
+    a.inc_elem = c.inc_elem.p;
+    a.inc_grad = c.inc_grad.p;
+    a.m_ptr = c.m_ptr.p;
+    a.m_idx = c.m_idx.p;
+    a.m_val = c.m_val.p;
+    a.l_ptr = c.l_ptr.p;
+    a.l_idx = c.l_idx.p;
+    a.l_val = c.l_val.p;
+    a.coil_b = c.coil_b.p;
+    a.coil_s = c.coil_s.p;
+    a.s2sat = c.s_sat * c.s_sat;
+    a.U = U;
+    a.Qx = c.Qx.p;
+    a.Qy = c.Qy.p;
+    a.R = R;
+    a.partials = c.part_d.p;
+    a.counter = c.counter.p;
+    a.status = c.status.p;
+    return a;
+}
+
+template <typename T>
+void outer_step(Ctx& c, Skip sk) {
+    ResidualArgs a = residual_args(c, c.U.p, nullptr);
+    a.scale = c.T / c.N;
+    if constexpr (sizeof(T) == 8) a.b_d = mgb<double>(c, 0); else a.b_f = mgb<float>(c, 0);
+    a.done = c.flag.p;
+    a.check = 1;
+    c.launches += launch_residual(a, c.stream);
+    const int cyc = std::max(1, c.opts.vcycles);
+    for (int v = 0; v < cyc; ++v) mgt_vcycle<T>(c, 0, v == 0, sk);
+    const double* sc = sizeof(T) == 4 ? &c.status.p->bscale_used : nullptr;
+    c.launches += launch_add_to_double<T>((size_t)c.n * c.N, mgx<T>(c, 0), c.U.p, sc, sk, c.stream);
+}
+
+void final_residual(Ctx& c) {
+    ResidualArgs a = residual_args(c, c.U.p, nullptr);
+    a.done = c.flag.p;
+    a.check = 1;
+    c.launches += launch_residual(a, c.stream);
+}
+
+template <typename T>
+void alloc_levels(Ctx& c, std::vector<DBuf<T>>& x, std::vector<DBuf<T>>& b) {
+    x.clear();
+    b.clear();
+    x.resize(c.tl.size());
+    b.resize(c.tl.size());
+    for (size_t l = 0; l < c.tl.size(); ++l) {
+        x[l].alloc((size_t)c.n * c.tl[l].N);
+        b[l].alloc((size_t)c.n * c.tl[l].N);
+    }
+}
+
+}  // namespace
+
+void alloc_work(Ctx& c) {
+    const size_t big = (size_t)c.n * c.N;
+    const bool mixed = c.opts.precision == PTP_MIXED;
+    for (int k = 0; k < 6; ++k) {
+        c.w_d[k].alloc(std::max(big, (size_t)c.n * 2));
+        c.w_f[k].alloc(big);
+    }
+    c.U.alloc(big);
+    c.R.alloc(big);
+    c.Ud.alloc(std::max(big, (size_t)c.n * 2));
+    c.Qx.alloc((size_t)std::max(c.n_iron, 1) * c.N);
+    c.Qy.alloc((size_t)std::max(c.n_iron, 1) * c.N);
+    alloc_levels<double>(c, c.mg_xd, c.mg_bd);
+    if (mixed) alloc_levels<float>(c, c.mg_xf, c.mg_bf);
+    else { c.mg_xf.clear(); c.mg_bf.clear(); }
+    const size_t S = c.sl.size();
+    c.g_xd.clear(); c.g_bd.clear(); c.g_rd.clear();
+    c.g_xf.clear(); c.g_bf.clear(); c.g_rf.clear();
+    c.g_xd.resize(S); c.g_bd.resize(S); c.g_rd.resize(S);
+    c.g_xf.resize(S); c.g_bf.resize(S); c.g_rf.resize(S);
+    for (size_t s = 1; s < S; ++s) {
+        const size_t m = (size_t)c.sl[s].n * c.N;
+        c.g_xd[s].alloc(m); c.g_bd[s].alloc(m); c.g_rd[s].alloc(m);
+        c.g_xf[s].alloc(m); c.g_bf[s].alloc(m); c.g_rf[s].alloc(m);
+    }
+    const size_t colN = 8 * (size_t)std::max(c.N, 2);
+    c.col_d.alloc(colN);
+    c.scal.alloc(8);
+    c.col_f.alloc(colN);
+    const size_t parts = std::max(reduction_partials(std::max(c.N, 2)), (size_t)num_sms() * 64);
+    c.part_d.alloc(parts);
+    c.part_f.alloc(parts);
+    c.counter.alloc(256);
+    PTP_CUDA(cudaMemsetAsync(c.counter.p, 0, 256 * sizeof(unsigned), c.stream));
+    c.status.alloc(1);
+    c.flag.alloc(4);
+    PTP_CUDA(cudaMemsetAsync(c.flag.p, 0, 4 * sizeof(int), c.stream));
+    if (!c.h_status) PTP_CUDA(cudaHostAlloc((void**)&c.h_status, 2 * sizeof(Status), cudaHostAllocDefault));
+}
+
+void residual_dev(Ctx& c, const double* U, double* R, double* b_out_d, float* b_out_f, double scale,
+                  bool outer_check) {
+    ResidualArgs a = residual_args(c, U, R);
+    a.b_d = b_out_d;
+    a.b_f = b_out_f;
+    a.scale = scale;
+    a.check = outer_check ? 1 : 0;
+    c.launches += launch_residual(a, c.stream);
+}
+
+double norm_dev(Ctx& c, const double* x, size_t count) {
+    double* out = c.scal.p + 1;
+    c.launches += launch_norm2<double>(count, x, c.part_d.p, c.counter.p, out, c.stream);
+    double h = 0.0;
+    PTP_CUDA(cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    PTP_CUDA(cudaStreamSynchronize(c.stream));
+    return std::sqrt(h);
+}
+
+void source_dev(Ctx& c, double* F) {
+    launch_source(c.n, c.N, c.n_coils, c.coil_b.p, c.coil_s.p, F, c.stream);
+    c.launches += 1;
+}
+
+template <typename T>
+void apply_op(Ctx& c, int s, int op, int N, const T* X, T* Y) {
+    Op<T> A = make_op<T>(c.sl[s].op, c.ops[op].cm, c.ops[op].cl);
+    c.launches += launch_spmm<T>(SP_APPLY, A, N, X, nullptr, Y, T(0), Skip{}, c.stream);
+}
+
+template <typename T>
+void periodic_apply(Ctx& c, int level, const T* X, T* Y) {
+    const TimeLevel& t = c.tl[level];
+    Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+    c.launches += launch_spmm<T>(SP_PAPPLY, A, t.N, X, nullptr, Y, T(0), Skip{}, c.stream);
+}
+
+template <typename T>
+int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check) {
+    cudaStream_t st = c.stream;
+    const size_t cnt = (size_t)c.n * N;
+    T* r = wbuf<T>(c, 0);
+    PTP_CUDA(cudaMemcpyAsync(r, B, cnt * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    c.launches += launch_fill<T>(cnt, T(0), X, Skip{}, st);
+    PCG<T> pcg(c, op, N, r, X, T(1), tol, Skip{}, false);
+    pcg.init();
+    int it = 0;
+    for (; it < max_it; ++it) {
+        pcg.iterate(it == max_it - 1);
+        if (host_check && tol > 0) {
+            int done = 0;
+            PTP_CUDA(cudaMemcpyAsync(&done, c.flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PTP_CUDA(cudaStreamSynchronize(st));
+            if (done) { ++it; break; }
+        }
+    }
+    PTP_CUDA(cudaStreamSynchronize(st));
+    return it;
+}
+
+static void require_coarse(const Ctx& c) {
+    PTP_REQUIRE(c.coarse_ok,
+                "multigrid in time needs a coarsest level with 1 or 2 steps (N must be a power of "
+                "two times 1 or 2, and time_levels large enough to reach it)");
+}
+
+void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres) {
+    require_coarse(c);
+    cudaStream_t st = c.stream;
+    const size_t cnt = (size_t)c.n * c.N;
+    const bool mixed = c.opts.precision == PTP_MIXED;
+    double* nb = c.scal.p;  // ||B||^2, then ||B|| (device scalar)
+    if (mixed) {
+        // the float V-cycle runs on B / ||B|| and its result is scaled back
+        c.launches += launch_norm2<double>(cnt, B, c.part_d.p, c.counter.p, nb, st);
+        double h = 0.0;
+        PTP_CUDA(cudaMemcpyAsync(&h, nb, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaStreamSynchronize(st));
+        h = h > 0 ? std::sqrt(h) : 1.0;
+        PTP_CUDA(cudaMemcpyAsync(nb, &h, sizeof(double), cudaMemcpyHostToDevice, st));
+        c.launches += launch_cast_scaled<double, float>(cnt, B, mgb<float>(c, 0), nullptr, nb, st);
+    } else {
+        PTP_CUDA(cudaMemcpyAsync(mgb<double>(c, 0), B, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    for (int v = 0; v < std::max(1, cycles); ++v) {
+        if (mixed) mgt_vcycle<float>(c, 0, v == 0, Skip{});
+        else mgt_vcycle<double>(c, 0, v == 0, Skip{});
+    }
+    if (mixed) c.launches += launch_cast_scaled<float, double>(cnt, mgx<float>(c, 0), X, nb, nullptr, st);
+    else PTP_CUDA(cudaMemcpyAsync(X, mgx<double>(c, 0), cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (relres) {
+        // ||B - P X|| / ||B|| in double
+        double* r = c.Ud.p;
+        Op<double> A = make_op<double>(c.sl[0].op, c.ops[c.tl[0].op].cm, c.ops[c.tl[0].op].cl);
+        c.launches += launch_spmm<double>(SP_PRESID, A, c.N, X, B, r, 0.0, Skip{}, st);
+        double* out = c.scal.p + 2;  // two scratch scalars
+        c.launches += launch_norm2<double>(cnt, r, c.part_d.p, c.counter.p, out, st);
+        c.launches += launch_norm2<double>(cnt, B, c.part_d.p, c.counter.p, out + 1, st);
+        double h[2];
+        PTP_CUDA(cudaMemcpyAsync(h, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaStreamSynchronize(st));
+        *relres = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    }
+    PTP_CUDA(cudaStreamSynchronize(st));
+}
+
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats) {
+    require_coarse(c);
+    cudaStream_t st = c.stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t cnt = (size_t)c.n * c.N;
+    PTP_REQUIRE(o.precision == c.opts.precision && o.spatial_prec == c.opts.spatial_prec &&
+                    o.time_levels == c.opts.time_levels && o.coarse_steps == c.opts.coarse_steps,
+                "precision / preconditioner / hierarchy options differ from ptp_setup");
+    c.opts = o;
+    const bool mixed = o.precision == PTP_MIXED;
+    if (U0) PTP_CUDA(cudaMemcpyAsync(c.U.p, U0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else PTP_CUDA(cudaMemsetAsync(c.U.p, 0, cnt * sizeof(double), st));
+    Status s0{};
+    s0.tol = o.tol;
+    s0.bscale = c.f_norm > 0 ? c.f_norm : 1.0;   // ||F||: the residual norm of the zero start
+    s0.bscale_used = s0.bscale;
+    c.h_status[0] = s0;
+    PTP_CUDA(cudaMemcpyAsync(c.status.p, &c.h_status[0], sizeof(Status), cudaMemcpyHostToDevice, st));
+    PTP_CUDA(cudaMemsetAsync(c.flag.p, 0, 4 * sizeof(int), st));
+    PTP_CUDA(cudaStreamSynchronize(st));  // h_status[0] is reused below
+
+    Skip sk;
+    sk.done = c.flag.p;
+    auto step = [&]() {
+        if (mixed) outer_step<float>(c, sk); else outer_step<double>(c, sk);
+    };
+    const int64_t l0 = c.launches;
+    // graph of one outer step, re-captured when the options change
+    const int key = (mixed ? 1 : 0) | (o.pcg_iters << 1) | (o.vcycles << 6) | (o.pre_smooth << 10) |
+                    (o.post_smooth << 14) | (o.gmg_smooth << 18) | (o.coarse_max_it << 22);
+    if (o.use_graph && (c.graph_exec == nullptr || c.graph_key != key)) {
+        if (c.graph_exec) { cudaGraphExecDestroy(c.graph_exec); c.graph_exec = nullptr; }
+        cudaGraph_t g;
+        const int64_t before = c.launches;
+        PTP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            step();
+        } catch (...) {
+            cudaStreamEndCapture(st, &g);
+            throw;
+        }
+        PTP_CUDA(cudaStreamEndCapture(st, &g));
+        PTP_CUDA(cudaGraphInstantiate(&c.graph_exec, g, 0));
+        cudaGraphDestroy(g);
+        c.launches_per_step = c.launches - before;
+        c.launches = before;
+        c.graph_key = key;
+    }
+    cudaEvent_t e0, e1;
+    PTP_CUDA(cudaEventCreate(&e0));
+    PTP_CUDA(cudaEventCreate(&e1));
+    cudaEvent_t chk[2];
+    PTP_CUDA(cudaEventCreateWithFlags(&chk[0], cudaEventDisableTiming));
+    PTP_CUDA(cudaEventCreateWithFlags(&chk[1], cudaEventDisableTiming));
+    PTP_CUDA(cudaEventRecord(e0, st));
+    const int every = std::max(1, o.check_every);
+    int launched = 0, slot = 0, pending = -1;
+    bool stop = false;
+    int64_t step_launches = 0;
+    while (launched < o.max_outer && !stop) {
+        const int chunk = std::min(every, o.max_outer - launched);
+        for (int k = 0; k < chunk; ++k) {
+            if (o.use_graph) {
+                PTP_CUDA(cudaGraphLaunch(c.graph_exec, st));
+                step_launches += c.launches_per_step;
+            } else {
+                const int64_t b = c.launches;
+                step();
+                step_launches += c.launches - b;
+                c.launches = b;
+            }
+        }
+        launched += chunk;
+        PTP_CUDA(cudaMemcpyAsync(&c.h_status[slot], c.status.p, sizeof(Status), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaEventRecord(chk[slot], st));
+        if (pending >= 0) {
+            PTP_CUDA(cudaEventSynchronize(chk[pending]));
+            if (c.h_status[pending].done) stop = true;
+        }
+        pending = slot;
+        slot ^= 1;
+    }
+    final_residual(c);
+    step_launches += 2;
+    PTP_CUDA(cudaEventRecord(e1, st));
+    PTP_CUDA(cudaMemcpyAsync(&c.h_status[0], c.status.p, sizeof(Status), cudaMemcpyDeviceToHost, st));
+    PTP_CUDA(cudaStreamSynchronize(st));
+    PTP_CUDA(cudaGetLastError());
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    cudaEventDestroy(chk[0]); cudaEventDestroy(chk[1]);
+    const Status fs = c.h_status[0];
+    if (U) PTP_CUDA(cudaMemcpyAsync(U, c.U.p, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    PTP_CUDA(cudaStreamSynchronize(st));
+    c.launches = l0 + step_launches;
+    const bool conv = fs.done == 1;
+    if (stats) {
+        stats->outer_iterations = fs.iteration > 0 ? fs.iteration - 1 : 0;
+        stats->converged = conv ? 1 : 0;
+        stats->res0 = fs.res0;
+        stats->res_final = fs.res;
+        stats->setup_ms = c.setup_ms;
+        stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        stats->residual_ms = ms;  // device time of the whole iteration
+        stats->kernel_launches = step_launches;
+        stats->time_levels = (int)c.tl.size();
+        stats->spatial_levels = (int)c.sl.size();
+    }
+    if (fs.done == 2) return PTP_ENAN;
+    return conv ? PTP_OK : PTP_ENOTCONV;
+}
+
+template void apply_op<double>(Ctx&, int, int, int, const double*, double*);
+template void apply_op<float>(Ctx&, int, int, int, const float*, float*);
+template void periodic_apply<double>(Ctx&, int, const double*, double*);
+template int spatial_pcg<double>(Ctx&, int, int, const double*, double*, double, int, bool);
+template int spatial_pcg<float>(Ctx&, int, int, const float*, float*, double, int, bool);
+
+}  // namespace ptp

@@ -1,0 +1,297 @@
+"""ctypes binding of libptp.so (argument marshalling only).
+
+Every method maps one-to-one onto a C entry point of include/ptp.h with the
+same name minus the `ptp_` prefix.  Host-pointer entry points take and return
+numpy arrays; `_dev` entry points take torch CUDA tensors (device memory and
+the stream come from PyTorch; all arithmetic runs in the library's kernels).
+There is no fallback: if libptp.so is missing or fails to load, importing
+this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libptp.so")
+
+PTP_OK, PTP_EINVAL, PTP_ECUDA, PTP_ENOTCONV, PTP_ENAN, PTP_ESTATE, PTP_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+PTP_FP64, PTP_MIXED = 0, 1
+PTP_PREC_JACOBI, PTP_PREC_GMG = 0, 1
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("precision", ctypes.c_int),
+        ("time_levels", ctypes.c_int), ("coarse_steps", ctypes.c_int), ("vcycles", ctypes.c_int),
+        ("pre_smooth", ctypes.c_int), ("post_smooth", ctypes.c_int), ("omega_t", ctypes.c_double),
+        ("pcg_iters", ctypes.c_int), ("spatial_prec", ctypes.c_int), ("gmg_smooth", ctypes.c_int),
+        ("gmg_omega", ctypes.c_double), ("coarse_tol", ctypes.c_double), ("coarse_max_it", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("outer_iterations", ctypes.c_int), ("converged", ctypes.c_int), ("res0", ctypes.c_double),
+        ("res_final", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+        ("residual_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("time_levels", ctypes.c_int),
+        ("spatial_levels", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PtpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ptp error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2502_21013_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pI, pD = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "ptp_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "ptp_version": (ctypes.c_char_p, []),
+        "ptp_abi_sizes": (None, [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+        "ptp_create": (I, [ctypes.POINTER(P), I]),
+        "ptp_destroy": (None, [P]),
+        "ptp_last_error": (ctypes.c_char_p, [P]),
+        "ptp_set_stream": (I, [P, P]),
+        "ptp_set_mesh": (I, [P, I, P, I, P, P]),
+        "ptp_set_structured": (I, [P, I, I, D, D, D, D]),
+        "ptp_set_materials": (I, [P, P, P, D, D, D, D]),
+        "ptp_set_sources": (I, [P, I, P, P, P]),
+        "ptp_set_time": (I, [P, D, I]),
+        "ptp_setup": (I, [P, ctypes.POINTER(Opts)]),
+        "ptp_sizes": (I, [P, pI, pI, pI, pI]),
+        "ptp_info": (I, [P, ctypes.POINTER(ctypes.c_int64), I]),
+        "ptp_source": (I, [P, P]),
+        "ptp_source_dev": (I, [P, P]),
+        "ptp_residual": (I, [P, P, P, pD]),
+        "ptp_residual_dev": (I, [P, P, P, pD]),
+        "ptp_apply_shifted_dev": (I, [P, I, P, P]),
+        "ptp_apply_shifted_f32_dev": (I, [P, I, P, P]),
+        "ptp_periodic_apply_dev": (I, [P, I, P, P]),
+        "ptp_spatial_solve_dev": (I, [P, I, P, P, D, I, pI]),
+        "ptp_spatial_solve_f32_dev": (I, [P, I, P, P, D, I, pI]),
+        "ptp_periodic_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, I, pD]),
+        "ptp_solve": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
+        "ptp_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    so, ss = ctypes.c_size_t(), ctypes.c_size_t()
+    lib.ptp_abi_sizes(ctypes.byref(so), ctypes.byref(ss))
+    if so.value != ctypes.sizeof(Opts) or ss.value != ctypes.sizeof(Stats):
+        raise ImportError(f"libptp.so struct sizes ({so.value}, {ss.value}) do not match the binding "
+                          f"({ctypes.sizeof(Opts)}, {ctypes.sizeof(Stats)}): rebuild the library")
+    return lib
+
+
+lib = _load()
+
+EXPORTED = [
+    "ptp_default_opts", "ptp_version", "ptp_abi_sizes", "ptp_create", "ptp_destroy", "ptp_last_error", "ptp_set_stream",
+    "ptp_set_mesh", "ptp_set_structured", "ptp_set_materials", "ptp_set_sources", "ptp_set_time",
+    "ptp_setup", "ptp_sizes", "ptp_info", "ptp_source", "ptp_source_dev", "ptp_residual", "ptp_residual_dev",
+    "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_spatial_solve_dev",
+    "ptp_spatial_solve_f32_dev", "ptp_periodic_solve_dev", "ptp_solve", "ptp_solve_dev",
+]
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib.ptp_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _np(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t, dtype_name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("_dev entry points take CUDA tensors")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One solver context (ptp_create ... ptp_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        rc = lib.ptp_create(ctypes.byref(self._h), int(device))
+        if rc != PTP_OK:
+            raise PtpError(rc, "ptp_create failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib.ptp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != PTP_OK and rc not in allow:
+            raise PtpError(rc, lib.ptp_last_error(self._h).decode())
+        return rc
+
+    # ---- problem definition ----
+    def set_stream(self, stream_ptr: int | None):
+        return self._check(lib.ptp_set_stream(self._h, ctypes.c_void_p(stream_ptr or 0)))
+
+    def set_mesh(self, xy, tri, dirichlet):
+        xy, pxy = _np(xy, np.float64)
+        tri, ptri = _np(tri, np.int32)
+        dr, pdr = _np(dirichlet, np.uint8)
+        return self._check(lib.ptp_set_mesh(self._h, xy.shape[0], pxy, tri.shape[0], ptri, pdr))
+
+    def set_structured(self, nx, ny, x0, y0, x1, y1):
+        return self._check(lib.ptp_set_structured(self._h, nx, ny, x0, y0, x1, y1))
+
+    def set_materials(self, sigma_e, nonlinear_e, nu_min, nu_max, s_sat, nu_linear):
+        s, ps = _np(sigma_e, np.float64)
+        nl, pnl = _np(nonlinear_e, np.uint8)
+        return self._check(lib.ptp_set_materials(self._h, ps, pnl, nu_min, nu_max, s_sat, nu_linear))
+
+    def set_sources(self, coil_of_elem, amp, phase):
+        c, pc = _np(coil_of_elem, np.int32)
+        a, pa = _np(amp, np.float64)
+        ph, pph = _np(phase, np.float64)
+        return self._check(lib.ptp_set_sources(self._h, a.shape[0], pc, pa, pph))
+
+    def set_time(self, T, N):
+        return self._check(lib.ptp_set_time(self._h, float(T), int(N)))
+
+    def setup(self, opts: Opts | None = None):
+        self.opts = opts if opts is not None else default_opts()
+        return self._check(lib.ptp_setup(self._h, ctypes.byref(self.opts)))
+
+    def sizes(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(lib.ptp_sizes(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    INFO_KEYS = ("n_free", "N", "n_tri", "n_iron", "iron_incidences", "lin_nnz", "mass_nnz", "op_nnz",
+                 "spatial_levels", "time_levels", "n_coils")
+
+    def info(self):
+        buf = (ctypes.c_int64 * len(self.INFO_KEYS))()
+        m = lib.ptp_info(self._h, buf, len(self.INFO_KEYS))
+        if m < 0:
+            self._check(m)
+        return {k: int(buf[i]) for i, k in enumerate(self.INFO_KEYS[:m])}
+
+    # ---- hot path, host pointers ----
+    def source(self):
+        n, N, _, _ = self.sizes()
+        F = np.empty((n, N))
+        self._check(lib.ptp_source(self._h, F.ctypes.data_as(ctypes.c_void_p)))
+        return F
+
+    def residual(self, U):
+        U, pU = _np(U, np.float64)
+        R = np.empty_like(U)
+        nrm = ctypes.c_double()
+        self._check(lib.ptp_residual(self._h, pU, R.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nrm)))
+        return R, nrm.value
+
+    def solve(self, opts: Opts | None = None, U0=None, U_out=None):
+        n, N, _, _ = self.sizes()
+        o = opts if opts is not None else self.opts
+        U = U_out if U_out is not None else np.empty((n, N))
+        p0 = None
+        if U0 is not None:
+            U0, p0 = _np(U0, np.float64)
+        st = Stats()
+        rc = lib.ptp_solve(self._h, ctypes.byref(o), p0, U.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
+        self._check(rc, allow=(PTP_ENOTCONV,))
+        return U, st, rc
+
+    # ---- hot path, device pointers (torch CUDA tensors) ----
+    def source_dev(self, F):
+        return self._check(lib.ptp_source_dev(self._h, _dev_ptr(F, "float64")))
+
+    def residual_dev(self, U, R=None, want_norm=True):
+        """R = F - A(U) on the device; returns ||R|| (synchronising) or None."""
+        nrm = ctypes.c_double()
+        pR = _dev_ptr(R, "float64") if R is not None else None
+        self._check(lib.ptp_residual_dev(self._h, _dev_ptr(U, "float64"), pR,
+                                         ctypes.byref(nrm) if want_norm else None))
+        return nrm.value if want_norm else None
+
+    def apply_shifted_dev(self, level, X, Y):
+        if X.dtype.is_floating_point and X.element_size() == 4:
+            return self._check(lib.ptp_apply_shifted_f32_dev(self._h, level, _dev_ptr(X, "float32"),
+                                                             _dev_ptr(Y, "float32")))
+        return self._check(lib.ptp_apply_shifted_dev(self._h, level, _dev_ptr(X, "float64"), _dev_ptr(Y, "float64")))
+
+    def periodic_apply_dev(self, level, X, Y):
+        return self._check(lib.ptp_periodic_apply_dev(self._h, level, _dev_ptr(X, "float64"), _dev_ptr(Y, "float64")))
+
+    def spatial_solve_dev(self, level, B, X, tol, max_it):
+        it = ctypes.c_int()
+        if B.element_size() == 4:
+            self._check(lib.ptp_spatial_solve_f32_dev(self._h, level, _dev_ptr(B, "float32"), _dev_ptr(X, "float32"),
+                                                      tol, max_it, ctypes.byref(it)))
+        else:
+            self._check(lib.ptp_spatial_solve_dev(self._h, level, _dev_ptr(B, "float64"), _dev_ptr(X, "float64"),
+                                                  tol, max_it, ctypes.byref(it)))
+        return it.value
+
+    def periodic_solve_dev(self, B, X, cycles, opts: Opts | None = None):
+        rel = ctypes.c_double()
+        o = ctypes.byref(opts) if opts is not None else None
+        self._check(lib.ptp_periodic_solve_dev(self._h, o, _dev_ptr(B, "float64"), _dev_ptr(X, "float64"),
+                                               int(cycles), ctypes.byref(rel)))
+        return rel.value
+
+    def solve_dev(self, U, opts: Opts | None = None, U0=None):
+        o = opts if opts is not None else self.opts
+        st = Stats()
+        p0 = _dev_ptr(U0, "float64") if U0 is not None else None
+        rc = lib.ptp_solve_dev(self._h, ctypes.byref(o), p0, _dev_ptr(U, "float64"), ctypes.byref(st))
+        self._check(rc, allow=(PTP_ENOTCONV,))
+        return st, rc
+
+
+def load_problem(ctx: Context, prob, structured: bool = True):
+    """Pass a problem description (mesh, materials, sources, time) to the
+    library.  `prob` is any object with the attributes of workloads.Problem.
+    When `structured` and the problem carries its grid, the library builds the
+    same uniform mesh itself and enables geometric multigrid."""
+    if structured and getattr(prob, "grid", None) is not None:
+        ctx.set_structured(*prob.grid)
+    else:
+        ctx.set_mesh(prob.xy, prob.tri, prob.dirichlet)
+    ctx.set_materials(prob.sigma_e, prob.nonlinear_e, prob.nu_min, prob.nu_max, prob.s_sat, prob.nu_linear)
+    ctx.set_sources(prob.coil_of_elem, prob.amp, prob.phase)
+    ctx.set_time(prob.T, prob.N)

@@ -1,0 +1,80 @@
+"""CPU checks of the C ABI library (no GPU calls): it builds, loads, exports
+every symbol include/ptp.h declares, its struct layouts match the binding,
+and the host-side validation of the set_* calls reports errors as codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ptp():
+    from paper_2502_21013_gb300 import build
+    build.build()
+    from paper_2502_21013_gb300 import ptp as mod
+    return mod
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ptp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(ptp):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(ptp.lib, name), name
+    assert set(names) == set(ptp.EXPORTED)
+
+
+def test_abi_sizes_and_defaults(ptp):
+    import ctypes
+    so, ss = ctypes.c_size_t(), ctypes.c_size_t()
+    ptp.lib.ptp_abi_sizes(ctypes.byref(so), ctypes.byref(ss))
+    assert so.value == ctypes.sizeof(ptp.Opts) and ss.value == ctypes.sizeof(ptp.Stats)
+    o = ptp.default_opts()
+    assert o.tol == 1e-8 and o.precision == ptp.PTP_MIXED and o.spatial_prec == ptp.PTP_PREC_GMG
+    assert b"sm_103a" in ptp.lib.ptp_version()
+
+
+def test_host_side_validation_without_gpu(ptp):
+    import workloads as W
+    prob = W.unit_square_problem(9, 4)
+    c = ptp.Context(0)
+    with pytest.raises(ptp.PtpError) as e:
+        c.set_materials(prob.sigma_e, prob.nonlinear_e, 1.0, 100.0, 1.0, 100.0)  # before the mesh
+    assert e.value.code == ptp.PTP_EINVAL
+    bad = prob.tri.copy()
+    bad[0, 0] = prob.n_nodes
+    with pytest.raises(ptp.PtpError):
+        c.set_mesh(prob.xy, bad, prob.dirichlet)
+    ptp.load_problem(c, prob)
+    with pytest.raises(ptp.PtpError):
+        c.set_materials(-prob.sigma_e - 1, prob.nonlinear_e, 1.0, 100.0, 1.0, 100.0)
+    with pytest.raises(ptp.PtpError):
+        c.set_materials(prob.sigma_e, prob.nonlinear_e, 1.0, 100.0, 0.0, 100.0)
+    coil = prob.coil_of_elem.copy()
+    coil[0] = 5
+    with pytest.raises(ptp.PtpError):
+        c.set_sources(coil, prob.amp, prob.phase)
+    with pytest.raises(ptp.PtpError):
+        c.set_time(1.0, 0)
+    with pytest.raises(ptp.PtpError) as e:
+        c.residual(np.zeros((49, 4)))
+    assert e.value.code in (ptp.PTP_ESTATE, ptp.PTP_ECUDA)
+    c.close()
+
+
+def test_no_cpu_fallback_in_product_package():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2502_21013_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", text).lower() or f.endswith(".h"), f
