@@ -194,6 +194,22 @@ int ptp_apply_shifted_dev(ptp_ctx* ctx, int level, const double* X, double* Y);
 /* Same in float (the operator values rounded to float), for PTP_MIXED. */
 int ptp_apply_shifted_f32_dev(ptp_ctx* ctx, int level, const float* X, float* Y);
 
+/* R = F - A(U) and ||R|| like ptp_residual_dev, for callers that cannot let
+   the library allocate device memory while they run (a framework whose own
+   pool owns the device, a hard memory budget, or a loop that cannot afford
+   the synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart:
+   this is an interface variant, not part of the method.
+   U, R (may be NULL) and norm (may be NULL) are DEVICE pointers; the norm is
+   written to device memory, nothing is synchronised.  The call allocates
+   nothing: its scratch is a fixed 4 MiB array compiled into the library,
+   held by every GPU that loads it until the process exits.  Limit: the iron
+   element fluxes must fit, 2 * n_iron * N <= 522232 doubles (PTP_EINVAL with
+   a message otherwise; ptp_info gives n_iron).  The first call on a device
+   looks up the array's device address; make that first call before any
+   stream capture begins.  All calls share the array and it keeps the last
+   call's contents, so calls that overlap on the GPU race. */
+int ptp_residual_noalloc_dev(ptp_ctx* ctx, const double* U, double* R, double* norm);
+
 /* Periodic operator of level l: Y^n = (M + tau_l L) X^n - M X^{n-1},
    X^0 = X^{N_l} (eq. iter1 multiplied by tau_l), double. */
 int ptp_periodic_apply_dev(ptp_ctx* ctx, int level, const double* X, double* Y);

@@ -12,6 +12,10 @@ struct ptp_ctx {
     Ctx c;
 };
 
+namespace ptp {
+Ctx* ctx_of(ptp_ctx* h) { return h ? &h->c : nullptr; }
+}  // namespace ptp
+
 namespace {
 
 // Runs f, mapping exceptions to status codes.  Entry points that only

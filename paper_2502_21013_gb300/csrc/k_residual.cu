@@ -140,7 +140,12 @@ k_node_residual(ResidualArgs a) {
         double tot = 0.0;
         for (int w = 0; w < kBlock / 32; ++w) tot += sm[w];
         const double nrm = sqrt(tot);
+        if (a.norm_out) *a.norm_out = nrm;
         Status* st = a.status;
+        if (!st) {
+            *a.counter = 0u;
+            return;
+        }
         st->bscale_used = st->bscale;
         if (isfinite(nrm) && nrm > 0.0) st->bscale = nrm;
         if (a.check) {

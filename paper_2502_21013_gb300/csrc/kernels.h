@@ -35,11 +35,14 @@ struct ResidualArgs {
     double scale;
     double* partials;         // >= grid doubles
     unsigned* counter;
-    Status* status;           // norm written to status->res (and check)
+    Status* status;           // norm written to status->res (and check); may be null
+    double* norm_out;         // if set, the last block also writes ||R|| here
     int* done;                // outer early-exit flag (may be null)
     int check;                // apply the stopping rule in the last block
 };
 int launch_residual(const ResidualArgs& a, cudaStream_t s);  // returns kernels launched
+// residual arguments of a set-up context (scratch pointers point into the context)
+ResidualArgs residual_args(Ctx& c, const double* U, double* R);
 void launch_source(int n, int N, int n_coils, const double* coil_b, const double* coil_s,
                    double* F, cudaStream_t s);
 

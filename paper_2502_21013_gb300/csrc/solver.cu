@@ -311,36 +311,6 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk) {
     for (int k = 0; k < post; ++k) bj_sweep<T>(c, l, x, b, false, sk);
 }
 
-ResidualArgs residual_args(Ctx& c, const double* U, double* R) {
-    ResidualArgs a{};
-    a.n = c.n;
-    a.N = c.N;
-    a.n_iron = c.n_iron;
-    a.n_coils = c.n_coils;
-    a.e_nodes = c.e_nodes.p;
-    a.e_geo = c.e_geo.p;
-    a.inc_ptr = c.inc_ptr.p;
-    a.inc_elem = c.inc_elem.p;
-    a.inc_grad = c.inc_grad.p;
-    a.m_ptr = c.m_ptr.p;
-    a.m_idx = c.m_idx.p;
-    a.m_val = c.m_val.p;
-    a.l_ptr = c.l_ptr.p;
-    a.l_idx = c.l_idx.p;
-    a.l_val = c.l_val.p;
-    a.coil_b = c.coil_b.p;
-    a.coil_s = c.coil_s.p;
-    a.s2sat = c.s_sat * c.s_sat;
-    a.U = U;
-    a.Qx = c.Qx.p;
-    a.Qy = c.Qy.p;
-    a.R = R;
-    a.partials = c.part_d.p;
-    a.counter = c.counter.p;
-    a.status = c.status.p;
-    return a;
-}
-
 template <typename T>
 void outer_step(Ctx& c, Skip sk) {
     ResidualArgs a = residual_args(c, c.U.p, nullptr);
@@ -375,6 +345,36 @@ void alloc_levels(Ctx& c, std::vector<DBuf<T>>& x, std::vector<DBuf<T>>& b) {
 }
 
 }  // namespace
+
+ResidualArgs residual_args(Ctx& c, const double* U, double* R) {
+    ResidualArgs a{};
+    a.n = c.n;
+    a.N = c.N;
+    a.n_iron = c.n_iron;
+    a.n_coils = c.n_coils;
+    a.e_nodes = c.e_nodes.p;
+    a.e_geo = c.e_geo.p;
+    a.inc_ptr = c.inc_ptr.p;
+    a.inc_elem = c.inc_elem.p;
+    a.inc_grad = c.inc_grad.p;
+    a.m_ptr = c.m_ptr.p;
+    a.m_idx = c.m_idx.p;
+    a.m_val = c.m_val.p;
+    a.l_ptr = c.l_ptr.p;
+    a.l_idx = c.l_idx.p;
+    a.l_val = c.l_val.p;
+    a.coil_b = c.coil_b.p;
+    a.coil_s = c.coil_s.p;
+    a.s2sat = c.s_sat * c.s_sat;
+    a.U = U;
+    a.Qx = c.Qx.p;
+    a.Qy = c.Qy.p;
+    a.R = R;
+    a.partials = c.part_d.p;
+    a.counter = c.counter.p;
+    a.status = c.status.p;
+    return a;
+}
 
 void alloc_work(Ctx& c) {
     const size_t big = (size_t)c.n * c.N;

@@ -80,6 +80,7 @@ def _load():
         "ptp_source_dev": (I, [P, P]),
         "ptp_residual": (I, [P, P, P, pD]),
         "ptp_residual_dev": (I, [P, P, P, pD]),
+        "ptp_residual_noalloc_dev": (I, [P, P, P, P]),
         "ptp_apply_shifted_dev": (I, [P, I, P, P]),
         "ptp_apply_shifted_f32_dev": (I, [P, I, P, P]),
         "ptp_periodic_apply_dev": (I, [P, I, P, P]),
@@ -107,6 +108,7 @@ EXPORTED = [
     "ptp_default_opts", "ptp_version", "ptp_abi_sizes", "ptp_create", "ptp_destroy", "ptp_last_error", "ptp_set_stream",
     "ptp_set_mesh", "ptp_set_structured", "ptp_set_materials", "ptp_set_sources", "ptp_set_time",
     "ptp_setup", "ptp_sizes", "ptp_info", "ptp_source", "ptp_source_dev", "ptp_residual", "ptp_residual_dev",
+    "ptp_residual_noalloc_dev",
     "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_spatial_solve_dev",
     "ptp_spatial_solve_f32_dev", "ptp_periodic_solve_dev", "ptp_solve", "ptp_solve_dev",
 ]
