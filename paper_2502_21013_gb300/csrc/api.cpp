@@ -93,10 +93,10 @@ void ptp_default_opts(ptp_opts* o) {
     o->omega_t = 0.5;
     o->pcg_iters = 1;
     o->spatial_prec = PTP_PREC_GMG;
-    o->gmg_smooth = 2;
+    o->gmg_smooth = 1;
     o->gmg_omega = 0.8;
     o->coarse_tol = 1e-6;
-    o->coarse_max_it = 8;
+    o->coarse_max_it = 4;
     o->use_graph = 1;
     o->check_every = 16;
 }

@@ -85,6 +85,13 @@ struct DevCSR {
     DBuf<int> ptr, idx;
     DBuf<double> v1d, v2d;
     DBuf<float> v1f, v2f;
+    // the same matrix as padded ELL (row-major, width ell_w; padding points
+    // at the row itself with value 0) so a row's loads can all be in flight
+    int ell_w = 0;
+    DBuf<int> eidx;
+    DBuf<int4> pk;          // float path: one 16-byte load per entry {idx, v1, v2, 0}
+    DBuf<double> e1d, e2d;
+    DBuf<float> e1f, e2f;
     DBuf<double> d1d, d2d;  // diagonals of v1 / v2 (rows == cols only)
     DBuf<float> d1f, d2f;
 };

@@ -19,6 +19,7 @@
 // Threads are mapped with the time index fastest, so every load of a node's
 // N values is a contiguous, coalesced run.
 #include <cmath>
+#include <cstdlib>
 
 #include "kernels.h"
 
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kBlock)
 k_elem_flux(int n_iron, int N, const int* __restrict__ e_nodes, const double* __restrict__ e_geo,
             const double* __restrict__ U, double* __restrict__ Qx, double* __restrict__ Qy,
             double s2sat, const int* done) {
+    pdl_enter();
     if (skip_now(done)) return;
     const size_t total = (size_t)n_iron * N;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
@@ -78,6 +80,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __global__ void __launch_bounds__(kBlock)
 k_node_residual(ResidualArgs a) {
+    pdl_enter();
     if (skip_now(a.done)) return;
     const int N = a.N;
     const size_t total = (size_t)a.n * N;
@@ -169,6 +172,7 @@ k_node_residual(ResidualArgs a) {
 
 __global__ void k_source(int n, int N, int n_coils, const double* __restrict__ coil_b,
                          const double* __restrict__ coil_s, double* __restrict__ F) {
+    pdl_enter();
     const size_t total = (size_t)n * N;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (size_t)gridDim.x * blockDim.x) {
@@ -190,6 +194,12 @@ int grid_for(size_t total, int per_sm) {
 
 }  // namespace
 
+bool pdl_enabled() {
+    static int on = -1;
+    if (on < 0) on = getenv("PTP_NO_PDL") ? 0 : 1;
+    return on == 1;
+}
+
 int num_sms() {
     static int sms = 0;
     if (sms == 0) {
@@ -207,19 +217,19 @@ int launch_residual(const ResidualArgs& a, cudaStream_t s) {
     int launched = 0;
     if (a.n_iron > 0) {
         const size_t te = (size_t)a.n_iron * a.N;
-        k_elem_flux<<<grid_for(te, 8), kBlock, 0, s>>>(a.n_iron, a.N, a.e_nodes, a.e_geo, a.U, a.Qx, a.Qy,
-                                                      a.s2sat, a.done);
+        launch_k(k_elem_flux, dim3(grid_for(te, 8)), dim3(kBlock), s, a.n_iron, a.N, a.e_nodes, a.e_geo, a.U,
+                 a.Qx, a.Qy, a.s2sat, (const int*)a.done);
         ++launched;
     }
     const size_t tn = (size_t)a.n * a.N;
-    k_node_residual<<<grid_for(tn, 8), kBlock, 0, s>>>(a);
+    launch_k(k_node_residual, dim3(grid_for(tn, 8)), dim3(kBlock), s, a);
     return launched + 1;
 }
 
 void launch_source(int n, int N, int n_coils, const double* coil_b, const double* coil_s,
                    double* F, cudaStream_t s) {
     const size_t t = (size_t)n * N;
-    k_source<<<grid_for(t, 8), kBlock, 0, s>>>(n, N, n_coils, coil_b, coil_s, F);
+    launch_k(k_source, dim3(grid_for(t, 8)), dim3(kBlock), s, n, N, n_coils, coil_b, coil_s, F);
 }
 
 }  // namespace ptp

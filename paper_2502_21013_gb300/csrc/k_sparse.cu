@@ -14,6 +14,8 @@
 // spatial block of the periodic system is M + tau_l L (Remark on parallel
 // solvers, Section 3), with v1 = M and v2 = L = nu_max * stiffness.
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -75,28 +77,68 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[VEC]) {
     }
 }
 
-// acc = (cm v1 + cl v2)[row, :] X[:, col0 .. col0+VEC)
-template <typename T, int VEC>
-__device__ __forceinline__ void row_apply(const Op<T>& op, int N, int row, int col0, const T* X,
-                                          T (&acc)[VEC]) {
+// Padded-ELL row with W entries, fully unrolled: every index and value load
+// is issued, then every X load, so a row costs two memory round trips
+// instead of one per entry.  PERIODIC adds -M X^{n-1} (time shift by one
+// column, X^0 = X^N).
+template <typename T, int VEC, int W, bool PERIODIC>
+__device__ __forceinline__ void row_ell(const Op<T>& op, int N, int row, int col0, const T* X,
+                                        T (&acc)[VEC]) {
+    int j[W];
+    T a[W], m[W];
+    const size_t base = (size_t)row * W;
+    if constexpr (sizeof(T) == 4) {
+        // one 16-byte load per entry: {column, v1, v2, 0}
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const int4 e = __ldg(op.pk + base + k);
+            j[k] = e.x;
+            m[k] = __int_as_float(e.y);
+            a[k] = op.cm * m[k] + op.cl * __int_as_float(e.z);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            j[k] = __ldg(op.eidx + base + k);
+            m[k] = __ldg(op.ev1 + base + k);
+            a[k] = op.cm * m[k];
+        }
+        if (op.ev2) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) a[k] += op.cl * __ldg(op.ev2 + base + k);
+        }
+    }
+    T x[W][VEC];
+    T xp[W];
+    const int cprev = col0 == 0 ? N - 1 : col0 - 1;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const T* xr = X + (size_t)j[k] * N;
+        ldg_vec<T, VEC>(xr + col0, x[k]);
+        if constexpr (PERIODIC) xp[k] = __ldg(xr + cprev);
+    }
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = T(0);
-    const int k0 = __ldg(op.ptr + row), k1 = __ldg(op.ptr + row + 1);
-    for (int k = k0; k < k1; ++k) {
-        const int j = __ldg(op.idx + k);
-        T a = op.cm * __ldg(op.v1 + k);
-        if (op.v2) a += op.cl * __ldg(op.v2 + k);
-        T x[VEC];
-        ldg_vec<T, VEC>(X + (size_t)j * N + col0, x);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] += a * x[v];
+    for (int k = 0; k < W; ++k) {
+        if constexpr (PERIODIC) {
+            T prev = xp[k];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                acc[v] += a[k] * x[k][v] - m[k] * prev;
+                prev = x[k][v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] += a[k] * x[k][v];
+        }
     }
 }
 
-// periodic operator of one row: (cm M + cl L) X^n - M X^{n-1}, X^0 = X^N
-template <typename T, int VEC>
-__device__ __forceinline__ void row_papply(const Op<T>& op, int N, int row, int col0, const T* X,
-                                           T (&acc)[VEC]) {
+// CSR row (any width): the fallback for rows wider than 8 entries
+template <typename T, int VEC, bool PERIODIC>
+__device__ __forceinline__ void row_csr(const Op<T>& op, int N, int row, int col0, const T* X,
+                                        T (&acc)[VEC]) {
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = T(0);
     const int k0 = __ldg(op.ptr + row), k1 = __ldg(op.ptr + row + 1);
@@ -109,13 +151,43 @@ __device__ __forceinline__ void row_papply(const Op<T>& op, int N, int row, int 
         T x[VEC];
         const T* xr = X + (size_t)j * N;
         ldg_vec<T, VEC>(xr + col0, x);
-        T xp = __ldg(xr + cprev);
+        if constexpr (PERIODIC) {
+            T xp = __ldg(xr + cprev);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            acc[v] += a * x[v] - m * xp;
-            xp = x[v];
+            for (int v = 0; v < VEC; ++v) {
+                acc[v] += a * x[v] - m * xp;
+                xp = x[v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] += a * x[v];
         }
     }
+}
+
+template <typename T, int VEC, bool PERIODIC>
+__device__ __forceinline__ void row_dispatch(const Op<T>& op, int N, int row, int col0, const T* X,
+                                             T (&acc)[VEC]) {
+    switch (op.ell_w) {
+        case 2: row_ell<T, VEC, 2, PERIODIC>(op, N, row, col0, X, acc); return;
+        case 4: row_ell<T, VEC, 4, PERIODIC>(op, N, row, col0, X, acc); return;
+        case 8: row_ell<T, VEC, 8, PERIODIC>(op, N, row, col0, X, acc); return;
+        default: row_csr<T, VEC, PERIODIC>(op, N, row, col0, X, acc); return;
+    }
+}
+
+// acc = (cm v1 + cl v2)[row, :] X[:, col0 .. col0+VEC)
+template <typename T, int VEC>
+__device__ __forceinline__ void row_apply(const Op<T>& op, int N, int row, int col0, const T* X,
+                                          T (&acc)[VEC]) {
+    row_dispatch<T, VEC, false>(op, N, row, col0, X, acc);
+}
+
+// periodic operator of one row: (cm M + cl L) X^n - M X^{n-1}, X^0 = X^N
+template <typename T, int VEC>
+__device__ __forceinline__ void row_papply(const Op<T>& op, int N, int row, int col0, const T* X,
+                                           T (&acc)[VEC]) {
+    row_dispatch<T, VEC, true>(op, N, row, col0, X, acc);
 }
 
 // periodic residual of one row: B^n - [(cm M + cl L) X^n - M X^{n-1}]
@@ -137,6 +209,18 @@ __device__ __forceinline__ T diag_of(const Op<T>& op, int row) {
     return d;
 }
 
+template <typename T, int VEC>
+__device__ __forceinline__ void fused_sweep(const Aux<T>& aux, int N, int row, int col0, const T (&y)[VEC]) {
+    if (!aux.Y2) return;
+    T d = aux.cm * __ldg(aux.d1 + row);
+    if (aux.d2) d += aux.cl * __ldg(aux.d2 + row);
+    const T w = aux.omega / d;
+    T o[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) o[v] = w * y[v];
+    st_vec<T, VEC>(aux.Y2 + (size_t)row * N + col0, o);
+}
+
 // grid-stride walk over (row, chunk); NC = N / VEC, rpb = rows per block
 #define PTP_ROW_LOOP(rows, NC, rpb)                                                    \
     const int chunk_ = threadIdx.x % (NC);                                             \
@@ -147,7 +231,9 @@ __device__ __forceinline__ T diag_of(const Op<T>& op, int row) {
 
 template <typename T, int VEC, int MODE>
 __global__ void __launch_bounds__(kMaxBlock)
-k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, T omega, Skip sk) {
+k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, T omega, Skip sk,
+       Aux<T> aux) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC;
     const int rpb = blockDim.x / NC;
@@ -156,6 +242,12 @@ k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, 
             T acc[VEC];
             row_apply<T, VEC>(op, N, row, col0, X, acc);
             st_vec<T, VEC>(Y + (size_t)row * N + col0, acc);
+            if constexpr (MODE == SP_RESTRICT) fused_sweep<T, VEC>(aux, N, row, col0, acc);
+        } else if constexpr (MODE == SP_COPY) {
+            T b[VEC];
+            ldg_vec<T, VEC>(B + (size_t)row * N + col0, b);
+            st_vec<T, VEC>(Y + (size_t)row * N + col0, b);
+            fused_sweep<T, VEC>(aux, N, row, col0, b);
         } else if constexpr (MODE == SP_RESID) {
             T acc[VEC], b[VEC];
             row_apply<T, VEC>(op, N, row, col0, X, acc);
@@ -186,6 +278,7 @@ k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, 
             T r[VEC];
             row_presid<T, VEC>(op, N, row, col0, X, B, r);
             st_vec<T, VEC>(Y + (size_t)row * N + col0, r);
+            fused_sweep<T, VEC>(aux, N, row, col0, r);
         } else if constexpr (MODE == SP_PRESID_RESTRICT) {
             T r[VEC];
             row_presid<T, VEC>(op, N, row, col0, X, B, r);
@@ -320,6 +413,7 @@ __device__ void col_reduce_finish(T (&acc)[NQ][VEC], int N, int NC, int rpb, Col
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kMaxBlock)
 k_pcg_apply_alpha(Op<T> op, int N, const T* __restrict__ p, T* __restrict__ q, ColRed<T> cr, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     T acc[1][VEC];
@@ -340,7 +434,8 @@ k_pcg_apply_alpha(Op<T> op, int N, const T* __restrict__ p, T* __restrict__ q, C
 template <typename T, int VEC, bool JAC>
 __global__ void __launch_bounds__(kMaxBlock)
 k_pcg_update(Op<T> op, int N, T xscale, int assign, T* x, const T* __restrict__ p, T* r,
-             const T* __restrict__ q, T* z, ColRed<T> cr, Skip sk) {
+             const T* __restrict__ q, T* z, ColRed<T> cr, Skip sk, Aux<T> aux) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     constexpr int NQ = JAC ? 2 : 1;
@@ -384,6 +479,7 @@ k_pcg_update(Op<T> op, int N, T xscale, int assign, T* x, const T* __restrict__ 
         } else {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) acc[0][v] += rv[v] * rv[v];
+            fused_sweep<T, VEC>(aux, N, row, col0, rv);
         }
     }
     col_reduce_finish<T, VEC, NQ, JAC ? FIN_UPDATE_JACOBI : FIN_UPDATE_RR>(acc, N, NC, rpb, cr);
@@ -394,6 +490,7 @@ template <typename T, int VEC>
 __global__ void __launch_bounds__(kMaxBlock)
 k_pcg_init_jacobi(Op<T> op, int N, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
                   ColRed<T> cr, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     T acc[2][VEC];
@@ -420,6 +517,7 @@ template <typename T, int VEC>
 __global__ void __launch_bounds__(kMaxBlock)
 k_pcg_dot_rz(int rows, int N, const T* __restrict__ r, const T* __restrict__ z, ColRed<T> cr, int first,
              Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     T acc[2][VEC];
@@ -446,6 +544,7 @@ k_pcg_dot_rz(int rows, int N, const T* __restrict__ r, const T* __restrict__ z, 
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kMaxBlock)
 k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     const T* beta = cr.col + S_BETA * N;
@@ -464,6 +563,7 @@ k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Sk
 template <typename T>
 __global__ void k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Y,
                               Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const size_t total = (size_t)n * N;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
@@ -477,6 +577,7 @@ __global__ void k_dense_apply(int n, int N, const T* __restrict__ A, const T* __
 
 template <typename T>
 __global__ void k_time_prolong_add(int rows, int Nc, const T* __restrict__ xc, T* __restrict__ x, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const size_t total = (size_t)rows * Nc;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
@@ -490,6 +591,7 @@ __global__ void k_time_prolong_add(int rows, int Nc, const T* __restrict__ xc, T
 
 template <typename T>
 __global__ void k_axpy(size_t count, T a, const T* __restrict__ x, T* __restrict__ y, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
         y[g] += a * x[g];
@@ -497,6 +599,7 @@ __global__ void k_axpy(size_t count, T a, const T* __restrict__ x, T* __restrict
 
 template <typename T>
 __global__ void k_fill(size_t count, T v, T* __restrict__ y, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
         y[g] = v;
@@ -504,6 +607,7 @@ __global__ void k_fill(size_t count, T v, T* __restrict__ y, Skip sk) {
 
 template <typename TI, typename TO>
 __global__ void k_cast(size_t count, const TI* __restrict__ x, TO* __restrict__ y, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
         y[g] = (TO)x[g];
@@ -512,6 +616,7 @@ __global__ void k_cast(size_t count, const TI* __restrict__ x, TO* __restrict__ 
 template <typename T>
 __global__ void k_add_to_double(size_t count, const T* __restrict__ d, double* __restrict__ U,
                                 const double* __restrict__ scale, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     const double s = scale ? *scale : 1.0;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
@@ -521,6 +626,7 @@ __global__ void k_add_to_double(size_t count, const T* __restrict__ d, double* _
 template <typename TI, typename TO>
 __global__ void k_cast_scaled(size_t count, const TI* __restrict__ x, TO* __restrict__ y,
                               const double* __restrict__ mul, const double* __restrict__ div) {
+    pdl_enter();
     const double s = (mul ? *mul : 1.0) / (div ? *div : 1.0);
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
         y[g] = (TO)(s * (double)x[g]);
@@ -528,6 +634,7 @@ __global__ void k_cast_scaled(size_t count, const TI* __restrict__ x, TO* __rest
 
 template <typename T>
 __global__ void k_split2(int rows, const T* __restrict__ b, double* __restrict__ bs, double* __restrict__ bd, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
         const double b0 = (double)b[2 * (size_t)i], b1 = (double)b[2 * (size_t)i + 1];
@@ -539,6 +646,7 @@ __global__ void k_split2(int rows, const T* __restrict__ b, double* __restrict__
 template <typename T>
 __global__ void k_combine2(int rows, const double* __restrict__ xs, const double* __restrict__ xd, T* __restrict__ x,
                            Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += gridDim.x * blockDim.x) {
         x[2 * (size_t)i] = (T)(0.5 * (xs[i] + xd[i]));
@@ -547,12 +655,14 @@ __global__ void k_combine2(int rows, const double* __restrict__ xs, const double
 }
 
 __global__ void k_flag(int* flag, int v, Skip sk) {
+    pdl_enter();
     if (skip_now(sk)) return;
     if (threadIdx.x == 0 && blockIdx.x == 0) *flag = v;
 }
 
 template <typename T>
 __global__ void k_norm2(size_t count, const T* __restrict__ x, double* partials, unsigned* counter, double* out) {
+    pdl_enter();
     double s = 0.0;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
         const double v = (double)x[g];
@@ -606,17 +716,38 @@ struct Launch {
     int grid, block;
 };
 
-Launch row_launch(int rows, int N, int vec) {
+// resident blocks per SM of `kernel` at `block` threads (cached per kernel)
+int blocks_per_sm(const void* kernel, int block) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(kernel, block);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess || nb < 1) nb = 1;
+    cache[key] = nb;
+    return nb;
+}
+
+Launch row_launch(int rows, int N, int vec, const void* kernel) {
     const int NC = N / vec;
     if (NC > kMaxBlock) throw Error(PTP_EINVAL, "too many time steps per level for one block (N/VEC > 256)");
     const int rpb = kMaxBlock / NC;
     const int block = NC * rpb;
     long groups = ((long)rows + rpb - 1) / rpb;
-    long cap = (long)num_sms() * std::min(8, 2048 / block);
+    // one full wave: grid-stride loops cover the rest (no partial second wave)
+    long cap = (long)num_sms() * std::min(8, blocks_per_sm(kernel, block));
     Launch l;
     l.grid = (int)std::max(1L, std::min(groups, cap));
     l.block = block;
     return l;
+}
+
+template <typename... KArgs, typename... Args>
+void launch_rows(void (*kernel)(KArgs...), int rows, int N, int vec, cudaStream_t s, Args&&... args) {
+    const Launch l = row_launch(rows, N, vec, (const void*)kernel);
+    launch_k(kernel, dim3(l.grid), dim3(l.block), s, std::forward<Args>(args)...);
 }
 
 int flat_grid(size_t total) {
@@ -639,24 +770,23 @@ size_t reduction_partials(int Nmax) { return (size_t)num_sms() * 9 * 2 * (size_t
 
 template <typename T>
 int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* Y, T omega, Skip sk,
-                cudaStream_t s) {
+                cudaStream_t s, Aux<T> aux) {
     const bool restrict_time = mode == SP_PRESID_RESTRICT;
-    int vec = pick_vec<T>(N, {X, B, Y}, restrict_time);
+    int vec = pick_vec<T>(N, {X, B, Y, aux.Y2}, restrict_time);
     if (sizeof(T) == 8 && vec == 4) vec = 2;
     if (restrict_time && sizeof(T) == 4 && vec == 4 && !aligned(Y, 8)) vec = 2;
-    const Launch l = row_launch(op.rows, N, vec);
 #define PTP_SPMM_CASE(M)                                                                          \
     case M:                                                                                       \
         if constexpr (M == SP_PRESID_RESTRICT) {                                                  \
             if (vec == 4) {                                                                       \
                 if constexpr (sizeof(T) == 4)                                                     \
-                    k_spmm<T, 4, M><<<l.grid, l.block, 0, s>>>(op, N, X, B, Y, omega, sk);        \
+                    launch_rows(k_spmm<T, 4, M>, op.rows, N, vec, s, op, N, X, B, Y, omega, sk, aux);        \
             } else                                                                                \
-                k_spmm<T, 2, M><<<l.grid, l.block, 0, s>>>(op, N, X, B, Y, omega, sk);            \
+                launch_rows(k_spmm<T, 2, M>, op.rows, N, vec, s, op, N, X, B, Y, omega, sk, aux);            \
         } else {                                                                                  \
             PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)                       \
-                                      k_spmm<T, VEC, M><<<l.grid, l.block, 0, s>>>(op, N, X, B, Y, \
-                                                                                 omega, sk));     \
+                                      launch_rows(k_spmm<T, VEC, M>, op.rows, N, vec, s, op, N, X, B, Y, \
+                                                                                 omega, sk, aux)); \
         }                                                                                         \
         break;
     switch (mode) {
@@ -668,6 +798,7 @@ int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* 
         PTP_SPMM_CASE(SP_INTERP_ADD)
         PTP_SPMM_CASE(SP_RESTRICT)
         PTP_SPMM_CASE(SP_PAPPLY)
+        PTP_SPMM_CASE(SP_COPY)
     }
 #undef PTP_SPMM_CASE
     return 1;
@@ -677,9 +808,8 @@ template <typename T>
 int launch_pcg_init_jacobi(const Op<T>& op, int N, T* r, T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {r, z, p});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    const Launch l = row_launch(op.rows, N, vec);
     PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              k_pcg_init_jacobi<T, VEC><<<l.grid, l.block, 0, s>>>(op, N, r, z, p, cr, sk));
+                              launch_rows(k_pcg_init_jacobi<T, VEC>, op.rows, N, vec, s, op, N, r, z, p, cr, sk));
     return 1;
 }
 
@@ -687,9 +817,8 @@ template <typename T>
 int launch_pcg_dot_rz(int rows, int N, const T* r, const T* z, ColRed<T> cr, int first, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {r, z});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    const Launch l = row_launch(rows, N, vec);
     PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              k_pcg_dot_rz<T, VEC><<<l.grid, l.block, 0, s>>>(rows, N, r, z, cr, first, sk));
+                              launch_rows(k_pcg_dot_rz<T, VEC>, rows, N, vec, s, rows, N, r, z, cr, first, sk));
     return 1;
 }
 
@@ -697,26 +826,24 @@ template <typename T>
 int launch_pcg_apply_alpha(const Op<T>& op, int N, const T* p, T* q, ColRed<T> cr, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {p, q});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    const Launch l = row_launch(op.rows, N, vec);
     PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              k_pcg_apply_alpha<T, VEC><<<l.grid, l.block, 0, s>>>(op, N, p, q, cr, sk));
+                              launch_rows(k_pcg_apply_alpha<T, VEC>, op.rows, N, vec, s, op, N, p, q, cr, sk));
     return 1;
 }
 
 template <typename T>
 int launch_pcg_update(const Op<T>& op, int N, T xscale, int assign, T* x, const T* p, T* r, const T* q, T* z,
-                      int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s) {
-    int vec = pick_vec<T>(N, {x, p, r, q, z});
+                      int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s, Aux<T> aux) {
+    int vec = pick_vec<T>(N, {x, p, r, q, z, aux.Y2});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    const Launch l = row_launch(op.rows, N, vec);
     if (jacobi) {
         PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                                  k_pcg_update<T, VEC, true><<<l.grid, l.block, 0, s>>>(op, N, xscale, assign, x, p,
-                                                                                       r, q, z, cr, sk));
+                                  launch_rows(k_pcg_update<T, VEC, true>, op.rows, N, vec, s, op, N, xscale, assign, x, p,
+                                                                                       r, q, z, cr, sk, aux));
     } else {
         PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                                  k_pcg_update<T, VEC, false><<<l.grid, l.block, 0, s>>>(op, N, xscale, assign, x, p,
-                                                                                        r, q, z, cr, sk));
+                                  launch_rows(k_pcg_update<T, VEC, false>, op.rows, N, vec, s, op, N, xscale, assign, x, p,
+                                                                                        r, q, z, cr, sk, aux));
     }
     return 1;
 }
@@ -725,84 +852,83 @@ template <typename T>
 int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {z, p});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    const Launch l = row_launch(rows, N, vec);
     PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              k_pcg_direction<T, VEC><<<l.grid, l.block, 0, s>>>(rows, N, z, p, cr, sk));
+                              launch_rows(k_pcg_direction<T, VEC>, rows, N, vec, s, rows, N, z, p, cr, sk));
     return 1;
 }
 
 template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    k_dense_apply<T><<<flat_grid((size_t)n * N), 256, 0, s>>>(n, N, Ainv, B, Y, sk);
+    launch_k(k_dense_apply<T>, flat_grid((size_t)n * N), 256, s, n, N, Ainv, B, Y, sk);
     return 1;
 }
 
 template <typename T>
 int launch_time_prolong_add(int rows, int Nc, const T* xc, T* x, Skip sk, cudaStream_t s) {
-    k_time_prolong_add<T><<<flat_grid((size_t)rows * Nc), 256, 0, s>>>(rows, Nc, xc, x, sk);
+    launch_k(k_time_prolong_add<T>, flat_grid((size_t)rows * Nc), 256, s, rows, Nc, xc, x, sk);
     return 1;
 }
 
 template <typename T>
 int launch_axpy(size_t count, T a, const T* x, T* y, Skip sk, cudaStream_t s) {
-    k_axpy<T><<<flat_grid(count), 256, 0, s>>>(count, a, x, y, sk);
+    launch_k(k_axpy<T>, flat_grid(count), 256, s, count, a, x, y, sk);
     return 1;
 }
 
 template <typename T>
 int launch_fill(size_t count, T v, T* y, Skip sk, cudaStream_t s) {
-    k_fill<T><<<flat_grid(count), 256, 0, s>>>(count, v, y, sk);
+    launch_k(k_fill<T>, flat_grid(count), 256, s, count, v, y, sk);
     return 1;
 }
 
 template <typename TI, typename TO>
 int launch_cast(size_t count, const TI* x, TO* y, Skip sk, cudaStream_t s) {
-    k_cast<TI, TO><<<flat_grid(count), 256, 0, s>>>(count, x, y, sk);
+    launch_k(k_cast<TI, TO>, flat_grid(count), 256, s, count, x, y, sk);
     return 1;
 }
 
 template <typename T>
 int launch_add_to_double(size_t count, const T* d, double* U, const double* scale, Skip sk, cudaStream_t s) {
-    k_add_to_double<T><<<flat_grid(count), 256, 0, s>>>(count, d, U, scale, sk);
+    launch_k(k_add_to_double<T>, flat_grid(count), 256, s, count, d, U, scale, sk);
     return 1;
 }
 
 template <typename TI, typename TO>
 int launch_cast_scaled(size_t count, const TI* x, TO* y, const double* mul, const double* div, cudaStream_t s) {
-    k_cast_scaled<TI, TO><<<flat_grid(count), 256, 0, s>>>(count, x, y, mul, div);
+    launch_k(k_cast_scaled<TI, TO>, flat_grid(count), 256, s, count, x, y, mul, div);
     return 1;
 }
 
 template <typename T>
 int launch_split2(int rows, const T* b, double* bs, double* bd, Skip sk, cudaStream_t s) {
-    k_split2<T><<<flat_grid(rows), 256, 0, s>>>(rows, b, bs, bd, sk);
+    launch_k(k_split2<T>, flat_grid(rows), 256, s, rows, b, bs, bd, sk);
     return 1;
 }
 
 template <typename T>
 int launch_combine2(int rows, const double* xs, const double* xd, T* x, Skip sk, cudaStream_t s) {
-    k_combine2<T><<<flat_grid(rows), 256, 0, s>>>(rows, xs, xd, x, sk);
+    launch_k(k_combine2<T>, flat_grid(rows), 256, s, rows, xs, xd, x, sk);
     return 1;
 }
 
 int launch_flag(int* flag, int v, Skip sk, cudaStream_t s) {
-    k_flag<<<1, 32, 0, s>>>(flag, v, sk);
+    launch_k(k_flag, 1, 32, s, flag, v, sk);
     return 1;
 }
 
 template <typename T>
 int launch_norm2(size_t count, const T* x, double* partials, unsigned* counter, double* out, cudaStream_t s) {
-    k_norm2<T><<<flat_grid(count), 256, 0, s>>>(count, x, partials, counter, out);
+    launch_k(k_norm2<T>, flat_grid(count), 256, s, count, x, partials, counter, out);
     return 1;
 }
 
 #define PTP_INST(T)                                                                                        \
-    template int launch_spmm<T>(SpMode, const Op<T>&, int, const T*, const T*, T*, T, Skip, cudaStream_t); \
+    template int launch_spmm<T>(SpMode, const Op<T>&, int, const T*, const T*, T*, T, Skip, cudaStream_t, Aux<T>); \
     template int launch_pcg_init_jacobi<T>(const Op<T>&, int, T*, T*, T*, ColRed<T>, Skip, cudaStream_t);  \
     template int launch_pcg_dot_rz<T>(int, int, const T*, const T*, ColRed<T>, int, Skip, cudaStream_t);   \
     template int launch_pcg_apply_alpha<T>(const Op<T>&, int, const T*, T*, ColRed<T>, Skip, cudaStream_t); \
     template int launch_pcg_update<T>(const Op<T>&, int, T, int, T*, const T*, T*, const T*, T*, int, ColRed<T>, \
-                                      Skip, cudaStream_t);                                                 \
+                                      Skip, cudaStream_t, Aux<T>);                                         \
     template int launch_pcg_direction<T>(int, int, const T*, T*, ColRed<T>, Skip, cudaStream_t);          \
     template int launch_dense_apply<T>(int, int, const T*, const T*, T*, Skip, cudaStream_t);              \
     template int launch_time_prolong_add<T>(int, int, const T*, T*, Skip, cudaStream_t);                   \

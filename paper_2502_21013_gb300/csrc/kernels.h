@@ -3,9 +3,44 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "common.h"
 
 namespace ptp {
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel of the library is launched
+// with programmatic stream serialisation, so the next kernel in the stream is
+// scheduled while the current one drains.  Each kernel therefore starts with
+// pdl_wait() (griddepcontrol.wait: block until the preceding grid has
+// completed and its memory is visible) as its FIRST statement, before any
+// early return, so that completion stays transitive along the stream; then
+// pdl_trigger() lets the following grid launch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+bool pdl_enabled();   // false if the environment sets PTP_NO_PDL
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // K1: outer residual R = F - A(U), double (fused source, mass, K(u), norm)
@@ -59,6 +94,11 @@ struct Op {             // cm * v1 + cl * v2 on a CSR pattern
     const T* d1 = nullptr;   // diagonal of v1
     const T* d2 = nullptr;   // diagonal of v2
     T cm = 1, cl = 0;
+    int ell_w = 0;           // > 0: use the padded ELL arrays below
+    const int* eidx = nullptr;
+    const int4* pk = nullptr; // float: packed {idx, v1, v2, 0} per entry
+    const T* ev1 = nullptr;
+    const T* ev2 = nullptr;
 };
 
 template <typename T>
@@ -75,6 +115,16 @@ struct Skip {           // early-exit flags checked by every kernel of a step
     const int* pdone = nullptr;
 };
 
+// Diagonal scaling fused into a producer: Y2 = omega Y / (cm d1 + cl d2) is the
+// first damped-Jacobi sweep (from zero) of the level whose right-hand side Y is.
+template <typename T>
+struct Aux {
+    const T* d1 = nullptr;
+    const T* d2 = nullptr;
+    T cm = 0, cl = 0, omega = 0;
+    T* Y2 = nullptr;          // null: no fused sweep
+};
+
 enum SpMode {
     SP_APPLY = 0,       // Y = A X
     SP_RESID = 1,       // Y = B - A X
@@ -84,11 +134,12 @@ enum SpMode {
     SP_INTERP_ADD = 5,  // Y += Op X   (interpolation, v1 only)
     SP_RESTRICT = 6,    // Y = Op X    (restriction, v1 only)
     SP_PAPPLY = 7,      // Y^n = A X^n - M X^{n-1}  (periodic operator)
+    SP_COPY = 8,        // Y = B (used with a fused sweep)
 };
 
 template <typename T>
 int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* Y, T omega,
-                Skip sk, cudaStream_t s);
+                Skip sk, cudaStream_t s, Aux<T> aux = Aux<T>());
 
 // PCG pieces (batched over N independent columns)
 template <typename T>
@@ -102,7 +153,8 @@ int launch_pcg_apply_alpha(const Op<T>& op, int N, const T* p, T* q, ColRed<T> c
                            cudaStream_t s);  // q = A p, alpha = rho / p.q
 template <typename T>
 int launch_pcg_update(const Op<T>& op, int N, T xscale, int assign, T* x, const T* p, T* r,
-                      const T* q, T* z, int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s);
+                      const T* q, T* z, int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s,
+                      Aux<T> aux = Aux<T>());
 // (assign = 1: x = xscale alpha p instead of x += ..., for a zero start)
 template <typename T>
 int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s);

@@ -5,6 +5,7 @@
 // homogeneous Dirichlet nodes removed, implicit Euler with tau = T/N.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 
 #include "common.h"
@@ -105,6 +106,27 @@ HostCSR matmul(const HostCSR& A, const HostCSR& B) {
     return C;
 }
 
+// Removes entries that are zero up to rounding (|a_ij| <= 1e-13 max_j |a_ij|):
+// the Galerkin product of the nested P1 operators carries structural entries
+// whose exact value is 0, which would widen every row for nothing.
+HostCSR drop_small(const HostCSR& A) {
+    HostCSR B;
+    B.rows = A.rows;
+    B.cols = A.cols;
+    B.ptr.assign(A.rows + 1, 0);
+    for (int i = 0; i < A.rows; ++i) {
+        double m = 0.0;
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) m = std::max(m, std::fabs(A.val[k]));
+        for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k)
+            if (std::fabs(A.val[k]) > 1e-13 * m || A.idx[k] == i) {
+                B.idx.push_back(A.idx[k]);
+                B.val.push_back(A.val[k]);
+            }
+        B.ptr[i + 1] = (int)B.idx.size();
+    }
+    return B;
+}
+
 // Values of A on the pattern `pat` (pat must contain A's pattern).
 std::vector<double> values_on(const HostCSR& pat, const HostCSR& A) {
     std::vector<double> v(pat.nnz(), 0.0);
@@ -196,6 +218,40 @@ void upload_csr(DevCSR& d, const HostCSR& a, const HostCSR* b, bool diag, cudaSt
         bv = values_on(a, *b);
         d.v2d.upload(bv, s);
         d.v2f.upload(to_float(bv), s);
+    }
+    // padded ELL copy for rows of at most 8 entries (wider rows keep CSR)
+    int wmax = 0;
+    for (int i = 0; i < a.rows; ++i) wmax = std::max(wmax, a.ptr[i + 1] - a.ptr[i]);
+    int w = wmax <= 2 ? 2 : wmax <= 4 ? 4 : wmax <= 8 ? 8 : 0;
+    d.ell_w = w;
+    if (w > 0) {
+        std::vector<int> ei((size_t)a.rows * w);
+        std::vector<double> e1((size_t)a.rows * w, 0.0), e2((size_t)a.rows * w, 0.0);
+        for (int i = 0; i < a.rows; ++i) {
+            int k = 0;
+            for (int q = a.ptr[i]; q < a.ptr[i + 1]; ++q, ++k) {
+                ei[(size_t)i * w + k] = a.idx[q];
+                e1[(size_t)i * w + k] = a.val[q];
+                if (b) e2[(size_t)i * w + k] = bv[q];
+            }
+            for (; k < w; ++k) ei[(size_t)i * w + k] = i < a.cols ? i : 0;
+        }
+        d.eidx.upload(ei, s);
+        std::vector<int4> pk((size_t)a.rows * w);
+        for (size_t q = 0; q < pk.size(); ++q) {
+            float f1 = (float)e1[q], f2 = (float)e2[q];
+            int b1, b2;
+            std::memcpy(&b1, &f1, 4);
+            std::memcpy(&b2, &f2, 4);
+            pk[q] = make_int4(ei[q], b1, b2, 0);
+        }
+        d.pk.upload(pk, s);
+        d.e1d.upload(e1, s);
+        d.e1f.upload(to_float(e1), s);
+        if (b) {
+            d.e2d.upload(e2, s);
+            d.e2f.upload(to_float(e2), s);
+        }
     }
     if (diag) {
         std::vector<double> d1(a.rows, 0.0), d2(a.rows, 0.0);
@@ -405,8 +461,8 @@ void build_hierarchy(Ctx& c) {
         cl.n = nc;
         cl.nx = cx;
         cl.ny = cy;
-        cl.hM = matmul(Rt, matmul(f.hM, P));
-        cl.hL = matmul(Rt, matmul(f.hL, P));
+        cl.hM = drop_small(matmul(Rt, matmul(f.hM, P)));
+        cl.hL = drop_small(matmul(Rt, matmul(f.hL, P)));
         f.hP = P;
         c.sl.push_back(std::move(cl));
     }

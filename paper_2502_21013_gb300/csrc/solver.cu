@@ -67,9 +67,14 @@ Op<T> make_op(const DevCSR& d, double cm, double cl) {
     o.idx = d.idx.p;
     if constexpr (sizeof(T) == 8) {
         o.v1 = d.v1d.p; o.v2 = d.v2d.p; o.d1 = d.d1d.p; o.d2 = d.d2d.p;
+        o.ev1 = d.e1d.p; o.ev2 = d.e2d.p;
     } else {
         o.v1 = d.v1f.p; o.v2 = d.v2f.p; o.d1 = d.d1f.p; o.d2 = d.d2f.p;
+        o.ev1 = d.e1f.p; o.ev2 = d.e2f.p;
     }
+    o.ell_w = d.ell_w;
+    o.eidx = d.eidx.p;
+    o.pk = sizeof(T) == 4 ? d.pk.p : nullptr;
     o.cm = (T)cm;
     o.cl = (T)cl;
     return o;
@@ -94,12 +99,34 @@ bool use_gmg(const Ctx& c) {
            (c.sl.size() > 1 || c.ops[0].inv_d.p != nullptr);
 }
 
+// Aux for a fused first damped-Jacobi sweep of spatial level s under op pair opi
+template <typename T>
+Aux<T> sweep_aux(Ctx& c, int s, int opi, T* Y2) {
+    Aux<T> a;
+    const DevCSR& d = c.sl[s].op;
+    if constexpr (sizeof(T) == 8) {
+        a.d1 = d.d1d.p;
+        a.d2 = d.d2d.p;
+    } else {
+        a.d1 = d.d1f.p;
+        a.d2 = d.d2f.p;
+    }
+    a.cm = (T)c.ops[opi].cm;
+    a.cl = (T)c.ops[opi].cl;
+    a.omega = (T)c.opts.gmg_omega;
+    a.Y2 = Y2;
+    return a;
+}
+
 // Spatial geometric-multigrid V-cycle for (cm M + cl L) on N columns:
 // z = V(b).  Damped-Jacobi pre/post sweeps (symmetric), Galerkin coarse
-// operators, dense inverse on the coarsest level.  Returns the buffer that
-// holds z (xa or xb).
+// operators, dense inverse on the coarsest level.  The first pre-smoothing
+// sweep of a level starts from zero, x = w D^-1 b, which is pointwise: it is
+// fused into the kernel that produces b (the restriction for coarser levels;
+// for level 0 the caller's producer of b0 when first_done).  Returns the
+// buffer that holds z (xa or xb).
 template <typename T>
-T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk) {
+T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool first_done) {
     const int S = (int)c.sl.size();
     const double cm = c.ops[opi].cm, cl = c.ops[opi].cl;
     const int nu = std::max(1, c.opts.gmg_smooth);
@@ -117,14 +144,17 @@ T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk) {
     }
     for (int s = 0; s < S - 1; ++s) {
         Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
-        c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
+        const bool have_first = (s == 0) ? first_done : true;
+        if (!have_first) c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
         for (int k = 1; k < nu; ++k) {
             c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
             std::swap(cur[s], oth[s]);
         }
         c.launches += launch_spmm<T>(SP_RESID, A, N, cur[s], b[s], oth[s], T(0), sk, st);
         Op<T> R = make_op<T>(c.sl[s].R, 1.0, 0.0);
-        c.launches += launch_spmm<T>(SP_RESTRICT, R, N, oth[s], nullptr, const_cast<T*>(b[s + 1]), T(0), sk, st);
+        // the next level's first sweep rides on the restriction unless it is the dense level
+        Aux<T> aux = (s + 1 < S - 1) ? sweep_aux<T>(c, s + 1, opi, cur[s + 1]) : Aux<T>();
+        c.launches += launch_spmm<T>(SP_RESTRICT, R, N, oth[s], nullptr, const_cast<T*>(b[s + 1]), T(0), sk, st, aux);
     }
     {
         const int s = S - 1;
@@ -135,7 +165,8 @@ T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk) {
             c.launches += launch_dense_apply<T>(c.sl[s].n, N, inv, b[s], cur[s], sk, st);
         } else {
             Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
-            c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
+            if (!(s == 0 && first_done))
+                c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
             for (int k = 1; k < 4 * nu; ++k) {
                 c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
                 std::swap(cur[s], oth[s]);
@@ -189,7 +220,12 @@ struct PCG {
         q = wbuf<T>(c, 3);
     }
 
-    void init() {
+    // Buffer into which the producer of r may write the fused first
+    // V-cycle sweep (GMG only).
+    T* first_sweep_buffer() const { return wbuf<T>(c, 1); }
+
+    // j0_done: the producer of r already wrote w D^-1 r into first_sweep_buffer()
+    void init(bool j0_done = false) {
         cudaStream_t st = c.stream;
         if (cr.pdone) c.launches += launch_flag(c.flag.p + 1, 0, sk, st);
         if (!gmg) {
@@ -197,7 +233,7 @@ struct PCG {
             p = wbuf<T>(c, 2);
             c.launches += launch_pcg_init_jacobi<T>(A, N, r, z, p, cr, sk2, st);
         } else {
-            T* zr = gmg_vcycle<T>(c, opi, N, r, wbuf<T>(c, 1), wbuf<T>(c, 4), sk2);
+            T* zr = gmg_vcycle<T>(c, opi, N, r, wbuf<T>(c, 1), wbuf<T>(c, 4), sk2, j0_done);
             c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, zr, cr, 1, sk2, st);
             p = zr;
             pa = zr == wbuf<T>(c, 1) ? wbuf<T>(c, 4) : wbuf<T>(c, 1);
@@ -210,11 +246,13 @@ struct PCG {
         c.launches += launch_pcg_apply_alpha<T>(A, N, p, q, cr, sk2, st);
         const int assign = (assign_first && iter == 0) ? 1 : 0;
         ++iter;
+        // the next V-cycle's first sweep rides on the residual update
+        Aux<T> aux = (gmg && !last) ? sweep_aux<T>(c, 0, opi, pa) : Aux<T>();
         c.launches += launch_pcg_update<T>(A, N, xscale, assign, x, p, r, q, gmg ? nullptr : z, gmg ? 0 : 1, cr,
-                                           sk2, st);
+                                           sk2, st, aux);
         if (last) return;
         if (gmg) {
-            z = gmg_vcycle<T>(c, opi, N, r, pa, pb, sk2);
+            z = gmg_vcycle<T>(c, opi, N, r, pa, pb, sk2, true);
             c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, z, cr, 0, sk2, st);
         }
         c.launches += launch_pcg_direction<T>(A.rows, N, z, p, cr, sk2, st);
@@ -227,15 +265,19 @@ void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
     const TimeLevel& t = c.tl[l];
     T* r = wbuf<T>(c, 0);
     const size_t cnt = (size_t)c.n * t.N;
-    if (x_zero) {
-        PTP_CUDA(cudaMemcpyAsync(r, b, cnt * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
-    } else {
-        Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
-        c.launches += launch_spmm<T>(SP_PRESID, A, t.N, x, b, r, T(0), sk, c.stream);
-    }
     // a zero start means x holds stale data: the first PCG update assigns it
     PCG<T> pcg(c, t.op, t.N, r, x, (T)c.opts.omega_t, 0.0, sk, x_zero);
-    pcg.init();
+    Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+    Aux<T> aux = pcg.gmg ? sweep_aux<T>(c, 0, t.op, pcg.first_sweep_buffer()) : Aux<T>();
+    if (x_zero) {
+        if (pcg.gmg)
+            c.launches += launch_spmm<T>(SP_COPY, A, t.N, nullptr, b, r, T(0), sk, c.stream, aux);
+        else
+            PTP_CUDA(cudaMemcpyAsync(r, b, cnt * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+        c.launches += launch_spmm<T>(SP_PRESID, A, t.N, x, b, r, T(0), sk, c.stream, aux);
+    }
+    pcg.init(pcg.gmg);
     const int it = std::max(1, c.opts.pcg_iters);
     for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
 }
