@@ -14,10 +14,13 @@ Also reported on the same line:
   e2e       the same metric through the host-pointer C-ABI call ptp_solve,
             copies of U0 (in) and U (out) from/to pinned host memory inside
             the timed region
-  roofline  the level-0 SpMM (M + tau L) X over N right-hand sides in float
-            (K2), timed alone on the context stream with CUDA events,
+  roofline  K1, the double outer residual (the largest single kernel of a
+            step), timed alone on the context stream with CUDA events:
+            algorithmic flops / duration against the FP64 FMA peak;
+            roofline_k2: the level-0 float SpMM (M + tau L) X over N columns,
             algorithmic bytes / duration against the measured HBM copy peak;
-            roofline_k1: the double outer residual against the FP64 FMA peak
+            traffic: DRAM bytes per launch from the ncu capture in profiles/
+            while the kernel source is unchanged since it, else null
   cpu_baseline  the CPU oracle on a bounded sample (see `sample`)
 
 Multi-GPU: every rank solves its own seeded instance (independent replicas,
@@ -155,6 +158,22 @@ def oracle_sample(prob, iterations_to_tol, repeats=1):
                    f"{iterations_to_tol} outer iterations: setup {setup:.0f} s + {per_iter:.2f} s/iteration"),
         "extrapolated_solve_s": total,
     }
+
+
+def profiled_traffic(profile, source):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/, or None
+    when the kernel source has changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        want = re.search(r"source_sha256\(" + re.escape(source) + r"\): ([0-9a-f]{64})", text).group(1)
+        have = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+        if want != have:
+            return None
+        return float(re.search(r"dram_bytes_per_launch: ([0-9.]+)", text).group(1))
+    except Exception:
+        return None
 
 
 def reduce_scalar(x, op, device, world):
@@ -351,14 +370,20 @@ def run_ours(args):
             "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dofs, "d2h_bytes_per_step": 8 * dofs},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "kernel": "K2 level-0 SpMM (M + tau L) X, float, N columns",
-                         "achieved": k2_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": k2_gbs / hbm_peak,
-                         "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes": k2_bytes,
-                         "duration_us": k2_s * 1e6},
-            "roofline_k1": {"bound": "alu", "kernel": "K1 outer residual, double",
-                            "achieved": k1_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": k1_tflops / FP64_PEAK_TFLOPS, "algorithmic_flops": k1_flops,
-                            "duration_us": k1_s * 1e6},
+            # the largest single kernel of a step (launch list in profiles/) is K1
+            "roofline": {"bound": "alu", "kernel": "K1 outer residual (k_elem_flux + k_node_residual), double",
+                         "achieved": k1_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": k1_tflops / FP64_PEAK_TFLOPS,
+                         "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (FMA loop measured 1.20)",
+                         "traffic": profiled_traffic("k1_residual_square257_N256.md",
+                                                     "paper_2502_21013_gb300/csrc/k_residual.cu"),
+                         "algorithmic_flops": k1_flops, "duration_us": k1_s * 1e6},
+            "roofline_k2": {"bound": "hbm", "kernel": "K2 level-0 SpMM (M + tau L) X, float, N columns",
+                            "achieved": k2_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": k2_gbs / hbm_peak,
+                            "peak_kind": peak_kind,
+                            "traffic": profiled_traffic("k2_spmm_square257_N256_float.md",
+                                                        "paper_2502_21013_gb300/csrc/k_sparse.cu"),
+                            "algorithmic_bytes": k2_bytes, "duration_us": k2_s * 1e6},
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

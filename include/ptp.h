@@ -240,6 +240,34 @@ int ptp_solve(ptp_ctx* ctx, const ptp_opts* opts, const double* U0, double* U,
 int ptp_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* U0,
                   double* U, ptp_stats* stats);
 
+/* ---- adjoint of the period-averaged eddy-current loss --------------- */
+
+/* J(U) = (1/N) sum_n sum_{iron e} sigma_e (d_tau u^n)_e^T M1_e (d_tau u^n)_e,
+   the eddy-current loss averaged over the period (M1_e: unit-conductivity
+   consistent element mass, d_tau u^n = (u^n - u^{n-1})/tau, u^0 = u^N).
+   U is a device [n_free][N] array; J is written to host memory.
+   Synchronises. */
+int ptp_loss_dev(ptp_ctx* ctx, const double* U, double* J);
+
+/* Gradient of J at the solution U of Problem 1 with respect to the coil
+   amplitudes (dJ_damp[n_coils]), the iron law parameters
+   (dJ_dnu[3] = d/d(nu_min, nu_max, s_sat)) and the conductivity of every
+   element (dJ_dsigma[n_tri]).  Implicit-function adjoint: solves the
+   transposed space-time Jacobian system (backward and periodic in time,
+   blocks M/tau + DK(u^n) with DK's element block
+   |T| grad(phi)^T [nu I + 2 nu'(s^2) g g^T] grad(phi)) by the same fixed
+   point and multigrid in time as ptp_solve, to opts->tol, then reduces
+   dJ/dp = dJ/dp|_U - lambda^T d(A - F)/dp.  nu_max enters the iron law only
+   (K_hat does not change the solution); nu_linear is not a parameter.
+   At most 8 coils.  J, dJ_damp and dJ_dnu are host pointers (may be NULL).
+   _dev: U and dJ_dsigma are device pointers; host form: host pointers.
+   Returns PTP_ENOTCONV (gradients still written) if the adjoint fixed point
+   did not reach opts->tol. */
+int ptp_adjoint_gradient_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* U, double* J,
+                             double* dJ_damp, double* dJ_dnu, double* dJ_dsigma, ptp_stats* stats);
+int ptp_adjoint_gradient(ptp_ctx* ctx, const ptp_opts* opts, const double* U, double* J,
+                         double* dJ_damp, double* dJ_dnu, double* dJ_dsigma, ptp_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,11 +51,13 @@ void need_ready(const Ctx& c) {
 
 void invalidate(Ctx& c) {
     c.ready = false;
-    if (c.graph_exec) {
-        cudaGraphExecDestroy(c.graph_exec);
-        c.graph_exec = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (c.graph_exec[k]) {
+            cudaGraphExecDestroy(c.graph_exec[k]);
+            c.graph_exec[k] = nullptr;
+        }
+        c.graph_key[k] = -1;
     }
-    c.graph_key = -1;
 }
 
 // device copies for the host-pointer entry points
@@ -432,6 +434,45 @@ int ptp_solve(ptp_ctx* h, const ptp_opts* opts, const double* U0, double* U, ptp
             PTP_CUDA(cudaMemcpyAsync(U, c.U.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
             PTP_CUDA(cudaStreamSynchronize(c.stream));
         }
+        return rc;
+    });
+}
+
+int ptp_loss_dev(ptp_ctx* h, const double* U, double* J) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        PTP_REQUIRE(U && J, "ptp_loss_dev: null pointer");
+        *J = ptp::loss_dev(c, U);
+        return PTP_OK;
+    });
+}
+
+int ptp_adjoint_gradient_dev(ptp_ctx* h, const ptp_opts* opts, const double* U, double* J, double* dJ_damp,
+                             double* dJ_dnu, double* dJ_dsigma, ptp_stats* stats) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        PTP_REQUIRE(U && dJ_dsigma, "ptp_adjoint_gradient_dev: null U or dJ_dsigma");
+        ptp_opts o = opts ? *opts : c.opts;
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return ptp::adjoint_gradient(c, o, U, J, dJ_damp, dJ_dnu, dJ_dsigma, stats);
+    });
+}
+
+int ptp_adjoint_gradient(ptp_ctx* h, const ptp_opts* opts, const double* U, double* J, double* dJ_damp,
+                         double* dJ_dnu, double* dJ_dsigma, ptp_stats* stats) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        PTP_REQUIRE(U && dJ_dsigma, "ptp_adjoint_gradient: null U or dJ_dsigma");
+        ptp_opts o = opts ? *opts : c.opts;
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        const size_t cnt = (size_t)c.n * c.N;
+        Staging su, sg;
+        double* du = su.get(cnt);
+        double* dg = sg.get((size_t)c.n_tri);
+        PTP_CUDA(cudaMemcpyAsync(du, U, cnt * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        int rc = ptp::adjoint_gradient(c, o, du, J, dJ_damp, dJ_dnu, dg, stats);
+        PTP_CUDA(cudaMemcpyAsync(dJ_dsigma, dg, (size_t)c.n_tri * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        PTP_CUDA(cudaStreamSynchronize(c.stream));
         return rc;
     });
 }

@@ -161,6 +161,7 @@ struct Ctx {
     std::vector<int> free_id;   // node -> free index or -1
     double setup_ms = 0;
     double f_norm = 0;          // ||F||, computed at setup
+    double g_norm = 0;          // ||g|| of the current adjoint right-hand side
 
     // residual (K1) data
     int n_iron = 0;             // iron (nonlinear) elements
@@ -176,6 +177,16 @@ struct Ctx {
     DBuf<double> coil_s;        // n_coils x N: amp sin(2 pi t^n/T + phase)
     std::vector<int> coil_rows; // nodes with a nonzero coil load (host)
     DBuf<double> Qx, Qy;        // iron element flux scratch, n_iron x N each
+    // adjoint data
+    DBuf<double> e_area;        // |T| per iron element
+    DBuf<int> mj_ptr, mj_idx;   // loss mass sum_iron sigma_e M1_e
+    DBuf<double> mj_val;
+    DBuf<double> coil_sin;      // n_coils x N: sin(2 pi t^n / T + phase_c)
+    DBuf<int> all_nodes;        // 3 per element, free index or -1
+    DBuf<double> all_area;
+    DBuf<uint8_t> all_iron;
+    DBuf<double> Jc, Lam, Gadj, Ustar;  // adjoint work (allocated on first use)
+    DBuf<double> adj_scal;
 
     // spatial hierarchy (level 0 = the mesh itself)
     std::vector<SpatialLevel> sl;
@@ -205,9 +216,9 @@ struct Ctx {
     DBuf<int> flag;              // device early-exit flags
     int red_blocks = 0;          // blocks of reduction kernels
 
-    // CUDA graph of one outer step
-    cudaGraphExec_t graph_exec = nullptr;
-    int graph_key = -1;
+    // CUDA graphs of one outer step: [0] forward solve, [1] adjoint solve
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    int graph_key[2] = {-1, -1};
     int64_t launches = 0;        // kernels issued (counting while capturing)
     int64_t launches_per_step = 0;
 
@@ -233,6 +244,9 @@ void periodic_apply(Ctx& c, int level, const T* X, T* Y);
 template <typename T>
 int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check);
 void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres);
-int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st);
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st, bool adjoint = false);
+int adjoint_gradient(Ctx& c, const ptp_opts& o, const double* U, double* J, double* dJ_damp, double* dJ_dnu,
+                     double* dJ_dsigma, ptp_stats* st);
+double loss_dev(Ctx& c, const double* U);
 
 }  // namespace ptp

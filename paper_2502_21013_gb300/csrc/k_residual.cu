@@ -108,8 +108,12 @@ k_node_residual(ResidualArgs a) {
             mv = fma(__ldg(a.m_val + k), __ldg(a.U + j + t) - __ldg(a.U + j + tm), mv);
         }
         double f = 0.0;
-        for (int c = 0; c < a.n_coils; ++c)
-            f += __ldg(a.coil_b + (size_t)c * a.n + i) * __ldg(a.coil_s + (size_t)c * N + t);
+        if (a.Fext) {
+            f = __ldg(a.Fext + g);
+        } else {
+            for (int c = 0; c < a.n_coils; ++c)
+                f += __ldg(a.coil_b + (size_t)c * a.n + i) * __ldg(a.coil_s + (size_t)c * N + t);
+        }
         const double r = f - mv - kv;
         if (a.R) a.R[g] = r;
         if (a.b_d) a.b_d[g] = a.scale * r;
@@ -215,7 +219,7 @@ int residual_grid(size_t total) { return grid_for(total, 8); }
 
 int launch_residual(const ResidualArgs& a, cudaStream_t s) {
     int launched = 0;
-    if (a.n_iron > 0) {
+    if (a.n_iron > 0 && !a.skip_flux) {
         const size_t te = (size_t)a.n_iron * a.N;
         launch_k(k_elem_flux, dim3(grid_for(te, 8)), dim3(kBlock), s, a.n_iron, a.N, a.e_nodes, a.e_geo, a.U,
                  a.Qx, a.Qy, a.s2sat, (const int*)a.done);

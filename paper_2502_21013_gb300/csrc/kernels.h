@@ -60,6 +60,8 @@ struct ResidualArgs {
     const double* l_val;
     const double* coil_b;
     const double* coil_s;
+    const double* Fext;       // if set, the source term is Fext[i*N + n] instead of the coils
+    int skip_flux;            // the iron fluxes Qx, Qy were written by another kernel
     double s2sat;             // s_sat^2
     const double* U;
     double* Qx;
@@ -78,6 +80,36 @@ struct ResidualArgs {
 int launch_residual(const ResidualArgs& a, cudaStream_t s);  // returns kernels launched
 // residual arguments of a set-up context (scratch pointers point into the context)
 ResidualArgs residual_args(Ctx& c, const double* U, double* R);
+
+// ---------------------------------------------------------------------------
+// Adjoint of the period-averaged eddy-current loss (k_adjoint.cu), double
+// ---------------------------------------------------------------------------
+constexpr int kMaxCoils = 8;
+struct AdjointArgs {
+    int n, N, n_iron, n_tri, n_coils;
+    double tau, nu_min, nu_max, s2sat;
+    const int* e_nodes;       // iron elements (as for the residual)
+    const double* e_geo;
+    const double* e_area;     // |T| of the iron elements
+    const int* mj_ptr;        // loss mass: sum over iron of sigma_e M1_e
+    const int* mj_idx;
+    const double* mj_val;
+    const double* coil_b;
+    const double* coil_sin;   // n_coils x N: sin(2 pi t^n / T + phase_c)
+    const int* all_nodes;     // 3 per element, free index or -1
+    const double* all_area;
+    const uint8_t* all_iron;
+    double* Jc;               // 3 x n_iron x N Jacobian coefficients (reversed columns)
+    double* partials;
+    unsigned* counter;
+    double* scalars;          // [0] N*J, [1..kMaxCoils] dJ/damp, [1+kMaxCoils..+3) dJ/dnu
+};
+AdjointArgs adjoint_args(Ctx& c);
+int launch_adj_jacobian(const AdjointArgs& a, const double* U, cudaStream_t s);
+int launch_adj_rhs(const AdjointArgs& a, const double* U, double* Gout, cudaStream_t s);
+int launch_adj_elem_flux(const AdjointArgs& a, const double* Lam, double* Qx, double* Qy, const int* done,
+                         cudaStream_t s);
+int launch_adj_gradients(const AdjointArgs& a, const double* U, const double* Lam, double* dsigma, cudaStream_t s);
 void launch_source(int n, int N, int n_coils, const double* coil_b, const double* coil_s,
                    double* F, cudaStream_t s);
 

@@ -322,6 +322,11 @@ void build_problem(Ctx& c) {
         if (c.nonlinear[e]) iron_of[e] = n_iron++;
     std::vector<int> e_nodes(3 * (size_t)std::max(n_iron, 1), -1);
     std::vector<double> e_geo(6 * (size_t)std::max(n_iron, 1), 0.0);
+    std::vector<double> e_area(std::max(n_iron, 1), 0.0);
+    std::vector<int> all_nodes(3 * (size_t)c.n_tri);
+    std::vector<double> all_area(c.n_tri);
+    std::vector<uint8_t> all_iron(c.n_tri);
+    RowAccum MJa(n);
     std::vector<std::vector<std::pair<int, int>>> inc(n);  // (iron element, local vertex)
     std::vector<Geo> geo(c.n_tri);
     RowAccum Ma(n), Aa(n), Llin(n);
@@ -334,6 +339,10 @@ void build_problem(Ctx& c) {
         Geo G = triangle_geo(&c.xy[2 * (size_t)t[0]], &c.xy[2 * (size_t)t[1]], &c.xy[2 * (size_t)t[2]]);
         geo[e] = G;
         const int ie = iron_of[e];
+        for (int a = 0; a < 3; ++a) all_nodes[3 * (size_t)e + a] = c.free_id[t[a]];
+        all_area[e] = G.area;
+        all_iron[e] = ie >= 0 ? 1 : 0;
+        if (ie >= 0) e_area[ie] = G.area;
         if (ie >= 0) {
             for (int a = 0; a < 3; ++a) e_nodes[3 * (size_t)ie + a] = c.free_id[t[a]];
             double* g = &e_geo[6 * (size_t)ie];
@@ -351,7 +360,11 @@ void build_problem(Ctx& c) {
                 if (j < 0) continue;
                 // consistent mass sigma |T| / 12 (1 + delta_ab); unit stiffness
                 const double k = G.area * (G.g[a][0] * G.g[b][0] + G.g[a][1] * G.g[b][1]);
-                if (c.sigma[e] != 0.0) Ma.add(i, j, c.sigma[e] * G.area * (a == b ? 2.0 : 1.0) / 12.0);
+                if (c.sigma[e] != 0.0) {
+                    const double mv = c.sigma[e] * G.area * (a == b ? 2.0 : 1.0) / 12.0;
+                    Ma.add(i, j, mv);
+                    if (ie >= 0) MJa.add(i, j, mv);
+                }
                 Aa.add(i, j, k);
                 if (ie < 0) Llin.add(i, j, c.nu_linear * k);
             }
@@ -362,6 +375,16 @@ void build_problem(Ctx& c) {
     c.n_iron = n_iron;
     c.e_nodes.upload(e_nodes, s);
     c.e_geo.upload(e_geo, s);
+    c.e_area.upload(e_area, s);
+    c.all_nodes.upload(all_nodes, s);
+    c.all_area.upload(all_area, s);
+    c.all_iron.upload(all_iron, s);
+    {
+        HostCSR MJ = MJa.finish(n, true);
+        c.mj_ptr.upload(MJ.ptr, s);
+        c.mj_idx.upload(MJ.idx, s);
+        c.mj_val.upload(MJ.val, s);
+    }
 
     std::vector<int> ip(n + 1, 0), ie;
     std::vector<double> ig;
@@ -411,13 +434,15 @@ void build_problem(Ctx& c) {
     l0.hL = L;
 
     // coils: loads and time factors amp sin(2 pi t^n / T + phase), t^n = n tau
-    std::vector<double> cs((size_t)std::max(c.n_coils, 1) * c.N, 0.0);
+    std::vector<double> cs((size_t)std::max(c.n_coils, 1) * c.N, 0.0), csin(cs.size(), 0.0);
     for (int k = 0; k < c.n_coils; ++k)
-        for (int j = 0; j < c.N; ++j)
-            cs[(size_t)k * c.N + j] =
-                c.amp[k] * std::sin(2.0 * M_PI * ((j + 1) * tau) / c.T + c.phase[k]);
+        for (int j = 0; j < c.N; ++j) {
+            csin[(size_t)k * c.N + j] = std::sin(2.0 * M_PI * ((j + 1) * tau) / c.T + c.phase[k]);
+            cs[(size_t)k * c.N + j] = c.amp[k] * csin[(size_t)k * c.N + j];
+        }
     c.coil_b.upload(cb, s);
     c.coil_s.upload(cs, s);
+    c.coil_sin.upload(csin, s);
 }
 
 void build_hierarchy(Ctx& c) {

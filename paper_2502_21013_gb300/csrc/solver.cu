@@ -30,7 +30,8 @@ size_t reduction_partials(int Nmax);
 int residual_grid(size_t total);
 
 Ctx::~Ctx() {
-    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    for (auto& g : graph_exec)
+        if (g) cudaGraphExecDestroy(g);
     if (h_status) cudaFreeHost(h_status);
     if (own_stream) cudaStreamDestroy(own_stream);
 }
@@ -353,24 +354,39 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk) {
     for (int k = 0; k < post; ++k) bj_sweep<T>(c, l, x, b, false, sk);
 }
 
+// One outer step of the fixed point (correction form of eq. iter1) on the
+// iterate X: the forward problem (X = U, residual F - A(U)) or the adjoint
+// (X = lambda in reversed time, residual g - (dA/dU)^T lambda).
 template <typename T>
-void outer_step(Ctx& c, Skip sk) {
-    ResidualArgs a = residual_args(c, c.U.p, nullptr);
+void outer_step(Ctx& c, Skip sk, bool adjoint) {
+    double* X = adjoint ? c.Lam.p : c.U.p;
+    ResidualArgs a = residual_args(c, X, nullptr);
     a.scale = c.T / c.N;
     if constexpr (sizeof(T) == 8) a.b_d = mgb<double>(c, 0); else a.b_f = mgb<float>(c, 0);
     a.done = c.flag.p;
     a.check = 1;
+    if (adjoint) {
+        c.launches += launch_adj_elem_flux(adjoint_args(c), X, c.Qx.p, c.Qy.p, c.flag.p, c.stream);
+        a.Fext = c.Gadj.p;
+        a.skip_flux = 1;
+    }
     c.launches += launch_residual(a, c.stream);
     const int cyc = std::max(1, c.opts.vcycles);
     for (int v = 0; v < cyc; ++v) mgt_vcycle<T>(c, 0, v == 0, sk);
     const double* sc = sizeof(T) == 4 ? &c.status.p->bscale_used : nullptr;
-    c.launches += launch_add_to_double<T>((size_t)c.n * c.N, mgx<T>(c, 0), c.U.p, sc, sk, c.stream);
+    c.launches += launch_add_to_double<T>((size_t)c.n * c.N, mgx<T>(c, 0), X, sc, sk, c.stream);
 }
 
-void final_residual(Ctx& c) {
-    ResidualArgs a = residual_args(c, c.U.p, nullptr);
+void final_residual(Ctx& c, bool adjoint) {
+    double* X = adjoint ? c.Lam.p : c.U.p;
+    ResidualArgs a = residual_args(c, X, nullptr);
     a.done = c.flag.p;
     a.check = 1;
+    if (adjoint) {
+        c.launches += launch_adj_elem_flux(adjoint_args(c), X, c.Qx.p, c.Qy.p, c.flag.p, c.stream);
+        a.Fext = c.Gadj.p;
+        a.skip_flux = 1;
+    }
     c.launches += launch_residual(a, c.stream);
 }
 
@@ -564,8 +580,10 @@ void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* r
     PTP_CUDA(cudaStreamSynchronize(st));
 }
 
-int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats) {
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats, bool adjoint) {
     require_coarse(c);
+    double* X = adjoint ? c.Lam.p : c.U.p;
+    const int gi = adjoint ? 1 : 0;
     cudaStream_t st = c.stream;
     const auto t0 = std::chrono::steady_clock::now();
     const size_t cnt = (size_t)c.n * c.N;
@@ -574,11 +592,13 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
                 "precision / preconditioner / hierarchy options differ from ptp_setup");
     c.opts = o;
     const bool mixed = o.precision == PTP_MIXED;
-    if (U0) PTP_CUDA(cudaMemcpyAsync(c.U.p, U0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else PTP_CUDA(cudaMemsetAsync(c.U.p, 0, cnt * sizeof(double), st));
+    if (U0) PTP_CUDA(cudaMemcpyAsync(X, U0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else PTP_CUDA(cudaMemsetAsync(X, 0, cnt * sizeof(double), st));
     Status s0{};
     s0.tol = o.tol;
-    s0.bscale = c.f_norm > 0 ? c.f_norm : 1.0;   // ||F||: the residual norm of the zero start
+    // the residual norm of the zero start: ||F|| (forward) or ||g|| (adjoint)
+    const double r0 = adjoint ? c.g_norm : c.f_norm;
+    s0.bscale = r0 > 0 ? r0 : 1.0;
     s0.bscale_used = s0.bscale;
     c.h_status[0] = s0;
     PTP_CUDA(cudaMemcpyAsync(c.status.p, &c.h_status[0], sizeof(Status), cudaMemcpyHostToDevice, st));
@@ -588,14 +608,14 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
     Skip sk;
     sk.done = c.flag.p;
     auto step = [&]() {
-        if (mixed) outer_step<float>(c, sk); else outer_step<double>(c, sk);
+        if (mixed) outer_step<float>(c, sk, adjoint); else outer_step<double>(c, sk, adjoint);
     };
     const int64_t l0 = c.launches;
     // graph of one outer step, re-captured when the options change
     const int key = (mixed ? 1 : 0) | (o.pcg_iters << 1) | (o.vcycles << 6) | (o.pre_smooth << 10) |
                     (o.post_smooth << 14) | (o.gmg_smooth << 18) | (o.coarse_max_it << 22);
-    if (o.use_graph && (c.graph_exec == nullptr || c.graph_key != key)) {
-        if (c.graph_exec) { cudaGraphExecDestroy(c.graph_exec); c.graph_exec = nullptr; }
+    if (o.use_graph && (c.graph_exec[gi] == nullptr || c.graph_key[gi] != key)) {
+        if (c.graph_exec[gi]) { cudaGraphExecDestroy(c.graph_exec[gi]); c.graph_exec[gi] = nullptr; }
         cudaGraph_t g;
         const int64_t before = c.launches;
         PTP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -606,11 +626,11 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
             throw;
         }
         PTP_CUDA(cudaStreamEndCapture(st, &g));
-        PTP_CUDA(cudaGraphInstantiate(&c.graph_exec, g, 0));
+        PTP_CUDA(cudaGraphInstantiate(&c.graph_exec[gi], g, 0));
         cudaGraphDestroy(g);
         c.launches_per_step = c.launches - before;
         c.launches = before;
-        c.graph_key = key;
+        c.graph_key[gi] = key;
     }
     cudaEvent_t e0, e1;
     PTP_CUDA(cudaEventCreate(&e0));
@@ -627,7 +647,7 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
         const int chunk = std::min(every, o.max_outer - launched);
         for (int k = 0; k < chunk; ++k) {
             if (o.use_graph) {
-                PTP_CUDA(cudaGraphLaunch(c.graph_exec, st));
+                PTP_CUDA(cudaGraphLaunch(c.graph_exec[gi], st));
                 step_launches += c.launches_per_step;
             } else {
                 const int64_t b = c.launches;
@@ -646,7 +666,7 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
         pending = slot;
         slot ^= 1;
     }
-    final_residual(c);
+    final_residual(c, adjoint);
     step_launches += 2;
     PTP_CUDA(cudaEventRecord(e1, st));
     PTP_CUDA(cudaMemcpyAsync(&c.h_status[0], c.status.p, sizeof(Status), cudaMemcpyDeviceToHost, st));
@@ -657,7 +677,7 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
     cudaEventDestroy(e0); cudaEventDestroy(e1);
     cudaEventDestroy(chk[0]); cudaEventDestroy(chk[1]);
     const Status fs = c.h_status[0];
-    if (U) PTP_CUDA(cudaMemcpyAsync(U, c.U.p, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (U) PTP_CUDA(cudaMemcpyAsync(U, X, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     PTP_CUDA(cudaStreamSynchronize(st));
     c.launches = l0 + step_launches;
     const bool conv = fs.done == 1;
@@ -675,6 +695,83 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
     }
     if (fs.done == 2) return PTP_ENAN;
     return conv ? PTP_OK : PTP_ENOTCONV;
+}
+
+AdjointArgs adjoint_args(Ctx& c) {
+    AdjointArgs a{};
+    a.n = c.n;
+    a.N = c.N;
+    a.n_iron = c.n_iron;
+    a.n_tri = c.n_tri;
+    a.n_coils = c.n_coils;
+    a.tau = c.T / c.N;
+    a.nu_min = c.nu_min;
+    a.nu_max = c.nu_max;
+    a.s2sat = c.s_sat * c.s_sat;
+    a.e_nodes = c.e_nodes.p;
+    a.e_geo = c.e_geo.p;
+    a.e_area = c.e_area.p;
+    a.mj_ptr = c.mj_ptr.p;
+    a.mj_idx = c.mj_idx.p;
+    a.mj_val = c.mj_val.p;
+    a.coil_b = c.coil_b.p;
+    a.coil_sin = c.coil_sin.p;
+    a.all_nodes = c.all_nodes.p;
+    a.all_area = c.all_area.p;
+    a.all_iron = c.all_iron.p;
+    a.Jc = c.Jc.p;
+    a.partials = c.part_d.p;
+    a.counter = c.counter.p;
+    a.scalars = c.adj_scal.p;
+    return a;
+}
+
+static void alloc_adjoint(Ctx& c) {
+    const size_t cnt = (size_t)c.n * c.N;
+    if (c.Lam.n != cnt) c.Lam.alloc(cnt);
+    if (c.Gadj.n != cnt) c.Gadj.alloc(cnt);
+    if (c.Ustar.n != cnt) c.Ustar.alloc(cnt);
+    const size_t jc = 3 * (size_t)std::max(c.n_iron, 1) * c.N;
+    if (c.Jc.n != jc) c.Jc.alloc(jc);
+    if (c.adj_scal.n < 16) c.adj_scal.alloc(16);
+}
+
+double loss_dev(Ctx& c, const double* U) {
+    alloc_adjoint(c);
+    AdjointArgs a = adjoint_args(c);
+    c.launches += launch_adj_rhs(a, U, c.Gadj.p, c.stream);
+    double h = 0.0;
+    PTP_CUDA(cudaMemcpyAsync(&h, c.adj_scal.p, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    PTP_CUDA(cudaStreamSynchronize(c.stream));
+    return h / c.N;
+}
+
+int adjoint_gradient(Ctx& c, const ptp_opts& o, const double* U, double* J, double* dJ_damp, double* dJ_dnu,
+                     double* dJ_dsigma, ptp_stats* st) {
+    PTP_REQUIRE(c.n_coils <= kMaxCoils, "the adjoint supports at most 8 coils");
+    cudaStream_t s = c.stream;
+    const size_t cnt = (size_t)c.n * c.N;
+    alloc_adjoint(c);
+    PTP_CUDA(cudaMemcpyAsync(c.Ustar.p, U, cnt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AdjointArgs a = adjoint_args(c);
+    c.launches += launch_adj_jacobian(a, c.Ustar.p, s);
+    c.launches += launch_adj_rhs(a, c.Ustar.p, c.Gadj.p, s);
+    double nJ = 0.0;
+    PTP_CUDA(cudaMemcpyAsync(&nJ, c.adj_scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    c.g_norm = norm_dev(c, c.Gadj.p, cnt);   // synchronises
+    const int rc = solve(c, o, nullptr, nullptr, st, true);
+    if (rc == PTP_ENAN) return rc;
+    c.launches += launch_adj_gradients(a, c.Ustar.p, c.Lam.p, dJ_dsigma, s);
+    double h[1 + kMaxCoils + 3];
+    PTP_CUDA(cudaMemcpyAsync(h, c.adj_scal.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PTP_CUDA(cudaStreamSynchronize(s));
+    PTP_CUDA(cudaGetLastError());
+    if (J) *J = nJ / c.N;
+    if (dJ_damp)
+        for (int k = 0; k < c.n_coils; ++k) dJ_damp[k] = h[1 + k];
+    if (dJ_dnu)
+        for (int k = 0; k < 3; ++k) dJ_dnu[k] = h[1 + kMaxCoils + k];
+    return rc;
 }
 
 template void apply_op<double>(Ctx&, int, int, int, const double*, double*);

@@ -89,6 +89,9 @@ def _load():
         "ptp_periodic_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, I, pD]),
         "ptp_solve": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
         "ptp_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
+        "ptp_loss_dev": (I, [P, P, pD]),
+        "ptp_adjoint_gradient_dev": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
+        "ptp_adjoint_gradient": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -111,6 +114,7 @@ EXPORTED = [
     "ptp_residual_noalloc_dev",
     "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_spatial_solve_dev",
     "ptp_spatial_solve_f32_dev", "ptp_periodic_solve_dev", "ptp_solve", "ptp_solve_dev",
+    "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient",
 ]
 
 
@@ -283,6 +287,32 @@ class Context:
         rc = lib.ptp_solve_dev(self._h, ctypes.byref(o), p0, _dev_ptr(U, "float64"), ctypes.byref(st))
         self._check(rc, allow=(PTP_ENOTCONV,))
         return st, rc
+
+
+def _loss_dev(ctx, U):
+    J = ctypes.c_double()
+    ctx._check(lib.ptp_loss_dev(ctx._h, _dev_ptr(U, "float64"), ctypes.byref(J)))
+    return J.value
+
+
+def _adjoint_gradient_dev(ctx, U, opts=None):
+    """(J, dJ/damp [n_coils], dJ/d(nu_min, nu_max, s_sat) [3], dJ/dsigma [n_tri] (CUDA), stats, rc)."""
+    import torch
+    info = ctx.info()
+    J = ctypes.c_double()
+    damp = (ctypes.c_double * max(1, info["n_coils"]))()
+    dnu = (ctypes.c_double * 3)()
+    dsig = torch.empty(info["n_tri"], dtype=torch.float64, device=U.device)
+    st = Stats()
+    o = opts if opts is not None else ctx.opts
+    rc = lib.ptp_adjoint_gradient_dev(ctx._h, ctypes.byref(o), _dev_ptr(U, "float64"), ctypes.byref(J), damp, dnu,
+                                      _dev_ptr(dsig, "float64"), ctypes.byref(st))
+    ctx._check(rc, allow=(PTP_ENOTCONV,))
+    return J.value, [damp[k] for k in range(info["n_coils"])], [dnu[k] for k in range(3)], dsig, st, rc
+
+
+Context.loss_dev = _loss_dev
+Context.adjoint_gradient_dev = _adjoint_gradient_dev
 
 
 def load_problem(ctx: Context, prob, structured: bool = True):
