@@ -171,9 +171,39 @@ int ptp_sizes(const ptp_ctx* ctx, int* n_free, int* N, int* n_tri,
      4 iron element-node incidences    5 nonzeros of the linear-element
      stiffness      6 nonzeros of the mass (M/tau) rows  7 nonzeros of the
      level-0 spatial operator M + tau L                  8 spatial levels
-     9 time levels  10 coils                                              */
-#define PTP_INFO_COUNT 11
+     9 time levels  10 coils  11 threads per block of the row kernels      */
+#define PTP_INFO_COUNT 12
 int ptp_info(const ptp_ctx* ctx, int64_t* counts, int n);
+
+/* Times the level-0 SpMM of this context with 128, 256 and 512 threads per
+   block (rows per block = threads / (N / vector width)) and keeps the
+   fastest for every row kernel of the context.  *block_threads and
+   *best_us (per launch) may be NULL.  Synchronises. */
+int ptp_autotune(ptp_ctx* ctx, int* block_threads, double* best_us);
+
+/* ---- batched independent instances ----------------------------------- */
+
+/* A batch advances many set-up contexts (uneven meshes and N allowed) with
+   one CUDA-graph launch per fixed-point step: the outer step of every
+   instance is a parallel branch of the graph, so their kernels run
+   concurrently.  The batch does not own the contexts; they must stay alive
+   and set up while the batch is used.  Same device only. */
+typedef struct ptp_batch ptp_batch;
+int  ptp_batch_create(ptp_batch** out, int device);
+void ptp_batch_destroy(ptp_batch* batch);
+const char* ptp_batch_last_error(const ptp_batch* batch);
+int  ptp_batch_add(ptp_batch* batch, ptp_ctx* ctx);
+int  ptp_batch_size(const ptp_batch* batch);
+/* Solves every instance from zero to opts->tol (tolerance, iteration cap and
+   check interval from opts; precision and hierarchy from each context's
+   ptp_setup).  stats: array of ptp_batch_size entries (may be NULL);
+   *n_converged (may be NULL) counts instances that met the stopping rule.
+   Each instance's iterate stays in its context (read with ptp_residual_dev
+   or a later ptp_solve); results are identical to solving the instance
+   alone.  Returns PTP_OK if all converged, else PTP_ENOTCONV or PTP_ENAN. */
+int  ptp_batch_solve(ptp_batch* batch, const ptp_opts* opts, ptp_stats* stats, int* n_converged);
+/* Copies instance i's current iterate (device U, [n_free][N]). */
+int  ptp_batch_result_dev(ptp_batch* batch, int i, double* U);
 
 /* ---- the hot path ---------------------------------------------------- */
 

@@ -27,6 +27,7 @@ int guarded(ptp_ctx* h, F&& f, bool device = true) {
         h->c.err.clear();
         if (device) {
             PTP_CUDA(cudaSetDevice(h->c.device));
+            ptp::set_row_block(h->c.row_block);
             if (!h->c.own_stream) {
                 PTP_CUDA(cudaStreamCreateWithFlags(&h->c.own_stream, cudaStreamNonBlocking));
                 if (!h->c.stream) h->c.stream = h->c.own_stream;
@@ -242,8 +243,11 @@ int ptp_setup(ptp_ctx* h, const ptp_opts* opts) {
         ptp::alloc_work(c);
         {   // ||F|| scales the float right-hand side of the first outer step
             const size_t cnt = (size_t)c.n * c.N;
-            ptp::source_dev(c, c.R.p);
-            c.f_norm = ptp::norm_dev(c, c.R.p, cnt);
+            double* F = nullptr;
+            PTP_CUDA(cudaMallocAsync((void**)&F, cnt * sizeof(double), c.stream));
+            ptp::source_dev(c, F);
+            c.f_norm = ptp::norm_dev(c, F, cnt);
+            PTP_CUDA(cudaFreeAsync(F, c.stream));
         }
         PTP_CUDA(cudaStreamSynchronize(c.stream));
         c.ready = true;
@@ -263,13 +267,22 @@ int ptp_sizes(const ptp_ctx* h, int* n_free, int* N, int* n_tri, int* time_level
     return PTP_OK;
 }
 
+int ptp_autotune(ptp_ctx* h, int* block_threads, double* best_us) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        const int b = ptp::autotune(c, best_us);
+        if (block_threads) *block_threads = b;
+        return PTP_OK;
+    });
+}
+
 int ptp_info(const ptp_ctx* h, int64_t* counts, int n) {
     if (!h || !counts || n < 0) return PTP_EINVAL;
     const Ctx& c = h->c;
     if (!c.ready) return PTP_ESTATE;
     const int64_t v[PTP_INFO_COUNT] = {c.n, c.N, c.n_tri, c.n_iron, (int64_t)c.inc_elem.n, (int64_t)c.l_idx.n,
                                        (int64_t)c.m_idx.n, c.sl[0].op.nnz, (int64_t)c.sl.size(),
-                                       (int64_t)c.tl.size(), c.n_coils};
+                                       (int64_t)c.tl.size(), c.n_coils, c.row_block};
     const int m = n < PTP_INFO_COUNT ? n : PTP_INFO_COUNT;
     for (int k = 0; k < m; ++k) counts[k] = v[k];
     return m;
@@ -290,6 +303,7 @@ int ptp_source(ptp_ctx* h, double* F) {
         need_ready(c);
         PTP_REQUIRE(F, "ptp_source: null output");
         const size_t cnt = (size_t)c.n * c.N;
+        ptp::ensure_staging(c);
         ptp::source_dev(c, c.R.p);
         PTP_CUDA(cudaMemcpyAsync(F, c.R.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
         PTP_CUDA(cudaStreamSynchronize(c.stream));
@@ -322,6 +336,7 @@ int ptp_residual(ptp_ctx* h, const double* U, double* R, double* norm) {
         need_ready(c);
         PTP_REQUIRE(U, "ptp_residual: null input");
         const size_t cnt = (size_t)c.n * c.N;
+        ptp::ensure_staging(c);
         PTP_CUDA(cudaMemcpyAsync(c.Ud.p, U, cnt * sizeof(double), cudaMemcpyHostToDevice, c.stream));
         residual_impl(c, c.Ud.p, R ? c.R.p : nullptr, norm);
         if (R) PTP_CUDA(cudaMemcpyAsync(R, c.R.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.stream));

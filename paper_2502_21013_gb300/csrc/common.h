@@ -218,9 +218,10 @@ struct Ctx {
 
     // CUDA graphs of one outer step: [0] forward solve, [1] adjoint solve
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
-    int graph_key[2] = {-1, -1};
+    int64_t graph_key[2] = {-1, -1};
     int64_t launches = 0;        // kernels issued (counting while capturing)
     int64_t launches_per_step = 0;
+    int row_block = 256;         // threads per block of the row kernels (autotuned)
 
     ~Ctx();
 };
@@ -233,6 +234,8 @@ void upload_csr(DevCSR& d, const HostCSR& a, const HostCSR* b, bool diag, cudaSt
 
 // ---- solver.cu ----
 void alloc_work(Ctx& c);
+void ensure_work(Ctx& c, bool doubles);   // full-size work vectors of one precision
+void ensure_staging(Ctx& c);              // R and Ud at [n][N]
 void residual_dev(Ctx& c, const double* U, double* R, double* b_out_d, float* b_out_f,
                   double scale, bool outer_check);
 void source_dev(Ctx& c, double* F);
@@ -248,5 +251,11 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st,
 int adjoint_gradient(Ctx& c, const ptp_opts& o, const double* U, double* J, double* dJ_damp, double* dJ_dnu,
                      double* dJ_dsigma, ptp_stats* st);
 double loss_dev(Ctx& c, const double* U);
+void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint);
+int64_t step_key(const Ctx& c, const ptp_opts& o);
+int64_t enqueue_step(Ctx& c, bool adjoint);
+int solve_end(Ctx& c, ptp_stats* stats, bool adjoint, int64_t step_launches, double solve_ms, float dev_ms);
+int autotune(Ctx& c, double* best_us);     // picks c.row_block by timing the level-0 SpMM
+void set_row_block(int threads);           // row-kernel block size for launches from this thread
 
 }  // namespace ptp

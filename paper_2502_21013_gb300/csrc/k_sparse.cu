@@ -23,7 +23,10 @@ namespace ptp {
 
 namespace {
 
-constexpr int kMaxBlock = 256;
+constexpr int kMaxBlock = 512;
+// threads per block of the row kernels for launches issued by this host thread
+// (each context sets its autotuned value before launching)
+thread_local int g_row_block = 256;
 
 __device__ __forceinline__ bool skip_now(const Skip& s) {
     return (s.done && *(volatile const int*)s.done) || (s.pdone && *(volatile const int*)s.pdone);
@@ -732,8 +735,9 @@ int blocks_per_sm(const void* kernel, int block) {
 
 Launch row_launch(int rows, int N, int vec, const void* kernel) {
     const int NC = N / vec;
-    if (NC > kMaxBlock) throw Error(PTP_EINVAL, "too many time steps per level for one block (N/VEC > 256)");
-    const int rpb = kMaxBlock / NC;
+    if (NC > kMaxBlock) throw Error(PTP_EINVAL, "too many time steps per level for one block (N/VEC > 512)");
+    const int target = std::max(g_row_block, NC);
+    const int rpb = std::max(1, target / NC);
     const int block = NC * rpb;
     long groups = ((long)rows + rpb - 1) / rpb;
     // one full wave: grid-stride loops cover the rest (no partial second wave)
@@ -757,6 +761,10 @@ int flat_grid(size_t total) {
 }
 
 }  // namespace
+
+void set_row_block(int threads) {
+    g_row_block = std::min(kMaxBlock, std::max(64, threads));
+}
 
 // max partial-buffer entries a reduction launch can need for N columns
 size_t reduction_partials(int Nmax) { return (size_t)num_sms() * 9 * 2 * (size_t)Nmax; }

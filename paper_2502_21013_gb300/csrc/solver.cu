@@ -434,21 +434,32 @@ ResidualArgs residual_args(Ctx& c, const double* U, double* R) {
     return a;
 }
 
+// Allocates what a solve in the set-up precision needs.  In mixed mode the
+// double work vectors only serve the one- or two-column coarsest time level;
+// double entry points called on a mixed context grow them on demand
+// (ensure_double_work).
 void alloc_work(Ctx& c) {
     const size_t big = (size_t)c.n * c.N;
     const bool mixed = c.opts.precision == PTP_MIXED;
+    const size_t dcols = mixed ? 2 : (size_t)std::max(c.N, 2);
     for (int k = 0; k < 6; ++k) {
-        c.w_d[k].alloc(std::max(big, (size_t)c.n * 2));
-        c.w_f[k].alloc(big);
+        c.w_d[k].alloc((size_t)c.n * dcols);
+        if (mixed) c.w_f[k].alloc(big); else c.w_f[k].release();
     }
     c.U.alloc(big);
-    c.R.alloc(big);
-    c.Ud.alloc(std::max(big, (size_t)c.n * 2));
+    c.R.release();
+    c.Ud.alloc((size_t)c.n * 2);
     c.Qx.alloc((size_t)std::max(c.n_iron, 1) * c.N);
     c.Qy.alloc((size_t)std::max(c.n_iron, 1) * c.N);
-    alloc_levels<double>(c, c.mg_xd, c.mg_bd);
-    if (mixed) alloc_levels<float>(c, c.mg_xf, c.mg_bf);
-    else { c.mg_xf.clear(); c.mg_bf.clear(); }
+    if (mixed) {
+        alloc_levels<float>(c, c.mg_xf, c.mg_bf);
+        c.mg_xd.clear();
+        c.mg_bd.clear();
+    } else {
+        alloc_levels<double>(c, c.mg_xd, c.mg_bd);
+        c.mg_xf.clear();
+        c.mg_bf.clear();
+    }
     const size_t S = c.sl.size();
     c.g_xd.clear(); c.g_bd.clear(); c.g_rd.clear();
     c.g_xf.clear(); c.g_bf.clear(); c.g_rf.clear();
@@ -456,8 +467,9 @@ void alloc_work(Ctx& c) {
     c.g_xf.resize(S); c.g_bf.resize(S); c.g_rf.resize(S);
     for (size_t s = 1; s < S; ++s) {
         const size_t m = (size_t)c.sl[s].n * c.N;
-        c.g_xd[s].alloc(m); c.g_bd[s].alloc(m); c.g_rd[s].alloc(m);
-        c.g_xf[s].alloc(m); c.g_bf[s].alloc(m); c.g_rf[s].alloc(m);
+        const size_t md = (size_t)c.sl[s].n * dcols;
+        c.g_xd[s].alloc(md); c.g_bd[s].alloc(md); c.g_rd[s].alloc(md);
+        if (mixed) { c.g_xf[s].alloc(m); c.g_bf[s].alloc(m); c.g_rf[s].alloc(m); }
     }
     const size_t colN = 8 * (size_t)std::max(c.N, 2);
     c.col_d.alloc(colN);
@@ -465,13 +477,39 @@ void alloc_work(Ctx& c) {
     c.col_f.alloc(colN);
     const size_t parts = std::max(reduction_partials(std::max(c.N, 2)), (size_t)num_sms() * 64);
     c.part_d.alloc(parts);
-    c.part_f.alloc(parts);
+    c.part_f.alloc(mixed ? parts : 0);
     c.counter.alloc(256);
     PTP_CUDA(cudaMemsetAsync(c.counter.p, 0, 256 * sizeof(unsigned), c.stream));
     c.status.alloc(1);
     c.flag.alloc(4);
     PTP_CUDA(cudaMemsetAsync(c.flag.p, 0, 4 * sizeof(int), c.stream));
     if (!c.h_status) PTP_CUDA(cudaHostAlloc((void**)&c.h_status, 2 * sizeof(Status), cudaHostAllocDefault));
+}
+
+template <typename T>
+static void grow(DBuf<T>& b, size_t n) {
+    if (b.n < n) b.alloc(n);
+}
+
+// full-size work vectors of precision T (entry points that run in the other
+// precision than the set-up one, and host staging of [n][N] blocks)
+void ensure_work(Ctx& c, bool doubles) {
+    const size_t big = (size_t)c.n * c.N;
+    for (int k = 0; k < 6; ++k) {
+        if (doubles) grow(c.w_d[k], big); else grow(c.w_f[k], big);
+    }
+    for (size_t s = 1; s < c.sl.size(); ++s) {
+        const size_t m = (size_t)c.sl[s].n * c.N;
+        if (doubles) { grow(c.g_xd[s], m); grow(c.g_bd[s], m); grow(c.g_rd[s], m); }
+        else { grow(c.g_xf[s], m); grow(c.g_bf[s], m); grow(c.g_rf[s], m); }
+    }
+    if (!doubles) grow(c.part_f, c.part_d.n);
+}
+
+void ensure_staging(Ctx& c) {
+    const size_t big = (size_t)c.n * c.N;
+    grow(c.R, big);
+    grow(c.Ud, std::max(big, (size_t)c.n * 2));
 }
 
 void residual_dev(Ctx& c, const double* U, double* R, double* b_out_d, float* b_out_f, double scale,
@@ -513,6 +551,7 @@ void periodic_apply(Ctx& c, int level, const T* X, T* Y) {
 
 template <typename T>
 int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check) {
+    ensure_work(c, sizeof(T) == 8);
     cudaStream_t st = c.stream;
     const size_t cnt = (size_t)c.n * N;
     T* r = wbuf<T>(c, 0);
@@ -542,6 +581,7 @@ static void require_coarse(const Ctx& c) {
 
 void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres) {
     require_coarse(c);
+    ensure_staging(c);
     cudaStream_t st = c.stream;
     const size_t cnt = (size_t)c.n * c.N;
     const bool mixed = c.opts.precision == PTP_MIXED;
@@ -580,19 +620,70 @@ void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* r
     PTP_CUDA(cudaStreamSynchronize(st));
 }
 
-int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats, bool adjoint) {
-    require_coarse(c);
-    double* X = adjoint ? c.Lam.p : c.U.p;
-    const int gi = adjoint ? 1 : 0;
+// ---- pieces of a fixed-point solve (shared with the batched solve) ----
+
+// identifies the captured outer step: everything that changes its launches
+int64_t step_key(const Ctx& c, const ptp_opts& o) {
+    int64_t k = o.precision == PTP_MIXED ? 1 : 0;
+    k = k * 64 + o.pcg_iters;
+    k = k * 64 + o.vcycles;
+    k = k * 16 + o.pre_smooth;
+    k = k * 16 + o.post_smooth;
+    k = k * 16 + o.gmg_smooth;
+    k = k * 256 + o.coarse_max_it;
+    k = k * 1024 + c.row_block;
+    return k;
+}
+
+int autotune(Ctx& c, double* best_us) {
+    const int cands[3] = {128, 256, 512};
+    const bool mixed = c.opts.precision == PTP_MIXED;
     cudaStream_t st = c.stream;
-    const auto t0 = std::chrono::steady_clock::now();
     const size_t cnt = (size_t)c.n * c.N;
+    if (mixed) PTP_CUDA(cudaMemsetAsync(c.w_f[0].p, 0, cnt * sizeof(float), st));
+    else PTP_CUDA(cudaMemsetAsync(c.w_d[0].p, 0, cnt * sizeof(double), st));
+    cudaEvent_t a, b;
+    PTP_CUDA(cudaEventCreate(&a));
+    PTP_CUDA(cudaEventCreate(&b));
+    double best = 1e300;
+    int bestb = c.row_block;
+    for (int cb : cands) {
+        set_row_block(cb);
+        auto run = [&]() {
+            if (mixed) apply_op<float>(c, 0, c.tl[0].op, c.N, c.w_f[0].p, c.w_f[1].p);
+            else apply_op<double>(c, 0, c.tl[0].op, c.N, c.w_d[0].p, c.w_d[1].p);
+        };
+        for (int r = 0; r < 3; ++r) run();
+        PTP_CUDA(cudaEventRecord(a, st));
+        for (int r = 0; r < 10; ++r) run();
+        PTP_CUDA(cudaEventRecord(b, st));
+        PTP_CUDA(cudaEventSynchronize(b));
+        float ms = 0;
+        PTP_CUDA(cudaEventElapsedTime(&ms, a, b));
+        const double us = ms * 100.0;  // per launch
+        if (us < best) {
+            best = us;
+            bestb = cb;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c.row_block = bestb;
+    set_row_block(bestb);
+    if (best_us) *best_us = best;
+    return bestb;
+}
+
+void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint) {
+    require_coarse(c);
     PTP_REQUIRE(o.precision == c.opts.precision && o.spatial_prec == c.opts.spatial_prec &&
                     o.time_levels == c.opts.time_levels && o.coarse_steps == c.opts.coarse_steps,
                 "precision / preconditioner / hierarchy options differ from ptp_setup");
     c.opts = o;
-    const bool mixed = o.precision == PTP_MIXED;
-    if (U0) PTP_CUDA(cudaMemcpyAsync(X, U0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    cudaStream_t st = c.stream;
+    double* X = adjoint ? c.Lam.p : c.U.p;
+    const size_t cnt = (size_t)c.n * c.N;
+    if (X0) PTP_CUDA(cudaMemcpyAsync(X, X0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     else PTP_CUDA(cudaMemsetAsync(X, 0, cnt * sizeof(double), st));
     Status s0{};
     s0.tol = o.tol;
@@ -604,23 +695,64 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
     PTP_CUDA(cudaMemcpyAsync(c.status.p, &c.h_status[0], sizeof(Status), cudaMemcpyHostToDevice, st));
     PTP_CUDA(cudaMemsetAsync(c.flag.p, 0, 4 * sizeof(int), st));
     PTP_CUDA(cudaStreamSynchronize(st));  // h_status[0] is reused below
+}
 
+// Enqueues one outer step on c.stream (also while a capture is active);
+// returns the kernels it launched.
+int64_t enqueue_step(Ctx& c, bool adjoint) {
     Skip sk;
     sk.done = c.flag.p;
-    auto step = [&]() {
-        if (mixed) outer_step<float>(c, sk, adjoint); else outer_step<double>(c, sk, adjoint);
-    };
-    const int64_t l0 = c.launches;
+    const int64_t b = c.launches;
+    if (c.opts.precision == PTP_MIXED) outer_step<float>(c, sk, adjoint);
+    else outer_step<double>(c, sk, adjoint);
+    const int64_t k = c.launches - b;
+    c.launches = b;
+    return k;
+}
+
+// Final residual of the returned iterate, status read-back and statistics.
+int solve_end(Ctx& c, ptp_stats* stats, bool adjoint, int64_t step_launches, double solve_ms, float dev_ms) {
+    cudaStream_t st = c.stream;
+    final_residual(c, adjoint);
+    step_launches += 2;
+    PTP_CUDA(cudaMemcpyAsync(&c.h_status[0], c.status.p, sizeof(Status), cudaMemcpyDeviceToHost, st));
+    PTP_CUDA(cudaStreamSynchronize(st));
+    PTP_CUDA(cudaGetLastError());
+    const Status fs = c.h_status[0];
+    c.launches += step_launches;
+    const bool conv = fs.done == 1;
+    if (stats) {
+        stats->outer_iterations = fs.iteration > 0 ? fs.iteration - 1 : 0;
+        stats->converged = conv ? 1 : 0;
+        stats->res0 = fs.res0;
+        stats->res_final = fs.res;
+        stats->setup_ms = c.setup_ms;
+        stats->solve_ms = solve_ms;
+        stats->residual_ms = dev_ms;
+        stats->kernel_launches = step_launches;
+        stats->time_levels = (int)c.tl.size();
+        stats->spatial_levels = (int)c.sl.size();
+    }
+    if (fs.done == 2) return PTP_ENAN;
+    return conv ? PTP_OK : PTP_ENOTCONV;
+}
+
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats, bool adjoint) {
+    const auto t0 = std::chrono::steady_clock::now();
+    solve_begin(c, o, U0, adjoint);
+    double* X = adjoint ? c.Lam.p : c.U.p;
+    const int gi = adjoint ? 1 : 0;
+    cudaStream_t st = c.stream;
+    const size_t cnt = (size_t)c.n * c.N;
+    const bool mixed = o.precision == PTP_MIXED;
     // graph of one outer step, re-captured when the options change
-    const int key = (mixed ? 1 : 0) | (o.pcg_iters << 1) | (o.vcycles << 6) | (o.pre_smooth << 10) |
-                    (o.post_smooth << 14) | (o.gmg_smooth << 18) | (o.coarse_max_it << 22);
+    const int64_t key = step_key(c, o);
     if (o.use_graph && (c.graph_exec[gi] == nullptr || c.graph_key[gi] != key)) {
         if (c.graph_exec[gi]) { cudaGraphExecDestroy(c.graph_exec[gi]); c.graph_exec[gi] = nullptr; }
         cudaGraph_t g;
-        const int64_t before = c.launches;
         PTP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
-            step();
+            c.launches_per_step = enqueue_step(c, adjoint);
         } catch (...) {
             cudaStreamEndCapture(st, &g);
             throw;
@@ -628,8 +760,6 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
         PTP_CUDA(cudaStreamEndCapture(st, &g));
         PTP_CUDA(cudaGraphInstantiate(&c.graph_exec[gi], g, 0));
         cudaGraphDestroy(g);
-        c.launches_per_step = c.launches - before;
-        c.launches = before;
         c.graph_key[gi] = key;
     }
     cudaEvent_t e0, e1;
@@ -650,10 +780,7 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
                 PTP_CUDA(cudaGraphLaunch(c.graph_exec[gi], st));
                 step_launches += c.launches_per_step;
             } else {
-                const int64_t b = c.launches;
-                step();
-                step_launches += c.launches - b;
-                c.launches = b;
+                step_launches += enqueue_step(c, adjoint);
             }
         }
         launched += chunk;
@@ -666,35 +793,19 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
         pending = slot;
         slot ^= 1;
     }
-    final_residual(c, adjoint);
-    step_launches += 2;
     PTP_CUDA(cudaEventRecord(e1, st));
-    PTP_CUDA(cudaMemcpyAsync(&c.h_status[0], c.status.p, sizeof(Status), cudaMemcpyDeviceToHost, st));
     PTP_CUDA(cudaStreamSynchronize(st));
-    PTP_CUDA(cudaGetLastError());
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0); cudaEventDestroy(e1);
     cudaEventDestroy(chk[0]); cudaEventDestroy(chk[1]);
-    const Status fs = c.h_status[0];
-    if (U) PTP_CUDA(cudaMemcpyAsync(U, X, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    PTP_CUDA(cudaStreamSynchronize(st));
-    c.launches = l0 + step_launches;
-    const bool conv = fs.done == 1;
-    if (stats) {
-        stats->outer_iterations = fs.iteration > 0 ? fs.iteration - 1 : 0;
-        stats->converged = conv ? 1 : 0;
-        stats->res0 = fs.res0;
-        stats->res_final = fs.res;
-        stats->setup_ms = c.setup_ms;
-        stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        stats->residual_ms = ms;  // device time of the whole iteration
-        stats->kernel_launches = step_launches;
-        stats->time_levels = (int)c.tl.size();
-        stats->spatial_levels = (int)c.sl.size();
+    const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int rc = solve_end(c, stats, adjoint, step_launches, wall, ms);
+    if (U) {
+        PTP_CUDA(cudaMemcpyAsync(U, X, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        PTP_CUDA(cudaStreamSynchronize(st));
     }
-    if (fs.done == 2) return PTP_ENAN;
-    return conv ? PTP_OK : PTP_ENOTCONV;
+    return rc;
 }
 
 AdjointArgs adjoint_args(Ctx& c) {

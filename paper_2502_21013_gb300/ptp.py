@@ -90,6 +90,14 @@ def _load():
         "ptp_solve": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
         "ptp_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
         "ptp_loss_dev": (I, [P, P, pD]),
+        "ptp_autotune": (I, [P, pI, pD]),
+        "ptp_batch_create": (I, [ctypes.POINTER(P), I]),
+        "ptp_batch_destroy": (None, [P]),
+        "ptp_batch_last_error": (ctypes.c_char_p, [P]),
+        "ptp_batch_add": (I, [P, P]),
+        "ptp_batch_size": (I, [P]),
+        "ptp_batch_solve": (I, [P, ctypes.POINTER(Opts), P, pI]),
+        "ptp_batch_result_dev": (I, [P, I, P]),
         "ptp_adjoint_gradient_dev": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
         "ptp_adjoint_gradient": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
     }
@@ -114,7 +122,9 @@ EXPORTED = [
     "ptp_residual_noalloc_dev",
     "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_spatial_solve_dev",
     "ptp_spatial_solve_f32_dev", "ptp_periodic_solve_dev", "ptp_solve", "ptp_solve_dev",
-    "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient",
+    "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient", "ptp_autotune",
+    "ptp_batch_create", "ptp_batch_destroy", "ptp_batch_last_error", "ptp_batch_add", "ptp_batch_size",
+    "ptp_batch_solve", "ptp_batch_result_dev",
 ]
 
 
@@ -207,7 +217,12 @@ class Context:
         return tuple(x.value for x in v)
 
     INFO_KEYS = ("n_free", "N", "n_tri", "n_iron", "iron_incidences", "lin_nnz", "mass_nnz", "op_nnz",
-                 "spatial_levels", "time_levels", "n_coils")
+                 "spatial_levels", "time_levels", "n_coils", "row_block")
+
+    def autotune(self):
+        b, us = ctypes.c_int(), ctypes.c_double()
+        self._check(lib.ptp_autotune(self._h, ctypes.byref(b), ctypes.byref(us)))
+        return b.value, us.value
 
     def info(self):
         buf = (ctypes.c_int64 * len(self.INFO_KEYS))()
@@ -313,6 +328,49 @@ def _adjoint_gradient_dev(ctx, U, opts=None):
 
 Context.loss_dev = _loss_dev
 Context.adjoint_gradient_dev = _adjoint_gradient_dev
+
+
+class Batch:
+    """Many set-up contexts advanced by one graph launch per fixed-point step
+    (ptp_batch_*).  Keeps references to its contexts."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        rc = lib.ptp_batch_create(ctypes.byref(self._h), int(device))
+        if rc != PTP_OK:
+            raise PtpError(rc, "ptp_batch_create failed")
+        self.contexts = []
+
+    def _check(self, rc, allow=()):
+        if rc != PTP_OK and rc not in allow:
+            raise PtpError(rc, lib.ptp_batch_last_error(self._h).decode())
+        return rc
+
+    def add(self, ctx: Context):
+        self._check(lib.ptp_batch_add(self._h, ctx._h))
+        self.contexts.append(ctx)
+
+    def solve(self, opts: Opts):
+        K = len(self.contexts)
+        stats = (Stats * K)()
+        nconv = ctypes.c_int()
+        rc = lib.ptp_batch_solve(self._h, ctypes.byref(opts), stats, ctypes.byref(nconv))
+        self._check(rc, allow=(PTP_ENOTCONV,))
+        return [stats[i] for i in range(K)], nconv.value, rc
+
+    def result_dev(self, i, U):
+        return self._check(lib.ptp_batch_result_dev(self._h, int(i), _dev_ptr(U, "float64")))
+
+    def close(self):
+        if self._h:
+            lib.ptp_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def load_problem(ctx: Context, prob, structured: bool = True):

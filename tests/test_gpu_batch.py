@@ -1,0 +1,81 @@
+"""Batched solve of uneven instances (one CUDA-graph launch per fixed-point
+step for the whole batch) and the per-context launch-shape autotuner."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import periodic as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+ptp = pytest.importorskip("paper_2502_21013_gb300.ptp")
+
+
+def _ctx(prob, **kw):
+    c = ptp.Context(0)
+    ptp.load_problem(c, prob)
+    c.setup(ptp.default_opts(**kw))
+    return c
+
+
+def _instances():
+    return [
+        W.unit_square_problem(17, 16, amps=(30.0,)),
+        W.unit_square_problem(33, 8, amps=(70.0,), s_sat=0.5),
+        W.transformer_problem(33, 17, 16),
+        W.unit_square_problem(17, 32, amps=(2000.0,)),
+        W.unit_square_problem(9, 2),
+    ]
+
+
+@pytest.mark.parametrize("precision", [ptp.PTP_FP64, ptp.PTP_MIXED])
+def test_batch_equals_individual_solves_bitwise(precision):
+    probs = _instances()
+    opts = ptp.default_opts(precision=precision, tol=1e-11, max_outer=20000)
+    alone = []
+    ctxs = []
+    for p in probs:
+        c = _ctx(p, precision=precision)
+        U = torch.zeros((p.n_free, p.N), dtype=torch.float64, device="cuda")
+        st, rc = c.solve_dev(U, opts)
+        assert rc == ptp.PTP_OK
+        alone.append((U.clone(), st.outer_iterations))
+        ctxs.append(c)
+    batch = ptp.Batch(0)
+    for c in ctxs:
+        batch.add(c)
+    stats, nconv, rc = batch.solve(opts)
+    assert rc == ptp.PTP_OK and nconv == len(probs)
+    for i, p in enumerate(probs):
+        Ub = torch.empty((p.n_free, p.N), dtype=torch.float64, device="cuda")
+        batch.result_dev(i, Ub)
+        assert stats[i].outer_iterations == alone[i][1]
+        assert torch.equal(Ub, alone[i][0])        # same kernels, deterministic reductions
+    # and the batch result is the oracle's solution
+    d = P.assemble(probs[0])
+    ref = P.fixed_point(probs[0], d, tol=1e-13, max_it=50000)
+    Ub = torch.empty((probs[0].n_free, probs[0].N), dtype=torch.float64, device="cuda")
+    batch.result_dev(0, Ub)
+    err = np.linalg.norm(Ub.cpu().numpy() - ref.U) / np.linalg.norm(ref.U)
+    assert err < (1e-9 if precision == ptp.PTP_FP64 else 1e-8)
+    # a second solve reuses the captured graph and gives the same result
+    stats2, nconv2, rc2 = batch.solve(opts)
+    Ub2 = torch.empty_like(Ub)
+    batch.result_dev(0, Ub2)
+    assert torch.equal(Ub, Ub2)
+
+
+def test_autotune_keeps_the_solution():
+    prob = W.unit_square_problem(33, 32)
+    d = P.assemble(prob)
+    c = _ctx(prob, precision=ptp.PTP_MIXED)
+    block, us = c.autotune()
+    assert block in (128, 256, 512) and us > 0
+    assert c.info()["row_block"] == block
+    opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=1e-11, max_outer=20000)
+    U, st, rc = c.solve(opts)
+    assert rc == ptp.PTP_OK
+    Uo = np.load(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
+                                             "square33_N32_oracle.npz"))["U"]
+    assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) < 1e-8
