@@ -74,8 +74,9 @@ typedef struct ptp_opts {
                             (stopping rule of Section 4)                     */
     int    max_outer;    /* maximum fixed-point iterations                   */
     int    precision;    /* PTP_FP64 or PTP_MIXED                            */
-    int    time_levels;  /* multigrid-in-time levels; 0 = coarsen by 2 while
-                            N_l is even and N_l > coarse_steps               */
+    int    time_levels;  /* multigrid-in-time levels used by the V-cycle;
+                            0 = all (coarsen by 2 while N_l is even and
+                            N_l > coarse_steps); see coarse_cycles           */
     int    coarse_steps; /* N_c of the coarsest level: 1 or 2 (exact solve)  */
     int    vcycles;      /* multigrid-in-time V-cycles per outer step        */
     int    pre_smooth;   /* damped block-Jacobi sweeps before coarsening     */
@@ -89,6 +90,11 @@ typedef struct ptp_opts {
     int    coarse_max_it;/* iteration cap of the coarsest-level PCG          */
     int    use_graph;    /* capture one outer step in a CUDA graph           */
     int    check_every;  /* host reads the residual every this many steps    */
+    int    coarse_cycles;/* when time_levels stops above the 1- or 2-step
+                            bottom, the periodic problem of its last level is
+                            solved "exactly" by this many V-cycles of the
+                            remaining hierarchy (two-level method: time_levels
+                            = 2)                                             */
 } ptp_opts;
 
 /* Statistics of the last solve. */

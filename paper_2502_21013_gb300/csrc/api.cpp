@@ -102,6 +102,7 @@ void ptp_default_opts(ptp_opts* o) {
     o->coarse_max_it = 4;
     o->use_graph = 1;
     o->check_every = 16;
+    o->coarse_cycles = 8;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }

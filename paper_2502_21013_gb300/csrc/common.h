@@ -194,6 +194,7 @@ struct Ctx {
     std::vector<TimeLevel> tl;
     int coarse_ops[2] = {-1, -1};  // ops of the coarsest time level (N_c = 1 or 2)
     bool coarse_ok = false;        // the coarsest time level has 1 or 2 steps
+    int active_levels = 0;         // levels of the V-cycle (opts.time_levels)
 
     // work vectors (sized n * N on the finest level)
     DBuf<double> U, R, F, Ud;              // double state / residual / scratch

@@ -111,8 +111,10 @@ k_node_residual(ResidualArgs a) {
         if (a.Fext) {
             f = __ldg(a.Fext + g);
         } else {
-            for (int c = 0; c < a.n_coils; ++c)
-                f += __ldg(a.coil_b + (size_t)c * a.n + i) * __ldg(a.coil_s + (size_t)c * N + t);
+            for (int c = 0; c < a.n_coils; ++c) {
+                const double cb = __ldg(a.coil_b + (size_t)c * a.n + i);
+                if (cb != 0.0) f = fma(cb, __ldg(a.coil_s + (size_t)c * N + t), f);   // warp-uniform
+            }
         }
         const double r = f - mv - kv;
         if (a.R) a.R[g] = r;

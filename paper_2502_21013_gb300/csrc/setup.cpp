@@ -513,8 +513,7 @@ void build_hierarchy(Ctx& c) {
         t.N = Nl;
         t.tau = c.T / Nl;
         c.tl.push_back(t);
-        bool can = (Nl % 2 == 0) && (Nl / 2 >= nc_target);
-        if (o.time_levels > 0 && (int)c.tl.size() >= o.time_levels) can = false;
+        const bool can = (Nl % 2 == 0) && (Nl / 2 >= nc_target);
         if (!can) break;
         Nl /= 2;
     }
@@ -531,6 +530,8 @@ void build_hierarchy(Ctx& c) {
     c.coarse_ops[0] = add_op(0.0, tc);            // sum mode:        tau_c L
     c.coarse_ops[1] = Nc == 2 ? add_op(2.0, tc) : -1;  // difference:  2M + tau_c L
     c.coarse_ok = Nc == 1 || Nc == 2;
+    const int full = (int)c.tl.size();
+    c.active_levels = o.time_levels > 0 ? std::min(o.time_levels, full) : full;
     // dense inverses on the coarsest spatial level
     const SpatialLevel& cs = c.sl.back();
     if (cs.n <= COARSE_MAX) {

@@ -325,9 +325,12 @@ void coarse_solve(Ctx& c, Skip sk) {
     }
 }
 
-// multigrid-in-time V-cycle at level l: improves x_l for P_l x_l = b_l
+// multigrid-in-time V-cycle at level l: improves x_l for P_l x_l = b_l.
+// The V-cycle uses levels 0..active_levels-1.  Its last level is solved
+// exactly: directly when it is the 1- or 2-step bottom of the hierarchy,
+// otherwise by coarse_cycles V-cycles over the levels below it (full = true).
 template <typename T>
-void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk) {
+void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
     const int L = (int)c.tl.size();
     T* x = mgx<T>(c, l);
     const T* b = mgb<T>(c, l);
@@ -335,6 +338,11 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk) {
     cudaStream_t st = c.stream;
     if (l == L - 1) {
         coarse_solve<T>(c, sk);  // x_zero is implied: exact solve
+        return;
+    }
+    if (!full && l == c.active_levels - 1) {
+        const int cyc = std::max(1, c.opts.coarse_cycles);
+        for (int k = 0; k < cyc; ++k) mgt_vcycle<T>(c, l, x_zero && k == 0, sk, true);
         return;
     }
     const int pre = c.opts.pre_smooth, post = c.opts.post_smooth;
@@ -349,7 +357,7 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk) {
     }
     Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
     c.launches += launch_spmm<T>(SP_PRESID_RESTRICT, A, t.N, x, b, mgb<T>(c, l + 1), T(0), sk, st);
-    mgt_vcycle<T>(c, l + 1, true, sk);
+    mgt_vcycle<T>(c, l + 1, true, sk, full);
     c.launches += launch_time_prolong_add<T>(c.n, c.tl[l + 1].N, mgx<T>(c, l + 1), x, sk, st);
     for (int k = 0; k < post; ++k) bj_sweep<T>(c, l, x, b, false, sk);
 }
@@ -632,6 +640,7 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
     k = k * 16 + o.gmg_smooth;
     k = k * 256 + o.coarse_max_it;
     k = k * 1024 + c.row_block;
+    k = k * 64 + o.coarse_cycles;
     return k;
 }
 
@@ -730,7 +739,7 @@ int solve_end(Ctx& c, ptp_stats* stats, bool adjoint, int64_t step_launches, dou
         stats->solve_ms = solve_ms;
         stats->residual_ms = dev_ms;
         stats->kernel_launches = step_launches;
-        stats->time_levels = (int)c.tl.size();
+        stats->time_levels = c.active_levels;
         stats->spatial_levels = (int)c.sl.size();
     }
     if (fs.done == 2) return PTP_ENAN;

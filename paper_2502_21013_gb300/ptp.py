@@ -29,7 +29,7 @@ class Opts(ctypes.Structure):
         ("pre_smooth", ctypes.c_int), ("post_smooth", ctypes.c_int), ("omega_t", ctypes.c_double),
         ("pcg_iters", ctypes.c_int), ("spatial_prec", ctypes.c_int), ("gmg_smooth", ctypes.c_int),
         ("gmg_omega", ctypes.c_double), ("coarse_tol", ctypes.c_double), ("coarse_max_it", ctypes.c_int),
-        ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
     ]
 
     def as_dict(self):
