@@ -392,6 +392,53 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Config 'batched64': independent instances of uneven mesh size and N
+    (grids {65,129,257,513}^2, N in {64..512}, J0 ~ U[20,80], s_sat ~
+    U[0.5,2]) solved together, one CUDA-graph launch per fixed-point step."""
+    import torch
+    from paper_2502_21013_gb300 import ptp
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    probs = W.config_batched(seed=rank, count=args.batch_count)
+    t0 = time.perf_counter()
+    ctxs = []
+    tuned = []
+    for p in probs:
+        c = ptp.Context(local)
+        ptp.load_problem(c, p)
+        c.setup(ptp.default_opts(precision=ptp.PTP_MIXED))
+        tuned.append(c.autotune()[0])
+        ctxs.append(c)
+    setup_s = time.perf_counter() - t0
+    batch = ptp.Batch(local)
+    for c in ctxs:
+        batch.add(c)
+    batch.solve(ptp.default_opts(precision=ptp.PTP_MIXED, tol=TOL, max_outer=2))   # graph capture
+    opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=TOL, max_outer=args.max_outer)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats, nconv, rc = batch.solve(opts)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    clocks = sampler.stop()
+    dofs = sum(p.n_free * p.N for p in probs)
+    line = {"metric": METRIC, "value": dofs / el, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched{len(probs)}", "instances": len(probs), "space_time_dofs": dofs,
+                       "converged": nconv, "tol": TOL, "setup_s": setup_s,
+                       "outer_iterations": [s.outer_iterations for s in stats],
+                       "largest_instance_dofs": max(p.n_free * p.N for p in probs),
+                       "row_block_choices": {str(b): tuned.count(b) for b in sorted(set(tuned))},
+                       "gpu_launches": int(sum(s.kernel_launches for s in stats))},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -429,6 +476,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["square257_N256", "batched64"], default="square257_N256")
+    ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--allow-unconverged", action="store_true",
                     help="profiling only: accept solves cut short by --max-outer")
     ap.add_argument("--ref-iterations", type=int, default=1800,
@@ -438,6 +487,8 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched64":
+        run_batched(args)
     else:
         run_ours(args)
 
