@@ -111,6 +111,9 @@ struct OpPair {
     double cm = 1.0, cl = 0.0;
     DBuf<double> inv_d;  // dense inverse on the coarsest spatial level (row-major)
     DBuf<float> inv_f;
+    // per spatial level, double: padded-ELL values cm M + cl L and its diagonal,
+    // formed once so the double row kernels spend no FMA on the combination
+    std::vector<DBuf<double>> comb, dcomb;
 };
 
 struct TimeLevel {

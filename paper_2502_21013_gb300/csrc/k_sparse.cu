@@ -99,6 +99,14 @@ __device__ __forceinline__ void row_ell(const Op<T>& op, int N, int row, int col
             m[k] = __int_as_float(e.y);
             a[k] = op.cm * m[k] + op.cl * __int_as_float(e.z);
         }
+    } else if (op.ecomb) {
+        // double: the combined values are precomputed; M is only needed for the time shift
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            j[k] = __ldg(op.eidx + base + k);
+            a[k] = __ldg(op.ecomb + base + k);
+            if constexpr (PERIODIC) m[k] = __ldg(op.ev1 + base + k);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -207,6 +215,7 @@ __device__ __forceinline__ void row_presid(const Op<T>& op, int N, int row, int 
 
 template <typename T>
 __device__ __forceinline__ T diag_of(const Op<T>& op, int row) {
+    if (op.dcomb) return __ldg(op.dcomb + row);
     T d = op.cm * __ldg(op.d1 + row);
     if (op.d2) d += op.cl * __ldg(op.d2 + row);
     return d;
@@ -761,6 +770,18 @@ int flat_grid(size_t total) {
 }
 
 }  // namespace
+
+__global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                          double* __restrict__ out) {
+    pdl_enter();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
+    if (n == 0) return;
+    launch_k(k_lincomb, dim3(flat_grid(n)), dim3(256), s, n, a, x, b, y, out);
+}
 
 void set_row_block(int threads) {
     g_row_block = std::min(kMaxBlock, std::max(64, threads));

@@ -129,6 +129,8 @@ struct Op {             // cm * v1 + cl * v2 on a CSR pattern
     int ell_w = 0;           // > 0: use the padded ELL arrays below
     const int* eidx = nullptr;
     const int4* pk = nullptr; // float: packed {idx, v1, v2, 0} per entry
+    const T* ecomb = nullptr; // precombined ELL values cm v1 + cl v2 (double path)
+    const T* dcomb = nullptr; // precombined diagonal
     const T* ev1 = nullptr;
     const T* ev2 = nullptr;
 };
@@ -220,5 +222,7 @@ int launch_norm2(size_t count, const T* x, double* partials, unsigned* counter, 
                  cudaStream_t s);
 
 int num_sms();
+// out = a x + b y (elementwise, double), for set-up
+void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
 
 }  // namespace ptp

@@ -9,6 +9,7 @@
 #include <map>
 
 #include "common.h"
+#include "kernels.h"
 
 namespace ptp {
 
@@ -532,6 +533,23 @@ void build_hierarchy(Ctx& c) {
     c.coarse_ok = Nc == 1 || Nc == 2;
     const int full = (int)c.tl.size();
     c.active_levels = o.time_levels > 0 ? std::min(o.time_levels, full) : full;
+    // precombined double operators cm M + cl L per spatial level (ELL values and diagonal)
+    for (auto& p : c.ops) {
+        p.comb.clear();
+        p.dcomb.clear();
+        p.comb.resize(c.sl.size());
+        p.dcomb.resize(c.sl.size());
+        for (size_t k = 0; k < c.sl.size(); ++k) {
+            const DevCSR& d = c.sl[k].op;
+            if (d.ell_w > 0) {
+                const size_t m = (size_t)d.rows * d.ell_w;
+                p.comb[k].alloc(m);
+                launch_lincomb(m, p.cm, d.e1d.p, p.cl, d.e2d.p, p.comb[k].p, s);
+            }
+            p.dcomb[k].alloc((size_t)d.rows);
+            launch_lincomb((size_t)d.rows, p.cm, d.d1d.p, p.cl, d.d2d.p, p.dcomb[k].p, s);
+        }
+    }
     // dense inverses on the coarsest spatial level
     const SpatialLevel& cs = c.sl.back();
     if (cs.n <= COARSE_MAX) {

@@ -81,6 +81,20 @@ Op<T> make_op(const DevCSR& d, double cm, double cl) {
     return o;
 }
 
+// operator cm M + cl L of op pair opi on spatial level s (double: precombined values)
+template <typename T>
+Op<T> level_op(Ctx& c, int s, int opi) {
+    const OpPair& p = c.ops[opi];
+    Op<T> o = make_op<T>(c.sl[s].op, p.cm, p.cl);
+    if constexpr (sizeof(T) == 8) {
+        if (s < (int)p.comb.size()) {
+            o.ecomb = p.comb[s].p;
+            o.dcomb = p.dcomb[s].p;
+        }
+    }
+    return o;
+}
+
 template <typename T>
 ColRed<T> make_cr(Ctx& c) {
     ColRed<T> r;
@@ -144,7 +158,7 @@ T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool f
         oth[s] = gr<T>(c, s);
     }
     for (int s = 0; s < S - 1; ++s) {
-        Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
+        Op<T> A = level_op<T>(c, s, opi);
         const bool have_first = (s == 0) ? first_done : true;
         if (!have_first) c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
         for (int k = 1; k < nu; ++k) {
@@ -165,7 +179,7 @@ T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool f
         if (inv) {
             c.launches += launch_dense_apply<T>(c.sl[s].n, N, inv, b[s], cur[s], sk, st);
         } else {
-            Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
+            Op<T> A = level_op<T>(c, s, opi);
             if (!(s == 0 && first_done))
                 c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
             for (int k = 1; k < 4 * nu; ++k) {
@@ -177,7 +191,7 @@ T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool f
     for (int s = S - 2; s >= 0; --s) {
         Op<T> P = make_op<T>(c.sl[s].P, 1.0, 0.0);
         c.launches += launch_spmm<T>(SP_INTERP_ADD, P, N, cur[s + 1], nullptr, cur[s], T(0), sk, st);
-        Op<T> A = make_op<T>(c.sl[s].op, cm, cl);
+        Op<T> A = level_op<T>(c, s, opi);
         for (int k = 0; k < nu; ++k) {
             c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
             std::swap(cur[s], oth[s]);
@@ -217,7 +231,7 @@ struct PCG {
             cr.tol2 = (T)(tol * tol);
             sk2.pdone = c.flag.p + 1;
         }
-        A = make_op<T>(c.sl[0].op, c.ops[opi].cm, c.ops[opi].cl);
+        A = level_op<T>(c, 0, opi);
         q = wbuf<T>(c, 3);
     }
 
@@ -268,7 +282,7 @@ void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
     const size_t cnt = (size_t)c.n * t.N;
     // a zero start means x holds stale data: the first PCG update assigns it
     PCG<T> pcg(c, t.op, t.N, r, x, (T)c.opts.omega_t, 0.0, sk, x_zero);
-    Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+    Op<T> A = level_op<T>(c, 0, t.op);
     Aux<T> aux = pcg.gmg ? sweep_aux<T>(c, 0, t.op, pcg.first_sweep_buffer()) : Aux<T>();
     if (x_zero) {
         if (pcg.gmg)
@@ -355,7 +369,7 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
         bj_sweep<T>(c, l, x, b, zero, sk);
         zero = false;
     }
-    Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+    Op<T> A = level_op<T>(c, 0, t.op);
     c.launches += launch_spmm<T>(SP_PRESID_RESTRICT, A, t.N, x, b, mgb<T>(c, l + 1), T(0), sk, st);
     mgt_vcycle<T>(c, l + 1, true, sk, full);
     c.launches += launch_time_prolong_add<T>(c.n, c.tl[l + 1].N, mgx<T>(c, l + 1), x, sk, st);
@@ -546,14 +560,14 @@ void source_dev(Ctx& c, double* F) {
 
 template <typename T>
 void apply_op(Ctx& c, int s, int op, int N, const T* X, T* Y) {
-    Op<T> A = make_op<T>(c.sl[s].op, c.ops[op].cm, c.ops[op].cl);
+    Op<T> A = level_op<T>(c, s, op);
     c.launches += launch_spmm<T>(SP_APPLY, A, N, X, nullptr, Y, T(0), Skip{}, c.stream);
 }
 
 template <typename T>
 void periodic_apply(Ctx& c, int level, const T* X, T* Y) {
     const TimeLevel& t = c.tl[level];
-    Op<T> A = make_op<T>(c.sl[0].op, c.ops[t.op].cm, c.ops[t.op].cl);
+    Op<T> A = level_op<T>(c, 0, t.op);
     c.launches += launch_spmm<T>(SP_PAPPLY, A, t.N, X, nullptr, Y, T(0), Skip{}, c.stream);
 }
 
@@ -615,7 +629,7 @@ void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* r
     if (relres) {
         // ||B - P X|| / ||B|| in double
         double* r = c.Ud.p;
-        Op<double> A = make_op<double>(c.sl[0].op, c.ops[c.tl[0].op].cm, c.ops[c.tl[0].op].cl);
+        Op<double> A = level_op<double>(c, 0, c.tl[0].op);
         c.launches += launch_spmm<double>(SP_PRESID, A, c.N, X, B, r, 0.0, Skip{}, st);
         double* out = c.scal.p + 2;  // two scratch scalars
         c.launches += launch_norm2<double>(cnt, r, c.part_d.p, c.counter.p, out, st);

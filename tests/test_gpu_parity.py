@@ -306,3 +306,20 @@ def test_full_size_mixed_solve_meets_tolerance_in_oracle_norm():
     Rs = R.cpu().numpy()[rows]
     assert np.abs(Rs - Ro[rows]).max() <= 1e-12 * np.abs(F).max()
     assert np.abs(Uh[:, N // 2:] + Uh[:, :N // 2]).max() <= 1e-6 * np.abs(Uh).max()
+
+
+@pytest.mark.parametrize("precision,tol,bar", [("fp64", 1e-13, 1e-10), ("mixed", 1e-11, 1e-8)])
+def test_unstructured_delaunay_mesh(precision, tol, bar):
+    """A seeded random Delaunay mesh (no grid structure: Jacobi-preconditioned
+    PCG, rows of up to a dozen entries on the CSR path): residual and
+    converged solution against the oracle."""
+    prob = W.delaunay_problem(300, 8, seed=1, amp=2000.0)
+    d = P.assemble(prob)
+    prec = ptp.PTP_FP64 if precision == "fp64" else ptp.PTP_MIXED
+    c, o = make_ctx(prob, precision=prec, tol=tol, max_outer=20000)
+    U = np.random.default_rng(7).normal(scale=0.05, size=(d.n, d.N))
+    assert rel(c.residual(U)[0], P.residual(prob, d, U)) < 1e-13
+    Us, st, rc = c.solve(o)
+    assert rc == ptp.PTP_OK
+    ref = P.fixed_point(prob, d, tol=1e-13, max_it=50000)
+    assert rel(Us, ref.U) < bar

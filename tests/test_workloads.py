@@ -35,3 +35,12 @@ def test_named_workloads():
     assert (s > 0).all() and abs(np.median(np.log(s)) - np.log(10)) < 0.2
     batch = W.config_batched(0, count=8)
     assert len(batch) == 8 and all(b.N in (64, 128, 256, 512) for b in batch)
+
+
+def test_delaunay_mesh_is_valid():
+    p = W.delaunay_problem(300, 8, seed=1)
+    a = _areas(p)
+    assert (a > 0).all() and abs(a.sum() - 1.0) < 1e-12
+    deg = np.bincount(p.tri.ravel(), minlength=p.n_nodes)
+    assert deg.max() >= 8                       # rows wider than the structured stencil
+    assert p.nonlinear_e.sum() > 0 and (p.coil_of_elem >= 0).sum() > 0

@@ -34,6 +34,7 @@ __all__ = [
     "config_adjoint",
     "config_batched",
     "one_node_problem",
+    "delaunay_problem",
 ]
 
 
@@ -179,6 +180,39 @@ def transformer_problem(nx: int, ny: int, N: int, *, J0: float = 60.0,
         phase=np.array([0.0, 2.0 * math.pi / 3.0]), nu_min=1.0, nu_max=100.0,
         s_sat=1.0, nu_linear=100.0, T=T, N=int(N),
         grid=(nx, ny, 0.0, 0.0, 2.0, 1.0))
+
+
+def delaunay_problem(n_interior: int, N: int, seed: int = 0, *, amp: float = 50.0,
+                     name: str | None = None) -> Problem:
+    """Unstructured mesh of the unit square: Delaunay triangulation of
+    `n_interior` seeded random points plus 12 points per side, with the iron
+    block, a strip coil and the materials of the unit-square workloads
+    (centroid rule).  Vertex degrees vary (some rows exceed 8 entries)."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    t = np.linspace(0.0, 1.0, 13)[:-1]
+    side = [np.stack([t, np.zeros_like(t)], 1), np.stack([np.ones_like(t), t], 1),
+            np.stack([1 - t, np.ones_like(t)], 1), np.stack([np.zeros_like(t), 1 - t], 1)]
+    bnd = np.concatenate(side)
+    pts = np.concatenate([bnd, 0.02 + 0.96 * rng.random((n_interior, 2))])
+    tri = Delaunay(pts).simplices.astype(np.int32)
+    p = pts[tri]
+    det = (p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1])
+    flip = det < 0
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    keep = np.abs(det) > 1e-12
+    tri = np.ascontiguousarray(tri[keep])
+    dirichlet = np.zeros(pts.shape[0], dtype=np.uint8)
+    dirichlet[: bnd.shape[0]] = 1
+    c = _centroids(pts, tri)
+    iron = _in_box(c, ((0.25, 0.75), (0.25, 0.75)))
+    coil = np.full(tri.shape[0], -1, dtype=np.int32)
+    coil[_in_box(c, ((0.05, 0.2), (0.2, 0.8)))] = 0
+    return Problem(
+        name=name or f"delaunay{n_interior}_N{N}_seed{seed}", xy=np.ascontiguousarray(pts), tri=tri,
+        dirichlet=dirichlet, sigma_e=np.where(iron, 10.0, 0.0), nonlinear_e=iron.astype(np.uint8),
+        coil_of_elem=coil, amp=np.array([amp]), phase=np.array([0.0]), nu_min=1.0, nu_max=100.0,
+        s_sat=1.0, nu_linear=100.0, T=1.0, N=int(N), grid=None)
 
 
 def one_node_problem(N: int, *, sigma: float = 10.0, nonlinear: bool = True,
