@@ -51,6 +51,13 @@ import workloads as W  # noqa: E402
 METRIC = "space-time DOF/s to fixed-point tol 1e-8 (FP64 vs mixed) and % HBM roofline"
 UNIT = "DOF/s"
 TOL = 1e-8
+# inner periodic solvers of the fixed-point step (solver options)
+INNER = {
+    "mg": {"name": "multigrid in time, full hierarchy", "opts": {}},
+    "dft2": {"name": "two-level multigrid in time, DFT-in-time coarse solve on N/2 steps",
+             "opts": {"coarse_solver": 1, "time_levels": 2}},
+    "dft": {"name": "DFT in time on all N steps", "opts": {"coarse_solver": 1, "time_levels": 1}},
+}
 WORKLOAD = "square257_N256"
 
 
@@ -231,11 +238,13 @@ def run_ours(args):
     prob = W.config_mixed(seed=rank)
     stream = torch.cuda.Stream(device=dev)
 
+    inner = INNER[args.inner]
+
     def make(precision):
         c = ptp.Context(local)
         c.set_stream(stream.cuda_stream)
         ptp.load_problem(c, prob)
-        o = ptp.default_opts(precision=precision, tol=TOL, max_outer=args.max_outer)
+        o = ptp.default_opts(precision=precision, tol=TOL, max_outer=args.max_outer, **inner["opts"])
         c.setup(o)
         return c, o
 
@@ -329,7 +338,7 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0:
         c64, o64 = make(ptp.PTP_FP64)
-        c64.solve_dev(U, ptp.default_opts(precision=ptp.PTP_FP64, tol=TOL, max_outer=3))  # graph capture
+        c64.solve_dev(U, ptp.default_opts(precision=ptp.PTP_FP64, tol=TOL, max_outer=3, **inner["opts"]))  # capture
         barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -364,6 +373,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "257x257 nodes, 131072 triangles", "free_nodes": n,
                        "time_steps": N, "space_time_dofs": dofs, "tol": TOL, "precision": "mixed",
+                       "inner_solver": inner["name"],
                        "outer_iterations": iters, "final_rel_residual": res_rel,
                        "l2": "inputs larger than L2 (U alone is 133 MB)", "parallelism": f"replicas{world}"},
             "fp64": fp64,
@@ -477,6 +487,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["square257_N256", "batched64"], default="square257_N256")
+    ap.add_argument("--inner", choices=sorted(INNER), default="mg",
+                    help="inner periodic solve: multigrid in time (mg), two-level with the DFT-in-time "
+                         "coarse solve (dft2), or the DFT in time alone (dft)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--allow-unconverged", action="store_true",
                     help="profiling only: accept solves cut short by --max-outer")

@@ -66,6 +66,19 @@ extern "C" {
 #define PTP_PREC_GMG    1 /* geometric multigrid V-cycle on the nested
                              structured grids (needs ptp_set_structured)    */
 
+/* ---- exact periodic solve of the last multigrid-in-time level --------- */
+#define PTP_COARSE_VCYCLES 0 /* N_c = 1: tau_c L x = b; N_c = 2: sum and
+                                difference split (both SPD, PCG in double);
+                                a truncated hierarchy: coarse_cycles V-cycles
+                                of the levels below                          */
+#define PTP_COARSE_DFT     1 /* discrete Fourier transform in time (Remark on
+                                parallel solvers, Section 3): mode k solves
+                                ((1 - e^{-2 pi i k/N_l}) M + tau_l L) x_k = b_k,
+                                k = 0..N_l/2 (conjugate symmetry), by
+                                conjugate-orthogonal CG in double with the
+                                tau_l L multigrid V-cycle as preconditioner;
+                                time_levels = 1 makes it the whole inner solve */
+
 typedef struct ptp_ctx ptp_ctx;
 
 /* Solver options; ptp_default_opts() fills sensible defaults. */
@@ -95,6 +108,12 @@ typedef struct ptp_opts {
                             solved "exactly" by this many V-cycles of the
                             remaining hierarchy (two-level method: time_levels
                             = 2)                                             */
+    int    coarse_solver;/* exact periodic solve of the last level used:
+                            PTP_COARSE_VCYCLES (the 1- or 2-step split at the
+                            bottom, coarse_cycles V-cycles above it) or
+                            PTP_COARSE_DFT (time DFT, one complex shifted
+                            spatial solve per mode; any N_l <= 1022)          */
+    int    dft_max_it;   /* iteration cap of each DFT mode solve (COCG)      */
 } ptp_opts;
 
 /* Statistics of the last solve. */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libptp.so")
-SOURCES = ["k_residual.cu", "k_sparse.cu", "solver.cu", "setup.cpp", "api.cpp", "noalloc.cu", "k_adjoint.cu", "batch.cu"]
+SOURCES = ["k_residual.cu", "k_sparse.cu", "solver.cu", "setup.cpp", "api.cpp", "noalloc.cu", "k_adjoint.cu", "batch.cu", "k_dft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 
@@ -30,7 +30,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
     objs, procs = [], []
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "ptp.h"))
     newest_header = max(os.path.getmtime(h) for h in headers)
     for src in SOURCES:

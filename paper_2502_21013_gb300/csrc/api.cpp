@@ -103,6 +103,8 @@ void ptp_default_opts(ptp_opts* o) {
     o->use_graph = 1;
     o->check_every = 16;
     o->coarse_cycles = 8;
+    o->coarse_solver = PTP_COARSE_VCYCLES;
+    o->dft_max_it = 30;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }
@@ -238,6 +240,8 @@ int ptp_setup(ptp_ctx* h, const ptp_opts* opts) {
         PTP_REQUIRE(o.spatial_prec == PTP_PREC_JACOBI || o.spatial_prec == PTP_PREC_GMG,
                     "ptp_setup: bad spatial preconditioner");
         PTP_REQUIRE(o.coarse_steps == 1 || o.coarse_steps == 2, "ptp_setup: coarse_steps must be 1 or 2");
+        PTP_REQUIRE(o.coarse_solver == PTP_COARSE_VCYCLES || o.coarse_solver == PTP_COARSE_DFT,
+                    "ptp_setup: bad coarse_solver");
         c.opts = o;
         ptp::build_problem(c);
         ptp::build_hierarchy(c);
@@ -412,7 +416,8 @@ int ptp_periodic_solve_dev(ptp_ctx* h, const ptp_opts* opts, const double* B, do
         PTP_REQUIRE(B && X && cycles >= 1, "ptp_periodic_solve: bad arguments");
         if (opts) {
             PTP_REQUIRE(opts->precision == c.opts.precision && opts->spatial_prec == c.opts.spatial_prec &&
-                            opts->time_levels == c.opts.time_levels && opts->coarse_steps == c.opts.coarse_steps,
+                            opts->time_levels == c.opts.time_levels && opts->coarse_steps == c.opts.coarse_steps &&
+                            opts->coarse_solver == c.opts.coarse_solver,
                         "ptp_periodic_solve: hierarchy options differ from ptp_setup");
             c.opts = *opts;
         }

@@ -130,6 +130,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
             o.spatial_prec = cs[i]->opts.spatial_prec;
             o.time_levels = cs[i]->opts.time_levels;
             o.coarse_steps = cs[i]->opts.coarse_steps;
+            o.coarse_solver = cs[i]->opts.coarse_solver;
             ptp::set_row_block(cs[i]->row_block);
             ptp::solve_begin(*cs[i], o, nullptr, false);
         }

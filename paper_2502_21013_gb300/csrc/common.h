@@ -198,6 +198,12 @@ struct Ctx {
     int coarse_ops[2] = {-1, -1};  // ops of the coarsest time level (N_c = 1 or 2)
     bool coarse_ok = false;        // the coarsest time level has 1 or 2 steps
     int active_levels = 0;         // levels of the V-cycle (opts.time_levels)
+    // exact periodic solve of one time level by a DFT in time (opts.coarse_solver)
+    int dft_level = -1;            // level solved this way, -1 = none
+    int dft_op = -1;               // op pair tau_l L: the preconditioner of every mode
+    DBuf<double> dft_W;            // e^{-2 pi i j / N_l}, j < N_l (re, im pairs)
+    DBuf<double> dft_ck;           // mode shifts c_k = 1 - e^{-2 pi i k / N_l}, k <= N_l / 2
+    DBuf<double> dft_w[6];         // complex work vectors, n x 2 (N_l / 2 + 1) doubles
 
     // work vectors (sized n * N on the finest level)
     DBuf<double> U, R, F, Ud;              // double state / residual / scratch

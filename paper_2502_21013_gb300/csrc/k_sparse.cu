@@ -17,68 +17,15 @@
 #include <map>
 #include <mutex>
 
-#include "kernels.h"
+#include "dev_util.cuh"
 
 namespace ptp {
 
 namespace {
 
-constexpr int kMaxBlock = 512;
 // threads per block of the row kernels for launches issued by this host thread
 // (each context sets its autotuned value before launching)
 thread_local int g_row_block = 256;
-
-__device__ __forceinline__ bool skip_now(const Skip& s) {
-    return (s.done && *(volatile const int*)s.done) || (s.pdone && *(volatile const int*)s.pdone);
-}
-
-template <typename T, int VEC>
-__device__ __forceinline__ void ldg_vec(const T* p, T (&o)[VEC]) {
-    if constexpr (sizeof(T) == 4 && VEC == 4) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
-        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
-        o[0] = a.x; o[1] = a.y;
-    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
-        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-        o[0] = a.x; o[1] = a.y;
-    } else {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) o[v] = __ldg(p + v);
-    }
-}
-
-template <typename T, int VEC>
-__device__ __forceinline__ void ld_vec(const T* p, T (&o)[VEC]) {  // coherent load
-    if constexpr (sizeof(T) == 4 && VEC == 4) {
-        const float4 a = *reinterpret_cast<const float4*>(p);
-        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
-    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
-        const float2 a = *reinterpret_cast<const float2*>(p);
-        o[0] = a.x; o[1] = a.y;
-    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
-        const double2 a = *reinterpret_cast<const double2*>(p);
-        o[0] = a.x; o[1] = a.y;
-    } else {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) o[v] = p[v];
-    }
-}
-
-template <typename T, int VEC>
-__device__ __forceinline__ void st_vec(T* p, const T (&o)[VEC]) {
-    if constexpr (sizeof(T) == 4 && VEC == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
-        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
-        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
-    } else {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) p[v] = o[v];
-    }
-}
 
 // Padded-ELL row with W entries, fully unrolled: every index and value load
 // is issued, then every X load, so a row costs two memory round trips
@@ -233,13 +180,6 @@ __device__ __forceinline__ void fused_sweep(const Aux<T>& aux, int N, int row, i
     st_vec<T, VEC>(aux.Y2 + (size_t)row * N + col0, o);
 }
 
-// grid-stride walk over (row, chunk); NC = N / VEC, rpb = rows per block
-#define PTP_ROW_LOOP(rows, NC, rpb)                                                    \
-    const int chunk_ = threadIdx.x % (NC);                                             \
-    const int rsub_ = threadIdx.x / (NC);                                              \
-    const int col0 = chunk_ * VEC;                                                     \
-    for (int rg_ = blockIdx.x; rg_ * (rpb) < (rows); rg_ += gridDim.x)                  \
-        for (int row = rg_ * (rpb) + rsub_; row < (rows) && rsub_ < (rpb); row = (rows))
 
 template <typename T, int VEC, int MODE>
 __global__ void __launch_bounds__(kMaxBlock)
@@ -308,116 +248,6 @@ k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, 
             for (int v = 0; v < VEC; ++v) y[v] += acc[v];
             st_vec<T, VEC>(yp, y);
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// per-column reductions with a last-block finish
-// ---------------------------------------------------------------------------
-
-enum Fin { FIN_ALPHA = 0, FIN_UPDATE_JACOBI = 1, FIN_UPDATE_RR = 2, FIN_RZ_FIRST = 3, FIN_RZ_NEXT = 4 };
-
-// column scalar slots in ColRed::col (each N long)
-enum Slot { S_RHO = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_BB = 4 };
-
-// num / den for PCG scalars, evaluated in double; 0 when the column has
-// no (or a non-finite) search direction, so a column whose right-hand side
-// is zero or underflows stays untouched instead of propagating NaN.
-template <typename T>
-__device__ __forceinline__ T safe_ratio(T num, T den) {
-    if (!(num > T(0) && den > T(0))) return T(0);
-    const double r = (double)num / (double)den;
-    return isfinite(r) && r < 1e30 ? (T)r : T(0);
-}
-
-// Blocks are grouped by kGroup; the last block of each group to finish sums
-// its group's partials, and the last group finisher sums the group results
-// and applies FIN to every column.  Both sums run in a fixed order, so the
-// result does not depend on block scheduling.  Counters: [0] for the groups,
-// [1 + g] for group g; each is reset by the block that consumed it.
-constexpr int kGroup = 32;
-
-template <typename T, int VEC, int NQ, int FIN>
-__device__ void col_reduce_finish(T (&acc)[NQ][VEC], int N, int NC, int rpb, ColRed<T> cr) {
-    __shared__ T sm[NQ * kMaxBlock * VEC];
-    __shared__ int stage;
-    __shared__ int all_conv;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) sm[(q * blockDim.x + threadIdx.x) * VEC + v] = acc[q][v];
-    __syncthreads();
-    const int G = gridDim.x;
-    const int QN = NQ * N;
-    for (int e = threadIdx.x; e < QN; e += blockDim.x) {
-        const int q = e / N, col = e - q * N;
-        const int chunk = col / VEC, v = col - chunk * VEC;
-        T s = T(0);
-        for (int r = 0; r < rpb; ++r) s += sm[(q * blockDim.x + r * NC + chunk) * VEC + v];
-        cr.partials[(size_t)blockIdx.x * QN + e] = s;
-    }
-    __threadfence();
-    __syncthreads();
-    const int ng = (G + kGroup - 1) / kGroup;
-    const int g = blockIdx.x / kGroup;
-    const int b0 = g * kGroup;
-    const int gsz = min(kGroup, G - b0);
-    T* part2 = cr.partials + (size_t)G * QN;
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(cr.counter + 1 + g, 1u);
-        stage = ticket == (unsigned)(gsz - 1) ? 1 : 0;
-        all_conv = 1;
-    }
-    __syncthreads();
-    if (!stage) return;
-    for (int e = threadIdx.x; e < QN; e += blockDim.x) {
-        T a = T(0);
-#pragma unroll 8
-        for (int b = 0; b < gsz; ++b) a += __ldcg(cr.partials + (size_t)(b0 + b) * QN + e);
-        part2[(size_t)g * QN + e] = a;
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        cr.counter[1 + g] = 0u;
-        const unsigned ticket = atomicAdd(cr.counter, 1u);
-        stage = ticket == (unsigned)(ng - 1) ? 2 : 0;
-    }
-    __syncthreads();
-    if (stage != 2) return;
-    for (int col = threadIdx.x; col < N; col += blockDim.x) {
-        T s[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            T a = T(0);
-            for (int b = 0; b < ng; ++b) a += __ldcg(part2 + (size_t)b * QN + q * N + col);
-            s[q] = a;
-        }
-        T* c = cr.col;
-        if constexpr (FIN == FIN_ALPHA) {
-            c[S_ALPHA * N + col] = safe_ratio<T>(c[S_RHO * N + col], s[0]);
-        } else if constexpr (FIN == FIN_UPDATE_JACOBI) {  // s = (rz, rr)
-            c[S_BETA * N + col] = safe_ratio<T>(s[0], c[S_RHO * N + col]);
-            c[S_RHO * N + col] = s[0];
-            c[S_RR * N + col] = s[1];
-            if (!(s[1] <= cr.tol2 * c[S_BB * N + col])) all_conv = 0;
-        } else if constexpr (FIN == FIN_UPDATE_RR) {
-            c[S_RR * N + col] = s[0];
-            if (!(s[0] <= cr.tol2 * c[S_BB * N + col])) all_conv = 0;
-        } else if constexpr (FIN == FIN_RZ_FIRST) {  // s = (rz, rr)
-            c[S_RHO * N + col] = s[0];
-            c[S_BB * N + col] = s[1];
-            c[S_RR * N + col] = s[1];
-        } else if constexpr (FIN == FIN_RZ_NEXT) {
-            c[S_BETA * N + col] = safe_ratio<T>(s[0], c[S_RHO * N + col]);
-            c[S_RHO * N + col] = s[0];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if constexpr (FIN == FIN_UPDATE_JACOBI || FIN == FIN_UPDATE_RR)
-            if (cr.pdone && all_conv) *cr.pdone = 1;
-        cr.counter[0] = 0u;
     }
 }
 
@@ -724,9 +554,6 @@ int pick_vec(int N, std::initializer_list<const void*> ptrs, bool need_even = fa
     return 1;
 }
 
-struct Launch {
-    int grid, block;
-};
 
 // resident blocks per SM of `kernel` at `block` threads (cached per kernel)
 int blocks_per_sm(const void* kernel, int block) {
@@ -742,6 +569,15 @@ int blocks_per_sm(const void* kernel, int block) {
     return nb;
 }
 
+
+int flat_grid(size_t total) {
+    size_t want = (total + 255) / 256;
+    size_t cap = (size_t)num_sms() * 8;
+    return (int)std::max<size_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
 Launch row_launch(int rows, int N, int vec, const void* kernel) {
     const int NC = N / vec;
     if (NC > kMaxBlock) throw Error(PTP_EINVAL, "too many time steps per level for one block (N/VEC > 512)");
@@ -756,20 +592,6 @@ Launch row_launch(int rows, int N, int vec, const void* kernel) {
     l.block = block;
     return l;
 }
-
-template <typename... KArgs, typename... Args>
-void launch_rows(void (*kernel)(KArgs...), int rows, int N, int vec, cudaStream_t s, Args&&... args) {
-    const Launch l = row_launch(rows, N, vec, (const void*)kernel);
-    launch_k(kernel, dim3(l.grid), dim3(l.block), s, std::forward<Args>(args)...);
-}
-
-int flat_grid(size_t total) {
-    size_t want = (total + 255) / 256;
-    size_t cap = (size_t)num_sms() * 8;
-    return (int)std::max<size_t>(1, std::min(want, cap));
-}
-
-}  // namespace
 
 __global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
                           double* __restrict__ out) {

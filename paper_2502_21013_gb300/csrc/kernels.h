@@ -42,6 +42,23 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// the same with dynamic shared memory
+template <typename... KArgs, typename... Args>
+inline void launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // K1: outer residual R = F - A(U), double (fused source, mass, K(u), norm)
 // ---------------------------------------------------------------------------
@@ -220,6 +237,26 @@ int launch_flag(int* flag, int v, Skip sk, cudaStream_t s);   // *flag = v
 template <typename T>
 int launch_norm2(size_t count, const T* x, double* partials, unsigned* counter, double* out,
                  cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Exact periodic solve of a time level by a DFT in time (k_dft.cu), double.
+// Spectra are [n][K] complex as interleaved (re, im) doubles, K = N/2 + 1;
+// W holds e^{-2 pi i j / N}, j < N, as (re, im) pairs.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDftSteps = 1022;   // K = N/2 + 1 <= 512 complex columns per row
+template <typename T>   // H_k = sum_t x_t e^{-2 pi i k t / N}
+int launch_dft_fwd(int n, int N, const T* x, const double* W, double* H, Skip sk, cudaStream_t s);
+template <typename T>   // x_t = (1/N) sum_k H_k e^{2 pi i k t / N}, H_{N-k} = conj(H_k)
+int launch_dft_inv(int n, int N, const double* H, const double* W, T* x, Skip sk, cudaStream_t s);
+// conjugate-orthogonal CG pieces over D = 2K doubles per row (complex scalars in ColRed)
+int launch_capply_alpha(const Op<double>& op, int D, const double* ck, double tau, const double* p, double* q,
+                        ColRed<double> cr, Skip sk, cudaStream_t s);   // q = (c_k M + tau L) p, alpha
+int launch_cupdate(int rows, int D, int assign, double* x, const double* p, double* r, const double* q,
+                   ColRed<double> cr, Skip sk, cudaStream_t s);      // x += alpha p, r -= alpha q, test
+int launch_cdot_rz(int rows, int D, const double* r, const double* z, ColRed<double> cr, int first, Skip sk,
+                   cudaStream_t s);                                  // rho (and bb) or beta
+int launch_cdirection(int rows, int D, const double* z, double* p, ColRed<double> cr, Skip sk,
+                      cudaStream_t s);                               // p = z + beta p
 
 int num_sms();
 // out = a x + b y (elementwise, double), for set-up

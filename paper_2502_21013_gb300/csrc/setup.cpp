@@ -533,6 +533,31 @@ void build_hierarchy(Ctx& c) {
     c.coarse_ok = Nc == 1 || Nc == 2;
     const int full = (int)c.tl.size();
     c.active_levels = o.time_levels > 0 ? std::min(o.time_levels, full) : full;
+    // DFT in time on the last level used: preconditioner tau_l L, twiddles and mode shifts
+    c.dft_level = -1;
+    c.dft_op = -1;
+    c.dft_W.release();
+    c.dft_ck.release();
+    if (o.coarse_solver == PTP_COARSE_DFT) {
+        const int l = c.active_levels - 1;
+        const int Nl = c.tl[l].N;
+        PTP_REQUIRE(Nl >= 1 && Nl <= kMaxDftSteps, "DFT coarse solver: the last level needs 1..1022 steps");
+        c.dft_level = l;
+        c.dft_op = add_op(0.0, c.tl[l].tau);
+        std::vector<double> W(2 * (size_t)Nl), ck(2 * (size_t)(Nl / 2 + 1));
+        for (int j = 0; j < Nl; ++j) {
+            const double th = 2.0 * M_PI * j / Nl;
+            W[2 * j] = std::cos(th);
+            W[2 * j + 1] = -std::sin(th);
+        }
+        for (int k = 0; k <= Nl / 2; ++k) {   // c_k = 1 - e^{-i theta_k}
+            const double th = 2.0 * M_PI * k / Nl;
+            ck[2 * k] = 1.0 - std::cos(th);
+            ck[2 * k + 1] = std::sin(th);
+        }
+        c.dft_W.upload(W, s);
+        c.dft_ck.upload(ck, s);
+    }
     // precombined double operators cm M + cl L per spatial level (ELL values and diagonal)
     for (auto& p : c.ops) {
         p.comb.clear();

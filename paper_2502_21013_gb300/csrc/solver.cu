@@ -18,6 +18,7 @@
 // With piecewise-constant prolongation P and restriction P^T the Galerkin
 // coarse operator of the level-l periodic operator is exactly the level-(l+1)
 // operator with tau_{l+1} = 2 tau_l, so coarse levels are rediscretisations.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -339,10 +340,59 @@ void coarse_solve(Ctx& c, Skip sk) {
     }
 }
 
+// Exact periodic solve of time level l by the DFT in time, in double
+// (k_dft.cu): b_l -> spectrum, one conjugate-orthogonal CG solve per mode
+// k = 0..N_l/2 on ((1 - e^{-2 pi i k/N_l}) M + tau_l L) x_k = b_k with the
+// tau_l L V-cycle (or its diagonal) as preconditioner, spectrum -> x_l.  The
+// iteration stops on the device once every mode has |r_k| <= coarse_tol |b_k|.
+template <typename T>
+void dft_solve(Ctx& c, int l, Skip sk) {
+    const int N = c.tl[l].N;
+    const int K = N / 2 + 1, D = 2 * K;
+    const int n = c.n;
+    const double tau = c.tl[l].tau;
+    cudaStream_t st = c.stream;
+    double* r = c.dft_w[0].p;   // spectrum of b, then the residual
+    double* x = c.dft_w[1].p;
+    double* q = c.dft_w[2].p;
+    double* za = c.dft_w[3].p;
+    double* zb = c.dft_w[4].p;
+    double* zc = c.dft_w[5].p;
+    c.launches += launch_dft_fwd<T>(n, N, mgb<T>(c, l), c.dft_W.p, r, sk, st);
+    ColRed<double> cr = make_cr<double>(c);
+    cr.pdone = c.flag.p + 1;
+    cr.tol2 = c.opts.coarse_tol * c.opts.coarse_tol;
+    Skip sk2 = sk;
+    sk2.pdone = c.flag.p + 1;
+    c.launches += launch_flag(c.flag.p + 1, 0, sk, st);
+    const bool gmg = use_gmg(c);
+    Op<double> P = level_op<double>(c, 0, c.dft_op);
+    auto precond = [&](double* xa, double* xb) -> double* {
+        if (gmg) return gmg_vcycle<double>(c, c.dft_op, D, r, xa, xb, sk2, false);
+        c.launches += launch_spmm<double>(SP_JACOBI, P, D, nullptr, r, xa, 1.0, sk2, st);
+        return xa;
+    };
+    double* p = precond(za, zb);
+    double* pa = p == za ? zb : za;
+    c.launches += launch_cdot_rz(n, D, r, p, cr, 1, sk2, st);
+    Op<double> A = make_op<double>(c.sl[0].op, 1.0, 0.0);   // v1 = M, v2 = L
+    const int maxit = std::max(1, c.opts.dft_max_it);
+    for (int it = 0; it < maxit; ++it) {
+        c.launches += launch_capply_alpha(A, D, c.dft_ck.p, tau, p, q, cr, sk2, st);
+        c.launches += launch_cupdate(n, D, it == 0 ? 1 : 0, x, p, r, q, cr, sk2, st);
+        if (it == maxit - 1) break;
+        double* z = precond(pa, zc);
+        c.launches += launch_cdot_rz(n, D, r, z, cr, 0, sk2, st);
+        c.launches += launch_cdirection(n, D, z, p, cr, sk2, st);
+    }
+    c.launches += launch_dft_inv<T>(n, N, x, c.dft_W.p, mgx<T>(c, l), sk, st);
+}
+
 // multigrid-in-time V-cycle at level l: improves x_l for P_l x_l = b_l.
 // The V-cycle uses levels 0..active_levels-1.  Its last level is solved
-// exactly: directly when it is the 1- or 2-step bottom of the hierarchy,
-// otherwise by coarse_cycles V-cycles over the levels below it (full = true).
+// exactly: by the DFT in time when that solver is chosen, directly when it
+// is the 1- or 2-step bottom of the hierarchy, otherwise by coarse_cycles
+// V-cycles over the levels below it (full = true).
 template <typename T>
 void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
     const int L = (int)c.tl.size();
@@ -350,6 +400,10 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
     const T* b = mgb<T>(c, l);
     const TimeLevel& t = c.tl[l];
     cudaStream_t st = c.stream;
+    if (l == c.dft_level) {
+        dft_solve<T>(c, l, sk);  // x_zero is implied: exact solve
+        return;
+    }
     if (l == L - 1) {
         coarse_solve<T>(c, sk);  // x_zero is implied: exact solve
         return;
@@ -482,6 +536,12 @@ void alloc_work(Ctx& c) {
         c.mg_xf.clear();
         c.mg_bf.clear();
     }
+    // the DFT solve works on 2 (N_l/2 + 1) double columns of its own
+    const size_t dft_cols = c.dft_level >= 0 ? 2 * (size_t)(c.tl[c.dft_level].N / 2 + 1) : 0;
+    for (int k = 0; k < 6; ++k) {
+        if (dft_cols) c.dft_w[k].alloc((size_t)c.n * dft_cols); else c.dft_w[k].release();
+    }
+    const size_t gcols = std::max(dcols, dft_cols);
     const size_t S = c.sl.size();
     c.g_xd.clear(); c.g_bd.clear(); c.g_rd.clear();
     c.g_xf.clear(); c.g_bf.clear(); c.g_rf.clear();
@@ -489,15 +549,15 @@ void alloc_work(Ctx& c) {
     c.g_xf.resize(S); c.g_bf.resize(S); c.g_rf.resize(S);
     for (size_t s = 1; s < S; ++s) {
         const size_t m = (size_t)c.sl[s].n * c.N;
-        const size_t md = (size_t)c.sl[s].n * dcols;
+        const size_t md = (size_t)c.sl[s].n * gcols;
         c.g_xd[s].alloc(md); c.g_bd[s].alloc(md); c.g_rd[s].alloc(md);
         if (mixed) { c.g_xf[s].alloc(m); c.g_bf[s].alloc(m); c.g_rf[s].alloc(m); }
     }
-    const size_t colN = 8 * (size_t)std::max(c.N, 2);
-    c.col_d.alloc(colN);
+    const int colmax = std::max({c.N, 2, (int)dft_cols});
+    c.col_d.alloc(8 * (size_t)colmax);
     c.scal.alloc(8);
-    c.col_f.alloc(colN);
-    const size_t parts = std::max(reduction_partials(std::max(c.N, 2)), (size_t)num_sms() * 64);
+    c.col_f.alloc(8 * (size_t)std::max(c.N, 2));
+    const size_t parts = std::max(reduction_partials(colmax), (size_t)num_sms() * 64);
     c.part_d.alloc(parts);
     c.part_f.alloc(mixed ? parts : 0);
     c.counter.alloc(256);
@@ -596,9 +656,9 @@ int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it,
 }
 
 static void require_coarse(const Ctx& c) {
-    PTP_REQUIRE(c.coarse_ok,
+    PTP_REQUIRE(c.coarse_ok || c.dft_level >= 0 || c.active_levels < (int)c.tl.size(),
                 "multigrid in time needs a coarsest level with 1 or 2 steps (N must be a power of "
-                "two times 1 or 2, and time_levels large enough to reach it)");
+                "two times 1 or 2, and time_levels large enough to reach it), or the DFT coarse solver");
 }
 
 void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres) {
@@ -646,16 +706,18 @@ void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* r
 
 // identifies the captured outer step: everything that changes its launches
 int64_t step_key(const Ctx& c, const ptp_opts& o) {
-    int64_t k = o.precision == PTP_MIXED ? 1 : 0;
-    k = k * 64 + o.pcg_iters;
-    k = k * 64 + o.vcycles;
-    k = k * 16 + o.pre_smooth;
-    k = k * 16 + o.post_smooth;
-    k = k * 16 + o.gmg_smooth;
-    k = k * 256 + o.coarse_max_it;
-    k = k * 1024 + c.row_block;
-    k = k * 64 + o.coarse_cycles;
-    return k;
+    // FNV-1a over every option whose value is baked into the captured step
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    const int ints[11] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+                          o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it};
+    const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
+    mix(ints, sizeof(ints));
+    mix(dbls, sizeof(dbls));
+    return (int64_t)(h >> 1);
 }
 
 int autotune(Ctx& c, double* best_us) {
@@ -700,7 +762,8 @@ int autotune(Ctx& c, double* best_us) {
 void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint) {
     require_coarse(c);
     PTP_REQUIRE(o.precision == c.opts.precision && o.spatial_prec == c.opts.spatial_prec &&
-                    o.time_levels == c.opts.time_levels && o.coarse_steps == c.opts.coarse_steps,
+                    o.time_levels == c.opts.time_levels && o.coarse_steps == c.opts.coarse_steps &&
+                    o.coarse_solver == c.opts.coarse_solver,
                 "precision / preconditioner / hierarchy options differ from ptp_setup");
     c.opts = o;
     cudaStream_t st = c.stream;

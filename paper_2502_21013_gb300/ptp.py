@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libptp.so")
 PTP_OK, PTP_EINVAL, PTP_ECUDA, PTP_ENOTCONV, PTP_ENAN, PTP_ESTATE, PTP_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 PTP_FP64, PTP_MIXED = 0, 1
 PTP_PREC_JACOBI, PTP_PREC_GMG = 0, 1
+PTP_COARSE_VCYCLES, PTP_COARSE_DFT = 0, 1
 
 
 class Opts(ctypes.Structure):
@@ -30,6 +31,7 @@ class Opts(ctypes.Structure):
         ("pcg_iters", ctypes.c_int), ("spatial_prec", ctypes.c_int), ("gmg_smooth", ctypes.c_int),
         ("gmg_omega", ctypes.c_double), ("coarse_tol", ctypes.c_double), ("coarse_max_it", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
+        ("coarse_solver", ctypes.c_int), ("dft_max_it", ctypes.c_int),
     ]
 
     def as_dict(self):
