@@ -79,12 +79,45 @@ def dnu_ds2(s2, nu_min, nu_max, s_sat):
     return (nu_max - nu_min) * c / (s2 + c) ** 2
 
 
+def exp_law(s2, a, b, c, d):
+    """Reluctivity of the paper's transformer materials (Section 4):
+    nu = a min(exp(b s^2), c) + d, s^2 = |grad u|^2."""
+    return a * np.minimum(np.exp(b * s2), c) + d
+
+
+def dexp_law_ds2(s2, a, b, c, d):
+    """Derivative of exp_law with respect to s^2: a b exp(b s^2) below the
+    cap exp(b s^2) < c, 0 above it (the law has a kink at the cap)."""
+    e = np.exp(b * s2)
+    return np.where(e < c, a * b * e, 0.0)
+
+
+def _law_columns(prob, ndim):
+    """The exponential-law constants a, b, c, d per element, shaped to
+    broadcast against an (n_tri, ...) array with `ndim` dimensions."""
+    sh = (-1,) + (1,) * (ndim - 1)
+    return [prob.law_abcd[:, k].reshape(sh) for k in range(4)]
+
+
 def element_nu(prob, s2):
     """nu per element: the nonlinear law on iron, nu_linear elsewhere.
     s2 has shape (n_tri, ...)."""
     iron = prob.nonlinear_e.astype(bool).reshape((-1,) + (1,) * (s2.ndim - 1))
-    return np.where(iron, nu_law(s2, prob.nu_min, prob.nu_max, prob.s_sat),
-                    prob.nu_linear)
+    if prob.law_abcd is not None:
+        law = exp_law(s2, *_law_columns(prob, s2.ndim))
+    else:
+        law = nu_law(s2, prob.nu_min, prob.nu_max, prob.s_sat)
+    return np.where(iron, law, prob.nu_linear)
+
+
+def element_dnu_ds2(prob, s2):
+    """d nu / d s^2 per element (0 on linear elements).  s2: (n_tri, ...)."""
+    iron = prob.nonlinear_e.astype(bool).reshape((-1,) + (1,) * (s2.ndim - 1))
+    if prob.law_abcd is not None:
+        dn = dexp_law_ds2(s2, *_law_columns(prob, s2.ndim))
+    else:
+        dn = dnu_ds2(s2, prob.nu_min, prob.nu_max, prob.s_sat)
+    return np.where(iron, dn, 0.0)
 
 
 def element_gradients(prob, u_full):
@@ -127,12 +160,23 @@ def scatter_matrix(prob):
 def energy(prob, u_full):
     """Magnetic co-energy E(u) = sum_T |T|/2 W(|g_T|^2) with W' = nu, so that
     grad E = K(u).  For the iron law W(x) = nu_max x - (nu_max-nu_min) c ln(1+x/c),
-    c = s_sat^2; for linear elements W(x) = nu_linear x.  Used only to pin K."""
+    c = s_sat^2; for the exponential law W(x) = (a/b)(exp(b min(x, x_c)) - 1)
+    + a c max(x - x_c, 0) + d x with x_c = ln(c)/b; for linear elements
+    W(x) = nu_linear x.  Used only to pin K."""
     area, _ = p1_geometry(prob.xy, prob.tri)
     g = element_gradients(prob, u_full)
     x = np.sum(g * g, axis=1)
-    c = prob.s_sat ** 2
-    W_iron = prob.nu_max * x - (prob.nu_max - prob.nu_min) * c * np.log1p(x / c)
+    if prob.law_abcd is not None:
+        # W(x) = integral of a min(exp(b y), c) + d over [0, x]
+        iron = prob.nonlinear_e.astype(bool)
+        a, b, cc, d = (np.where(iron, prob.law_abcd[:, k], 1.0) for k in range(4))
+        xc = np.log(cc) / b
+        below = a / b * np.expm1(b * np.minimum(x, xc))
+        above = a * cc * np.maximum(x - xc, 0.0)
+        W_iron = below + above + d * x
+    else:
+        c = prob.s_sat ** 2
+        W_iron = prob.nu_max * x - (prob.nu_max - prob.nu_min) * c * np.log1p(x / c)
     W_lin = prob.nu_linear * x
     W = np.where(prob.nonlinear_e.astype(bool), W_iron, W_lin)
     return float(np.sum(0.5 * area * W))
@@ -145,8 +189,7 @@ def K_jacobian(prob, u_full):
     g = element_gradients(prob, u_full)                       # (n_tri, 2)
     s2 = np.sum(g * g, axis=1)
     nu = element_nu(prob, s2)
-    iron = prob.nonlinear_e.astype(bool)
-    dnu = np.where(iron, dnu_ds2(s2, prob.nu_min, prob.nu_max, prob.s_sat), 0.0)
+    dnu = element_dnu_ds2(prob, s2)
     D = nu[:, None, None] * np.eye(2)[None] + 2.0 * dnu[:, None, None] * np.einsum("ea,eb->eab", g, g)
     loc = area[:, None, None] * np.einsum("eia,eab,ejb->eij", grad, D, grad)
     rows = np.repeat(prob.tri, 3, axis=1).ravel()

@@ -35,7 +35,7 @@ class Disc:
     free: np.ndarray      # free node ids (ascending)
     M: sp.csr_matrix      # sigma-weighted consistent mass
     A: sp.csr_matrix      # stiffness with unit coefficient
-    L: sp.csr_matrix      # K_hat = nu_max * A
+    L: sp.csr_matrix      # K_hat = nu_max * A, or sum_T khat_T A_T
     b: np.ndarray         # (n_coils, n_V) coil load vectors
     tau: float
     N: int
@@ -52,8 +52,11 @@ def assemble(prob) -> Disc:
     A = fem.restrict(fem.stiffness(prob.xy, prob.tri, ones), free)
     M = fem.restrict(fem.mass(prob.xy, prob.tri, prob.sigma_e), free)
     b = fem.coil_load(prob)[:, free]
-    return Disc(free=free, M=M, A=A, L=(prob.nu_max * A).tocsr(), b=b,
-                tau=prob.T / prob.N, N=prob.N)
+    if prob.khat_e is not None:   # K_hat = sum_T khat_T A_T (element weights of the problem)
+        L = fem.restrict(fem.stiffness(prob.xy, prob.tri, prob.khat_e), free)
+    else:
+        L = (prob.nu_max * A).tocsr()
+    return Disc(free=free, M=M, A=A, L=L, b=b, tau=prob.T / prob.N, N=prob.N)
 
 
 def lift(prob, disc, U):
@@ -219,6 +222,55 @@ def fixed_point(prob, disc=None, U0=None, tol=1e-10, max_it=10000,
         converged = r <= tol * r0
     return FixedPointResult(U=U, iterations=k, res_history=hist,
                             step_knorms=steps, converged=converged)
+
+
+# ---------------------------------------------------------------------------
+# Initialisation (Section 4): the decoupled nonlinear static problems
+# ---------------------------------------------------------------------------
+
+def static_jacobian(prob, disc, U):
+    """Block-diagonal Jacobian of U -> (K(u^1)..K(u^N)) in the (n_V, N) C-order
+    layout: block n is DK(u^n) restricted to the free nodes."""
+    n, N = U.shape
+    full = lift(prob, disc, U)
+    rows, cols, vals = [], [], []
+    for j in range(N):
+        D = fem.restrict(fem.K_jacobian(prob, full[:, j]), disc.free).tocoo()
+        rows.append(D.row * N + j); cols.append(D.col * N + j); vals.append(D.data)
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n * N, n * N))
+
+
+def static_solve(prob, disc=None, tol=1e-14, max_it=60, F=None):
+    """The initialisation of Section 4: with sigma = 0 the mass term drops and
+    the time steps decouple into the nonlinear static problems
+        K(u^n) = f^n,   n = 1..N.
+    Solved here by Newton with step halving on ||F - K(U)|| (all N problems
+    at once through the block-diagonal Jacobian, sparse direct solves), from
+    U = 0, until ||F - K(U)|| <= tol ||F||."""
+    if disc is None:
+        disc = assemble(prob)
+    if F is None:
+        F = source(prob, disc)
+    U = np.zeros((disc.n, disc.N))
+    R = F - K_free(prob, disc, U)
+    r0 = float(np.linalg.norm(R))
+    r = r0
+    for _ in range(max_it):
+        if r <= tol * max(r0, 1e-300):
+            break
+        J = static_jacobian(prob, disc, U).tocsc()
+        dU = spla.spsolve(J, R.ravel()).reshape(U.shape)
+        t = 1.0
+        while True:
+            Un = U + t * dU
+            Rn = F - K_free(prob, disc, Un)
+            rn = float(np.linalg.norm(Rn))
+            if rn < r or t < 1e-4:
+                break
+            t *= 0.5
+        U, R, r = Un, Rn, rn
+    return U, r / max(r0, 1e-300)
 
 
 # ---------------------------------------------------------------------------

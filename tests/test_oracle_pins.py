@@ -324,3 +324,164 @@ def test_newton_jacobian_matches_differences():
     h = 1e-7
     fd = (P.A_apply(prob, d, U + h * V) - P.A_apply(prob, d, U - h * V)) / (2 * h)
     np.testing.assert_allclose((J @ V.ravel()).reshape(V.shape), fd, rtol=1e-6, atol=1e-7)
+
+
+# --------------------------------------------------------------------------
+# Initialisation (Section 4): the decoupled static problems K(u^n) = f^n
+# --------------------------------------------------------------------------
+
+def test_static_solve_linear_material_is_a_linear_solve():
+    """nu = c on every element makes K = c A, so the static problems are the
+    linear systems c A u^n = f^n (a library sparse solve)."""
+    c = 40.0
+    prob = W.unit_square_problem(9, 6)
+    prob = prob.replace(nonlinear_e=np.zeros(prob.n_tri, np.uint8), nu_linear=c)
+    d = P.assemble(prob)
+    F = P.source(prob, d)
+    U, rel = P.static_solve(prob, d)
+    ref = sp.linalg.spsolve((c * d.A).tocsc(), F)
+    assert rel < 1e-14
+    assert np.linalg.norm(U - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_static_solve_residual_zero_source_and_odd_symmetry():
+    """A strongly saturated case reaches K(U) = F to rounding; K is odd, so
+    -F gives -U; zero source gives U = 0."""
+    prob = W.unit_square_problem(9, 4, amps=(4000.0,))
+    d = P.assemble(prob)
+    F = P.source(prob, d)
+    U, rel = P.static_solve(prob, d)
+    assert rel < 1e-13
+    assert np.linalg.norm(F - P.K_free(prob, d, U)) <= 1e-12 * np.linalg.norm(F)
+    full = P.lift(prob, d, U)
+    s = np.sqrt((fem.element_gradients(prob, full) ** 2).sum(axis=1))
+    iron = prob.nonlinear_e.astype(bool)
+    assert s[iron].max() > prob.s_sat   # the iron saturates: nu is not constant
+    Um, _ = P.static_solve(prob, d, F=-F)
+    assert np.abs(Um + U).max() <= 1e-12 * np.abs(U).max()
+    Z, _ = P.static_solve(prob, d, F=np.zeros_like(F))
+    assert np.abs(Z).max() == 0.0
+
+
+def test_static_solve_is_the_zero_conductivity_periodic_solution():
+    """With sigma = 0 the mass term of Problem 1 vanishes and the time steps
+    decouple: the periodic fixed point (exact inner solves) equals the static
+    solutions.  The same holds for N = 1 with any sigma, since u^0 = u^1
+    cancels the mass term."""
+    prob = W.unit_square_problem(9, 4, amps=(3000.0,))
+    prob0 = prob.replace(sigma_e=np.zeros(prob.n_tri))
+    d0 = P.assemble(prob0)
+    U, _ = P.static_solve(prob0, d0)
+    res = P.fixed_point(prob0, d0, tol=1e-14, max_it=20000)
+    assert res.converged
+    assert np.linalg.norm(res.U - U) <= 1e-11 * np.linalg.norm(U)
+    prob1 = W.unit_square_problem(9, 1, amps=(3000.0,))
+    d1 = P.assemble(prob1)
+    U1, _ = P.static_solve(prob1, d1)
+    res1 = P.fixed_point(prob1, d1, tol=1e-14, max_it=20000)
+    assert res1.converged
+    assert np.linalg.norm(res1.U - U1) <= 1e-11 * np.linalg.norm(U1)
+
+
+def test_static_jacobian_matches_differences():
+    prob = W.unit_square_problem(6, 3, amps=(2000.0,))
+    d = P.assemble(prob)
+    rng = np.random.default_rng(8)
+    U = rng.normal(scale=0.05, size=(d.n, d.N))
+    V = rng.normal(size=(d.n, d.N))
+    J = P.static_jacobian(prob, d, U)
+    h = 1e-7
+    fd = (P.K_free(prob, d, U + h * V) - P.K_free(prob, d, U - h * V)) / (2 * h)
+    np.testing.assert_allclose((J @ V.ravel()).reshape(V.shape), fd, rtol=1e-6, atol=1e-7)
+
+
+# --------------------------------------------------------------------------
+# The paper's transformer (Section 4): exponential law, K_hat weights
+# --------------------------------------------------------------------------
+
+def test_exp_law_closed_forms():
+    """nu = a min(exp(b s^2), c) + d: a + d at zero field, a c + d above the
+    cap s^2 = ln(c)/b, continuous there; the paper's iron and steel constants
+    make the saturated value the air value 1e7/(4 pi) to within 0.01%."""
+    for key in ("iron", "steel"):
+        _, a, b, c, d = W.PAPER_MATERIALS[key]
+        assert fem.exp_law(0.0, a, b, c, d) == a + d
+        xc = math.log(c) / b
+        assert fem.exp_law(xc * (1 + 1e-12), a, b, c, d) == pytest.approx(a * c + d, rel=1e-10)
+        assert fem.exp_law(xc * (1 - 1e-12), a, b, c, d) == pytest.approx(a * c + d, rel=1e-9)
+        assert fem.exp_law(4 * xc, a, b, c, d) == a * c + d
+        assert abs(a * c + d - W.PAPER_NU_AIR) < 1e-4 * W.PAPER_NU_AIR
+        x = 0.3 * xc
+        assert fem.exp_law(x, a, b, c, d) == pytest.approx(a * math.exp(b * x) + d, rel=1e-15)
+        assert fem.dexp_law_ds2(x, a, b, c, d) == pytest.approx(a * b * math.exp(b * x), rel=1e-15)
+        assert fem.dexp_law_ds2(2 * xc, a, b, c, d) == 0.0
+
+
+def _paper_small(N=4, scale=1.0):
+    prob = W.paper_transformer_problem(21, 27, N)
+    return prob.replace(amp=prob.amp * scale)
+
+
+def test_exp_law_K_is_gradient_of_coenergy_and_jacobian():
+    """With the exponential law K(u) = grad E(u) and DK = d K / du, checked by
+    central differences on a field that puts elements on both sides of the
+    cap (s of a few tesla)."""
+    prob = _paper_small()
+    rng = np.random.default_rng(21)
+    u = rng.normal(size=prob.n_nodes) * 0.04
+    u[prob.dirichlet == 1] = 0.0
+    g = fem.element_gradients(prob, u)
+    s2 = (g * g).sum(axis=1)
+    iron = prob.nonlinear_e.astype(bool)
+    xc = np.log(prob.law_abcd[iron, 2]) / prob.law_abcd[iron, 1]
+    assert (s2[iron] > xc).any() and (s2[iron] < xc).any()
+    K = fem.K_apply(prob, u)
+    v = rng.normal(size=prob.n_nodes)
+    v[prob.dirichlet == 1] = 0.0
+    h = 1e-9
+    dE = (fem.energy(prob, u + h * v) - fem.energy(prob, u - h * v)) / (2 * h)
+    assert dE == pytest.approx(float(K @ v), rel=1e-6)
+    J = fem.K_jacobian(prob, u)
+    fd = (fem.K_apply(prob, u + h * v) - fem.K_apply(prob, u - h * v)) / (2 * h)
+    np.testing.assert_allclose(J @ v, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+
+
+def test_khat_weights_assemble_the_weighted_stiffness():
+    """K_hat = sum_T khat_T A_T: a constant weight gives khat A; the weight of
+    one right triangle with legs h gives its textbook element matrix
+    [[1,-1,0],[-1,2,-1],[0,-1,1]]/2 (vertices in the order of the split)."""
+    prob = _paper_small()
+    free = prob.interior
+    A = fem.restrict(fem.stiffness(prob.xy, prob.tri, np.ones(prob.n_tri)), free)
+    L = P.assemble(prob.replace(khat_e=np.full(prob.n_tri, 7.5))).L
+    assert abs(L - 7.5 * A).max() < 1e-12
+    # element 0 = [(0,0), (1,0), (1,1)] of cell (0,0): legs h_x, h_y
+    w = np.zeros(prob.n_tri)
+    w[0] = 1.0
+    Kel = fem.stiffness(prob.xy, prob.tri, w).toarray()
+    hx = prob.xy[1, 0] - prob.xy[0, 0]
+    hy = prob.xy[prob.grid[0], 1] - prob.xy[0, 1]
+    t = prob.tri[0]
+    ref = np.array([[hy / hx, -hy / hx, 0.0],
+                    [-hy / hx, hy / hx + hx / hy, -hx / hy],
+                    [0.0, -hx / hy, hx / hy]]) / 2.0
+    np.testing.assert_allclose(Kel[np.ix_(t, t)], ref, rtol=1e-12, atol=1e-15)
+
+
+def test_paper_transformer_fixed_point_matches_newton_and_linear_limit():
+    """The fixed point with the zero-field K_hat weights reaches the unique
+    solution found by the independent Newton solver; at a tiny current the
+    problem is linear with nu = a + d on iron and steel."""
+    prob = _paper_small()
+    d = P.assemble(prob)
+    Un, r = P.newton(prob, d, tol=1e-14)
+    assert r < 1e-12
+    res = P.fixed_point(prob, d, tol=1e-14, max_it=200)
+    assert res.converged
+    assert np.linalg.norm(res.U - Un) <= 1e-11 * np.linalg.norm(Un)
+    small = _paper_small(scale=1e-6)
+    ds = P.assemble(small)
+    Us = P.fixed_point(small, ds, tol=1e-14, max_it=50).U
+    # linear reference: K = K_hat (nu = a + d on iron and steel), one exact periodic solve
+    ref = P.DFTSolver(ds.M, ds.L, ds.tau, ds.N).solve(P.source(small, ds))
+    assert np.linalg.norm(Us - ref) <= 1e-9 * np.linalg.norm(ref)

@@ -12,9 +12,13 @@ The problem is the 2D magneto-quasistatic model of the paper's Section 4
 synthetic geometries: a unit square with an iron block and strip coils, and a
 transformer-shaped 2x1 rectangle with an iron frame and two window coils.
 
-Material law (iron elements): nu(s) = nu_min + (nu_max - nu_min) s^2/(s^2 + s_sat^2).
-Non-iron elements use the constant nu_linear. The source in coil c is the
-element-constant current density amp_c * sin(2 pi t / T + phase_c).
+Material law (iron elements): nu(s) = nu_min + (nu_max - nu_min) s^2/(s^2 + s_sat^2),
+or, when a problem carries per-element law constants `law_abcd` (the paper's
+transformer, Section 4), nu(s) = a min(exp(b s^2), c) + d.  Non-iron elements
+use the constant nu_linear.  The source in coil c is the element-constant
+current density amp_c * sin(2 pi t / T + phase_c).  `khat_e`, when present,
+gives per-element weights of the linear operator K_hat = sum_T khat_T A_T of
+the fixed-point iteration (else K_hat = nu_max A).
 """
 from __future__ import annotations
 
@@ -35,6 +39,8 @@ __all__ = [
     "config_batched",
     "one_node_problem",
     "delaunay_problem",
+    "paper_transformer_problem",
+    "config_paper_transformer",
 ]
 
 
@@ -58,6 +64,8 @@ class Problem:
     T: float
     N: int
     grid: tuple | None = None  # (nx, ny, x0, y0, x1, y1) when structured
+    law_abcd: np.ndarray | None = None  # (n_tri, 4) a, b, c, d of the exponential law, or None
+    khat_e: np.ndarray | None = None    # (n_tri,) weights of K_hat, or None (nu_max everywhere)
 
     @property
     def n_nodes(self) -> int:
@@ -276,3 +284,62 @@ def config_batched(seed: int = 0, count: int = 64,
         out.append(unit_square_problem(n, N, amps=(J0,), s_sat=s_sat,
                                        name=f"batch{k}_n{n}_N{N}"))
     return out
+
+
+# Section 4 of the paper: cross-section of a power transformer (figure of the
+# domain and table of material constants), in metres.  Tank 355 x 466 mm with
+# a 10 mm steel wall; iron core [60,295] x [28,438] mm minus the window
+# [140,215] x [108,358] mm; four windings 13 x 220 mm with lower-left corners
+# at x = 28, 159, 183, 314 mm, y = 123 mm (winding+ at 159 and 314, winding-
+# at 28 and 183); air elsewhere.
+PAPER_MATERIALS = {
+    #         sigma [S/m], a [m/H], b, c, d [m/H]
+    "iron": (0.0, 5.85, 2.196, 136026.0, 23.15),
+    "steel": (1.0e7, 130.171, 1.102, 6112.97, 43.742),
+}
+PAPER_NU_AIR = 1.0e7 / (4.0 * math.pi)   # air and windings [m/H]
+PAPER_J = 1.9e4                          # winding current density amplitude [A/m^2]
+PAPER_T = 0.02                           # period [s]
+
+
+def paper_transformer_problem(nx: int, ny: int, N: int, name: str | None = None) -> Problem:
+    """The paper's transformer on a structured nx x ny node grid over the
+    355 x 466 mm tank (regions by triangle centroid).  Iron and steel follow
+    nu = a min(exp(b s^2), c) + d with the paper's constants; j = +-J cos(2 pi
+    t / T) in the windings (phase pi/2 of the sine convention); T = 0.02 s.
+    K_hat weights: the zero-field reluctivity of each element (a + d on iron
+    and steel, the air value elsewhere)."""
+    mm = 1.0e-3
+    xy, tri, dirichlet = structured_mesh(nx, ny, 0.0, 0.0, 355 * mm, 466 * mm)
+    c = _centroids(xy, tri)
+    box = lambda x0, x1, y0, y1: _in_box(c, ((x0 * mm, x1 * mm), (y0 * mm, y1 * mm)))
+    steel = ~box(10, 345, 10, 456)
+    iron = box(60, 295, 28, 438) & ~box(140, 215, 108, 358)
+    w_plus = box(159, 172, 123, 343) | box(314, 327, 123, 343)
+    w_minus = box(28, 41, 123, 343) | box(183, 196, 123, 343)
+    coil = np.full(tri.shape[0], -1, dtype=np.int32)
+    coil[w_plus] = 0
+    coil[w_minus] = 1
+    n_tri = tri.shape[0]
+    sigma = np.zeros(n_tri)
+    abcd = np.zeros((n_tri, 4))
+    for mask, key in ((iron, "iron"), (steel, "steel")):
+        sg, a, b, cc, d = PAPER_MATERIALS[key]
+        sigma[mask] = sg
+        abcd[mask] = (a, b, cc, d)
+    nonlinear = (iron | steel).astype(np.uint8)
+    khat = np.where(nonlinear == 1, abcd[:, 0] + abcd[:, 3], PAPER_NU_AIR)
+    return Problem(
+        name=name or f"paper_transformer{nx}x{ny}_N{N}", xy=xy, tri=tri, dirichlet=dirichlet,
+        sigma_e=sigma, nonlinear_e=nonlinear, coil_of_elem=coil,
+        amp=np.array([PAPER_J, -PAPER_J]), phase=np.array([0.5 * math.pi, 0.5 * math.pi]),
+        nu_min=1.0, nu_max=1.0, s_sat=1.0, nu_linear=PAPER_NU_AIR, T=PAPER_T, N=int(N),
+        grid=(nx, ny, 0.0, 0.0, 355 * mm, 466 * mm), law_abcd=abcd, khat_e=khat)
+
+
+def config_paper_transformer(size: str = "8208", N: int = 128) -> Problem:
+    """The paper's transformer at its two mesh sizes, matched approximately by
+    structured grids: N_V = 8208 -> 81 x 105 nodes (8137 free), N_V = 32451 ->
+    161 x 209 nodes (32913 free); N in {128, 256, 512}."""
+    nx, ny = {"8208": (81, 105), "32451": (161, 209)}[size]
+    return paper_transformer_problem(nx, ny, N, name=f"paper_transformer{size}_N{N}")
