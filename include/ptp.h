@@ -114,6 +114,12 @@ typedef struct ptp_opts {
                             PTP_COARSE_DFT (time DFT, one complex shifted
                             spatial solve per mode; any N_l <= 1022)          */
     int    dft_max_it;   /* iteration cap of each DFT mode solve (COCG)      */
+    double init_tol;     /* tolerance of the static initialisation (0: tol) */
+    int    init_static;  /* 1: a solve without U0 starts from the static
+                            solutions (initialisation of Section 4)         */
+    double newton_eta;   /* Newton: relative tolerance of each linear solve */
+    int    krylov_dim;   /* Newton: flexible GMRES iterations per linear
+                            solve (1..31, no restart)                        */
 } ptp_opts;
 
 /* Statistics of the last solve. */
@@ -129,6 +135,9 @@ typedef struct ptp_stats {
                                  counted once per replay)                    */
     int    time_levels;       /* levels actually used                        */
     int    spatial_levels;    /* GMG levels actually used (1 = none)         */
+    double init_ms;           /* wall time of the static initialisation      */
+    int    init_iterations;   /* its fixed-point steps (0: not run)          */
+    int    inner_iterations;  /* Newton: Krylov iterations of all steps      */
 } ptp_stats;
 
 void        ptp_default_opts(ptp_opts* opts);
@@ -172,6 +181,20 @@ int ptp_set_structured(ptp_ctx* ctx, int nx, int ny, double x0, double y0,
 int ptp_set_materials(ptp_ctx* ctx, const double* sigma_e,
                       const uint8_t* nonlinear_e, double nu_min,
                       double nu_max, double s_sat, double nu_linear);
+
+/* Reluctivity law of the paper's transformer (Section 4, "Test problem") on
+   the nonlinear elements instead of the saturating law:
+       nu(s) = a min(exp(b s^2), c) + d,
+   abcd[4 * n_tri] = (a, b, c, d) per element, read on nonlinear elements
+   only (a >= 0, b > 0, c >= 1, d > 0).  NULL restores the saturating law.
+   Call after ptp_set_materials.  The adjoint entry points reject this law. */
+int ptp_set_law_exp(ptp_ctx* ctx, const double* abcd);
+
+/* Per-element weights of the linear operator of the fixed-point iteration,
+   K_hat = sum_T khat_e[T] A_T (A_T the unit-coefficient element stiffness;
+   eq. iter1, Theorem 3 allows any linear symmetric elliptic K_hat).  khat_e:
+   n_tri positive doubles; NULL restores K_hat = nu_max A. */
+int ptp_set_khat(ptp_ctx* ctx, const double* khat_e);
 
 /* Coils: coil_of_elem[n_tri] in [-1, n_coils), amplitude and phase per
    coil; the current density on coil c is amp_c sin(2 pi t/T + phase_c). */
@@ -284,6 +307,38 @@ int ptp_spatial_solve_f32_dev(ptp_ctx* ctx, int level, const float* B, float* X,
    *relres receives ||b - P x|| / ||b|| (may be NULL).  Synchronises. */
 int ptp_periodic_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* B,
                            double* X, int cycles, double* relres);
+
+/* Initialisation of Section 4: the decoupled nonlinear static problems
+   K(u^n) = f^n, n = 1..N (sigma = 0, so the mass term drops), solved for all
+   N steps at once by eq. (iter1) with M = 0:  L d^n = f^n - K(u^n),
+   u^n <- u^n + d^n, each spatial solve a batched multigrid-preconditioned PCG
+   (opts->pcg_iters iterations), from U = 0 until
+   ||F - K(U)||_2 <= init_tol ||F||_2 (init_tol 0: opts->tol).  U: [n_free][N]
+   doubles, host (ptp_static_solve) or device (ptp_static_solve_dev, which
+   synchronises).  Returns PTP_ENOTCONV after max_outer steps.  `stats` may be
+   NULL; its outer_iterations and res0/res_final describe this solve. */
+int ptp_static_solve(ptp_ctx* ctx, const ptp_opts* opts, double* U, ptp_stats* stats);
+int ptp_static_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, double* U, ptp_stats* stats);
+
+/* Newton's method for Problem 1 (method (M2) of Section 4): J(U) d = F - A(U)
+   with the Jacobian blocks M/tau + DK(u^n) and -M/tau (cyclic), solved by
+   flexible GMRES (at most krylov_dim iterations, relative tolerance
+   newton_eta) preconditioned by the inner periodic solve of the fixed point
+   (opts->vcycles V-cycles of multigrid in time); then U += t d with Armijo
+   back-tracking t = 1, 1/2, ... on ||F - A(U)||.  Stops when
+   ||F - A(U)|| <= tol ||F - A(U^0)|| or after max_outer Newton steps.  U0:
+   NULL = zero start (or the static solutions with init_static).  Saturating
+   law only (PTP_EINVAL for the exponential law).  Host (ptp_newton_solve) or
+   device pointers (ptp_newton_solve_dev, which synchronises).  stats:
+   outer_iterations = Newton steps, inner_iterations = Krylov iterations. */
+int ptp_newton_solve(ptp_ctx* ctx, const ptp_opts* opts, const double* U0, double* U,
+                     ptp_stats* stats);
+int ptp_newton_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* U0,
+                         double* U, ptp_stats* stats);
+
+/* Y = J(U) V, the Jacobian of A at U applied to V (all device pointers,
+   [n_free][N] doubles; synchronises).  Saturating law only. */
+int ptp_jacobian_apply_dev(ptp_ctx* ctx, const double* U, const double* V, double* Y);
 
 /* Fixed-point solve of Problem 1 (eq. iter1-iter2 in correction form) from
    U0 (NULL = zero start) to opts->tol; U receives the last iterate.

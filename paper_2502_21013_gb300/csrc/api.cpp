@@ -1,9 +1,10 @@
 // C ABI of the library (declared in include/ptp.h).  Every entry point
 // catches exceptions and turns them into status codes and a message.
 #include <chrono>
+#include <cmath>
 #include <cstring>
 
-#include "common.h"
+#include "kernels.h"
 
 using ptp::Ctx;
 using ptp::Error;
@@ -52,7 +53,7 @@ void need_ready(const Ctx& c) {
 
 void invalidate(Ctx& c) {
     c.ready = false;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         if (c.graph_exec[k]) {
             cudaGraphExecDestroy(c.graph_exec[k]);
             c.graph_exec[k] = nullptr;
@@ -105,6 +106,10 @@ void ptp_default_opts(ptp_opts* o) {
     o->coarse_cycles = 8;
     o->coarse_solver = PTP_COARSE_VCYCLES;
     o->dft_max_it = 30;
+    o->init_tol = 0.0;
+    o->init_static = 0;
+    o->newton_eta = 1e-3;
+    o->krylov_dim = 30;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }
@@ -193,6 +198,43 @@ int ptp_set_materials(ptp_ctx* h, const double* sigma_e, const uint8_t* nonlinea
         c.s_sat = s_sat;
         c.nu_linear = nu_linear;
         c.have_materials = true;
+        invalidate(c);
+        return PTP_OK;
+    }, false);
+}
+
+int ptp_set_law_exp(ptp_ctx* h, const double* abcd) {
+    return guarded(h, [&](Ctx& c) {
+        PTP_REQUIRE(c.have_materials, "ptp_set_law_exp: set the materials first");
+        if (!abcd) {
+            c.law_exp = false;
+            c.law_abcd.clear();
+        } else {
+            for (int e = 0; e < c.n_tri; ++e) {
+                if (!c.nonlinear[e]) continue;
+                const double* L = abcd + 4 * (size_t)e;
+                PTP_REQUIRE(L[0] >= 0.0 && L[1] > 0.0 && L[2] >= 1.0 && L[3] > 0.0 && std::isfinite(L[0]) &&
+                                std::isfinite(L[1]) && std::isfinite(L[2]) && std::isfinite(L[3]),
+                            "ptp_set_law_exp: need a >= 0, b > 0, c >= 1, d > 0 on every nonlinear element");
+            }
+            c.law_abcd.assign(abcd, abcd + 4 * (size_t)c.n_tri);
+            c.law_exp = true;
+        }
+        invalidate(c);
+        return PTP_OK;
+    }, false);
+}
+
+int ptp_set_khat(ptp_ctx* h, const double* khat_e) {
+    return guarded(h, [&](Ctx& c) {
+        PTP_REQUIRE(c.n_tri > 0, "ptp_set_khat: set the mesh first");
+        if (!khat_e) {
+            c.khat.clear();
+        } else {
+            for (int e = 0; e < c.n_tri; ++e)
+                PTP_REQUIRE(khat_e[e] > 0.0 && std::isfinite(khat_e[e]), "ptp_set_khat: weights must be positive");
+            c.khat.assign(khat_e, khat_e + c.n_tri);
+        }
         invalidate(c);
         return PTP_OK;
     }, false);
@@ -434,6 +476,78 @@ int ptp_solve_dev(ptp_ctx* h, const ptp_opts* opts, const double* U0, double* U,
         PTP_REQUIRE(o.max_outer >= 1 && o.tol >= 0, "ptp_solve: bad options");
         if (stats) std::memset(stats, 0, sizeof(*stats));
         return ptp::solve(c, o, U0, U, stats);
+    });
+}
+
+int ptp_static_solve_dev(ptp_ctx* h, const ptp_opts* opts, double* U, ptp_stats* stats) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        ptp_opts o = opts ? *opts : c.opts;
+        PTP_REQUIRE(o.max_outer >= 1 && o.tol >= 0 && o.init_tol >= 0, "ptp_static_solve: bad options");
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return ptp::solve(c, o, nullptr, U, stats, ptp::STEP_STATIC);
+    });
+}
+
+int ptp_static_solve(ptp_ctx* h, const ptp_opts* opts, double* U, ptp_stats* stats) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        ptp_opts o = opts ? *opts : c.opts;
+        PTP_REQUIRE(o.max_outer >= 1 && o.tol >= 0 && o.init_tol >= 0, "ptp_static_solve: bad options");
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        int rc = ptp::solve(c, o, nullptr, nullptr, stats, ptp::STEP_STATIC);
+        if (U) {
+            const size_t cnt = (size_t)c.n * c.N;
+            PTP_CUDA(cudaMemcpyAsync(U, c.U.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            PTP_CUDA(cudaStreamSynchronize(c.stream));
+        }
+        return rc;
+    });
+}
+
+int ptp_newton_solve_dev(ptp_ctx* h, const ptp_opts* opts, const double* U0, double* U, ptp_stats* stats) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        ptp_opts o = opts ? *opts : c.opts;
+        PTP_REQUIRE(o.max_outer >= 1 && o.tol >= 0, "ptp_newton_solve: bad options");
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return ptp::newton_solve(c, o, U0, U, stats);
+    });
+}
+
+int ptp_newton_solve(ptp_ctx* h, const ptp_opts* opts, const double* U0, double* U, ptp_stats* stats) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        ptp_opts o = opts ? *opts : c.opts;
+        PTP_REQUIRE(o.max_outer >= 1 && o.tol >= 0, "ptp_newton_solve: bad options");
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        const size_t cnt = (size_t)c.n * c.N;
+        Staging s0;
+        double* d0 = nullptr;
+        if (U0) {
+            d0 = s0.get(cnt);
+            PTP_CUDA(cudaMemcpyAsync(d0, U0, cnt * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+        }
+        int rc = ptp::newton_solve(c, o, d0, nullptr, stats);
+        if (U) {
+            PTP_CUDA(cudaMemcpyAsync(U, c.U.p, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+            PTP_CUDA(cudaStreamSynchronize(c.stream));
+        }
+        return rc;
+    });
+}
+
+int ptp_jacobian_apply_dev(ptp_ctx* h, const double* U, const double* V, double* Y) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        PTP_REQUIRE(U && V && Y, "ptp_jacobian_apply_dev: null pointer");
+        PTP_REQUIRE(!c.law_exp, "ptp_jacobian_apply_dev: saturating reluctivity law only");
+        ptp::alloc_adjoint(c);
+        c.launches += ptp::launch_adj_jacobian(ptp::adjoint_args(c), U, c.stream, false);
+        ptp::jacobian_apply(c, V, Y);
+        PTP_CUDA(cudaStreamSynchronize(c.stream));
+        PTP_CUDA(cudaGetLastError());
+        return PTP_OK;
     });
 }
 

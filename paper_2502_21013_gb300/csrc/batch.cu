@@ -132,7 +132,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
             o.coarse_steps = cs[i]->opts.coarse_steps;
             o.coarse_solver = cs[i]->opts.coarse_solver;
             ptp::set_row_block(cs[i]->row_block);
-            ptp::solve_begin(*cs[i], o, nullptr, false);
+            ptp::solve_begin(*cs[i], o, nullptr, ptp::STEP_FORWARD);
         }
         // capture one step of every instance (re-captured when any step changes)
         std::vector<int64_t> keys(K);
@@ -152,7 +152,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
                 for (int i = 0; i < K; ++i) {
                     PTP_CUDA(cudaStreamWaitEvent(cs[i]->stream, b->events[K], 0));
                     ptp::set_row_block(cs[i]->row_block);
-                    b->per_step[i] = ptp::enqueue_step(*cs[i], false);
+                    b->per_step[i] = ptp::enqueue_step(*cs[i], ptp::STEP_FORWARD);
                     PTP_CUDA(cudaEventRecord(b->events[i], cs[i]->stream));
                     PTP_CUDA(cudaStreamWaitEvent(b->stream, b->events[i], 0));
                 }
@@ -208,7 +208,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
             ptp::set_row_block(cs[i]->row_block);
             ptp_stats st;
             std::memset(&st, 0, sizeof(st));
-            const int rc = ptp::solve_end(*cs[i], &st, false, (int64_t)launched * b->per_step[i], wall, ms);
+            const int rc = ptp::solve_end(*cs[i], &st, ptp::STEP_FORWARD, (int64_t)launched * b->per_step[i], wall, ms);
             if (stats) stats[i] = st;
             if (rc == PTP_OK) ++conv;
             else if (worst == PTP_OK || rc == PTP_ENAN) worst = rc;

@@ -151,6 +151,9 @@ struct Ctx {
     std::vector<uint8_t> nonlinear;
     double nu_min = 1, nu_max = 100, s_sat = 1, nu_linear = 100;
     bool have_materials = false;
+    bool law_exp = false;             // iron follows a min(exp(b s^2), c) + d (Section 4)
+    std::vector<double> law_abcd;     // 4 per element: a, b, c, d
+    std::vector<double> khat;         // per-element weights of K_hat (empty: nu_max everywhere)
     int n_coils = 0;
     std::vector<int> coil_of_elem;
     std::vector<double> amp, phase;
@@ -170,9 +173,11 @@ struct Ctx {
     int n_iron = 0;             // iron (nonlinear) elements
     DBuf<int> e_nodes;          // 3 per iron element, free index or -1
     DBuf<double> e_geo;         // 6 per iron element: g1x g1y g2x g2y |T| nu_max, |T| dnu s_sat^2
+    DBuf<double> e_law;         // exponential law: 4 per iron element |T| a, b, ln c, |T| d
     DBuf<int> inc_ptr, inc_elem;// node -> incident iron elements
     DBuf<double> inc_grad;      // 2 per incidence: grad phi_i on that element
     DBuf<int> m_ptr, m_idx;     // mass rows (only nonzero entries), scaled 1/tau
+    DBuf<int> zero_ptr;         // n + 1 zeros: a mass pattern with every row empty (sigma = 0)
     DBuf<double> m_val;
     DBuf<int> l_ptr, l_idx;     // stiffness of the linear elements (nu_linear)
     DBuf<double> l_val;
@@ -190,6 +195,8 @@ struct Ctx {
     DBuf<uint8_t> all_iron;
     DBuf<double> Jc, Lam, Gadj, Ustar;  // adjoint work (allocated on first use)
     DBuf<double> adj_scal;
+    // Newton (method M2): Krylov bases, trial iterate and residual, device scalars
+    DBuf<double> kr_v, kr_z, kr_w, kr_t, kr_r, kr_d, kr_s;
 
     // spatial hierarchy (level 0 = the mesh itself)
     std::vector<SpatialLevel> sl;
@@ -226,11 +233,11 @@ struct Ctx {
     DBuf<int> flag;              // device early-exit flags
     int red_blocks = 0;          // blocks of reduction kernels
 
-    // CUDA graphs of one outer step: [0] forward solve, [1] adjoint solve
-    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
-    int64_t graph_key[2] = {-1, -1};
+    // CUDA graphs of one outer step, per step kind (STEP_FORWARD, STEP_ADJOINT, STEP_STATIC)
+    cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
+    int64_t graph_key[3] = {-1, -1, -1};
     int64_t launches = 0;        // kernels issued (counting while capturing)
-    int64_t launches_per_step = 0;
+    int64_t launches_per_step[3] = {0, 0, 0};
     int row_block = 256;         // threads per block of the row kernels (autotuned)
 
     ~Ctx();
@@ -241,6 +248,9 @@ void build_problem(Ctx& c);       // free numbering, K1 data, mass, coils
 void build_hierarchy(Ctx& c);     // spatial levels, time levels, op pairs
 void make_structured_mesh(Ctx& c, int nx, int ny, double x0, double y0, double x1, double y1);
 void upload_csr(DevCSR& d, const HostCSR& a, const HostCSR* b, bool diag, cudaStream_t s);
+
+// kinds of fixed-point step (solver.cu)
+enum StepKind { STEP_FORWARD = 0, STEP_ADJOINT = 1, STEP_STATIC = 2 };
 
 // ---- solver.cu ----
 void alloc_work(Ctx& c);
@@ -257,15 +267,22 @@ void periodic_apply(Ctx& c, int level, const T* X, T* Y);
 template <typename T>
 int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check);
 void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres);
-int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st, bool adjoint = false);
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st, int kind = STEP_FORWARD);
 int adjoint_gradient(Ctx& c, const ptp_opts& o, const double* U, double* J, double* dJ_damp, double* dJ_dnu,
                      double* dJ_dsigma, ptp_stats* st);
 double loss_dev(Ctx& c, const double* U);
-void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint);
+void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, int kind);
 int64_t step_key(const Ctx& c, const ptp_opts& o);
-int64_t enqueue_step(Ctx& c, bool adjoint);
-int solve_end(Ctx& c, ptp_stats* stats, bool adjoint, int64_t step_launches, double solve_ms, float dev_ms);
+int64_t enqueue_step(Ctx& c, int kind);
+int solve_end(Ctx& c, ptp_stats* stats, int kind, int64_t step_launches, double solve_ms, float dev_ms);
 int autotune(Ctx& c, double* best_us);     // picks c.row_block by timing the level-0 SpMM
+void require_coarse(const Ctx& c);         // the time hierarchy has an exact last-level solve
+void alloc_adjoint(Ctx& c);                // Jacobian coefficients and adjoint work
+void mg_precondition(Ctx& c, const double* v, double* z);   // z = inner periodic solve of v
+
+// ---- newton.cpp ----
+int newton_solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st);
+void jacobian_apply(Ctx& c, const double* V, double* Y);    // Y = J(U) V, coefficients of U in c.Jc
 void set_row_block(int threads);           // row-kernel block size for launches from this thread
 
 }  // namespace ptp

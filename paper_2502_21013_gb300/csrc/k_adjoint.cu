@@ -71,9 +71,10 @@ __device__ __forceinline__ void elem_grad(const int* e_nodes, const double* G, c
 }
 
 // Jacobian coefficients of the iron elements at every step:
-// A = |T| [nu I + 2 nu'(s^2) g g^T] as (a11, a12, a22), stored at reversed column.
+// A = |T| [nu I + 2 nu'(s^2) g g^T] as (a11, a12, a22), stored at the reversed
+// column (adjoint) or at the step's own column (Newton's forward Jacobian).
 __global__ void __launch_bounds__(kBlock)
-k_adj_jacobian(AdjointArgs a, const double* __restrict__ U) {
+k_adj_jacobian(AdjointArgs a, const double* __restrict__ U, int reversed) {
     pdl_enter();
     const int N = a.N;
     const size_t total = (size_t)a.n_iron * N;
@@ -89,7 +90,7 @@ k_adj_jacobian(AdjointArgs a, const double* __restrict__ U) {
         const double dnu_ds2 = dnu * c / (den * den);
         const double A = __ldg(a.e_area + e);
         const double w = 2.0 * dnu_ds2 * A;
-        const size_t o = (size_t)e * N + (N - 1 - n);
+        const size_t o = (size_t)e * N + (reversed ? N - 1 - n : n);
         a.Jc[o] = A * nu + w * gx * gx;
         a.Jc[total + o] = w * gx * gy;
         a.Jc[2 * total + o] = A * nu + w * gy * gy;
@@ -245,9 +246,9 @@ int flat_grid(size_t total) {
 
 }  // namespace
 
-int launch_adj_jacobian(const AdjointArgs& a, const double* U, cudaStream_t s) {
+int launch_adj_jacobian(const AdjointArgs& a, const double* U, cudaStream_t s, bool reversed) {
     if (a.n_iron == 0) return 0;
-    launch_k(k_adj_jacobian, dim3(flat_grid((size_t)a.n_iron * a.N)), dim3(kBlock), s, a, U);
+    launch_k(k_adj_jacobian, dim3(flat_grid((size_t)a.n_iron * a.N)), dim3(kBlock), s, a, U, reversed ? 1 : 0);
     return 1;
 }
 

@@ -1,0 +1,123 @@
+// Vector kernels of the flexible GMRES used by Newton's method (method (M2)
+// of Section 4), in double over whole space-time blocks of `count` values:
+// several dot products against one vector at once, a combination of several
+// basis vectors, and a division by a device scalar.  The dot products are
+// deterministic: per-block partials, then the last block to finish (atomic
+// ticket, no waiting) sums them in block order.
+#include "kernels.h"
+
+namespace ptp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// out[i] = sum_g V[i * stride + g] w[g], i < k <= kMaxKrylovDots
+__global__ void __launch_bounds__(kThreads)
+k_mdot(size_t count, int k, const double* __restrict__ V, size_t stride, const double* __restrict__ w,
+       double* __restrict__ partials, unsigned* counter, double* __restrict__ out) {
+    pdl_enter();
+    double acc[kMaxKrylovDots];
+#pragma unroll
+    for (int i = 0; i < kMaxKrylovDots; ++i) acc[i] = 0.0;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
+        const double wg = __ldg(w + g);
+#pragma unroll
+        for (int i = 0; i < kMaxKrylovDots; ++i)
+            if (i < k) acc[i] = fma(__ldg(V + (size_t)i * stride + g), wg, acc[i]);
+    }
+    __shared__ double sm[kMaxKrylovDots][kThreads / 32];
+    __shared__ bool last;
+#pragma unroll
+    for (int i = 0; i < kMaxKrylovDots; ++i) {
+        if (i >= k) break;
+        const double s = warp_sum(acc[i]);
+        if ((threadIdx.x & 31) == 0) sm[i][threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += sm[i][wi];
+        partials[(size_t)blockIdx.x * k + i] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + (size_t)b * k + i);
+        out[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// w += sign * sum_{i<k} coef[i] V[i * stride + g]
+__global__ void __launch_bounds__(kThreads)
+k_maxpy(size_t count, int k, const double* __restrict__ V, size_t stride, const double* __restrict__ coef,
+        double sign, double* __restrict__ w) {
+    pdl_enter();
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s = fma(__ldg(coef + i), __ldg(V + (size_t)i * stride + g), s);
+        w[g] = fma(sign, s, w[g]);
+    }
+}
+
+// y = x / *h
+__global__ void __launch_bounds__(kThreads)
+k_div_scalar(size_t count, const double* __restrict__ x, const double* __restrict__ h, double* __restrict__ y) {
+    pdl_enter();
+    const double inv = 1.0 / *h;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
+        y[g] = x[g] * inv;
+}
+
+// *x = sqrt(*x) when positive and finite, else 1 (a norm used as a divisor)
+__global__ void k_sqrt_or_one(double* x) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double v = *x;
+        *x = (v > 0.0 && isfinite(v)) ? sqrt(v) : 1.0;
+    }
+}
+
+int grid_of(size_t count) {
+    const size_t want = (count + kThreads - 1) / kThreads;
+    return (int)std::max<size_t>(1, std::min(want, (size_t)num_sms() * 8));
+}
+
+}  // namespace
+
+int launch_mdot(size_t count, int k, const double* V, size_t stride, const double* w, double* partials,
+                unsigned* counter, double* out, cudaStream_t s) {
+    if (k < 1 || k > kMaxKrylovDots) throw Error(PTP_EINVAL, "launch_mdot: 1..32 dot products per launch");
+    launch_k(k_mdot, dim3(grid_of(count)), dim3(kThreads), s, count, k, V, stride, w, partials, counter, out);
+    return 1;
+}
+
+int launch_maxpy(size_t count, int k, const double* V, size_t stride, const double* coef, double sign, double* w,
+                 cudaStream_t s) {
+    if (k < 1) return 0;
+    launch_k(k_maxpy, dim3(grid_of(count)), dim3(kThreads), s, count, k, V, stride, coef, sign, w);
+    return 1;
+}
+
+int launch_div_scalar(size_t count, const double* x, const double* h, double* y, cudaStream_t s) {
+    launch_k(k_div_scalar, dim3(grid_of(count)), dim3(kThreads), s, count, x, h, y);
+    return 1;
+}
+
+int launch_sqrt_or_one(double* x, cudaStream_t s) {
+    launch_k(k_sqrt_or_one, dim3(1), dim3(32), s, x);
+    return 1;
+}
+
+}  // namespace ptp

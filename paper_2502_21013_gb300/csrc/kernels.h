@@ -95,6 +95,9 @@ struct ResidualArgs {
     int check;                // apply the stopping rule in the last block
 };
 int launch_residual(const ResidualArgs& a, cudaStream_t s);  // returns kernels launched
+// the same, with the iron fluxes of the exponential law of Section 4 when e_law
+// (4 per iron element: |T| a, b, ln c, |T| d) is set (k_law.cu)
+int launch_residual_law(const ResidualArgs& a, const double* e_law, cudaStream_t s);
 // residual arguments of a set-up context (scratch pointers point into the context)
 ResidualArgs residual_args(Ctx& c, const double* U, double* R);
 
@@ -122,7 +125,8 @@ struct AdjointArgs {
     double* scalars;          // [0] N*J, [1..kMaxCoils] dJ/damp, [1+kMaxCoils..+3) dJ/dnu
 };
 AdjointArgs adjoint_args(Ctx& c);
-int launch_adj_jacobian(const AdjointArgs& a, const double* U, cudaStream_t s);
+// reversed: store at the reversed column (adjoint); else at the step's column (Newton)
+int launch_adj_jacobian(const AdjointArgs& a, const double* U, cudaStream_t s, bool reversed = true);
 int launch_adj_rhs(const AdjointArgs& a, const double* U, double* Gout, cudaStream_t s);
 int launch_adj_elem_flux(const AdjointArgs& a, const double* Lam, double* Qx, double* Qy, const int* done,
                          cudaStream_t s);
@@ -257,6 +261,17 @@ int launch_cdot_rz(int rows, int D, const double* r, const double* z, ColRed<dou
                    cudaStream_t s);                                  // rho (and bb) or beta
 int launch_cdirection(int rows, int D, const double* z, double* p, ColRed<double> cr, Skip sk,
                       cudaStream_t s);                               // p = z + beta p
+
+// ---------------------------------------------------------------------------
+// Flexible GMRES vectors for Newton's method (k_krylov.cu), double
+// ---------------------------------------------------------------------------
+constexpr int kMaxKrylovDots = 32;   // dot products per k_mdot launch
+int launch_mdot(size_t count, int k, const double* V, size_t stride, const double* w, double* partials,
+                unsigned* counter, double* out, cudaStream_t s);    // out[i] = V_i . w
+int launch_maxpy(size_t count, int k, const double* V, size_t stride, const double* coef, double sign, double* w,
+                 cudaStream_t s);                                    // w += sign sum_i coef_i V_i
+int launch_div_scalar(size_t count, const double* x, const double* h, double* y, cudaStream_t s);   // y = x / *h
+int launch_sqrt_or_one(double* x, cudaStream_t s);   // *x = sqrt(*x), or 1 if not positive
 
 int num_sms();
 // out = a x + b y (elementwise, double), for set-up

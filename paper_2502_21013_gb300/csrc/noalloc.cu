@@ -89,7 +89,7 @@ extern "C" int ptp_residual_noalloc_dev(ptp_ctx* h, const double* U, double* R, 
         a.check = 0;
         // the ticket counter must start at zero; the kernel resets it when done
         PTP_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(unsigned), c.stream));
-        launch_residual(a, c.stream);
+        launch_residual_law(a, c.law_exp ? c.e_law.p : nullptr, c.stream);
         PTP_CUDA(cudaGetLastError());
         return PTP_OK;
     } catch (const Error& e) {

@@ -324,13 +324,15 @@ void build_problem(Ctx& c) {
     std::vector<int> e_nodes(3 * (size_t)std::max(n_iron, 1), -1);
     std::vector<double> e_geo(6 * (size_t)std::max(n_iron, 1), 0.0);
     std::vector<double> e_area(std::max(n_iron, 1), 0.0);
+    std::vector<double> e_law(c.law_exp ? 4 * (size_t)std::max(n_iron, 1) : 0, 0.0);
+    const bool weighted = !c.khat.empty();
     std::vector<int> all_nodes(3 * (size_t)c.n_tri);
     std::vector<double> all_area(c.n_tri);
     std::vector<uint8_t> all_iron(c.n_tri);
     RowAccum MJa(n);
     std::vector<std::vector<std::pair<int, int>>> inc(n);  // (iron element, local vertex)
     std::vector<Geo> geo(c.n_tri);
-    RowAccum Ma(n), Aa(n), Llin(n);
+    RowAccum Ma(n), Aa(n), Llin(n), Lw(weighted ? n : 0);
     std::vector<double> cb((size_t)std::max(c.n_coils, 1) * n, 0.0);
     const double dnu_c = (c.nu_max - c.nu_min) * c.s_sat * c.s_sat;
     for (int e = 0; e < c.n_tri; ++e) {
@@ -351,6 +353,14 @@ void build_problem(Ctx& c) {
             // nu |T| = |T| nu_max - |T| (nu_max - nu_min) s_sat^2 / (s^2 + s_sat^2)
             g[4] = G.area * c.nu_max;
             g[5] = G.area * dnu_c;
+            if (c.law_exp) {
+                const double* L = &c.law_abcd[4 * (size_t)e];
+                double* w = &e_law[4 * (size_t)ie];
+                w[0] = G.area * L[0];
+                w[1] = L[1];
+                w[2] = std::log(L[2]);
+                w[3] = G.area * L[3];
+            }
         }
         for (int a = 0; a < 3; ++a) {
             int i = c.free_id[t[a]];
@@ -367,6 +377,7 @@ void build_problem(Ctx& c) {
                     if (ie >= 0) MJa.add(i, j, mv);
                 }
                 Aa.add(i, j, k);
+                if (weighted) Lw.add(i, j, c.khat[e] * k);
                 if (ie < 0) Llin.add(i, j, c.nu_linear * k);
             }
             if (c.n_coils > 0 && c.coil_of_elem[e] >= 0)
@@ -376,6 +387,7 @@ void build_problem(Ctx& c) {
     c.n_iron = n_iron;
     c.e_nodes.upload(e_nodes, s);
     c.e_geo.upload(e_geo, s);
+    if (c.law_exp) c.e_law.upload(e_law, s); else c.e_law.release();
     c.e_area.upload(e_area, s);
     c.all_nodes.upload(all_nodes, s);
     c.all_area.upload(all_area, s);
@@ -414,6 +426,7 @@ void build_problem(Ctx& c) {
         std::vector<double> mv(M.val);
         for (auto& v : mv) v /= tau;
         c.m_ptr.upload(M.ptr, s);
+        c.zero_ptr.upload(std::vector<int>((size_t)n + 1, 0), s);
         c.m_idx.upload(M.idx, s);
         c.m_val.upload(mv, s);
         HostCSR Ll = Llin.finish(n, true);
@@ -421,8 +434,14 @@ void build_problem(Ctx& c) {
         c.l_idx.upload(Ll.idx, s);
         c.l_val.upload(Ll.val, s);
     }
+    // K_hat: nu_max A, or sum_T khat_T A_T with the per-element weights
     HostCSR L = A;
-    for (auto& v : L.val) v *= c.nu_max;
+    if (weighted) {
+        HostCSR Lk = Lw.finish(n, false);
+        L.val = values_on(A, Lk);
+    } else {
+        for (auto& v : L.val) v *= c.nu_max;
+    }
 
     // spatial level 0
     c.sl.clear();

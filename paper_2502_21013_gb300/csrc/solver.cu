@@ -39,6 +39,9 @@ Ctx::~Ctx() {
 
 namespace {
 
+// per-iron-element constants of the exponential law, or null for the saturating law
+const double* law_data(const Ctx& c) { return c.law_exp ? c.e_law.p : nullptr; }
+
 template <typename T> T* wbuf(Ctx& c, int k);
 template <> double* wbuf<double>(Ctx& c, int k) { return c.w_d[k].p; }
 template <> float* wbuf<float>(Ctx& c, int k) { return c.w_f[k].p; }
@@ -431,13 +434,20 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
 }
 
 // One outer step of the fixed point (correction form of eq. iter1) on the
-// iterate X: the forward problem (X = U, residual F - A(U)) or the adjoint
-// (X = lambda in reversed time, residual g - (dA/dU)^T lambda).
+// iterate X:
+//   STEP_FORWARD  X = U, residual F - A(U), periodic inner solve;
+//   STEP_ADJOINT  X = lambda in reversed time, residual g - (dA/dU)^T lambda;
+//   STEP_STATIC   X = U with sigma = 0 (the initialisation of Section 4): the
+//                 mass term drops, the steps decouple, and the inner solve is
+//                 tau_c L x = tau_c (F - K(U)) for every column (batched PCG
+//                 with the spatial multigrid preconditioner), i.e. eq. (iter1)
+//                 with M = 0.
 template <typename T>
-void outer_step(Ctx& c, Skip sk, bool adjoint) {
+void outer_step(Ctx& c, Skip sk, int kind) {
+    const bool adjoint = kind == STEP_ADJOINT;
     double* X = adjoint ? c.Lam.p : c.U.p;
     ResidualArgs a = residual_args(c, X, nullptr);
-    a.scale = c.T / c.N;
+    a.scale = kind == STEP_STATIC ? c.tl.back().tau : c.T / c.N;
     if constexpr (sizeof(T) == 8) a.b_d = mgb<double>(c, 0); else a.b_f = mgb<float>(c, 0);
     a.done = c.flag.p;
     a.check = 1;
@@ -446,14 +456,23 @@ void outer_step(Ctx& c, Skip sk, bool adjoint) {
         a.Fext = c.Gadj.p;
         a.skip_flux = 1;
     }
-    c.launches += launch_residual(a, c.stream);
-    const int cyc = std::max(1, c.opts.vcycles);
-    for (int v = 0; v < cyc; ++v) mgt_vcycle<T>(c, 0, v == 0, sk);
+    if (kind == STEP_STATIC) a.m_ptr = c.zero_ptr.p;   // every mass row empty
+    c.launches += launch_residual_law(a, law_data(c), c.stream);
+    if (kind == STEP_STATIC) {
+        PCG<T> pcg(c, c.coarse_ops[0], c.N, mgb<T>(c, 0), mgx<T>(c, 0), T(1), 0.0, sk, true);
+        pcg.init();
+        const int it = std::max(1, c.opts.pcg_iters);
+        for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
+    } else {
+        const int cyc = std::max(1, c.opts.vcycles);
+        for (int v = 0; v < cyc; ++v) mgt_vcycle<T>(c, 0, v == 0, sk);
+    }
     const double* sc = sizeof(T) == 4 ? &c.status.p->bscale_used : nullptr;
     c.launches += launch_add_to_double<T>((size_t)c.n * c.N, mgx<T>(c, 0), X, sc, sk, c.stream);
 }
 
-void final_residual(Ctx& c, bool adjoint) {
+void final_residual(Ctx& c, int kind) {
+    const bool adjoint = kind == STEP_ADJOINT;
     double* X = adjoint ? c.Lam.p : c.U.p;
     ResidualArgs a = residual_args(c, X, nullptr);
     a.done = c.flag.p;
@@ -463,7 +482,8 @@ void final_residual(Ctx& c, bool adjoint) {
         a.Fext = c.Gadj.p;
         a.skip_flux = 1;
     }
-    c.launches += launch_residual(a, c.stream);
+    if (kind == STEP_STATIC) a.m_ptr = c.zero_ptr.p;
+    c.launches += launch_residual_law(a, law_data(c), c.stream);
 }
 
 template <typename T>
@@ -601,7 +621,7 @@ void residual_dev(Ctx& c, const double* U, double* R, double* b_out_d, float* b_
     a.b_f = b_out_f;
     a.scale = scale;
     a.check = outer_check ? 1 : 0;
-    c.launches += launch_residual(a, c.stream);
+    c.launches += launch_residual_law(a, law_data(c), c.stream);
 }
 
 double norm_dev(Ctx& c, const double* x, size_t count) {
@@ -655,7 +675,7 @@ int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it,
     return it;
 }
 
-static void require_coarse(const Ctx& c) {
+void require_coarse(const Ctx& c) {
     PTP_REQUIRE(c.coarse_ok || c.dft_level >= 0 || c.active_levels < (int)c.tl.size(),
                 "multigrid in time needs a coarsest level with 1 or 2 steps (N must be a power of "
                 "two times 1 or 2, and time_levels large enough to reach it), or the DFT coarse solver");
@@ -700,6 +720,28 @@ void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* r
         *relres = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
     }
     PTP_CUDA(cudaStreamSynchronize(st));
+}
+
+// z = one application of the inner periodic solve (opts.vcycles V-cycles of
+// multigrid in time from zero) to v, in the set-up precision; the float
+// cycle runs on v / ||v|| and is scaled back.  Used as the preconditioner of
+// Newton's linear solves.
+void mg_precondition(Ctx& c, const double* v, double* z) {
+    cudaStream_t st = c.stream;
+    const size_t cnt = (size_t)c.n * c.N;
+    const int cyc = std::max(1, c.opts.vcycles);
+    if (c.opts.precision == PTP_MIXED) {
+        double* nb = c.scal.p + 4;
+        c.launches += launch_norm2<double>(cnt, v, c.part_d.p, c.counter.p, nb, st);
+        c.launches += launch_sqrt_or_one(nb, st);
+        c.launches += launch_cast_scaled<double, float>(cnt, v, mgb<float>(c, 0), nullptr, nb, st);
+        for (int k = 0; k < cyc; ++k) mgt_vcycle<float>(c, 0, k == 0, Skip{});
+        c.launches += launch_cast_scaled<float, double>(cnt, mgx<float>(c, 0), z, nb, nullptr, st);
+    } else {
+        PTP_CUDA(cudaMemcpyAsync(mgb<double>(c, 0), v, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        for (int k = 0; k < cyc; ++k) mgt_vcycle<double>(c, 0, k == 0, Skip{});
+        PTP_CUDA(cudaMemcpyAsync(z, mgx<double>(c, 0), cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
 }
 
 // ---- pieces of a fixed-point solve (shared with the batched solve) ----
@@ -759,8 +801,9 @@ int autotune(Ctx& c, double* best_us) {
     return bestb;
 }
 
-void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint) {
-    require_coarse(c);
+void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, int kind) {
+    const bool adjoint = kind == STEP_ADJOINT;
+    if (kind != STEP_STATIC) require_coarse(c);   // the static step has no time hierarchy
     PTP_REQUIRE(o.precision == c.opts.precision && o.spatial_prec == c.opts.spatial_prec &&
                     o.time_levels == c.opts.time_levels && o.coarse_steps == c.opts.coarse_steps &&
                     o.coarse_solver == c.opts.coarse_solver,
@@ -769,10 +812,10 @@ void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint) {
     cudaStream_t st = c.stream;
     double* X = adjoint ? c.Lam.p : c.U.p;
     const size_t cnt = (size_t)c.n * c.N;
-    if (X0) PTP_CUDA(cudaMemcpyAsync(X, X0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    else PTP_CUDA(cudaMemsetAsync(X, 0, cnt * sizeof(double), st));
+    if (X0 && X0 != X) PTP_CUDA(cudaMemcpyAsync(X, X0, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else if (!X0) PTP_CUDA(cudaMemsetAsync(X, 0, cnt * sizeof(double), st));
     Status s0{};
-    s0.tol = o.tol;
+    s0.tol = kind == STEP_STATIC && o.init_tol > 0 ? o.init_tol : o.tol;
     // the residual norm of the zero start: ||F|| (forward) or ||g|| (adjoint)
     const double r0 = adjoint ? c.g_norm : c.f_norm;
     s0.bscale = r0 > 0 ? r0 : 1.0;
@@ -785,21 +828,21 @@ void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, bool adjoint) {
 
 // Enqueues one outer step on c.stream (also while a capture is active);
 // returns the kernels it launched.
-int64_t enqueue_step(Ctx& c, bool adjoint) {
+int64_t enqueue_step(Ctx& c, int kind) {
     Skip sk;
     sk.done = c.flag.p;
     const int64_t b = c.launches;
-    if (c.opts.precision == PTP_MIXED) outer_step<float>(c, sk, adjoint);
-    else outer_step<double>(c, sk, adjoint);
+    if (c.opts.precision == PTP_MIXED) outer_step<float>(c, sk, kind);
+    else outer_step<double>(c, sk, kind);
     const int64_t k = c.launches - b;
     c.launches = b;
     return k;
 }
 
 // Final residual of the returned iterate, status read-back and statistics.
-int solve_end(Ctx& c, ptp_stats* stats, bool adjoint, int64_t step_launches, double solve_ms, float dev_ms) {
+int solve_end(Ctx& c, ptp_stats* stats, int kind, int64_t step_launches, double solve_ms, float dev_ms) {
     cudaStream_t st = c.stream;
-    final_residual(c, adjoint);
+    final_residual(c, kind);
     step_launches += 2;
     PTP_CUDA(cudaMemcpyAsync(&c.h_status[0], c.status.p, sizeof(Status), cudaMemcpyDeviceToHost, st));
     PTP_CUDA(cudaStreamSynchronize(st));
@@ -823,14 +866,16 @@ int solve_end(Ctx& c, ptp_stats* stats, bool adjoint, int64_t step_launches, dou
     return conv ? PTP_OK : PTP_ENOTCONV;
 }
 
-int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats, bool adjoint) {
+// Fixed-point iteration of one kind from X0 (null: zero start) until its
+// stopping rule or max_outer; the graph of one step is re-captured when the
+// options change.
+static int run_fixed_point(Ctx& c, const ptp_opts& o, const double* X0, double* U, ptp_stats* stats, int kind) {
     const auto t0 = std::chrono::steady_clock::now();
-    solve_begin(c, o, U0, adjoint);
-    double* X = adjoint ? c.Lam.p : c.U.p;
-    const int gi = adjoint ? 1 : 0;
+    solve_begin(c, o, X0, kind);
+    double* X = kind == STEP_ADJOINT ? c.Lam.p : c.U.p;
+    const int gi = kind;
     cudaStream_t st = c.stream;
     const size_t cnt = (size_t)c.n * c.N;
-    const bool mixed = o.precision == PTP_MIXED;
     // graph of one outer step, re-captured when the options change
     const int64_t key = step_key(c, o);
     if (o.use_graph && (c.graph_exec[gi] == nullptr || c.graph_key[gi] != key)) {
@@ -838,7 +883,7 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
         cudaGraph_t g;
         PTP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
-            c.launches_per_step = enqueue_step(c, adjoint);
+            c.launches_per_step[gi] = enqueue_step(c, kind);
         } catch (...) {
             cudaStreamEndCapture(st, &g);
             throw;
@@ -864,9 +909,9 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
         for (int k = 0; k < chunk; ++k) {
             if (o.use_graph) {
                 PTP_CUDA(cudaGraphLaunch(c.graph_exec[gi], st));
-                step_launches += c.launches_per_step;
+                step_launches += c.launches_per_step[gi];
             } else {
-                step_launches += enqueue_step(c, adjoint);
+                step_launches += enqueue_step(c, kind);
             }
         }
         launched += chunk;
@@ -886,10 +931,29 @@ int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* sta
     cudaEventDestroy(e0); cudaEventDestroy(e1);
     cudaEventDestroy(chk[0]); cudaEventDestroy(chk[1]);
     const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    const int rc = solve_end(c, stats, adjoint, step_launches, wall, ms);
+    const int rc = solve_end(c, stats, kind, step_launches, wall, ms);
     if (U) {
         PTP_CUDA(cudaMemcpyAsync(U, X, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
         PTP_CUDA(cudaStreamSynchronize(st));
+    }
+    return rc;
+}
+
+int solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* stats, int kind) {
+    if (kind != STEP_FORWARD || !o.init_static || U0) return run_fixed_point(c, o, U0, U, stats, kind);
+    // initialisation of Section 4: start from the static solutions (sigma = 0)
+    ptp_stats si;
+    std::memset(&si, 0, sizeof(si));
+    const int rs = run_fixed_point(c, o, nullptr, nullptr, &si, STEP_STATIC);
+    if (rs == PTP_ENAN) {
+        if (stats) *stats = si;
+        return rs;
+    }
+    const int rc = run_fixed_point(c, o, c.U.p, U, stats, STEP_FORWARD);
+    if (stats) {
+        stats->init_ms = si.solve_ms;
+        stats->init_iterations = si.outer_iterations;
+        stats->kernel_launches += si.kernel_launches;
     }
     return rc;
 }
@@ -923,7 +987,7 @@ AdjointArgs adjoint_args(Ctx& c) {
     return a;
 }
 
-static void alloc_adjoint(Ctx& c) {
+void alloc_adjoint(Ctx& c) {
     const size_t cnt = (size_t)c.n * c.N;
     if (c.Lam.n != cnt) c.Lam.alloc(cnt);
     if (c.Gadj.n != cnt) c.Gadj.alloc(cnt);
@@ -946,6 +1010,7 @@ double loss_dev(Ctx& c, const double* U) {
 int adjoint_gradient(Ctx& c, const ptp_opts& o, const double* U, double* J, double* dJ_damp, double* dJ_dnu,
                      double* dJ_dsigma, ptp_stats* st) {
     PTP_REQUIRE(c.n_coils <= kMaxCoils, "the adjoint supports at most 8 coils");
+    PTP_REQUIRE(!c.law_exp, "the adjoint supports the saturating reluctivity law only");
     cudaStream_t s = c.stream;
     const size_t cnt = (size_t)c.n * c.N;
     alloc_adjoint(c);
@@ -956,7 +1021,7 @@ int adjoint_gradient(Ctx& c, const ptp_opts& o, const double* U, double* J, doub
     double nJ = 0.0;
     PTP_CUDA(cudaMemcpyAsync(&nJ, c.adj_scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     c.g_norm = norm_dev(c, c.Gadj.p, cnt);   // synchronises
-    const int rc = solve(c, o, nullptr, nullptr, st, true);
+    const int rc = solve(c, o, nullptr, nullptr, st, STEP_ADJOINT);
     if (rc == PTP_ENAN) return rc;
     c.launches += launch_adj_gradients(a, c.Ustar.p, c.Lam.p, dJ_dsigma, s);
     double h[1 + kMaxCoils + 3];

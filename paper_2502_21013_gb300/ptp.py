@@ -31,7 +31,8 @@ class Opts(ctypes.Structure):
         ("pcg_iters", ctypes.c_int), ("spatial_prec", ctypes.c_int), ("gmg_smooth", ctypes.c_int),
         ("gmg_omega", ctypes.c_double), ("coarse_tol", ctypes.c_double), ("coarse_max_it", ctypes.c_int),
         ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
-        ("coarse_solver", ctypes.c_int), ("dft_max_it", ctypes.c_int),
+        ("coarse_solver", ctypes.c_int), ("dft_max_it", ctypes.c_int), ("init_tol", ctypes.c_double),
+        ("init_static", ctypes.c_int), ("newton_eta", ctypes.c_double), ("krylov_dim", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -43,7 +44,8 @@ class Stats(ctypes.Structure):
         ("outer_iterations", ctypes.c_int), ("converged", ctypes.c_int), ("res0", ctypes.c_double),
         ("res_final", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
         ("residual_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("time_levels", ctypes.c_int),
-        ("spatial_levels", ctypes.c_int),
+        ("spatial_levels", ctypes.c_int), ("init_ms", ctypes.c_double), ("init_iterations", ctypes.c_int),
+        ("inner_iterations", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -91,6 +93,13 @@ def _load():
         "ptp_periodic_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, I, pD]),
         "ptp_solve": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
         "ptp_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
+        "ptp_static_solve": (I, [P, ctypes.POINTER(Opts), P, ctypes.POINTER(Stats)]),
+        "ptp_set_law_exp": (I, [P, P]),
+        "ptp_newton_solve": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
+        "ptp_newton_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, ctypes.POINTER(Stats)]),
+        "ptp_jacobian_apply_dev": (I, [P, P, P, P]),
+        "ptp_set_khat": (I, [P, P]),
+        "ptp_static_solve_dev": (I, [P, ctypes.POINTER(Opts), P, ctypes.POINTER(Stats)]),
         "ptp_loss_dev": (I, [P, P, pD]),
         "ptp_autotune": (I, [P, pI, pD]),
         "ptp_batch_create": (I, [ctypes.POINTER(P), I]),
@@ -119,11 +128,14 @@ lib = _load()
 
 EXPORTED = [
     "ptp_default_opts", "ptp_version", "ptp_abi_sizes", "ptp_create", "ptp_destroy", "ptp_last_error", "ptp_set_stream",
-    "ptp_set_mesh", "ptp_set_structured", "ptp_set_materials", "ptp_set_sources", "ptp_set_time",
+    "ptp_set_mesh", "ptp_set_structured", "ptp_set_materials", "ptp_set_law_exp", "ptp_set_khat",
+    "ptp_set_sources", "ptp_set_time",
     "ptp_setup", "ptp_sizes", "ptp_info", "ptp_source", "ptp_source_dev", "ptp_residual", "ptp_residual_dev",
     "ptp_residual_noalloc_dev",
     "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_spatial_solve_dev",
     "ptp_spatial_solve_f32_dev", "ptp_periodic_solve_dev", "ptp_solve", "ptp_solve_dev",
+    "ptp_static_solve", "ptp_static_solve_dev", "ptp_newton_solve", "ptp_newton_solve_dev",
+    "ptp_jacobian_apply_dev",
     "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient", "ptp_autotune",
     "ptp_batch_create", "ptp_batch_destroy", "ptp_batch_last_error", "ptp_batch_add", "ptp_batch_size",
     "ptp_batch_solve", "ptp_batch_result_dev",
@@ -200,6 +212,18 @@ class Context:
         nl, pnl = _np(nonlinear_e, np.uint8)
         return self._check(lib.ptp_set_materials(self._h, ps, pnl, nu_min, nu_max, s_sat, nu_linear))
 
+    def set_law_exp(self, abcd):
+        if abcd is None:
+            return self._check(lib.ptp_set_law_exp(self._h, None))
+        a, pa = _np(abcd, np.float64)
+        return self._check(lib.ptp_set_law_exp(self._h, pa))
+
+    def set_khat(self, khat_e):
+        if khat_e is None:
+            return self._check(lib.ptp_set_khat(self._h, None))
+        k, pk = _np(khat_e, np.float64)
+        return self._check(lib.ptp_set_khat(self._h, pk))
+
     def set_sources(self, coil_of_elem, amp, phase):
         c, pc = _np(coil_of_elem, np.int32)
         a, pa = _np(amp, np.float64)
@@ -259,6 +283,16 @@ class Context:
         self._check(rc, allow=(PTP_ENOTCONV,))
         return U, st, rc
 
+    def static_solve(self, opts: Opts | None = None, U_out=None):
+        """Initialisation of Section 4: U with K(u^n) = f^n for every step (host array)."""
+        n, N, _, _ = self.sizes()
+        o = opts if opts is not None else self.opts
+        U = U_out if U_out is not None else np.empty((n, N))
+        st = Stats()
+        rc = lib.ptp_static_solve(self._h, ctypes.byref(o), U.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
+        self._check(rc, allow=(PTP_ENOTCONV,))
+        return U, st, rc
+
     # ---- hot path, device pointers (torch CUDA tensors) ----
     def source_dev(self, F):
         return self._check(lib.ptp_source_dev(self._h, _dev_ptr(F, "float64")))
@@ -304,6 +338,50 @@ class Context:
         rc = lib.ptp_solve_dev(self._h, ctypes.byref(o), p0, _dev_ptr(U, "float64"), ctypes.byref(st))
         self._check(rc, allow=(PTP_ENOTCONV,))
         return st, rc
+
+
+def _newton_solve(ctx, opts=None, U0=None):
+    """Newton's method (M2); returns (U, stats, rc) with U a host array."""
+    n, N, _, _ = ctx.sizes()
+    o = opts if opts is not None else ctx.opts
+    U = np.empty((n, N))
+    p0 = None
+    if U0 is not None:
+        U0, p0 = _np(U0, np.float64)
+    st = Stats()
+    rc = lib.ptp_newton_solve(ctx._h, ctypes.byref(o), p0, U.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
+    ctx._check(rc, allow=(PTP_ENOTCONV,))
+    return U, st, rc
+
+
+def _newton_solve_dev(ctx, U, opts=None, U0=None):
+    o = opts if opts is not None else ctx.opts
+    st = Stats()
+    p0 = _dev_ptr(U0, "float64") if U0 is not None else None
+    rc = lib.ptp_newton_solve_dev(ctx._h, ctypes.byref(o), p0, _dev_ptr(U, "float64"), ctypes.byref(st))
+    ctx._check(rc, allow=(PTP_ENOTCONV,))
+    return st, rc
+
+
+def _jacobian_apply_dev(ctx, U, V, Y):
+    return ctx._check(lib.ptp_jacobian_apply_dev(ctx._h, _dev_ptr(U, "float64"), _dev_ptr(V, "float64"),
+                                                 _dev_ptr(Y, "float64")))
+
+
+Context.newton_solve = _newton_solve
+Context.newton_solve_dev = _newton_solve_dev
+Context.jacobian_apply_dev = _jacobian_apply_dev
+
+
+def _static_solve_dev(ctx, U, opts=None):
+    o = opts if opts is not None else ctx.opts
+    st = Stats()
+    rc = lib.ptp_static_solve_dev(ctx._h, ctypes.byref(o), _dev_ptr(U, "float64"), ctypes.byref(st))
+    ctx._check(rc, allow=(PTP_ENOTCONV,))
+    return st, rc
+
+
+Context.static_solve_dev = _static_solve_dev
 
 
 def _loss_dev(ctx, U):
@@ -385,5 +463,7 @@ def load_problem(ctx: Context, prob, structured: bool = True):
     else:
         ctx.set_mesh(prob.xy, prob.tri, prob.dirichlet)
     ctx.set_materials(prob.sigma_e, prob.nonlinear_e, prob.nu_min, prob.nu_max, prob.s_sat, prob.nu_linear)
+    ctx.set_law_exp(getattr(prob, "law_abcd", None))
+    ctx.set_khat(getattr(prob, "khat_e", None))
     ctx.set_sources(prob.coil_of_elem, prob.amp, prob.phase)
     ctx.set_time(prob.T, prob.N)
