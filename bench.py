@@ -352,6 +352,26 @@ def run_ours(args):
                 "outer_iterations": s64.outer_iterations, "dtype": "f64"}
         del c64
 
+    # ---- Newton's method (M2) on the same workload, mixed precision ----
+    newton = None
+    if args.newton_steps > 0:
+        cn, on = make(ptp.PTP_MIXED)
+        cn.newton_solve_dev(U, on)   # allocation of the Krylov basis
+        barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.newton_steps):
+            sn, rcn = cn.newton_solve_dev(U, on)
+            if rcn != ptp.PTP_OK:
+                raise RuntimeError(f"Newton solve did not converge (rc {rcn})")
+        torch.cuda.synchronize()
+        msn = max_over_ranks((time.perf_counter() - t) * 1e3 / args.newton_steps)
+        newton = {"value": sum_over_ranks(dofs) / (msn / 1e3), "unit": UNIT, "ms_per_step": msn,
+                  "newton_iterations": sn.outer_iterations, "krylov_iterations": sn.inner_iterations,
+                  "final_rel_residual": sn.res_final / sn.res0, "dtype": "f32+f64",
+                  "method": "Newton (M2), flexible GMRES preconditioned by multigrid in time, Armijo"}
+        del cn
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(prob, iterations_to_tol=iters[-1])
@@ -378,6 +398,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (U alone is 133 MB)", "parallelism": f"replicas{world}"},
             "fp64": fp64,
             "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "newton": newton,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dofs, "d2h_bytes_per_step": 8 * dofs},
             "gpu_launches": int(launches),
             # the largest single kernel of a step (launch list in profiles/) is K1
@@ -559,6 +580,7 @@ def main():
     ap.add_argument("--max-outer", type=int, default=6000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--newton-steps", type=int, default=1, help="timed Newton (M2) solves of the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["square257_N256", "batched64", "paper_transformer"],
                     default="square257_N256")

@@ -239,6 +239,7 @@ struct Ctx {
     int64_t launches = 0;        // kernels issued (counting while capturing)
     int64_t launches_per_step[3] = {0, 0, 0};
     int row_block = 256;         // threads per block of the row kernels (autotuned)
+    int64_t buf_gen = 0;         // bumped when a buffer a captured graph may use is reallocated
 
     ~Ctx();
 };

@@ -204,12 +204,10 @@ int newton_solve(Ctx& c, const ptp_opts& o, const double* U0, double* Uout, ptp_
             if ((std::isfinite(rt) && rt <= (1.0 - 1e-4 * t) * r) || t < 1.0 / 1024.0) break;
             t *= 0.5;
         }
-        std::swap(c.U, c.kr_t);   // accept the trial iterate and its residual
-        std::swap(c.R, c.kr_r);
-        U = c.U.p;
-        R = c.R.p;
-        Ut = c.kr_t.p;
-        Rt = c.kr_r.p;
+        // accept the trial iterate (copied: captured graphs of this context
+        // hold the address of U) and its residual (local buffers, swapped)
+        PTP_CUDA(cudaMemcpyAsync(U, Ut, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        std::swap(R, Rt);
         r = rt;
         ++it;
         conv = r <= o.tol * r0;

@@ -589,29 +589,37 @@ void alloc_work(Ctx& c) {
 }
 
 template <typename T>
-static void grow(DBuf<T>& b, size_t n) {
-    if (b.n < n) b.alloc(n);
+static bool grow(DBuf<T>& b, size_t n) {
+    if (b.n >= n) return false;
+    b.alloc(n);
+    return true;
 }
 
 // full-size work vectors of precision T (entry points that run in the other
 // precision than the set-up one, and host staging of [n][N] blocks)
+// A reallocated buffer may be baked into a captured graph (of this context or
+// of a batch holding it): bumping buf_gen changes the step key, so those
+// graphs are captured again before their next launch.
 void ensure_work(Ctx& c, bool doubles) {
     const size_t big = (size_t)c.n * c.N;
+    bool changed = false;
     for (int k = 0; k < 6; ++k) {
-        if (doubles) grow(c.w_d[k], big); else grow(c.w_f[k], big);
+        if (doubles) changed |= grow(c.w_d[k], big); else changed |= grow(c.w_f[k], big);
     }
     for (size_t s = 1; s < c.sl.size(); ++s) {
         const size_t m = (size_t)c.sl[s].n * c.N;
-        if (doubles) { grow(c.g_xd[s], m); grow(c.g_bd[s], m); grow(c.g_rd[s], m); }
-        else { grow(c.g_xf[s], m); grow(c.g_bf[s], m); grow(c.g_rf[s], m); }
+        if (doubles) { changed |= grow(c.g_xd[s], m); changed |= grow(c.g_bd[s], m); changed |= grow(c.g_rd[s], m); }
+        else { changed |= grow(c.g_xf[s], m); changed |= grow(c.g_bf[s], m); changed |= grow(c.g_rf[s], m); }
     }
-    if (!doubles) grow(c.part_f, c.part_d.n);
+    if (!doubles) changed |= grow(c.part_f, c.part_d.n);
+    if (changed) ++c.buf_gen;
 }
 
 void ensure_staging(Ctx& c) {
     const size_t big = (size_t)c.n * c.N;
-    grow(c.R, big);
-    grow(c.Ud, std::max(big, (size_t)c.n * 2));
+    bool changed = grow(c.R, big);
+    changed |= grow(c.Ud, std::max(big, (size_t)c.n * 2));
+    if (changed) ++c.buf_gen;
 }
 
 void residual_dev(Ctx& c, const double* U, double* R, double* b_out_d, float* b_out_f, double scale,
@@ -759,6 +767,7 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));
+    mix(&c.buf_gen, sizeof(c.buf_gen));   // buffers the captured step uses were reallocated
     return (int64_t)(h >> 1);
 }
 
@@ -989,12 +998,14 @@ AdjointArgs adjoint_args(Ctx& c) {
 
 void alloc_adjoint(Ctx& c) {
     const size_t cnt = (size_t)c.n * c.N;
+    const size_t jc = 3 * (size_t)std::max(c.n_iron, 1) * c.N;
+    if (c.Lam.n == cnt && c.Gadj.n == cnt && c.Ustar.n == cnt && c.Jc.n == jc && c.adj_scal.n >= 16) return;
     if (c.Lam.n != cnt) c.Lam.alloc(cnt);
     if (c.Gadj.n != cnt) c.Gadj.alloc(cnt);
     if (c.Ustar.n != cnt) c.Ustar.alloc(cnt);
-    const size_t jc = 3 * (size_t)std::max(c.n_iron, 1) * c.N;
     if (c.Jc.n != jc) c.Jc.alloc(jc);
     if (c.adj_scal.n < 16) c.adj_scal.alloc(16);
+    ++c.buf_gen;
 }
 
 double loss_dev(Ctx& c, const double* U) {

@@ -104,3 +104,33 @@ def test_adjoint_full_size_fp64():
     h = 1e-6 * abs(prob.amp[0])
     fd = (J_of(prob.amp[0] + h) - J_of(prob.amp[0] - h)) / (2 * h)
     assert abs(fd - damp[0]) <= 1e-5 * abs(fd)
+
+
+def test_newton_full_size_mixed():
+    """The bench workload (257x257, N = 256) by Newton's method (M2) to 1e-8:
+    the oracle's residual of the iterate meets the stopping rule, the limit is
+    half-period antisymmetric, and it agrees with the fixed point's limit."""
+    prob = W.config_mixed(0)
+    d = P.assemble(prob)
+    c, o = _ctx(prob, precision=ptp.PTP_MIXED, tol=1e-8, max_outer=40)
+    U, st, rc = c.newton_solve(o)
+    assert rc == ptp.PTP_OK and st.outer_iterations <= 20
+    r, fn = oracle_residual_norm(prob, d, U)
+    assert r <= 1.05e-8 * fn
+    N = prob.N
+    assert np.abs(U[:, N // 2:] + U[:, :N // 2]).max() <= 1e-6 * np.abs(U).max()
+    Uf, st2, rc2 = c.solve(ptp.default_opts(precision=ptp.PTP_MIXED, tol=1e-8, max_outer=6000))
+    assert rc2 == ptp.PTP_OK
+    assert np.linalg.norm(U - Uf) <= 1e-5 * np.linalg.norm(Uf)
+
+
+def test_dft_two_level_full_size_mixed():
+    """Two-level multigrid in time with the DFT coarse solve on 128 steps, the
+    bench workload to 1e-8: the oracle's residual meets the stopping rule."""
+    prob = W.config_mixed(0)
+    d = P.assemble(prob)
+    c, o = _ctx(prob, precision=ptp.PTP_MIXED, tol=1e-8, max_outer=6000, coarse_solver=1, time_levels=2)
+    U, st, rc = c.solve(o)
+    assert rc == ptp.PTP_OK and st.time_levels == 2
+    r, fn = oracle_residual_norm(prob, d, U)
+    assert r <= 1.05e-8 * fn
