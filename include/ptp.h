@@ -117,9 +117,10 @@ typedef struct ptp_opts {
     double init_tol;     /* tolerance of the static initialisation (0: tol) */
     int    init_static;  /* 1: a solve without U0 starts from the static
                             solutions (initialisation of Section 4)         */
-    double newton_eta;   /* Newton: relative tolerance of each linear solve */
+    double newton_eta;   /* Newton: relative tolerance of each linear solve
+                            (default 1e-2)                                   */
     int    krylov_dim;   /* Newton: flexible GMRES iterations per linear
-                            solve (1..31, no restart)                        */
+                            solve (1..31, no restart; default 20)            */
 } ptp_opts;
 
 /* Statistics of the last solve. */

@@ -60,6 +60,11 @@ void invalidate(Ctx& c) {
         }
         c.graph_key[k] = -1;
     }
+    if (c.newton_exec) {
+        cudaGraphExecDestroy(c.newton_exec);
+        c.newton_exec = nullptr;
+    }
+    c.newton_key = -1;
 }
 
 // device copies for the host-pointer entry points
@@ -108,8 +113,8 @@ void ptp_default_opts(ptp_opts* o) {
     o->dft_max_it = 30;
     o->init_tol = 0.0;
     o->init_static = 0;
-    o->newton_eta = 1e-3;
-    o->krylov_dim = 30;
+    o->newton_eta = 1e-2;
+    o->krylov_dim = 20;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }

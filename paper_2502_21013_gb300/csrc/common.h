@@ -197,6 +197,9 @@ struct Ctx {
     DBuf<double> adj_scal;
     // Newton (method M2): Krylov bases, trial iterate and residual, device scalars
     DBuf<double> kr_v, kr_z, kr_w, kr_t, kr_r, kr_d, kr_s;
+    DBuf<double> kr_vin, kr_zout;      // fixed input / output of the captured Krylov step
+    cudaGraphExec_t newton_exec = nullptr;   // graph: precondition vin -> zout, w = J zout
+    int64_t newton_key = -1;
 
     // spatial hierarchy (level 0 = the mesh itself)
     std::vector<SpatialLevel> sl;

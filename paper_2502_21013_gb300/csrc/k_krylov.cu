@@ -17,24 +17,26 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// out[i] = sum_g V[i * stride + g] w[g], i < k <= kMaxKrylovDots
+// out[i] = sum_g V[i * stride + g] w[g], i < k <= KB (KB a power of two, so
+// a launch issues at most twice the FMAs its k dot products need)
+template <int KB>
 __global__ void __launch_bounds__(kThreads)
 k_mdot(size_t count, int k, const double* __restrict__ V, size_t stride, const double* __restrict__ w,
        double* __restrict__ partials, unsigned* counter, double* __restrict__ out) {
     pdl_enter();
-    double acc[kMaxKrylovDots];
+    double acc[KB];
 #pragma unroll
-    for (int i = 0; i < kMaxKrylovDots; ++i) acc[i] = 0.0;
+    for (int i = 0; i < KB; ++i) acc[i] = 0.0;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
         const double wg = __ldg(w + g);
 #pragma unroll
-        for (int i = 0; i < kMaxKrylovDots; ++i)
+        for (int i = 0; i < KB; ++i)
             if (i < k) acc[i] = fma(__ldg(V + (size_t)i * stride + g), wg, acc[i]);
     }
-    __shared__ double sm[kMaxKrylovDots][kThreads / 32];
+    __shared__ double sm[KB][kThreads / 32];
     __shared__ bool last;
 #pragma unroll
-    for (int i = 0; i < kMaxKrylovDots; ++i) {
+    for (int i = 0; i < KB; ++i) {
         if (i >= k) break;
         const double s = warp_sum(acc[i]);
         if ((threadIdx.x & 31) == 0) sm[i][threadIdx.x >> 5] = s;
@@ -99,7 +101,13 @@ int grid_of(size_t count) {
 int launch_mdot(size_t count, int k, const double* V, size_t stride, const double* w, double* partials,
                 unsigned* counter, double* out, cudaStream_t s) {
     if (k < 1 || k > kMaxKrylovDots) throw Error(PTP_EINVAL, "launch_mdot: 1..32 dot products per launch");
-    launch_k(k_mdot, dim3(grid_of(count)), dim3(kThreads), s, count, k, V, stride, w, partials, counter, out);
+    const dim3 gr(grid_of(count)), bl(kThreads);
+    if (k == 1) launch_k(k_mdot<1>, gr, bl, s, count, k, V, stride, w, partials, counter, out);
+    else if (k <= 2) launch_k(k_mdot<2>, gr, bl, s, count, k, V, stride, w, partials, counter, out);
+    else if (k <= 4) launch_k(k_mdot<4>, gr, bl, s, count, k, V, stride, w, partials, counter, out);
+    else if (k <= 8) launch_k(k_mdot<8>, gr, bl, s, count, k, V, stride, w, partials, counter, out);
+    else if (k <= 16) launch_k(k_mdot<16>, gr, bl, s, count, k, V, stride, w, partials, counter, out);
+    else launch_k(k_mdot<32>, gr, bl, s, count, k, V, stride, w, partials, counter, out);
     return 1;
 }
 

@@ -38,20 +38,59 @@ double residual_norm(Ctx& c, const double* X, double* R) {
     return h;
 }
 
-// Flexible GMRES (right preconditioning, classical Gram-Schmidt applied
-// twice) for J x = b from x = 0; stops when the least-squares residual is
-// below eta ||b|| or after m iterations.  Returns the iterations taken.
-int fgmres(Ctx& c, const double* b, double* x, double eta, int m, double* relres) {
+// The preconditioner and Jacobian of one Krylov step, zout = P^{-1} vin and
+// w = J zout, on fixed buffers: captured once as a CUDA graph (re-captured
+// when the step key of the context changes) or enqueued directly.
+void krylov_step(Ctx& c, const ptp_opts& o) {
+    auto enqueue = [&]() {
+        mg_precondition(c, c.kr_vin.p, c.kr_zout.p);
+        jacobian_apply(c, c.kr_zout.p, c.kr_w.p);
+    };
+    if (!o.use_graph) {
+        enqueue();
+        return;
+    }
+    const int64_t key = step_key(c, o);
+    if (!c.newton_exec || c.newton_key != key) {
+        if (c.newton_exec) {
+            cudaGraphExecDestroy(c.newton_exec);
+            c.newton_exec = nullptr;
+        }
+        cudaGraph_t g;
+        PTP_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = c.launches;
+        try {
+            enqueue();
+        } catch (...) {
+            cudaStreamEndCapture(c.stream, &g);
+            throw;
+        }
+        c.launches = l0;
+        PTP_CUDA(cudaStreamEndCapture(c.stream, &g));
+        PTP_CUDA(cudaGraphInstantiate(&c.newton_exec, g, 0));
+        cudaGraphDestroy(g);
+        c.newton_key = key;
+    }
+    PTP_CUDA(cudaGraphLaunch(c.newton_exec, c.stream));
+}
+
+// Flexible GMRES (right preconditioning, classical Gram-Schmidt with a
+// second pass only when the first removed most of the vector: ||w|| after
+// < 0.7 ||w|| before, the "twice is enough" rule) for J x = b from x = 0;
+// stops when the least-squares residual is below eta ||b|| or after m
+// iterations.  Returns the iterations taken.
+int fgmres(Ctx& c, const ptp_opts& o, const double* b, double* x, double eta, int m, double* relres) {
     cudaStream_t st = c.stream;
     const size_t cnt = (size_t)c.n * c.N;
     double* V = c.kr_v.p;   // m + 1 basis vectors
     double* Z = c.kr_z.p;   // m preconditioned vectors
     double* w = c.kr_w.p;
-    double* ds = c.kr_s.p;  // device scalars: [1..] dots, [kMaxKrylovDots + 2 ..] second pass
+    double* ds = c.kr_s.p;  // device scalars: [1 .. 1+32) dots, [33 .. 65) second pass, [65] ||w||^2
     double* d1 = ds + 1;
-    double* d2 = ds + 2 + kMaxKrylovDots;
-    double* dn = ds + 3 + 2 * kMaxKrylovDots;   // ||w||^2, then ||w||
-    double* dy = ds + 4 + 2 * kMaxKrylovDots;   // solution coefficients
+    double* d2 = ds + 1 + kMaxKrylovDots;
+    double* dn = ds + 1 + 2 * kMaxKrylovDots;   // ||w||^2 after the first pass, then ||w||
+    double* dy = ds + 2 + 2 * kMaxKrylovDots;   // solution coefficients
+    double* d0 = ds + 2 + 3 * kMaxKrylovDots;   // ||w||^2 before orthogonalisation
     c.launches += launch_mdot(cnt, 1, b, cnt, b, c.part_d.p, c.counter.p, dn, st);
     double beta2 = 0.0;
     PTP_CUDA(cudaMemcpyAsync(&beta2, dn, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -64,34 +103,43 @@ int fgmres(Ctx& c, const double* b, double* x, double eta, int m, double* relres
     }
     PTP_CUDA(cudaMemcpyAsync(dn, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
     c.launches += launch_div_scalar(cnt, b, dn, V, st);
+    PTP_CUDA(cudaMemcpyAsync(c.kr_vin.p, V, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
     auto Hat = [&](int i, int j) -> double& { return H[(size_t)j * (m + 1) + i]; };
     g[0] = beta;
-    std::vector<double> h1(m + 1), h2(m + 1);
+    std::vector<double> hd(2 * kMaxKrylovDots + 1);   // both passes and ||w||^2, one copy
     int k = 0;
     double res = beta;
     for (int j = 0; j < m; ++j) {
-        double* vj = V + (size_t)j * cnt;
         double* zj = Z + (size_t)j * cnt;
-        mg_precondition(c, vj, zj);
-        jacobian_apply(c, zj, w);
+        krylov_step(c, o);   // vin holds v_j
+        ++c.launches;
+        PTP_CUDA(cudaMemcpyAsync(zj, c.kr_zout.p, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        c.launches += launch_mdot(cnt, 1, w, cnt, w, c.part_d.p, c.counter.p, d0, st);
         c.launches += launch_mdot(cnt, j + 1, V, cnt, w, c.part_d.p, c.counter.p, d1, st);
         c.launches += launch_maxpy(cnt, j + 1, V, cnt, d1, -1.0, w, st);
-        c.launches += launch_mdot(cnt, j + 1, V, cnt, w, c.part_d.p, c.counter.p, d2, st);
-        c.launches += launch_maxpy(cnt, j + 1, V, cnt, d2, -1.0, w, st);
         c.launches += launch_mdot(cnt, 1, w, cnt, w, c.part_d.p, c.counter.p, dn, st);
-        PTP_CUDA(cudaMemcpyAsync(h1.data(), d1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        PTP_CUDA(cudaMemcpyAsync(h2.data(), d2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-        double wn2 = 0.0;
-        PTP_CUDA(cudaMemcpyAsync(&wn2, dn, sizeof(double), cudaMemcpyDeviceToHost, st));
+        double w0 = 0.0;
+        PTP_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaMemcpyAsync(&w0, d0, sizeof(double), cudaMemcpyDeviceToHost, st));
         PTP_CUDA(cudaStreamSynchronize(st));
-        for (int i = 0; i <= j; ++i) Hat(i, j) = h1[i] + h2[i];
-        const double hn = std::sqrt(std::max(wn2, 0.0));
+        for (int i = 0; i <= j; ++i) Hat(i, j) = hd[i];
+        if (hd[2 * kMaxKrylovDots] < 0.49 * w0) {   // second pass
+            c.launches += launch_mdot(cnt, j + 1, V, cnt, w, c.part_d.p, c.counter.p, d2, st);
+            c.launches += launch_maxpy(cnt, j + 1, V, cnt, d2, -1.0, w, st);
+            c.launches += launch_mdot(cnt, 1, w, cnt, w, c.part_d.p, c.counter.p, dn, st);
+            PTP_CUDA(cudaMemcpyAsync(hd.data(), d1, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            PTP_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i <= j; ++i) Hat(i, j) += hd[kMaxKrylovDots + i];
+        }
+        const double hn = std::sqrt(std::max(hd[2 * kMaxKrylovDots], 0.0));
         Hat(j + 1, j) = hn;
         if (!std::isfinite(hn)) throw Error(PTP_ENAN, "newton: non-finite Krylov vector");
         if (hn > 0.0 && j + 1 < m) {
             PTP_CUDA(cudaMemcpyAsync(dn, &hn, sizeof(double), cudaMemcpyHostToDevice, st));
             c.launches += launch_div_scalar(cnt, w, dn, V + (size_t)(j + 1) * cnt, st);
+            PTP_CUDA(cudaMemcpyAsync(c.kr_vin.p, V + (size_t)(j + 1) * cnt, cnt * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, st));
         }
         // Givens rotations on column j
         for (int i = 0; i < j; ++i) {
@@ -180,7 +228,9 @@ int newton_solve(Ctx& c, const ptp_opts& o, const double* U0, double* Uout, ptp_
     grow(c.kr_t, cnt);
     grow(c.kr_r, cnt);
     grow(c.kr_d, cnt);
-    grow(c.kr_s, 8 + 3 * (size_t)kMaxKrylovDots);
+    grow(c.kr_vin, cnt);
+    grow(c.kr_zout, cnt);
+    grow(c.kr_s, 8 + 4 * (size_t)kMaxKrylovDots);
     const int64_t launches0 = c.launches;
     double* U = c.U.p;
     double* R = c.R.p;
@@ -195,7 +245,7 @@ int newton_solve(Ctx& c, const ptp_opts& o, const double* U0, double* Uout, ptp_
         if (!std::isfinite(r)) break;
         c.launches += launch_adj_jacobian(adjoint_args(c), U, st, false);
         double rel = 0.0;
-        inner += fgmres(c, R, d, o.newton_eta, m, &rel);
+        inner += fgmres(c, o, R, d, o.newton_eta, m, &rel);
         double t = 1.0, rt = 0.0;
         for (;;) {
             launch_lincomb(cnt, 1.0, U, t, d, Ut, st);

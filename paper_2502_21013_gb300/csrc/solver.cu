@@ -33,6 +33,7 @@ int residual_grid(size_t total);
 Ctx::~Ctx() {
     for (auto& g : graph_exec)
         if (g) cudaGraphExecDestroy(g);
+    if (newton_exec) cudaGraphExecDestroy(newton_exec);
     if (h_status) cudaFreeHost(h_status);
     if (own_stream) cudaStreamDestroy(own_stream);
 }
