@@ -52,12 +52,22 @@ k_mdot(size_t count, int k, const double* __restrict__ V, size_t stride, const d
     if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partials + (size_t)b * k + i);
-        out[i] = s;
+    // the whole last block sums the partials of each dot product: a strided
+    // share per thread, then the warp and block trees (a fixed order)
+    __shared__ double red[kThreads / 32];
+    for (int i = 0; i < k; ++i) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + (size_t)b * k + i);
+        t = warp_sum(t);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double u = 0.0;
+            for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) u += red[wi];
+            out[i] = u;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (threadIdx.x == 0) *counter = 0u;
 }
 

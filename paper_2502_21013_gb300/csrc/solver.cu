@@ -741,7 +741,7 @@ void mg_precondition(Ctx& c, const double* v, double* z) {
     const int cyc = std::max(1, c.opts.vcycles);
     if (c.opts.precision == PTP_MIXED) {
         double* nb = c.scal.p + 4;
-        c.launches += launch_norm2<double>(cnt, v, c.part_d.p, c.counter.p, nb, st);
+        c.launches += launch_mdot(cnt, 1, v, cnt, v, c.part_d.p, c.counter.p, nb, st);
         c.launches += launch_sqrt_or_one(nb, st);
         c.launches += launch_cast_scaled<double, float>(cnt, v, mgb<float>(c, 0), nullptr, nb, st);
         for (int k = 0; k < cyc; ++k) mgt_vcycle<float>(c, 0, k == 0, Skip{});
