@@ -495,8 +495,9 @@ def run_paper(args):
     c = ptp.Context(local)
     c.set_stream(stream.cuda_stream)
     ptp.load_problem(c, prob)
-    # FP64: the element weights of K_hat span 29..8e5, beyond float precision at
-    # this resolution; ten PCG iterations per spatial solve (see DESIGN)
+    # FP64: the element weights of K_hat span 29..8e5, so its condition number at
+    # this resolution is beyond float precision; several PCG iterations per
+    # spatial solve, since linear-interpolation multigrid is weaker on such jumps
     o = ptp.default_opts(precision=ptp.PTP_FP64, tol=1e-4, max_outer=2000, init_static=1, init_tol=1e-8,
                          pcg_iters=args.paper_pcg, **INNER[args.inner]["opts"])
     c.setup(o)
