@@ -4,7 +4,7 @@
 // basis vectors, and a division by a device scalar.  The dot products are
 // deterministic: per-block partials, then the last block to finish (atomic
 // ticket, no waiting) sums them in block order.
-#include "kernels.h"
+#include "dev_util.cuh"
 
 namespace ptp {
 
@@ -101,6 +101,32 @@ __global__ void k_sqrt_or_one(double* x) {
     }
 }
 
+// The last update of a batched PCG whose residual and residual norm are not
+// used again: x = xscale alpha p (assign) or x += xscale alpha p, with the
+// per-column alpha of the ColRed scalars (the same arithmetic as the full update).
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock)
+k_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* __restrict__ p, const T* __restrict__ alpha,
+              Skip sk) {
+    pdl_enter();
+    if (skip_now(sk)) return;
+    const int NC = N / VEC, rpb = blockDim.x / NC;
+    PTP_ROW_LOOP(rows, NC, rpb) {
+        const size_t o = (size_t)row * N + col0;
+        T pv[VEC], xv[VEC];
+        ldg_vec<T, VEC>(p + o, pv);
+        if (assign) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) xv[v] = T(0);
+        } else {
+            ld_vec<T, VEC>(x + o, xv);
+        }
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) xv[v] += xscale * alpha[col0 + v] * pv[v];
+        st_vec<T, VEC>(x + o, xv);
+    }
+}
+
 int grid_of(size_t count) {
     const size_t want = (count + kThreads - 1) / kThreads;
     return (int)std::max<size_t>(1, std::min(want, (size_t)num_sms() * 8));
@@ -132,6 +158,24 @@ int launch_div_scalar(size_t count, const double* x, const double* h, double* y,
     launch_k(k_div_scalar, dim3(grid_of(count)), dim3(kThreads), s, count, x, h, y);
     return 1;
 }
+
+template <typename T>
+int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, ColRed<T> cr, Skip sk,
+                       cudaStream_t s) {
+    const T* alpha = cr.col + S_ALPHA * N;
+    auto al = [](const void* q, size_t b) { return ((uintptr_t)q % b) == 0; };
+    if (sizeof(T) == 4 && N % 4 == 0 && al(x, 16) && al(p, 16)) {
+        if constexpr (sizeof(T) == 4) launch_rows(k_pcg_xupdate<T, 4>, rows, N, 4, s, rows, N, xscale, assign, x, p, alpha, sk);
+    } else if (N % 2 == 0 && al(x, 2 * sizeof(T)) && al(p, 2 * sizeof(T))) {
+        launch_rows(k_pcg_xupdate<T, 2>, rows, N, 2, s, rows, N, xscale, assign, x, p, alpha, sk);
+    } else {
+        launch_rows(k_pcg_xupdate<T, 1>, rows, N, 1, s, rows, N, xscale, assign, x, p, alpha, sk);
+    }
+    return 1;
+}
+template int launch_pcg_xupdate<float>(int, int, float, int, float*, const float*, ColRed<float>, Skip, cudaStream_t);
+template int launch_pcg_xupdate<double>(int, int, double, int, double*, const double*, ColRed<double>, Skip,
+                                        cudaStream_t);
 
 int launch_sqrt_or_one(double* x, cudaStream_t s) {
     launch_k(k_sqrt_or_one, dim3(1), dim3(32), s, x);

@@ -213,6 +213,10 @@ int launch_pcg_update(const Op<T>& op, int N, T xscale, int assign, T* x, const 
 // (assign = 1: x = xscale alpha p instead of x += ..., for a zero start)
 template <typename T>
 int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s);
+// x (+)= xscale alpha p only: the last update when r and its norm are not needed (k_krylov.cu)
+template <typename T>
+int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, ColRed<T> cr, Skip sk,
+                       cudaStream_t s);
 
 // dense coarse-level apply Y = Ainv B  (n x n, row-major)
 template <typename T>

@@ -266,6 +266,10 @@ struct PCG {
         c.launches += launch_pcg_apply_alpha<T>(A, N, p, q, cr, sk2, st);
         const int assign = (assign_first && iter == 0) ? 1 : 0;
         ++iter;
+        if (last && !cr.pdone) {   // no tolerance: the final r and its norm are never read
+            c.launches += launch_pcg_xupdate<T>(A.rows, N, xscale, assign, x, p, cr, sk2, st);
+            return;
+        }
         // the next V-cycle's first sweep rides on the residual update
         Aux<T> aux = (gmg && !last) ? sweep_aux<T>(c, 0, opi, pa) : Aux<T>();
         c.launches += launch_pcg_update<T>(A, N, xscale, assign, x, p, r, q, gmg ? nullptr : z, gmg ? 0 : 1, cr,
