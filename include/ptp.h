@@ -188,7 +188,8 @@ int ptp_set_materials(ptp_ctx* ctx, const double* sigma_e,
        nu(s) = a min(exp(b s^2), c) + d,
    abcd[4 * n_tri] = (a, b, c, d) per element, read on nonlinear elements
    only (a >= 0, b > 0, c >= 1, d > 0).  NULL restores the saturating law.
-   Call after ptp_set_materials.  The adjoint entry points reject this law. */
+   Call after ptp_set_materials.  The adjoint and Newton entry points reject
+   this law. */
 int ptp_set_law_exp(ptp_ctx* ctx, const double* abcd);
 
 /* Per-element weights of the linear operator of the fixed-point iteration,
@@ -304,8 +305,10 @@ int ptp_spatial_solve_f32_dev(ptp_ctx* ctx, int level, const float* B, float* X,
 
 /* Multigrid in time for the periodic linear system of level 0,
    (M + tau L) x^n - M x^{n-1} = b^n, x^0 = x^N: `cycles` V-cycles from
-   x = 0 in the precision chosen at setup (inputs/outputs double).
-   *relres receives ||b - P x|| / ||b|| (may be NULL).  Synchronises. */
+   x = 0 in the precision chosen at setup (inputs/outputs double); with
+   coarse_solver = PTP_COARSE_DFT and time_levels = 1 one cycle is the DFT
+   solve itself.  *relres receives ||b - P x|| / ||b|| (may be NULL).
+   Synchronises. */
 int ptp_periodic_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* B,
                            double* X, int cycles, double* relres);
 
