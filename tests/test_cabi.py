@@ -78,3 +78,33 @@ def test_no_cpu_fallback_in_product_package():
             if f.endswith((".py", ".cu", ".cpp", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", text).lower() or f.endswith(".h"), f
+
+
+def test_new_option_defaults(ptp):
+    o = ptp.default_opts()
+    assert o.coarse_solver == ptp.PTP_COARSE_VCYCLES and o.dft_max_it == 30
+    assert o.init_static == 0 and o.init_tol == 0.0
+    assert o.newton_eta == 1e-2 and o.krylov_dim == 20
+
+
+def test_law_and_khat_validation_without_gpu(ptp):
+    import workloads as W
+    prob = W.paper_transformer_problem(11, 13, 4)
+    c = ptp.Context(0)
+    c.set_structured(*prob.grid)
+    with pytest.raises(ptp.PtpError) as e:          # the law needs the materials first
+        c.set_law_exp(prob.law_abcd)
+    assert e.value.code == ptp.PTP_EINVAL
+    c.set_materials(prob.sigma_e, prob.nonlinear_e, prob.nu_min, prob.nu_max, prob.s_sat, prob.nu_linear)
+    c.set_law_exp(prob.law_abcd)
+    bad = prob.law_abcd.copy()
+    bad[np.flatnonzero(prob.nonlinear_e)[0], 2] = 0.5   # c < 1
+    with pytest.raises(ptp.PtpError):
+        c.set_law_exp(bad)
+    c.set_law_exp(None)
+    c.set_khat(prob.khat_e)
+    k = prob.khat_e.copy()
+    k[3] = -1.0
+    with pytest.raises(ptp.PtpError):
+        c.set_khat(k)
+    c.set_khat(None)
