@@ -61,6 +61,14 @@ INNER = {
 WORKLOAD = "square257_N256"
 
 
+def inner_opts(args):
+    """Solver options of the chosen inner solve, with --dft-max-it applied."""
+    o = dict(INNER[args.inner]["opts"])
+    if args.dft_max_it is not None:
+        o["dft_max_it"] = args.dft_max_it
+    return o
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -258,7 +266,7 @@ def run_ours(args):
         c = ptp.Context(local)
         c.set_stream(stream.cuda_stream)
         ptp.load_problem(c, prob)
-        o = ptp.default_opts(precision=precision, tol=TOL, max_outer=args.max_outer, **inner["opts"])
+        o = ptp.default_opts(precision=precision, tol=TOL, max_outer=args.max_outer, **inner_opts(args))
         c.setup(o)
         return c, o
 
@@ -408,6 +416,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": "257x257 nodes, 131072 triangles", "free_nodes": n,
                        "time_steps": N, "space_time_dofs": dofs, "tol": TOL, "precision": "mixed",
                        "inner_solver": inner["name"],
+                       "dft_max_it": opts.dft_max_it if opts.coarse_solver == ptp.PTP_COARSE_DFT else None,
                        "outer_iterations": iters, "final_rel_residual": res_rel,
                        "l2": "inputs larger than L2 (U alone is 133 MB)", "parallelism": f"replicas{world}"},
             "fp64": fp64,
@@ -513,7 +522,7 @@ def run_paper(args):
     # this resolution is beyond float precision; several PCG iterations per
     # spatial solve, since linear-interpolation multigrid is weaker on such jumps
     o = ptp.default_opts(precision=ptp.PTP_FP64, tol=1e-4, max_outer=2000, init_static=1, init_tol=1e-8,
-                         pcg_iters=args.paper_pcg, **INNER[args.inner]["opts"])
+                         pcg_iters=args.paper_pcg, **inner_opts(args))
     c.setup(o)
     n, Nn = prob.n_free, prob.N
     dofs = n * Nn
@@ -548,6 +557,7 @@ def run_paper(args):
             "config": {"workload": prob.name, "free_nodes": n, "time_steps": Nn, "space_time_dofs": dofs,
                        "tol": 1e-4, "precision": "fp64", "init": "static solutions, init_tol 1e-8",
                        "inner_solver": INNER[args.inner]["name"], "pcg_iters": args.paper_pcg,
+                       "dft_max_it": o.dft_max_it if o.coarse_solver == ptp.PTP_COARSE_DFT else None,
                        "outer_iterations": its, "init_iterations": init_its,
                        "fixed_point_ms": fp_ms, "init_ms": ini_ms,
                        "with_init_dofs_per_s": dofs / (total_ms / 1e3)},
@@ -608,6 +618,8 @@ def main():
     ap.add_argument("--inner", choices=sorted(INNER), default="mg",
                     help="inner periodic solve: multigrid in time (mg), two-level with the DFT-in-time "
                          "coarse solve (dft2), or the DFT in time alone (dft)")
+    ap.add_argument("--dft-max-it", type=int, default=None,
+                    help="COCG iterations per DFT-in-time solve (library default 30)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--allow-unconverged", action="store_true",
                     help="profiling only: accept solves cut short by --max-outer")
