@@ -164,8 +164,9 @@ int  ptp_set_stream(ptp_ctx* ctx, void* stream);
 
 /* Triangle mesh: xy[2*n_nodes] coordinates, tri[3*n_tri] counter-clockwise
    vertex ids (0-based), dirichlet[n_nodes] = 1 for homogeneous Dirichlet
-   nodes (u = 0, Section 4).  Returns PTP_EINVAL for bad ids or clockwise /
-   degenerate triangles. */
+   nodes (u = 0, Section 4).  Returns PTP_EINVAL for vertex ids out of range
+   or non-finite coordinates; clockwise or degenerate triangles make
+   ptp_setup return PTP_EINVAL. */
 int ptp_set_mesh(ptp_ctx* ctx, int n_nodes, const double* xy, int n_tri,
                  const int32_t* tri, const uint8_t* dirichlet);
 
@@ -173,12 +174,16 @@ int ptp_set_mesh(ptp_ctx* ctx, int n_nodes, const double* xy, int n_tri,
    with node (i,j) = j*nx+i, cells split along (i,j)-(i+1,j+1), boundary
    Dirichlet, and build exactly that mesh (replacing any previous mesh).
    Enables the geometric-multigrid preconditioner when nx-1 and ny-1 are
-   divisible by 2 on at least one coarsening. */
+   divisible by 2 on at least one coarsening.  PTP_EINVAL unless nx, ny >= 2,
+   nx * ny <= 2^28 and the bounds are finite with x0 < x1, y0 < y1. */
 int ptp_set_structured(ptp_ctx* ctx, int nx, int ny, double x0, double y0,
                        double x1, double y1);
 
 /* Materials per element (Section 4, "Test problem"): conductivity sigma_e
-   (>= 0), nonlinear_e = 1 for the iron law, else nu_linear. */
+   (finite, >= 0), nonlinear_e = 1 for the iron law, else nu_linear; both
+   arrays hold n_tri entries of the mesh set last.  PTP_EINVAL unless
+   0 < nu_min <= nu_max, 0 < nu_linear (both finite) and
+   1e-15 <= s_sat <= 1e15. */
 int ptp_set_materials(ptp_ctx* ctx, const double* sigma_e,
                       const uint8_t* nonlinear_e, double nu_min,
                       double nu_max, double s_sat, double nu_linear);
@@ -199,11 +204,15 @@ int ptp_set_law_exp(ptp_ctx* ctx, const double* abcd);
 int ptp_set_khat(ptp_ctx* ctx, const double* khat_e);
 
 /* Coils: coil_of_elem[n_tri] in [-1, n_coils), amplitude and phase per
-   coil; the current density on coil c is amp_c sin(2 pi t/T + phase_c). */
+   coil (finite); the current density on coil c is amp_c sin(2 pi t/T +
+   phase_c).  n_coils = 0 removes every source (the arrays may then be NULL).
+   Every entry is checked before the context changes: a call that returns
+   PTP_EINVAL leaves the previous sources in place. */
 int ptp_set_sources(ptp_ctx* ctx, int n_coils, const int32_t* coil_of_elem,
                     const double* amp, const double* phase);
 
-/* Period T > 0 and number of implicit-Euler steps N >= 1 (tau = T/N). */
+/* Period T > 0 (finite) and number of implicit-Euler steps N >= 1
+   (tau = T/N). */
 int ptp_set_time(ptp_ctx* ctx, double T, int N);
 
 /* Assemble every operator and hierarchy on the device for `opts`

@@ -168,6 +168,8 @@ int ptp_set_mesh(ptp_ctx* h, int n_nodes, const double* xy, int n_tri, const int
         PTP_REQUIRE(n_nodes > 0 && n_tri > 0 && xy && tri && dirichlet, "ptp_set_mesh: bad arguments");
         for (int64_t k = 0; k < 3 * (int64_t)n_tri; ++k)
             PTP_REQUIRE(tri[k] >= 0 && tri[k] < n_nodes, "ptp_set_mesh: vertex id out of range");
+        for (int64_t k = 0; k < 2 * (int64_t)n_nodes; ++k)
+            PTP_REQUIRE(std::isfinite(xy[k]), "ptp_set_mesh: non-finite coordinate");
         c.n_nodes = n_nodes;
         c.n_tri = n_tri;
         c.xy.assign(xy, xy + 2 * (size_t)n_nodes);
@@ -192,10 +194,12 @@ int ptp_set_materials(ptp_ctx* h, const double* sigma_e, const uint8_t* nonlinea
     return guarded(h, [&](Ctx& c) {
         PTP_REQUIRE(c.n_tri > 0, "ptp_set_materials: set the mesh first");
         PTP_REQUIRE(sigma_e && nonlinear_e, "ptp_set_materials: null array");
-        PTP_REQUIRE(nu_min > 0 && nu_max >= nu_min && nu_linear > 0 && s_sat >= 1e-15 && s_sat <= 1e15,
-                    "ptp_set_materials: need 0 < nu_min <= nu_max, nu_linear > 0, 1e-15 <= s_sat <= 1e15");
+        PTP_REQUIRE(nu_min > 0 && nu_max >= nu_min && nu_linear > 0 && s_sat >= 1e-15 && s_sat <= 1e15 &&
+                        std::isfinite(nu_max) && std::isfinite(nu_linear),
+                    "ptp_set_materials: need 0 < nu_min <= nu_max, nu_linear > 0 (finite), 1e-15 <= s_sat <= 1e15");
         for (int e = 0; e < c.n_tri; ++e)
-            PTP_REQUIRE(sigma_e[e] >= 0.0, "ptp_set_materials: negative conductivity");
+            PTP_REQUIRE(sigma_e[e] >= 0.0 && std::isfinite(sigma_e[e]),
+                        "ptp_set_materials: negative or non-finite conductivity");
         c.sigma.assign(sigma_e, sigma_e + c.n_tri);
         c.nonlinear.assign(nonlinear_e, nonlinear_e + c.n_tri);
         c.nu_min = nu_min;
@@ -211,6 +215,7 @@ int ptp_set_materials(ptp_ctx* h, const double* sigma_e, const uint8_t* nonlinea
 int ptp_set_law_exp(ptp_ctx* h, const double* abcd) {
     return guarded(h, [&](Ctx& c) {
         PTP_REQUIRE(c.have_materials, "ptp_set_law_exp: set the materials first");
+        PTP_REQUIRE((int)c.nonlinear.size() == c.n_tri, "ptp_set_law_exp: the materials do not match the mesh");
         if (!abcd) {
             c.law_exp = false;
             c.law_abcd.clear();
@@ -251,16 +256,25 @@ int ptp_set_sources(ptp_ctx* h, int n_coils, const int32_t* coil_of_elem, const 
         PTP_REQUIRE(c.n_tri > 0, "ptp_set_sources: set the mesh first");
         PTP_REQUIRE(n_coils >= 0, "ptp_set_sources: negative coil count");
         PTP_REQUIRE(n_coils == 0 || (coil_of_elem && amp && phase), "ptp_set_sources: null array");
-        c.n_coils = n_coils;
-        c.coil_of_elem.assign(c.n_tri, -1);
+        // everything is checked before the context changes, so a rejected
+        // call leaves the previous sources in place
         if (n_coils > 0) {
-            for (int e = 0; e < c.n_tri; ++e) {
+            for (int e = 0; e < c.n_tri; ++e)
                 PTP_REQUIRE(coil_of_elem[e] >= -1 && coil_of_elem[e] < n_coils,
                             "ptp_set_sources: coil id out of range");
-                c.coil_of_elem[e] = coil_of_elem[e];
-            }
+            for (int k = 0; k < n_coils; ++k)
+                PTP_REQUIRE(std::isfinite(amp[k]) && std::isfinite(phase[k]),
+                            "ptp_set_sources: non-finite amplitude or phase");
+        }
+        c.n_coils = n_coils;
+        if (n_coils > 0) {
+            c.coil_of_elem.assign(coil_of_elem, coil_of_elem + c.n_tri);
             c.amp.assign(amp, amp + n_coils);
             c.phase.assign(phase, phase + n_coils);
+        } else {
+            c.coil_of_elem.assign(c.n_tri, -1);
+            c.amp.clear();
+            c.phase.clear();
         }
         invalidate(c);
         return PTP_OK;
@@ -269,7 +283,7 @@ int ptp_set_sources(ptp_ctx* h, int n_coils, const int32_t* coil_of_elem, const 
 
 int ptp_set_time(ptp_ctx* h, double T, int N) {
     return guarded(h, [&](Ctx& c) {
-        PTP_REQUIRE(T > 0 && N >= 1, "ptp_set_time: need T > 0 and N >= 1");
+        PTP_REQUIRE(T > 0 && std::isfinite(T) && N >= 1, "ptp_set_time: need a finite T > 0 and N >= 1");
         c.T = T;
         c.N = N;
         invalidate(c);

@@ -271,7 +271,10 @@ void upload_csr(DevCSR& d, const HostCSR& a, const HostCSR* b, bool diag, cudaSt
 
 void make_structured_mesh(Ctx& c, int nx, int ny, double x0, double y0, double x1, double y1) {
     PTP_REQUIRE(nx >= 2 && ny >= 2, "structured grid needs nx, ny >= 2");
-    PTP_REQUIRE(x1 > x0 && y1 > y0, "structured grid needs x1 > x0 and y1 > y0");
+    PTP_REQUIRE((int64_t)nx * ny <= ((int64_t)1 << 28), "structured grid: at most 2^28 nodes");
+    PTP_REQUIRE(x1 > x0 && y1 > y0 && std::isfinite(x0) && std::isfinite(x1) && std::isfinite(y0) &&
+                    std::isfinite(y1),
+                "structured grid needs finite x1 > x0 and y1 > y0");
     c.n_nodes = nx * ny;
     c.xy.assign(2 * (size_t)c.n_nodes, 0.0);
     for (int j = 0; j < ny; ++j)
@@ -304,6 +307,9 @@ void build_problem(Ctx& c) {
     PTP_REQUIRE(c.N >= 1 && c.T > 0, "time not set");
     PTP_REQUIRE((int)c.sigma.size() == c.n_tri, "materials do not match the mesh");
     PTP_REQUIRE((int)c.coil_of_elem.size() == c.n_tri || c.n_coils == 0, "sources do not match the mesh");
+    PTP_REQUIRE((int)c.nonlinear.size() == c.n_tri, "materials do not match the mesh");
+    PTP_REQUIRE(!c.law_exp || c.law_abcd.size() == 4 * (size_t)c.n_tri, "the exponential law does not match the mesh");
+    PTP_REQUIRE(c.khat.empty() || (int)c.khat.size() == c.n_tri, "the K_hat weights do not match the mesh");
     cudaStream_t s = c.stream;
     const double tau = c.T / c.N;
 

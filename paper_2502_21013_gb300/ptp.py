@@ -177,6 +177,13 @@ class Context:
         if rc != PTP_OK:
             raise PtpError(rc, "ptp_create failed")
         self.device = device
+        self._n_tri = None    # triangles of the mesh last set, for the array-length checks
+
+    def _need_len(self, name, a, shape):
+        """The per-element arrays are read with the mesh's triangle count by
+        the library, so their lengths are checked here first."""
+        if tuple(a.shape) != tuple(shape):
+            raise PtpError(PTP_EINVAL, f"{name}: expected shape {tuple(shape)}, got {tuple(a.shape)}")
 
     def close(self):
         if self._h:
@@ -202,32 +209,51 @@ class Context:
         xy, pxy = _np(xy, np.float64)
         tri, ptri = _np(tri, np.int32)
         dr, pdr = _np(dirichlet, np.uint8)
-        return self._check(lib.ptp_set_mesh(self._h, xy.shape[0], pxy, tri.shape[0], ptri, pdr))
+        if xy.ndim != 2 or xy.shape[1] != 2 or tri.ndim != 2 or tri.shape[1] != 3:
+            raise PtpError(PTP_EINVAL, "set_mesh: xy must be (n_nodes, 2) and tri (n_tri, 3)")
+        self._need_len("set_mesh dirichlet", dr, (xy.shape[0],))
+        rc = self._check(lib.ptp_set_mesh(self._h, xy.shape[0], pxy, tri.shape[0], ptri, pdr))
+        self._n_tri = tri.shape[0]
+        return rc
 
     def set_structured(self, nx, ny, x0, y0, x1, y1):
-        return self._check(lib.ptp_set_structured(self._h, nx, ny, x0, y0, x1, y1))
+        rc = self._check(lib.ptp_set_structured(self._h, nx, ny, x0, y0, x1, y1))
+        self._n_tri = 2 * (int(nx) - 1) * (int(ny) - 1)
+        return rc
 
     def set_materials(self, sigma_e, nonlinear_e, nu_min, nu_max, s_sat, nu_linear):
         s, ps = _np(sigma_e, np.float64)
         nl, pnl = _np(nonlinear_e, np.uint8)
+        if self._n_tri is not None:
+            self._need_len("set_materials sigma_e", s, (self._n_tri,))
+            self._need_len("set_materials nonlinear_e", nl, (self._n_tri,))
         return self._check(lib.ptp_set_materials(self._h, ps, pnl, nu_min, nu_max, s_sat, nu_linear))
 
     def set_law_exp(self, abcd):
         if abcd is None:
             return self._check(lib.ptp_set_law_exp(self._h, None))
         a, pa = _np(abcd, np.float64)
+        if self._n_tri is not None:
+            self._need_len("set_law_exp abcd", a, (self._n_tri, 4))
         return self._check(lib.ptp_set_law_exp(self._h, pa))
 
     def set_khat(self, khat_e):
         if khat_e is None:
             return self._check(lib.ptp_set_khat(self._h, None))
         k, pk = _np(khat_e, np.float64)
+        if self._n_tri is not None:
+            self._need_len("set_khat khat_e", k, (self._n_tri,))
         return self._check(lib.ptp_set_khat(self._h, pk))
 
     def set_sources(self, coil_of_elem, amp, phase):
         c, pc = _np(coil_of_elem, np.int32)
         a, pa = _np(amp, np.float64)
         ph, pph = _np(phase, np.float64)
+        if a.ndim != 1:
+            raise PtpError(PTP_EINVAL, "set_sources: amp must be one-dimensional")
+        self._need_len("set_sources phase", ph, a.shape)
+        if self._n_tri is not None and a.shape[0] > 0:
+            self._need_len("set_sources coil_of_elem", c, (self._n_tri,))
         return self._check(lib.ptp_set_sources(self._h, a.shape[0], pc, pa, pph))
 
     def set_time(self, T, N):

@@ -108,3 +108,47 @@ def test_law_and_khat_validation_without_gpu(ptp):
     with pytest.raises(ptp.PtpError):
         c.set_khat(k)
     c.set_khat(None)
+
+
+def test_non_finite_inputs_and_array_lengths_are_rejected(ptp):
+    import workloads as W
+    prob = W.unit_square_problem(9, 4)
+    c = ptp.Context(0)
+    xy = prob.xy.copy()
+    xy[3, 0] = np.nan
+    with pytest.raises(ptp.PtpError):
+        c.set_mesh(xy, prob.tri, prob.dirichlet)
+    with pytest.raises(ptp.PtpError):
+        c.set_structured(9, 9, 0.0, 0.0, np.inf, 1.0)
+    with pytest.raises(ptp.PtpError):
+        c.set_structured(1 << 15, 1 << 15, 0.0, 0.0, 1.0, 1.0)   # more than 2^28 nodes
+    ptp.load_problem(c, prob)
+    s = prob.sigma_e.copy()
+    s[0] = np.inf
+    with pytest.raises(ptp.PtpError):
+        c.set_materials(s, prob.nonlinear_e, 1.0, 100.0, 1.0, 100.0)
+    with pytest.raises(ptp.PtpError):
+        c.set_materials(prob.sigma_e, prob.nonlinear_e, 1.0, np.inf, 1.0, 100.0)
+    with pytest.raises(ptp.PtpError):
+        c.set_time(np.inf, 4)
+    amp = np.array(prob.amp, dtype=np.float64)
+    amp[0] = np.nan
+    with pytest.raises(ptp.PtpError):
+        c.set_sources(prob.coil_of_elem, amp, prob.phase)
+    # per-element arrays must match the mesh: the library reads n_tri entries
+    with pytest.raises(ptp.PtpError) as e:
+        c.set_materials(prob.sigma_e[:-1], prob.nonlinear_e[:-1], 1.0, 100.0, 1.0, 100.0)
+    assert e.value.code == ptp.PTP_EINVAL
+    with pytest.raises(ptp.PtpError):
+        c.set_sources(prob.coil_of_elem[:-1], prob.amp, prob.phase)
+    with pytest.raises(ptp.PtpError):
+        c.set_sources(prob.coil_of_elem, prob.amp, np.zeros(len(prob.amp) + 1))
+    with pytest.raises(ptp.PtpError):
+        c.set_khat(np.ones(prob.n_tri + 1))
+    with pytest.raises(ptp.PtpError):
+        c.set_law_exp(np.ones((prob.n_tri, 3)))
+    with pytest.raises(ptp.PtpError):
+        c.set_mesh(prob.xy, prob.tri, prob.dirichlet[:-1])
+    # the valid problem still loads after the rejected calls
+    ptp.load_problem(c, prob)
+    c.close()
