@@ -157,9 +157,15 @@ def _np(a, dtype):
     return a, a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _dev_ptr(t, dtype_name):
+def _dev_ptr(t, dtype_name, count=None):
+    """Device address of a contiguous CUDA tensor of the given dtype; `count`
+    (when known) is the number of elements the library reads or writes."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("_dev entry points take CUDA tensors")
+    if count is not None and t.numel() != count:
+        raise PtpError(PTP_EINVAL, f"expected a tensor of {count} elements, got {t.numel()}")
+    if not t.is_cuda:
         raise TypeError("_dev entry points take CUDA tensors")
     if str(t.dtype) != f"torch.{dtype_name}":
         raise TypeError(f"expected {dtype_name}, got {t.dtype}")
@@ -178,6 +184,31 @@ class Context:
             raise PtpError(rc, "ptp_create failed")
         self.device = device
         self._n_tri = None    # triangles of the mesh last set, for the array-length checks
+        self._sizes = None    # (n_free, N, n_tri, time levels) after a successful ptp_setup
+
+    def _count(self, level=0):
+        """Values of a space-time block on time level `level` (N >> level
+        steps: every coarsening halves an even step count), or None before
+        setup or for a level out of range (the library then reports the error)."""
+        if self._sizes is None:
+            return None
+        n, N, _, levels = self._sizes
+        level = int(level)
+        if not 0 <= level < levels:
+            return None
+        return n * (N >> level)
+
+    def _nN(self):
+        """(n_free, N) of the set-up problem."""
+        n, N, _, _ = self._sizes if self._sizes is not None else self.sizes()
+        return n, N
+
+    def _host_in(self, a, name):
+        a, pa = _np(a, np.float64)
+        count = self._count()
+        if count is not None and a.size != count:
+            raise PtpError(PTP_EINVAL, f"{name}: expected {count} values, got {a.size}")
+        return a, pa
 
     def _need_len(self, name, a, shape):
         """The per-element arrays are read with the mesh's triangle count by
@@ -203,9 +234,11 @@ class Context:
 
     # ---- problem definition ----
     def set_stream(self, stream_ptr: int | None):
+        self._sizes = None
         return self._check(lib.ptp_set_stream(self._h, ctypes.c_void_p(stream_ptr or 0)))
 
     def set_mesh(self, xy, tri, dirichlet):
+        self._sizes = None
         xy, pxy = _np(xy, np.float64)
         tri, ptri = _np(tri, np.int32)
         dr, pdr = _np(dirichlet, np.uint8)
@@ -217,11 +250,13 @@ class Context:
         return rc
 
     def set_structured(self, nx, ny, x0, y0, x1, y1):
+        self._sizes = None
         rc = self._check(lib.ptp_set_structured(self._h, nx, ny, x0, y0, x1, y1))
         self._n_tri = 2 * (int(nx) - 1) * (int(ny) - 1)
         return rc
 
     def set_materials(self, sigma_e, nonlinear_e, nu_min, nu_max, s_sat, nu_linear):
+        self._sizes = None
         s, ps = _np(sigma_e, np.float64)
         nl, pnl = _np(nonlinear_e, np.uint8)
         if self._n_tri is not None:
@@ -230,6 +265,7 @@ class Context:
         return self._check(lib.ptp_set_materials(self._h, ps, pnl, nu_min, nu_max, s_sat, nu_linear))
 
     def set_law_exp(self, abcd):
+        self._sizes = None
         if abcd is None:
             return self._check(lib.ptp_set_law_exp(self._h, None))
         a, pa = _np(abcd, np.float64)
@@ -238,6 +274,7 @@ class Context:
         return self._check(lib.ptp_set_law_exp(self._h, pa))
 
     def set_khat(self, khat_e):
+        self._sizes = None
         if khat_e is None:
             return self._check(lib.ptp_set_khat(self._h, None))
         k, pk = _np(khat_e, np.float64)
@@ -246,6 +283,7 @@ class Context:
         return self._check(lib.ptp_set_khat(self._h, pk))
 
     def set_sources(self, coil_of_elem, amp, phase):
+        self._sizes = None
         c, pc = _np(coil_of_elem, np.int32)
         a, pa = _np(amp, np.float64)
         ph, pph = _np(phase, np.float64)
@@ -257,11 +295,15 @@ class Context:
         return self._check(lib.ptp_set_sources(self._h, a.shape[0], pc, pa, pph))
 
     def set_time(self, T, N):
+        self._sizes = None
         return self._check(lib.ptp_set_time(self._h, float(T), int(N)))
 
     def setup(self, opts: Opts | None = None):
         self.opts = opts if opts is not None else default_opts()
-        return self._check(lib.ptp_setup(self._h, ctypes.byref(self.opts)))
+        self._sizes = None
+        rc = self._check(lib.ptp_setup(self._h, ctypes.byref(self.opts)))
+        self._sizes = self.sizes()
+        return rc
 
     def sizes(self):
         v = [ctypes.c_int() for _ in range(4)]
@@ -284,26 +326,35 @@ class Context:
         return {k: int(buf[i]) for i, k in enumerate(self.INFO_KEYS[:m])}
 
     # ---- hot path, host pointers ----
+    @staticmethod
+    def _check_out(U, count):
+        """A caller's output array must be a writable C-contiguous float64
+        block of `count` values: the library writes it in place."""
+        if (not isinstance(U, np.ndarray) or U.dtype != np.float64 or not U.flags.c_contiguous
+                or not U.flags.writeable or U.size != count):
+            raise PtpError(PTP_EINVAL, f"output: expected a writable C-contiguous float64 array of {count} values")
+
     def source(self):
-        n, N, _, _ = self.sizes()
+        n, N = self._nN()
         F = np.empty((n, N))
         self._check(lib.ptp_source(self._h, F.ctypes.data_as(ctypes.c_void_p)))
         return F
 
     def residual(self, U):
-        U, pU = _np(U, np.float64)
+        U, pU = self._host_in(U, "residual U")
         R = np.empty_like(U)
         nrm = ctypes.c_double()
         self._check(lib.ptp_residual(self._h, pU, R.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nrm)))
         return R, nrm.value
 
     def solve(self, opts: Opts | None = None, U0=None, U_out=None):
-        n, N, _, _ = self.sizes()
+        n, N = self._nN()
         o = opts if opts is not None else self.opts
         U = U_out if U_out is not None else np.empty((n, N))
+        self._check_out(U, n * N)
         p0 = None
         if U0 is not None:
-            U0, p0 = _np(U0, np.float64)
+            U0, p0 = self._host_in(U0, "solve U0")
         st = Stats()
         rc = lib.ptp_solve(self._h, ctypes.byref(o), p0, U.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
         self._check(rc, allow=(PTP_ENOTCONV,))
@@ -311,9 +362,10 @@ class Context:
 
     def static_solve(self, opts: Opts | None = None, U_out=None):
         """Initialisation of Section 4: U with K(u^n) = f^n for every step (host array)."""
-        n, N, _, _ = self.sizes()
+        n, N = self._nN()
         o = opts if opts is not None else self.opts
         U = U_out if U_out is not None else np.empty((n, N))
+        self._check_out(U, n * N)
         st = Stats()
         rc = lib.ptp_static_solve(self._h, ctypes.byref(o), U.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
         self._check(rc, allow=(PTP_ENOTCONV,))
@@ -321,59 +373,67 @@ class Context:
 
     # ---- hot path, device pointers (torch CUDA tensors) ----
     def source_dev(self, F):
-        return self._check(lib.ptp_source_dev(self._h, _dev_ptr(F, "float64")))
+        return self._check(lib.ptp_source_dev(self._h, _dev_ptr(F, "float64", self._count())))
 
     def residual_dev(self, U, R=None, want_norm=True):
         """R = F - A(U) on the device; returns ||R|| (synchronising) or None."""
         nrm = ctypes.c_double()
-        pR = _dev_ptr(R, "float64") if R is not None else None
-        self._check(lib.ptp_residual_dev(self._h, _dev_ptr(U, "float64"), pR,
+        n = self._count()
+        pR = _dev_ptr(R, "float64", n) if R is not None else None
+        self._check(lib.ptp_residual_dev(self._h, _dev_ptr(U, "float64", n), pR,
                                          ctypes.byref(nrm) if want_norm else None))
         return nrm.value if want_norm else None
 
     def apply_shifted_dev(self, level, X, Y):
+        n = self._count(level)
         if X.dtype.is_floating_point and X.element_size() == 4:
-            return self._check(lib.ptp_apply_shifted_f32_dev(self._h, level, _dev_ptr(X, "float32"),
-                                                             _dev_ptr(Y, "float32")))
-        return self._check(lib.ptp_apply_shifted_dev(self._h, level, _dev_ptr(X, "float64"), _dev_ptr(Y, "float64")))
+            return self._check(lib.ptp_apply_shifted_f32_dev(self._h, level, _dev_ptr(X, "float32", n),
+                                                             _dev_ptr(Y, "float32", n)))
+        return self._check(lib.ptp_apply_shifted_dev(self._h, level, _dev_ptr(X, "float64", n),
+                                                     _dev_ptr(Y, "float64", n)))
 
     def periodic_apply_dev(self, level, X, Y):
-        return self._check(lib.ptp_periodic_apply_dev(self._h, level, _dev_ptr(X, "float64"), _dev_ptr(Y, "float64")))
+        n = self._count(level)
+        return self._check(lib.ptp_periodic_apply_dev(self._h, level, _dev_ptr(X, "float64", n),
+                                                      _dev_ptr(Y, "float64", n)))
 
     def spatial_solve_dev(self, level, B, X, tol, max_it):
         it = ctypes.c_int()
+        n = self._count(level)
         if B.element_size() == 4:
-            self._check(lib.ptp_spatial_solve_f32_dev(self._h, level, _dev_ptr(B, "float32"), _dev_ptr(X, "float32"),
-                                                      tol, max_it, ctypes.byref(it)))
+            self._check(lib.ptp_spatial_solve_f32_dev(self._h, level, _dev_ptr(B, "float32", n),
+                                                      _dev_ptr(X, "float32", n), tol, max_it, ctypes.byref(it)))
         else:
-            self._check(lib.ptp_spatial_solve_dev(self._h, level, _dev_ptr(B, "float64"), _dev_ptr(X, "float64"),
-                                                  tol, max_it, ctypes.byref(it)))
+            self._check(lib.ptp_spatial_solve_dev(self._h, level, _dev_ptr(B, "float64", n),
+                                                  _dev_ptr(X, "float64", n), tol, max_it, ctypes.byref(it)))
         return it.value
 
     def periodic_solve_dev(self, B, X, cycles, opts: Opts | None = None):
         rel = ctypes.c_double()
         o = ctypes.byref(opts) if opts is not None else None
-        self._check(lib.ptp_periodic_solve_dev(self._h, o, _dev_ptr(B, "float64"), _dev_ptr(X, "float64"),
+        n = self._count()
+        self._check(lib.ptp_periodic_solve_dev(self._h, o, _dev_ptr(B, "float64", n), _dev_ptr(X, "float64", n),
                                                int(cycles), ctypes.byref(rel)))
         return rel.value
 
     def solve_dev(self, U, opts: Opts | None = None, U0=None):
         o = opts if opts is not None else self.opts
         st = Stats()
-        p0 = _dev_ptr(U0, "float64") if U0 is not None else None
-        rc = lib.ptp_solve_dev(self._h, ctypes.byref(o), p0, _dev_ptr(U, "float64"), ctypes.byref(st))
+        n = self._count()
+        p0 = _dev_ptr(U0, "float64", n) if U0 is not None else None
+        rc = lib.ptp_solve_dev(self._h, ctypes.byref(o), p0, _dev_ptr(U, "float64", n), ctypes.byref(st))
         self._check(rc, allow=(PTP_ENOTCONV,))
         return st, rc
 
 
 def _newton_solve(ctx, opts=None, U0=None):
     """Newton's method (M2); returns (U, stats, rc) with U a host array."""
-    n, N, _, _ = ctx.sizes()
+    n, N = ctx._nN()
     o = opts if opts is not None else ctx.opts
     U = np.empty((n, N))
     p0 = None
     if U0 is not None:
-        U0, p0 = _np(U0, np.float64)
+        U0, p0 = ctx._host_in(U0, "newton_solve U0")
     st = Stats()
     rc = lib.ptp_newton_solve(ctx._h, ctypes.byref(o), p0, U.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
     ctx._check(rc, allow=(PTP_ENOTCONV,))
@@ -383,15 +443,17 @@ def _newton_solve(ctx, opts=None, U0=None):
 def _newton_solve_dev(ctx, U, opts=None, U0=None):
     o = opts if opts is not None else ctx.opts
     st = Stats()
-    p0 = _dev_ptr(U0, "float64") if U0 is not None else None
-    rc = lib.ptp_newton_solve_dev(ctx._h, ctypes.byref(o), p0, _dev_ptr(U, "float64"), ctypes.byref(st))
+    n = ctx._count()
+    p0 = _dev_ptr(U0, "float64", n) if U0 is not None else None
+    rc = lib.ptp_newton_solve_dev(ctx._h, ctypes.byref(o), p0, _dev_ptr(U, "float64", n), ctypes.byref(st))
     ctx._check(rc, allow=(PTP_ENOTCONV,))
     return st, rc
 
 
 def _jacobian_apply_dev(ctx, U, V, Y):
-    return ctx._check(lib.ptp_jacobian_apply_dev(ctx._h, _dev_ptr(U, "float64"), _dev_ptr(V, "float64"),
-                                                 _dev_ptr(Y, "float64")))
+    n = ctx._count()
+    return ctx._check(lib.ptp_jacobian_apply_dev(ctx._h, _dev_ptr(U, "float64", n), _dev_ptr(V, "float64", n),
+                                                 _dev_ptr(Y, "float64", n)))
 
 
 Context.newton_solve = _newton_solve
@@ -402,7 +464,7 @@ Context.jacobian_apply_dev = _jacobian_apply_dev
 def _static_solve_dev(ctx, U, opts=None):
     o = opts if opts is not None else ctx.opts
     st = Stats()
-    rc = lib.ptp_static_solve_dev(ctx._h, ctypes.byref(o), _dev_ptr(U, "float64"), ctypes.byref(st))
+    rc = lib.ptp_static_solve_dev(ctx._h, ctypes.byref(o), _dev_ptr(U, "float64", ctx._count()), ctypes.byref(st))
     ctx._check(rc, allow=(PTP_ENOTCONV,))
     return st, rc
 
@@ -412,7 +474,7 @@ Context.static_solve_dev = _static_solve_dev
 
 def _loss_dev(ctx, U):
     J = ctypes.c_double()
-    ctx._check(lib.ptp_loss_dev(ctx._h, _dev_ptr(U, "float64"), ctypes.byref(J)))
+    ctx._check(lib.ptp_loss_dev(ctx._h, _dev_ptr(U, "float64", ctx._count()), ctypes.byref(J)))
     return J.value
 
 
@@ -426,7 +488,8 @@ def _adjoint_gradient_dev(ctx, U, opts=None):
     dsig = torch.empty(info["n_tri"], dtype=torch.float64, device=U.device)
     st = Stats()
     o = opts if opts is not None else ctx.opts
-    rc = lib.ptp_adjoint_gradient_dev(ctx._h, ctypes.byref(o), _dev_ptr(U, "float64"), ctypes.byref(J), damp, dnu,
+    rc = lib.ptp_adjoint_gradient_dev(ctx._h, ctypes.byref(o), _dev_ptr(U, "float64", ctx._count()),
+                                      ctypes.byref(J), damp, dnu,
                                       _dev_ptr(dsig, "float64"), ctypes.byref(st))
     ctx._check(rc, allow=(PTP_ENOTCONV,))
     return J.value, [damp[k] for k in range(info["n_coils"])], [dnu[k] for k in range(3)], dsig, st, rc
@@ -465,7 +528,9 @@ class Batch:
         return [stats[i] for i in range(K)], nconv.value, rc
 
     def result_dev(self, i, U):
-        return self._check(lib.ptp_batch_result_dev(self._h, int(i), _dev_ptr(U, "float64")))
+        i = int(i)
+        n = self.contexts[i]._count() if 0 <= i < len(self.contexts) else None
+        return self._check(lib.ptp_batch_result_dev(self._h, i, _dev_ptr(U, "float64", n)))
 
     def close(self):
         if self._h:

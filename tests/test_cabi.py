@@ -152,3 +152,35 @@ def test_non_finite_inputs_and_array_lengths_are_rejected(ptp):
     # the valid problem still loads after the rejected calls
     ptp.load_problem(c, prob)
     c.close()
+
+
+def test_binding_checks_block_sizes_before_calling_the_library(ptp):
+    """The library reads and writes n * (N >> level) values per block; the
+    binding compares every array with that count first (sizes of a set-up
+    context are faked here, since ptp_setup needs a GPU)."""
+    torch = pytest.importorskip("torch")
+    c = ptp.Context(0)
+    c._sizes = (10, 8, 30, 3)          # n_free, N, n_tri, time levels
+    assert [c._count(l) for l in range(4)] == [80, 40, 20, None]
+    with pytest.raises(ptp.PtpError) as e:
+        c.apply_shifted_dev(0, torch.zeros(10, 4), torch.zeros(10, 4))
+    assert e.value.code == ptp.PTP_EINVAL and "80 elements" in str(e.value)
+    with pytest.raises(TypeError):     # right size, but not a CUDA tensor
+        c.apply_shifted_dev(1, torch.zeros(10, 4), torch.zeros(10, 4))
+    for call in (lambda: c.solve_dev(torch.zeros(10, 7), ptp.default_opts()),
+                 lambda: c.residual_dev(torch.zeros(10, 8), torch.zeros(81)),
+                 lambda: c.spatial_solve_dev(2, torch.zeros(10, 4), torch.zeros(10, 4), 1e-6, 5),
+                 lambda: c.periodic_solve_dev(torch.zeros(79), torch.zeros(80), 1),
+                 lambda: c.jacobian_apply_dev(torch.zeros(8), torch.zeros(80), torch.zeros(80)),
+                 lambda: c.loss_dev(torch.zeros(10, 9))):
+        with pytest.raises(ptp.PtpError):
+            call()
+    with pytest.raises(ptp.PtpError) as e:
+        c.residual(np.zeros((10, 7)))
+    assert "expected 80 values" in str(e.value)
+    with pytest.raises(ptp.PtpError) as e:
+        c.solve(ptp.default_opts(), U_out=np.zeros((10, 8), dtype=np.float32))
+    assert "float64" in str(e.value)
+    c.set_time(1.0, 4)                 # any change of the problem forgets the sizes
+    assert c._sizes is None and c._count() is None
+    c.close()
