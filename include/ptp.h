@@ -273,12 +273,14 @@ int ptp_source_dev(ptp_ctx* ctx, double* F);
 /* Outer residual R = F - A(U), A(U)^n = M (u^n - u^{n-1})/tau + K(u^n),
    u^0 = u^N (proof of Theorem 2), all [n_free][N] in double, and its
    Euclidean norm (stopping rule of Section 4).  `norm` may be NULL.
-   The _dev form writes the norm to host memory after synchronising. */
+   The _dev form writes the norm to host memory after synchronising; its R
+   must not be U (PTP_EINVAL). */
 int ptp_residual(ptp_ctx* ctx, const double* U, double* R, double* norm);
 int ptp_residual_dev(ptp_ctx* ctx, const double* U, double* R, double* norm);
 
 /* Y = (M + tau_l L) X for the N_l = N / 2^l columns of time level l
-   (the diagonal blocks of the periodic system at level l), double. */
+   (the diagonal blocks of the periodic system at level l), double.  X and Y
+   are different buffers (PTP_EINVAL if equal). */
 int ptp_apply_shifted_dev(ptp_ctx* ctx, int level, const double* X, double* Y);
 /* Same in float (the operator values rounded to float), for PTP_MIXED. */
 int ptp_apply_shifted_f32_dev(ptp_ctx* ctx, int level, const float* X, float* Y);
@@ -300,13 +302,15 @@ int ptp_apply_shifted_f32_dev(ptp_ctx* ctx, int level, const float* X, float* Y)
 int ptp_residual_noalloc_dev(ptp_ctx* ctx, const double* U, double* R, double* norm);
 
 /* Periodic operator of level l: Y^n = (M + tau_l L) X^n - M X^{n-1},
-   X^0 = X^{N_l} (eq. iter1 multiplied by tau_l), double. */
+   X^0 = X^{N_l} (eq. iter1 multiplied by tau_l), double.  X and Y are
+   different buffers (PTP_EINVAL if equal). */
 int ptp_periodic_apply_dev(ptp_ctx* ctx, int level, const double* X, double* Y);
 
 /* Batched PCG: solve (M + tau_l L) X = B column by column (N_l columns),
    starting from X = 0, with the preconditioner chosen at setup, until every
    column's residual is <= tol * ||b_col|| or max_it iterations.  *iters
-   receives the iterations run (may be NULL).  Synchronises. */
+   receives the iterations run (may be NULL).  B and X are different buffers
+   (PTP_EINVAL if equal).  Synchronises. */
 int ptp_spatial_solve_dev(ptp_ctx* ctx, int level, const double* B, double* X,
                           double tol, int max_it, int* iters);
 int ptp_spatial_solve_f32_dev(ptp_ctx* ctx, int level, const float* B, float* X,
@@ -316,8 +320,8 @@ int ptp_spatial_solve_f32_dev(ptp_ctx* ctx, int level, const float* B, float* X,
    (M + tau L) x^n - M x^{n-1} = b^n, x^0 = x^N: `cycles` V-cycles from
    x = 0 in the precision chosen at setup (inputs/outputs double); with
    coarse_solver = PTP_COARSE_DFT and time_levels = 1 one cycle is the DFT
-   solve itself.  *relres receives ||b - P x|| / ||b|| (may be NULL).
-   Synchronises. */
+   solve itself.  *relres receives ||b - P x|| / ||b|| (may be NULL).  B and X
+   are different buffers (PTP_EINVAL if equal).  Synchronises. */
 int ptp_periodic_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* B,
                            double* X, int cycles, double* relres);
 
@@ -350,7 +354,8 @@ int ptp_newton_solve_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* U0,
                          double* U, ptp_stats* stats);
 
 /* Y = J(U) V, the Jacobian of A at U applied to V (all device pointers,
-   [n_free][N] doubles; synchronises).  Saturating law only. */
+   [n_free][N] doubles; Y is neither U nor V; synchronises).  Saturating law
+   only. */
 int ptp_jacobian_apply_dev(ptp_ctx* ctx, const double* U, const double* V, double* Y);
 
 /* Fixed-point solve of Problem 1 (eq. iter1-iter2 in correction form) from

@@ -392,7 +392,7 @@ static int residual_impl(Ctx& c, const double* U, double* R, double* norm) {
 int ptp_residual_dev(ptp_ctx* h, const double* U, double* R, double* norm) {
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
-        PTP_REQUIRE(U, "ptp_residual: null input");
+        PTP_REQUIRE(U && U != R, "ptp_residual: null input, or R is U");
         return residual_impl(c, U, R, norm);
     });
 }
@@ -415,7 +415,7 @@ int ptp_apply_shifted_dev(ptp_ctx* h, int level, const double* X, double* Y) {
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
         const int N = check_level(c, level);
-        PTP_REQUIRE(X && Y, "ptp_apply_shifted: null pointer");
+        PTP_REQUIRE(X && Y && (const void*)X != (const void*)Y, "ptp_apply_shifted: null or aliased pointers");
         ptp::apply_op<double>(c, 0, c.tl[level].op, N, X, Y);
         PTP_CUDA(cudaGetLastError());
         return PTP_OK;
@@ -426,7 +426,7 @@ int ptp_apply_shifted_f32_dev(ptp_ctx* h, int level, const float* X, float* Y) {
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
         const int N = check_level(c, level);
-        PTP_REQUIRE(X && Y, "ptp_apply_shifted_f32: null pointer");
+        PTP_REQUIRE(X && Y && (const void*)X != (const void*)Y, "ptp_apply_shifted_f32: null or aliased pointers");
         ptp::apply_op<float>(c, 0, c.tl[level].op, N, X, Y);
         PTP_CUDA(cudaGetLastError());
         return PTP_OK;
@@ -449,7 +449,7 @@ int ptp_spatial_solve_dev(ptp_ctx* h, int level, const double* B, double* X, dou
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
         const int N = check_level(c, level);
-        PTP_REQUIRE(B && X && max_it >= 1, "ptp_spatial_solve: bad arguments");
+        PTP_REQUIRE(B && X && (const void*)B != (const void*)X && max_it >= 1, "ptp_spatial_solve: bad arguments");
         int it = ptp::spatial_pcg<double>(c, c.tl[level].op, N, B, X, tol, max_it, true);
         PTP_CUDA(cudaGetLastError());
         if (iters) *iters = it;
@@ -462,7 +462,7 @@ int ptp_spatial_solve_f32_dev(ptp_ctx* h, int level, const float* B, float* X, d
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
         const int N = check_level(c, level);
-        PTP_REQUIRE(B && X && max_it >= 1, "ptp_spatial_solve_f32: bad arguments");
+        PTP_REQUIRE(B && X && (const void*)B != (const void*)X && max_it >= 1, "ptp_spatial_solve_f32: bad arguments");
         int it = ptp::spatial_pcg<float>(c, c.tl[level].op, N, B, X, tol, max_it, true);
         PTP_CUDA(cudaGetLastError());
         if (iters) *iters = it;
@@ -474,7 +474,7 @@ int ptp_periodic_solve_dev(ptp_ctx* h, const ptp_opts* opts, const double* B, do
                            double* relres) {
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
-        PTP_REQUIRE(B && X && cycles >= 1, "ptp_periodic_solve: bad arguments");
+        PTP_REQUIRE(B && X && (const void*)B != (const void*)X && cycles >= 1, "ptp_periodic_solve: bad arguments");
         if (opts) {
             PTP_REQUIRE(opts->precision == c.opts.precision && opts->spatial_prec == c.opts.spatial_prec &&
                             opts->time_levels == c.opts.time_levels && opts->coarse_steps == c.opts.coarse_steps &&
@@ -559,7 +559,7 @@ int ptp_newton_solve(ptp_ctx* h, const ptp_opts* opts, const double* U0, double*
 int ptp_jacobian_apply_dev(ptp_ctx* h, const double* U, const double* V, double* Y) {
     return guarded(h, [&](Ctx& c) {
         need_ready(c);
-        PTP_REQUIRE(U && V && Y, "ptp_jacobian_apply_dev: null pointer");
+        PTP_REQUIRE(U && V && Y && Y != U && Y != V, "ptp_jacobian_apply_dev: null pointer, or Y is U or V");
         PTP_REQUIRE(!c.law_exp, "ptp_jacobian_apply_dev: saturating reluctivity law only");
         ptp::alloc_adjoint(c);
         c.launches += ptp::launch_adj_jacobian(ptp::adjoint_args(c), U, c.stream, false);
