@@ -44,3 +44,83 @@ def test_delaunay_mesh_is_valid():
     deg = np.bincount(p.tri.ravel(), minlength=p.n_nodes)
     assert deg.max() >= 8                       # rows wider than the structured stencil
     assert p.nonlinear_e.sum() > 0 and (p.coil_of_elem >= 0).sum() > 0
+
+
+def _paper_fixture():
+    import math
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_transformer_section4.txt")
+    labels, materials, out = [], {}, {}
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if not f:
+            continue
+        if f[0] == "label":
+            labels.append((f[1], float(f[2]), float(f[3])))
+        elif f[0] == "material":
+            val = [1e7 / (4 * math.pi) if v == "nu_air" else (None if v == "-" else float(v)) for v in f[2:]]
+            materials[f[1]] = val
+        else:
+            out[f[0]] = [float(v) for v in f[1:]]
+    return labels, materials, out
+
+
+def _region_of_elements(prob):
+    steel = prob.nonlinear_e.astype(bool) & (prob.sigma_e > 0)
+    iron = prob.nonlinear_e.astype(bool) & (prob.sigma_e == 0)
+    reg = np.full(prob.n_tri, "air", dtype=object)
+    reg[steel] = "steel"
+    reg[iron] = "iron"
+    reg[prob.coil_of_elem == 0] = "winding+"
+    reg[prob.coil_of_elem == 1] = "winding-"
+    return reg
+
+
+def test_paper_transformer_matches_section4_figure_and_table():
+    """The transformer workload against the paper's printed data: the region
+    under each label arrow of the figure, the material constants of the table,
+    the cos source of amplitude +-j, the period and the tank outline."""
+    import math
+    labels, materials, fx = _paper_fixture()
+    prob = W.config_paper_transformer("32451", 8)
+    mm = 1e-3
+    assert np.allclose(prob.xy.max(axis=0), np.array(fx["tank"]) * mm) and np.allclose(prob.xy.min(axis=0), 0.0)
+    assert prob.T == fx["period"][0]
+    reg = _region_of_elements(prob)
+    p = prob.xy[prob.tri]                                        # (n_tri, 3, 2)
+    for name, x, y in labels:
+        q = np.array([x, y]) * mm
+        # triangles that contain the point (barycentric coordinates >= 0)
+        a, b, c = p[:, 0], p[:, 1], p[:, 2]
+        det = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1])
+        l1 = ((q[0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (q[1] - a[:, 1])) / det
+        l2 = ((b[:, 0] - a[:, 0]) * (q[1] - a[:, 1]) - (q[0] - a[:, 0]) * (b[:, 1] - a[:, 1])) / det
+        inside = (l1 >= -1e-12) & (l2 >= -1e-12) & (l1 + l2 <= 1 + 1e-12)
+        assert inside.any()
+        assert set(reg[inside]) == {name}, (name, x, y, set(reg[inside]))
+    for name, (sigma, a, b, c, d, j) in materials.items():
+        e = np.flatnonzero(reg == name)
+        assert e.size > 0
+        assert np.all(prob.sigma_e[e] == sigma)
+        if b is not None:                                        # iron and steel: the exponential law
+            assert np.all(prob.nonlinear_e[e] == 1)
+            assert np.all(prob.law_abcd[e] == np.array([a, b, c, d]))
+        else:                                                    # linear: nu = d
+            assert np.all(prob.nonlinear_e[e] == 0) and prob.nu_linear == d
+        if j != 0:
+            k = int(prob.coil_of_elem[e[0]])
+            t = np.linspace(0.0, prob.T, 7)
+            src = prob.amp[k] * np.sin(2 * math.pi * t / prob.T + prob.phase[k])
+            assert np.allclose(src, j * np.cos(2 * math.pi * t / prob.T), rtol=0, atol=1e-9 * abs(j))
+        else:
+            assert np.all(prob.coil_of_elem[e] == -1)
+
+
+def test_paper_transformer_mesh_sizes_match_table1():
+    """The structured grids stand in for the paper's meshes: their free-node
+    counts are within 2% of Table 1's N_V."""
+    _, _, fx = _paper_fixture()
+    for size, nv in zip(("8208", "32451"), fx["nv"]):
+        assert size == str(int(nv))
+        prob = W.config_paper_transformer(size, 4)
+        assert abs(prob.n_free - nv) <= 0.02 * nv
