@@ -81,15 +81,19 @@ def dnu_ds2(s2, nu_min, nu_max, s_sat):
 
 def exp_law(s2, a, b, c, d):
     """Reluctivity of the paper's transformer materials (Section 4):
-    nu = a min(exp(b s^2), c) + d, s^2 = |grad u|^2."""
-    return a * np.minimum(np.exp(b * s2), c) + d
+    nu = a min(exp(b s^2), c) + d, s^2 = |grad u|^2.  Where exp(b s^2)
+    overflows to inf the minimum is c, as it should be; the overflow is
+    expected and not reported."""
+    with np.errstate(over="ignore"):
+        return a * np.minimum(np.exp(b * s2), c) + d
 
 
 def dexp_law_ds2(s2, a, b, c, d):
     """Derivative of exp_law with respect to s^2: a b exp(b s^2) below the
     cap exp(b s^2) < c, 0 above it (the law has a kink at the cap)."""
-    e = np.exp(b * s2)
-    return np.where(e < c, a * b * e, 0.0)
+    with np.errstate(over="ignore", invalid="ignore"):
+        e = np.exp(b * s2)
+        return np.where(e < c, a * b * e, 0.0)
 
 
 def _law_columns(prob, ndim):
