@@ -171,12 +171,6 @@ def dense_periodic_solve(M, Khat, tau, B):
     return np.linalg.solve(P, B.ravel()).reshape(B.shape)
 
 
-def spatial_solve(M, Khat, tau, B):
-    """(M + tau Khat) X = B for every column (one implicit-Euler step)."""
-    lu = spla.splu((M + tau * Khat).tocsc())
-    return lu.solve(np.ascontiguousarray(B))
-
-
 # ---------------------------------------------------------------------------
 # Fixed-point iteration, eq. (iter1)-(iter2)
 # ---------------------------------------------------------------------------

@@ -9,10 +9,15 @@ from oracle import adjoint as AD
 from oracle import periodic as P
 
 
-def _problem():
+def _problem(T=1.0, s_sat=1.0):
     prob = W.config_adjoint(0, n=7, N=4)
     # strong coils so the iron law is exercised on both sides of s_sat
-    return prob.replace(amp=np.array([7000.0, 4500.0]), phase=np.array([0.0, 0.7]))
+    return prob.replace(amp=np.array([7000.0, 4500.0]), phase=np.array([0.0, 0.7]), T=T, s_sat=s_sat)
+
+
+# the period and s_sat enter the time derivative, the source and the law:
+# a second case away from 1 keeps a misplaced T or s_sat from cancelling
+CASES = [(1.0, 1.0), (0.5, 0.7)]
 
 
 def _J(prob):
@@ -21,8 +26,25 @@ def _J(prob):
     return AD.objective(prob, d, U)
 
 
-def test_objective_gradient_in_U_matches_differences():
-    prob = _problem()
+def test_objective_closed_form():
+    """U^n = n w with w = 1 on every free node: the periodic difference is
+    w / tau for n >= 2 and (1 - N) w / tau for n = 1, and w^T M_J w is the sum
+    of sigma_e |T_e| over the iron elements (all inside the domain, and a
+    consistent element mass sums to the element area), so
+    J = (1/N) [(N - 1) + (N - 1)^2] w^T M_J w / tau^2 = (N - 1) sum sigma_e |T_e| / tau^2."""
+    for T, s_sat in CASES:
+        prob = _problem(T, s_sat)
+        d = P.assemble(prob)
+        U = np.outer(np.ones(d.n), np.arange(1, d.N + 1, dtype=np.float64))
+        iron = prob.nonlinear_e.astype(bool)
+        h = 1.0 / 6.0                                   # 7 x 7 nodes on the unit square
+        ref = (d.N - 1) * np.sum(prob.sigma_e[iron]) * (h * h / 2) / (T / d.N) ** 2
+        assert AD.objective(prob, d, U) == pytest.approx(ref, rel=1e-12)
+
+
+@pytest.mark.parametrize("T,s_sat", CASES)
+def test_objective_gradient_in_U_matches_differences(T, s_sat):
+    prob = _problem(T, s_sat)
     d = P.assemble(prob)
     rng = np.random.default_rng(0)
     U = rng.normal(scale=0.05, size=(d.n, d.N))
@@ -33,8 +55,9 @@ def test_objective_gradient_in_U_matches_differences():
     assert abs(fd - np.sum(g * V)) <= 1e-7 * abs(fd)
 
 
-def test_adjoint_gradient_matches_central_differences():
-    prob = _problem()
+@pytest.mark.parametrize("T,s_sat", CASES)
+def test_adjoint_gradient_matches_central_differences(T, s_sat):
+    prob = _problem(T, s_sat)
     J0, d_amp, d_nu, d_sigma, _ = AD.gradient(prob)
     assert J0 > 0
     d = P.assemble(prob)

@@ -64,6 +64,17 @@ def test_mass_stencil_and_total():
     np.testing.assert_allclose(M[k], row, atol=1e-15)
 
 
+def test_degenerate_or_clockwise_triangles_are_rejected():
+    """The P1 map needs det B > 0: a zero-area or clockwise triangle has none."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [0.0, 1.0]])
+    with pytest.raises(ValueError, match="counter-clockwise"):
+        fem.p1_geometry(xy, np.array([[0, 1, 2]]))      # collinear: zero area
+    with pytest.raises(ValueError, match="counter-clockwise"):
+        fem.p1_geometry(xy, np.array([[0, 3, 1]]))      # clockwise
+    area, _ = fem.p1_geometry(xy, np.array([[0, 1, 3]]))
+    assert area[0] == 0.5
+
+
 def test_stiffness_kernel_and_symmetry():
     """The full-node stiffness annihilates constants (rows sum to zero) and
     is symmetric."""
@@ -86,11 +97,12 @@ def test_K_vanishes_on_linear_field():
     assert np.abs(Ku[prob.interior]).max() < 1e-12
 
 
-def test_K_is_gradient_of_coenergy():
+@pytest.mark.parametrize("s_sat", [1.0, 0.6])
+def test_K_is_gradient_of_coenergy(s_sat):
     """K(u) = grad E(u) with E = sum_T |T|/2 W(|g_T|^2), W' = nu, where W is
     the closed-form antiderivative of the reluctivity law (log form).
     Checked by central differences on a random field, mixed materials."""
-    prob = W.unit_square_problem(9, 4)
+    prob = W.unit_square_problem(9, 4, s_sat=s_sat)
     rng = np.random.default_rng(3)
     u = np.zeros(prob.n_nodes)
     u[prob.interior] = rng.normal(scale=0.8, size=prob.n_free)
@@ -125,9 +137,10 @@ def test_nu_law_limits():
     assert abs(fem.nu_law(1e12, 1.0, 100.0, 1.0) - 100.0) < 1e-8
 
 
-def test_K_jacobian_matches_differences():
+@pytest.mark.parametrize("s_sat", [1.0, 0.6])
+def test_K_jacobian_matches_differences(s_sat):
     """DK(u) v equals the central difference of K along v."""
-    prob = W.unit_square_problem(9, 4)
+    prob = W.unit_square_problem(9, 4, s_sat=s_sat)
     rng = np.random.default_rng(5)
     u = np.zeros(prob.n_nodes)
     v = np.zeros(prob.n_nodes)
@@ -154,10 +167,12 @@ def test_coil_load_total_is_coil_area():
     assert abs(b.sum() - count * h * h / 2) < 1e-14
 
 
-def test_source_sampling_times():
+@pytest.mark.parametrize("T", [1.0, 0.02])
+def test_source_sampling_times(T):
     """f^n is sampled at t^n = n tau, n = 1..N: for one coil with phase 0,
-    column N-1 (t = T) is sin(2 pi) b = 0 and column N/4 - 1 is b."""
-    prob = W.config_plain_fp64()
+    column N-1 (t = T) is sin(2 pi) b = 0 and column N/4 - 1 is b, whatever
+    the period."""
+    prob = W.config_plain_fp64().replace(T=T)
     d = P.assemble(prob)
     F = P.source(prob, d)
     b = d.b[0] * prob.amp[0]
