@@ -184,3 +184,50 @@ def test_binding_checks_block_sizes_before_calling_the_library(ptp):
     c.set_time(1.0, 4)                 # any change of the problem forgets the sizes
     assert c._sizes is None and c._count() is None
     c.close()
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ptp.h"
+
+int main(void) {
+    ptp_opts o;
+    size_t so = 0, ss = 0;
+    ptp_ctx* ctx = NULL;
+    ptp_default_opts(&o);
+    ptp_abi_sizes(&so, &ss);
+    if (so != sizeof(ptp_opts) || ss != sizeof(ptp_stats)) return 2;
+    if (o.precision != PTP_MIXED || o.tol != 1e-8) return 3;
+    if (ptp_create(&ctx, 0) != PTP_OK || ctx == NULL) return 4;
+    if (ptp_set_time(ctx, -1.0, 4) != PTP_EINVAL) return 5;     /* host-side check, no GPU */
+    if (strlen(ptp_last_error(ctx)) == 0) return 6;
+    if (ptp_set_time(ctx, 0.02, 4) != PTP_OK) return 7;
+    ptp_destroy(ctx);
+    printf("%s\n", ptp_version());
+    return 0;
+}
+"""
+
+
+def test_header_is_c99_and_the_library_links_from_c(ptp):
+    """include/ptp.h is plain C: a C99 program (-pedantic -Werror) compiles
+    against it, links libptp and calls the host-only entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    out = os.path.join(ROOT, "paper_2502_21013_gb300", "_build", "c_abi_check")
+    os.makedirs(out, exist_ok=True)
+    src, exe = os.path.join(out, "main.c"), os.path.join(out, "main")
+    with open(src, "w") as fh:
+        fh.write(C_PROGRAM)
+    libdir = os.path.dirname(ptp.LIB_PATH)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), src, "-o", exe,
+                        "-L", libdir, "-lptp", "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert "sm_103a" in r.stdout
