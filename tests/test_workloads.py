@@ -124,3 +124,25 @@ def test_paper_transformer_mesh_sizes_match_table1():
         assert size == str(int(nv))
         prob = W.config_paper_transformer(size, 4)
         assert abs(prob.n_free - nv) <= 0.02 * nv
+
+
+def test_workload_recipes():
+    """The input recipes as stated for the named workloads: the batched draw
+    (grids, steps, J0 ~ U[20, 80], s_sat ~ U[0.5, 2]), the transformer-shaped
+    rectangle (sigma 5 on iron, coils J0 = 60 at phases 0 and 2 pi/3, inside
+    the windows) and the adjoint case (two in-phase coils, log-normal sigma)."""
+    import math
+    batch = W.config_batched(0, count=64)
+    assert {b.grid[0] for b in batch} <= {65, 129, 257, 513} and len({b.grid[0] for b in batch}) > 1
+    assert {b.N for b in batch} <= {64, 128, 256, 512} and len({b.N for b in batch}) > 1
+    assert all(20.0 <= b.amp[0] <= 80.0 and 0.5 <= b.s_sat <= 2.0 for b in batch)
+    assert [b.amp[0] for b in batch] == [b.amp[0] for b in W.config_batched(0, count=64)]   # seeded
+    tr = W.config_transformer(65, 33, 4)
+    iron = tr.nonlinear_e.astype(bool)
+    assert np.all(tr.sigma_e[iron] == 5.0) and np.all(tr.sigma_e[~iron] == 0.0)
+    assert np.allclose(tr.amp, 60.0) and np.allclose(tr.phase, [0.0, 2 * math.pi / 3])
+    assert tr.grid[4:] == (2.0, 1.0)
+    adj = W.config_adjoint(0, n=33, N=4)
+    assert adj.n_coils == 2 and np.allclose(adj.phase, 0.0) and np.allclose(adj.amp, 50.0)
+    ls = np.log(adj.sigma_e[adj.nonlinear_e.astype(bool)])
+    assert abs(ls.mean() - math.log(10.0)) < 0.05 and abs(ls.std() - 0.3) < 0.05
