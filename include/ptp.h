@@ -295,10 +295,11 @@ int ptp_apply_shifted_f32_dev(ptp_ctx* ctx, int level, const float* X, float* Y)
    nothing: its scratch is a fixed 4 MiB array compiled into the library,
    held by every GPU that loads it until the process exits.  Limit: the iron
    element fluxes must fit, 2 * n_iron * N <= 522232 doubles (PTP_EINVAL with
-   a message otherwise; ptp_info gives n_iron).  The first call on a device
-   looks up the array's device address; make that first call before any
-   stream capture begins.  All calls share the array and it keeps the last
-   call's contents, so calls that overlap on the GPU race. */
+   a message otherwise; ptp_info gives n_iron).  R must not be U, and norm
+   must be neither (PTP_EINVAL).  The first call in a CUDA context looks up
+   the array's device address and keeps it for that context; make that first
+   call before any stream capture begins.  All calls share the array and it
+   keeps the last call's contents, so calls that overlap on the GPU race. */
 int ptp_residual_noalloc_dev(ptp_ctx* ctx, const double* U, double* R, double* norm);
 
 /* Periodic operator of level l: Y^n = (M + tau_l L) X^n - M X^{n-1},
@@ -395,6 +396,26 @@ int ptp_adjoint_gradient_dev(ptp_ctx* ctx, const ptp_opts* opts, const double* U
                              double* dJ_damp, double* dJ_dnu, double* dJ_dsigma, ptp_stats* stats);
 int ptp_adjoint_gradient(ptp_ctx* ctx, const ptp_opts* opts, const double* U, double* J,
                          double* dJ_damp, double* dJ_dnu, double* dJ_dsigma, ptp_stats* stats);
+
+/* ---- measurement probes ---------------------------------------------- */
+
+/* Measured fused multiply-add rate of the device, in TFLOP/s (2 flops per
+   FMA): independent FMA chains in every thread of one full wave of blocks on
+   every SM, the loop sized to about 20 ms, best of 3 launches timed with CUDA
+   events.  fp64 != 0: double FMAs, else float.  The paper has no
+   counterpart: this measures the arithmetic roofline of the double kernels
+   (the outer residual, the coarsest level), which the device's copy
+   bandwidth does not bound.  Allocates and frees a small buffer; host
+   output; synchronises.  PTP_ECUDA if a CUDA call failed. */
+int ptp_probe_fma(int device, int fp64, double* tflops);
+
+/* out[i] = 1/d[i] by the Newton reciprocal of the outer residual kernels
+   (two Newton-Raphson steps from the float reciprocal), for testing it
+   against the device's double division.  Valid for d in [2^-126, 2^127].
+   d and out are DEVICE arrays of n doubles (not the same buffer); stream
+   may be NULL (the default stream); synchronises.  The paper has no
+   counterpart. */
+int ptp_probe_recip_dev(int device, const double* d, double* out, int64_t n, void* stream);
 
 #ifdef __cplusplus
 }

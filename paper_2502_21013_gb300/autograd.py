@@ -26,6 +26,10 @@ class PeriodicLoss(torch.autograd.Function):
         c.setup(o)
         U = torch.zeros((prob.n_free, prob.N), dtype=torch.float64, device=f"cuda:{device}")
         st, rc = c.solve_dev(U, o)
+        if rc != ptp.PTP_OK:
+            # an unconverged state would give a loss and a gradient of the wrong problem
+            raise ptp.PtpError(rc, f"forward solve did not converge ({st.outer_iterations} outer iterations, "
+                                   f"relative residual {st.res_final / max(st.res0, 1e-300):.2e})")
         J = c.loss_dev(U)
         ctx.c, ctx.U, ctx.opts = c, U, o
         ctx.devices = (amp.device, nu_params.device, sigma.device)
@@ -34,6 +38,8 @@ class PeriodicLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gJ):
         J, damp, dnu, dsig, st, rc = ctx.c.adjoint_gradient_dev(ctx.U, ctx.opts)
+        if rc != ptp.PTP_OK:
+            raise ptp.PtpError(rc, f"adjoint solve did not converge ({st.outer_iterations} outer iterations)")
         g = float(gJ)
         da = torch.tensor(damp, dtype=torch.float64, device=ctx.devices[0]) * g
         dn = torch.tensor(dnu, dtype=torch.float64, device=ctx.devices[1]) * g

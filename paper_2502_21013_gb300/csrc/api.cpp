@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 #include "kernels.h"
 
@@ -50,6 +51,21 @@ int guarded(ptp_ctx* h, F&& f, bool device = true) {
 void need_ready(const Ctx& c) {
     if (!c.ready) throw Error(PTP_ESTATE, "call ptp_setup first");
 }
+
+}  // namespace
+
+// The same error handling and per-call set-up (device, row-block size, own
+// stream) for entry points defined in other translation units.
+namespace ptp {
+int run_entry(ptp_ctx* h, const std::function<int(Ctx&)>& f) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        return f(c);
+    });
+}
+}  // namespace ptp
+
+namespace {
 
 void invalidate(Ctx& c) {
     c.ready = false;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -283,6 +284,12 @@ int autotune(Ctx& c, double* best_us);     // picks c.row_block by timing the le
 void require_coarse(const Ctx& c);         // the time hierarchy has an exact last-level solve
 void alloc_adjoint(Ctx& c);                // Jacobian coefficients and adjoint work
 void mg_precondition(Ctx& c, const double* v, double* z);   // z = inner periodic solve of v
+
+// ---- api.cpp ----
+// Runs f on the context of h (which must be set up) with the error handling
+// and per-call set-up of every entry point: exceptions become status codes
+// and the message of ptp_last_error.
+int run_entry(ptp_ctx* h, const std::function<int(Ctx&)>& f);
 
 // ---- newton.cpp ----
 int newton_solve(Ctx& c, const ptp_opts& o, const double* U0, double* U, ptp_stats* st);

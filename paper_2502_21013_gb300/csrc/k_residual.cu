@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdlib>
 
+#include "dev_math.cuh"
 #include "kernels.h"
 
 namespace ptp {
@@ -31,17 +32,6 @@ constexpr int kBlock = 256;
 
 __device__ __forceinline__ bool skip_now(const int* done) {
     return done != nullptr && *(volatile const int*)done != 0;
-}
-
-// 1/d for d > 0 by the Newton-Raphson iteration x <- x (2 - d x) started from
-// the single-precision reciprocal (relative error <= 2^-24); the error
-// squares at every step, so two steps reach double precision.
-__device__ __forceinline__ double recip_newton(double d) {
-    double x = (double)__frcp_rn(__double2float_rn(d));
-    double e = fma(-d, x, 1.0);
-    x = fma(x, e, x);
-    e = fma(-d, x, 1.0);
-    return fma(x, e, x);
 }
 
 // Iron elements only: q = nu(|g|^2) |T| g with

@@ -111,6 +111,8 @@ def _load():
         "ptp_batch_result_dev": (I, [P, I, P]),
         "ptp_adjoint_gradient_dev": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
         "ptp_adjoint_gradient": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
+        "ptp_probe_fma": (I, [I, I, pD]),
+        "ptp_probe_recip_dev": (I, [I, P, P, ctypes.c_int64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -138,8 +140,25 @@ EXPORTED = [
     "ptp_jacobian_apply_dev",
     "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient", "ptp_autotune",
     "ptp_batch_create", "ptp_batch_destroy", "ptp_batch_last_error", "ptp_batch_add", "ptp_batch_size",
-    "ptp_batch_solve", "ptp_batch_result_dev",
+    "ptp_batch_solve", "ptp_batch_result_dev", "ptp_probe_fma", "ptp_probe_recip_dev",
 ]
+
+
+def probe_fma(device=0, fp64=True):
+    """Measured FMA rate of the device in TFLOP/s (ptp_probe_fma)."""
+    r = ctypes.c_double()
+    rc = lib.ptp_probe_fma(int(device), 1 if fp64 else 0, ctypes.byref(r))
+    if rc != PTP_OK:
+        raise PtpError(rc, "ptp_probe_fma failed")
+    return r.value
+
+
+def probe_recip_dev(d, out, stream=None):
+    """out = 1/d by the residual kernels' Newton reciprocal (ptp_probe_recip_dev)."""
+    rc = lib.ptp_probe_recip_dev(d.device.index or 0, _dev_ptr(d, "float64"), _dev_ptr(out, "float64", d.numel()),
+                                 d.numel(), ctypes.c_void_p(stream or 0))
+    if rc != PTP_OK:
+        raise PtpError(rc, "ptp_probe_recip_dev failed")
 
 
 def default_opts(**kw) -> Opts:

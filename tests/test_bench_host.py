@@ -37,8 +37,25 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "DOF/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    # value = space-time DOFs / extrapolated solve time
-    assert abs(line["value"] * line["ms_per_step"] / 1e3 - 65025 * 256) < 1e-6 * 65025 * 256
+    # value = space-time DOFs / extrapolated solve time, labelled as an
+    # extrapolation; ms_per_step is the sample's own wall time
+    ext = line["config"]["extrapolated_solve_s"]
+    assert abs(line["value"] * ext - 65025 * 256) < 1e-6 * 65025 * 256
+    assert line["cpu_baseline"]["extrapolated"] is True and "not an oracle measurement" in \
+        line["config"]["iterations_source"]
+    assert line["ms_per_step"] / 1e3 == line["config"]["sample_wall_s_per_step"] * 1e3 / 1e3
+    assert line["ms_per_step"] / 1e3 < 120.0
+
+
+def test_oracle_to_tolerance_is_a_measured_solve():
+    """cpu_baseline: the oracle's fixed point timed from U = 0 to the stopping
+    rule on the 33x33, N = 32 workload (its own iteration count)."""
+    import bench
+    s = bench.oracle_to_tolerance()
+    assert s["converged"] and s["outer_iterations"] > 100
+    assert s["workload"] == "square33_N32" and s["space_time_dofs"] == 961 * 32
+    assert abs(s["value"] * s["solve_s"] - 961 * 32) < 1e-6 * 961 * 32
+    assert 1 <= s["cores"] <= max(1, s["cores_visible"]) + 1
 
 
 def test_reference_arm_other_ranks_exit_without_work():

@@ -101,3 +101,17 @@ def test_autograd_function_backward_is_the_adjoint():
     assert np.abs(amp.grad.numpy() - damp_o).max() <= 1e-7 * np.abs(damp_o).max()
     assert np.abs(nu.grad.numpy() - dnu_o).max() <= 1e-7 * np.abs(dnu_o).max()
     assert np.abs(sig.grad.numpy() - dsig_o).max() <= 1e-7 * np.abs(dsig_o).max()
+
+
+def test_autograd_function_raises_on_an_unconverged_solve():
+    """A forward solve stopped by max_outer is not the solution of the problem,
+    so neither its loss nor a gradient at it may be returned."""
+    from paper_2502_21013_gb300.autograd import periodic_loss
+    prob = _problem(n=9, N=8)
+    amp = torch.tensor(prob.amp, dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor([prob.nu_min, prob.nu_max, prob.s_sat], dtype=torch.float64, requires_grad=True)
+    sig = torch.tensor(prob.sigma_e, dtype=torch.float64, requires_grad=True)
+    opts = ptp.default_opts(precision=ptp.PTP_FP64, tol=1e-12, max_outer=2)
+    with pytest.raises(ptp.PtpError) as e:
+        periodic_loss(amp, nu, sig, prob, opts)
+    assert e.value.code == ptp.PTP_ENOTCONV

@@ -29,10 +29,25 @@ def _instances():
     ]
 
 
-@pytest.mark.parametrize("precision", [ptp.PTP_FP64, ptp.PTP_MIXED])
-def test_batch_equals_individual_solves_bitwise(precision):
+_ORACLE = {}
+
+
+def _oracle_solution(i, prob):
+    """The oracle's fixed point of instance i (exact inner solves), to 1e-13."""
+    if i not in _ORACLE:
+        d = P.assemble(prob)
+        ref = P.fixed_point(prob, d, tol=1e-13, max_it=50000)
+        assert ref.converged
+        _ORACLE[i] = ref.U
+    return _ORACLE[i]
+
+
+# FP64 solved to 1e-13 and compared at 1e-10; mixed solved to 1e-11 (its
+# double outer residual) and compared at 1e-8
+@pytest.mark.parametrize("precision,tol,bar", [(ptp.PTP_FP64, 1e-13, 1e-10), (ptp.PTP_MIXED, 1e-11, 1e-8)])
+def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar):
     probs = _instances()
-    opts = ptp.default_opts(precision=precision, tol=1e-11, max_outer=20000)
+    opts = ptp.default_opts(precision=precision, tol=tol, max_outer=20000)
     alone = []
     ctxs = []
     for p in probs:
@@ -47,23 +62,25 @@ def test_batch_equals_individual_solves_bitwise(precision):
         batch.add(c)
     stats, nconv, rc = batch.solve(opts)
     assert rc == ptp.PTP_OK and nconv == len(probs)
+    results = []
     for i, p in enumerate(probs):
         Ub = torch.empty((p.n_free, p.N), dtype=torch.float64, device="cuda")
         batch.result_dev(i, Ub)
         assert stats[i].outer_iterations == alone[i][1]
         assert torch.equal(Ub, alone[i][0])        # same kernels, deterministic reductions
-    # and the batch result is the oracle's solution
-    d = P.assemble(probs[0])
-    ref = P.fixed_point(probs[0], d, tol=1e-13, max_it=50000)
-    Ub = torch.empty((probs[0].n_free, probs[0].N), dtype=torch.float64, device="cuda")
-    batch.result_dev(0, Ub)
-    err = np.linalg.norm(Ub.cpu().numpy() - ref.U) / np.linalg.norm(ref.U)
-    assert err < (1e-9 if precision == ptp.PTP_FP64 else 1e-8)
-    # a second solve reuses the captured graph and gives the same result
+        results.append(Ub)
+    # every instance of the batch is the oracle's solution of its problem
+    for i, p in enumerate(probs):
+        ref = _oracle_solution(i, p)
+        err = np.linalg.norm(results[i].cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err < bar, (i, err)
+    # a second solve reuses the captured graph and gives the same results
     stats2, nconv2, rc2 = batch.solve(opts)
-    Ub2 = torch.empty_like(Ub)
-    batch.result_dev(0, Ub2)
-    assert torch.equal(Ub, Ub2)
+    assert rc2 == ptp.PTP_OK and nconv2 == len(probs)
+    for i, p in enumerate(probs):
+        Ub2 = torch.empty_like(results[i])
+        batch.result_dev(i, Ub2)
+        assert torch.equal(results[i], Ub2)
 
 
 def test_autotune_keeps_the_solution():

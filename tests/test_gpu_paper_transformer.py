@@ -53,7 +53,10 @@ def test_residual_with_the_exponential_law(structured):
         assert abs(nrm - np.linalg.norm(Ro)) <= 1e-13 * np.linalg.norm(Ro)
 
 
-@pytest.mark.parametrize("precision,tol,bar", [("fp64", 1e-13, 1e-10), ("mixed", 1e-11, 1e-8)])
+# The double residual of this operator (element weights 29..8e5) has a
+# rounding floor near 1e-12 of its start, so the FP64 case is solved to 3e-12
+# (not 1e-13 as on the unit square) and every solve must report PTP_OK.
+@pytest.mark.parametrize("precision,tol,bar", [("fp64", 3e-12, 1e-10), ("mixed", 1e-11, 1e-8)])
 def test_static_and_periodic_solves_against_oracle(precision, tol, bar):
     """The static initialisation (sigma = 0) and the periodic fixed point with
     the zero-field K_hat weights reach the oracle's solutions (static: Newton;
@@ -66,13 +69,11 @@ def test_static_and_periodic_solves_against_oracle(precision, tol, bar):
     assert ref.converged
     prec = ptp.PTP_FP64 if precision == "fp64" else ptp.PTP_MIXED
     c, o = make_ctx(prob, precision=prec, tol=tol, max_outer=3000, pcg_iters=10)
-    # the double residuals of this operator (weights 29..8e5) have a rounding
-    # floor near 1e-12 of their start, so an unmet 1e-13 is accepted from there
     Us, st, rc = c.static_solve(o)
-    assert rc == ptp.PTP_OK or (rc == ptp.PTP_ENOTCONV and st.res_final <= 1e-11 * st.res0)
+    assert rc == ptp.PTP_OK and st.res_final <= tol * st.res0
     assert rel(Us, Us_o) < bar
     U, st, rc = c.solve(o)
-    assert rc == ptp.PTP_OK or (rc == ptp.PTP_ENOTCONV and st.res_final <= 1e-11 * st.res0)
+    assert rc == ptp.PTP_OK and st.res_final <= tol * st.res0
     assert rel(U, ref.U) < bar
 
 
