@@ -121,6 +121,11 @@ typedef struct ptp_opts {
                             (default 1e-2)                                   */
     int    krylov_dim;   /* Newton: flexible GMRES iterations per linear
                             solve (1..31, no restart; default 20)            */
+    int    stencil;      /* structured grids, PTP_MIXED, GMG: 1 = the float
+                            inner solve runs the shared-memory stencil
+                            kernels (fused residual + restriction,
+                            interpolation + sweep + dot products; default),
+                            0 = the padded-ELL row kernels                   */
 } ptp_opts;
 
 /* Statistics of the last solve. */
@@ -401,8 +406,8 @@ int ptp_adjoint_gradient(ptp_ctx* ctx, const ptp_opts* opts, const double* U, do
 
 /* Measured fused multiply-add rate of the device, in TFLOP/s (2 flops per
    FMA): independent FMA chains in every thread of one full wave of blocks on
-   every SM, the loop sized to about 20 ms, best of 3 launches timed with CUDA
-   events.  fp64 != 0: double FMAs, else float.  The paper has no
+   every SM (8 and 16 chains per thread), the loop sized to about 40 ms, best
+   of 3 launches of each timed with CUDA events.  fp64 != 0: double FMAs, else float.  The paper has no
    counterpart: this measures the arithmetic roofline of the double kernels
    (the outer residual, the coarsest level), which the device's copy
    bandwidth does not bound.  Allocates and frees a small buffer; host

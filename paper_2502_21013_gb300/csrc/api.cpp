@@ -131,6 +131,7 @@ void ptp_default_opts(ptp_opts* o) {
     o->init_static = 0;
     o->newton_eta = 1e-2;
     o->krylov_dim = 20;
+    o->stencil = 1;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }

@@ -105,6 +105,11 @@ struct SpatialLevel {
     DevCSR P;           // interpolation from the next coarser level (n x n_c)
     DevCSR R;           // restriction = P^T (n_c x n)
     HostCSR hM, hL, hP;
+    // the same operators as a 7-point stencil on the structured grid (free
+    // nodes (a, b), W = nx - 2 per row, H = ny - 2 rows, row-major), float,
+    // 4 float4 per node: M {C, E, W, N}, M {S, NE, SW, 0}, L {...}, L {...}
+    bool st_ok = false;
+    DBuf<float4> st_coef;
 };
 
 // A spatial operator  cm * M + cl * L  used somewhere in the hierarchy.
@@ -243,6 +248,7 @@ struct Ctx {
     int64_t launches = 0;        // kernels issued (counting while capturing)
     int64_t launches_per_step[3] = {0, 0, 0};
     int row_block = 256;         // threads per block of the row kernels (autotuned)
+    bool stencil_ok = false;     // every spatial level has a 7-point stencil (structured GMG hierarchy)
     int64_t buf_gen = 0;         // bumped when a buffer a captured graph may use is reallocated
 
     ~Ctx();

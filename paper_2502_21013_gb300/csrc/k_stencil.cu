@@ -1,0 +1,674 @@
+// Structured-grid stencil kernels of the float inner solve (multigrid in time
+// whose block-Jacobi spatial solves are PCG with a geometric-multigrid
+// preconditioner).
+//
+// On the nested structured grids every spatial operator cm M + cl L is a
+// 7-point stencil (neighbours C, E, W, N, S, NE, SW of the P1 pattern whose
+// cells are split along (i, j)-(i+1, j+1)); its coefficients are stored per
+// free node.  A block owns a time tile of TT consecutive columns (one 128-byte
+// line per node at TT = 32 floats), a segment of a grid row and a strip of
+// rows.  It marches up the strip keeping the rows it needs in a shared-memory
+// ring (the next row is fetched into registers while the current one is
+// computed), so each value is read from global memory about once per pass,
+// plus the halo, and from shared memory once per stencil entry.  Dirichlet
+// neighbours outside the grid read as zero.
+//
+// Fused passes (each replaces two or three row-kernel passes):
+//   st_presid          r = b - (A x^n - M x^{n-1})  and  z0 = w D^-1 r
+//                      (the periodic residual of block Jacobi, Section 3's
+//                      time-periodic system, with the first GMG sweep)
+//   st_presid_restrict the same residual summed over the pairs (2m, 2m+1):
+//                      restriction to the next time level
+//   st_resid_restrict  t = b - A x on the fine level, restricted by P^T to
+//                      the coarse level, and the coarse level's first sweep
+//   st_interp_sweep    x' = x + P x_c, then one damped-Jacobi sweep
+//                      x' + w D^-1 (b - A x'), with the PCG dot products
+//                      r.z and r.r on the finest level
+//   st_apply_dot       p.(A p) per column: the PCG step length, without
+//                      writing A p
+// Per-column sums are deterministic: block partials in global memory, summed
+// in a fixed order by the last block of each time tile (atomic ticket, no
+// waiting).
+#include <algorithm>
+
+#include "dev_util.cuh"
+
+namespace ptp {
+
+namespace {
+
+constexpr int kStBlock = 256;
+
+struct A7 {
+    float c, e, w, n, s, ne, sw;
+};
+
+// coefficients of node `node`: a = cm M + cl L and m = M
+__device__ __forceinline__ void load_coef(const float4* __restrict__ coef, size_t node, float cm, float cl,
+                                          A7& a, A7& m) {
+    const float4 m0 = __ldg(coef + 4 * node), m1 = __ldg(coef + 4 * node + 1);
+    const float4 l0 = __ldg(coef + 4 * node + 2), l1 = __ldg(coef + 4 * node + 3);
+    m = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z};
+    a.c = cm * m0.x + cl * l0.x;
+    a.e = cm * m0.y + cl * l0.y;
+    a.w = cm * m0.z + cl * l0.z;
+    a.n = cm * m0.w + cl * l0.w;
+    a.s = cm * m1.x + cl * l1.x;
+    a.ne = cm * m1.y + cl * l1.y;
+    a.sw = cm * m1.z + cl * l1.z;
+}
+
+__device__ __forceinline__ float diag_coef(const float4* __restrict__ coef, size_t node, float cm, float cl) {
+    return cm * __ldg(&coef[4 * node].x) + cl * __ldg(&coef[4 * node + 2].x);
+}
+
+// thread geometry of a block: TPN = TT / VEC threads per node (a time tile),
+// SX = blockDim / TPN node slots
+struct Lanes {
+    int tpn, lc, ln, sx, col;   // col: first column of this thread
+};
+
+template <int VEC>
+__device__ __forceinline__ Lanes lanes(int TT) {
+    Lanes L;
+    L.tpn = TT / VEC;
+    L.lc = threadIdx.x % L.tpn;
+    L.ln = threadIdx.x / L.tpn;
+    L.sx = blockDim.x / L.tpn;
+    L.col = blockIdx.y * TT + L.lc * VEC;
+    return L;
+}
+
+template <int VEC>
+__device__ __forceinline__ void zero_vec(float (&v)[VEC]) {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] = 0.f;
+}
+
+// shared-memory row of SX nodes x TT floats: the VEC values of (slot, node, lane)
+template <int VEC>
+__device__ __forceinline__ float* srow(float* ring, int slot, int node, int sx, int TT, int lc) {
+    return ring + ((size_t)slot * sx + node) * TT + lc * VEC;
+}
+
+template <int VEC>
+__device__ __forceinline__ void lds(const float* p, float (&v)[VEC]) {
+    if constexpr (VEC == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (VEC == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = p[0];
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void sts(float* p, const float (&v)[VEC]) {
+    if constexpr (VEC == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (VEC == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+        p[0] = v[0];
+    }
+}
+
+// global value block of free node (a, b) at this thread's columns, zero outside the grid
+template <int VEC>
+__device__ __forceinline__ void gload(const float* __restrict__ X, int W, int H, int N, int a, int b, int col,
+                                      float (&v)[VEC]) {
+    if (a >= 0 && a < W && b >= 0 && b < H)
+        ldg_vec<float, VEC>(X + ((size_t)b * W + a) * N + col, v);
+    else
+        zero_vec<VEC>(v);
+}
+
+// Per-column sums of NQ quantities over the block, then over the blocks of
+// the same time tile by the last of them (fixed order), then FIN on every
+// column of the tile.  `scratch` holds at least NQ * SX * TT floats and is
+// free (the caller synchronised after its last use).
+template <int VEC, int NQ, int FIN>
+__device__ void tile_reduce_finish(float (&acc)[NQ][VEC], const Lanes& L, int TT, int N, float* scratch,
+                                   ColRed<float> cr) {
+    __shared__ int last;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sts<VEC>(scratch + ((size_t)q * L.sx + L.ln) * TT + L.lc * VEC, acc[q]);
+    __syncthreads();
+    const int tiles = gridDim.x;
+    const int chunk = blockIdx.y;
+    float* part = cr.partials + ((size_t)chunk * tiles) * NQ * TT;
+    for (int e = threadIdx.x; e < NQ * TT; e += blockDim.x) {
+        const int q = e / TT, j = e - q * TT;
+        float s = 0.f;
+        for (int r = 0; r < L.sx; ++r) s += scratch[((size_t)q * L.sx + r) * TT + j];
+        part[(size_t)blockIdx.x * NQ * TT + e] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(cr.counter + 1 + chunk, 1u);
+        last = t == (unsigned)(tiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    for (int e = threadIdx.x; e < NQ * TT; e += blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < tiles; ++b) s += __ldcg(part + (size_t)b * NQ * TT + e);
+        scratch[e] = s;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < TT; j += blockDim.x) {
+        const int col = chunk * TT + j;
+        float* c = cr.col;
+        if constexpr (FIN == FIN_ALPHA) {
+            c[S_ALPHA * N + col] = safe_ratio<float>(c[S_RHO * N + col], scratch[j]);
+        } else if constexpr (FIN == FIN_RZ_FIRST) {   // (rz, rr)
+            c[S_RHO * N + col] = scratch[j];
+            c[S_BB * N + col] = scratch[TT + j];
+            c[S_RR * N + col] = scratch[TT + j];
+        } else if constexpr (FIN == FIN_RZ_NEXT) {
+            c[S_BETA * N + col] = safe_ratio<float>(scratch[j], c[S_RHO * N + col]);
+            c[S_RHO * N + col] = scratch[j];
+        }
+    }
+    if (threadIdx.x == 0) cr.counter[1 + chunk] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// periodic residual (+ first GMG sweep), or its time restriction
+// ---------------------------------------------------------------------------
+// MODE 0: R = B - (A X^n - M X^{n-1}), Z0 = omega D^-1 R (if Z0 set)
+// MODE 1: Yc^m = sum over n in {2m, 2m+1} of the same residual (N/2 columns)
+template <int VEC, int MODE>
+__global__ void __launch_bounds__(kStBlock)
+k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __restrict__ X,
+            const float* __restrict__ B, float* __restrict__ R, float* __restrict__ Z0, float omega, Skip sk) {
+    pdl_enter();
+    if (skip_now(sk)) return;
+    extern __shared__ float4 smem4[];
+    float* ring = reinterpret_cast<float*>(smem4);
+    const Lanes L = lanes<VEC>(TT);
+    float* prev = ring + 4 * (size_t)L.sx * TT;   // column col0 - 1 of each node, lc == 0 lanes
+    const int W = A.W, H = A.H;
+    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int a0 = seg * (L.sx - 2) - 1;          // node slot 0 is a0; outputs at slots 1..sx-2
+    const int y0 = strip * sy, y1 = min(H, y0 + sy);
+    const int a = a0 + L.ln;
+    const int pcol = (blockIdx.y * TT == 0 ? N : blockIdx.y * TT) - 1;   // previous column of the tile
+    auto fetch = [&](int b, float (&v)[VEC], float& pv) {
+        gload<VEC>(X, W, H, N, a, b, L.col, v);
+        pv = 0.f;
+        if (L.lc == 0 && a >= 0 && a < W && b >= 0 && b < H) pv = __ldg(X + ((size_t)b * W + a) * N + pcol);
+    };
+    auto stash = [&](int slot, const float (&v)[VEC], float pv) {
+        sts<VEC>(srow<VEC>(ring, slot, L.ln, L.sx, TT, L.lc), v);
+        if (L.lc == 0) prev[slot * L.sx + L.ln] = pv;
+    };
+    {
+        float v[VEC], pv;
+        for (int r = 0; r < 3; ++r) {
+            fetch(y0 - 1 + r, v, pv);
+            stash(r, v, pv);
+        }
+    }
+    __syncthreads();
+    const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
+    for (int b = y0; b < y1; ++b) {
+        const int k = b - y0;
+        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
+        const bool pre = b + 1 < y1;
+        float nv[VEC], npv;
+        if (pre) fetch(b + 2, nv, npv);
+        if (out_lane) {
+            const size_t node = (size_t)b * W + a;
+            A7 c, m;
+            load_coef(A.coef, node, A.cm, A.cl, c, m);
+            float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
+            lds<VEC>(srow<VEC>(ring, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(ring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(ring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(ring, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(ring, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(ring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(ring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            // column col - 1 of the seven nodes: from the lane to the left, or the tile's previous column
+            auto before = [&](int slot, int nd) -> float {
+                return L.lc > 0 ? ring[((size_t)slot * L.sx + nd) * TT + L.lc * VEC - 1] : prev[slot * L.sx + nd];
+            };
+            float p_c = before(sC, L.ln), p_e = before(sC, L.ln + 1), p_w = before(sC, L.ln - 1);
+            float p_n = before(sN, L.ln), p_s = before(sS, L.ln), p_ne = before(sN, L.ln + 1),
+                  p_sw = before(sS, L.ln - 1);
+            float bv[VEC], r[VEC];
+            ldg_vec<float, VEC>(B + node * N + L.col, bv);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
+                                 c.ne * xne[v] + c.sw * xsw[v];
+                const float mx = m.c * p_c + m.e * p_e + m.w * p_w + m.n * p_n + m.s * p_s + m.ne * p_ne +
+                                 m.sw * p_sw;
+                r[v] = bv[v] - (ax - mx);
+                p_c = xc[v]; p_e = xe[v]; p_w = xw[v]; p_n = xn[v]; p_s = xs[v]; p_ne = xne[v]; p_sw = xsw[v];
+            }
+            if constexpr (MODE == 0) {
+                st_vec<float, VEC>(R + node * N + L.col, r);
+                if (Z0) {
+                    const float w = omega / c.c;
+                    float z[VEC];
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) z[v] = w * r[v];
+                    st_vec<float, VEC>(Z0 + node * N + L.col, z);
+                }
+            } else {
+                constexpr int HV = VEC / 2;
+                float o[HV];
+#pragma unroll
+                for (int v = 0; v < HV; ++v) o[v] = r[2 * v] + r[2 * v + 1];
+                st_vec<float, HV>(R + node * (N / 2) + L.col / 2, o);
+            }
+        }
+        if (pre) stash((k + 3) & 3, nv, npv);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GMG: residual on the fine level, restriction to the coarse level (+ sweep)
+// ---------------------------------------------------------------------------
+// Bc = P^T (Bf - Af Xf) with P the P1 interpolation of the nested grids:
+//   coarse free node (A, B) sits on fine free node (2A+1, 2B+1) and takes the
+//   fine residual there plus half of it at the six pattern neighbours.
+// Xc = omega Dc^-1 Bc (the coarse level's first sweep from zero) if Xc is set.
+template <int VEC>
+__global__ void __launch_bounds__(kStBlock)
+k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int cy, int nseg,
+                    const float* __restrict__ Xf, const float* __restrict__ Bf, float* __restrict__ Bc,
+                    float* __restrict__ Xc, float omega, Skip sk) {
+    pdl_enter();
+    if (skip_now(sk)) return;
+    extern __shared__ float4 smem4[];
+    float* zring = reinterpret_cast<float*>(smem4);
+    const Lanes L = lanes<VEC>(TT);
+    float* tring = zring + 4 * (size_t)L.sx * TT;
+    const int W = Af.W, H = Af.H, Wc = Ac.W, Hc = Ac.H;
+    const int cxo = (L.sx - 3) / 2;                 // coarse nodes per block row segment
+    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int A0 = seg * cxo;
+    const int a = 2 * A0 - 1 + L.ln;                // fine node of slot ln
+    const int B0 = strip * cy, B1 = min(Hc, B0 + cy);
+    const int f0 = 2 * B0, f1 = 2 * B1;             // fine rows whose residual is needed: f0..f1
+    {
+        float v[VEC];
+        for (int r = 0; r < 3; ++r) {
+            gload<VEC>(Xf, W, H, N, a, f0 - 1 + r, L.col, v);
+            sts<VEC>(srow<VEC>(zring, r, L.ln, L.sx, TT, L.lc), v);
+        }
+    }
+    __syncthreads();
+    const bool t_lane = L.ln >= 1 && L.ln <= 2 * cxo + 1 && a < W;
+    for (int f = f0; f <= f1; ++f) {
+        const int k = f - f0;
+        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
+        const bool pre = f < f1;
+        float nv[VEC];
+        if (pre) gload<VEC>(Xf, W, H, N, a, f + 2, L.col, nv);
+        if (t_lane) {
+            float t[VEC];
+            if (f < H) {
+                const size_t node = (size_t)f * W + a;
+                A7 c, m;
+                load_coef(Af.coef, node, Af.cm, Af.cl, c, m);
+                float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC];
+                lds<VEC>(srow<VEC>(zring, sC, L.ln, L.sx, TT, L.lc), xc);
+                lds<VEC>(srow<VEC>(zring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+                lds<VEC>(srow<VEC>(zring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+                lds<VEC>(srow<VEC>(zring, sN, L.ln, L.sx, TT, L.lc), xn);
+                lds<VEC>(srow<VEC>(zring, sS, L.ln, L.sx, TT, L.lc), xs);
+                lds<VEC>(srow<VEC>(zring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+                lds<VEC>(srow<VEC>(zring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+                ldg_vec<float, VEC>(Bf + node * N + L.col, bv);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                    t[v] = bv[v] - (c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
+                                    c.ne * xne[v] + c.sw * xsw[v]);
+            } else {
+                zero_vec<VEC>(t);
+            }
+            sts<VEC>(srow<VEC>(tring, k % 3, L.ln, L.sx, TT, L.lc), t);
+        }
+        __syncthreads();
+        if (k >= 2 && (k & 1) == 0) {
+            // coarse row Bq: fine rows f-2 (S), f-1 (centre), f (N)
+            const int Bq = B0 + (k - 2) / 2;
+            const int Aq = A0 + L.ln;
+            if (L.ln < cxo && Aq < Wc && Bq < Hc) {
+                const int tS = (k - 2) % 3, tC = (k - 1) % 3, tN = k % 3;
+                const int sl = 2 * L.ln + 2;   // slot of the fine centre node 2 Aq + 1
+                float vc[VEC], ve[VEC], vw[VEC], vn[VEC], vs[VEC], vne[VEC], vsw[VEC], o[VEC];
+                lds<VEC>(srow<VEC>(tring, tC, sl, L.sx, TT, L.lc), vc);
+                lds<VEC>(srow<VEC>(tring, tC, sl + 1, L.sx, TT, L.lc), ve);
+                lds<VEC>(srow<VEC>(tring, tC, sl - 1, L.sx, TT, L.lc), vw);
+                lds<VEC>(srow<VEC>(tring, tN, sl, L.sx, TT, L.lc), vn);
+                lds<VEC>(srow<VEC>(tring, tS, sl, L.sx, TT, L.lc), vs);
+                lds<VEC>(srow<VEC>(tring, tN, sl + 1, L.sx, TT, L.lc), vne);
+                lds<VEC>(srow<VEC>(tring, tS, sl - 1, L.sx, TT, L.lc), vsw);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                    o[v] = vc[v] + 0.5f * (ve[v] + vw[v] + vn[v] + vs[v] + vne[v] + vsw[v]);
+                const size_t cn = (size_t)Bq * Wc + Aq;
+                st_vec<float, VEC>(Bc + cn * N + L.col, o);
+                if (Xc) {
+                    const float w = omega / diag_coef(Ac.coef, cn, Ac.cm, Ac.cl);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) o[v] *= w;
+                    st_vec<float, VEC>(Xc + cn * N + L.col, o);
+                }
+            }
+        }
+        if (pre) sts<VEC>(srow<VEC>(zring, (k + 3) & 3, L.ln, L.sx, TT, L.lc), nv);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// GMG: interpolation of the coarse correction + one damped-Jacobi sweep
+// ---------------------------------------------------------------------------
+// x' = X + P Xc on the fine level, Out = x' + omega D^-1 (B - A x').
+// DOTS 1: (B.Out, B.B) per column -> rho, bb, rr (first PCG direction);
+// DOTS 2: B.Out -> beta, rho (later directions).  B is the PCG residual there.
+template <int VEC>
+__device__ __forceinline__ void xprime(const float* __restrict__ X, const float* __restrict__ Xc, int W, int H,
+                                       int Wc, int Hc, int N, int a, int f, int col, float (&v)[VEC]) {
+    gload<VEC>(X, W, H, N, a, f, col, v);
+    if (a < 0 || a >= W || f < 0 || f >= H) return;
+    float c1[VEC], c2[VEC];
+    const bool ao = a & 1, fo = f & 1;
+    if (ao && fo) {                       // on a coarse node
+        gload<VEC>(Xc, Wc, Hc, N, (a - 1) / 2, (f - 1) / 2, col, c1);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[k] += c1[k];
+        return;
+    }
+    if (!ao && fo) {                      // horizontal edge midpoint
+        gload<VEC>(Xc, Wc, Hc, N, a / 2 - 1, (f - 1) / 2, col, c1);
+        gload<VEC>(Xc, Wc, Hc, N, a / 2, (f - 1) / 2, col, c2);
+    } else if (ao && !fo) {               // vertical edge midpoint
+        gload<VEC>(Xc, Wc, Hc, N, (a - 1) / 2, f / 2 - 1, col, c1);
+        gload<VEC>(Xc, Wc, Hc, N, (a - 1) / 2, f / 2, col, c2);
+    } else {                              // midpoint of the diagonal (i,j)-(i+1,j+1)
+        gload<VEC>(Xc, Wc, Hc, N, a / 2 - 1, f / 2 - 1, col, c1);
+        gload<VEC>(Xc, Wc, Hc, N, a / 2, f / 2, col, c2);
+    }
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) v[k] += 0.5f * (c1[k] + c2[k]);
+}
+
+template <int VEC, int DOTS>
+__global__ void __launch_bounds__(kStBlock)
+k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int nseg,
+                  const float* __restrict__ Xc, const float* __restrict__ X, const float* __restrict__ B,
+                  float* __restrict__ Out, float omega, ColRed<float> cr, Skip sk) {
+    pdl_enter();
+    if (skip_now(sk)) return;
+    extern __shared__ float4 smem4[];
+    float* ring = reinterpret_cast<float*>(smem4);
+    const Lanes L = lanes<VEC>(TT);
+    const int W = A.W, H = A.H;
+    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int a0 = seg * (L.sx - 2) - 1;
+    const int y0 = strip * sy, y1 = min(H, y0 + sy);
+    const int a = a0 + L.ln;
+    {
+        float v[VEC];
+        for (int r = 0; r < 3; ++r) {
+            xprime<VEC>(X, Xc, W, H, Wc, Hc, N, a, y0 - 1 + r, L.col, v);
+            sts<VEC>(srow<VEC>(ring, r, L.ln, L.sx, TT, L.lc), v);
+        }
+    }
+    __syncthreads();
+    constexpr int NQ = DOTS == 1 ? 2 : 1;
+    float acc[NQ][VEC];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) zero_vec<VEC>(acc[q]);
+    const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
+    for (int b = y0; b < y1; ++b) {
+        const int k = b - y0;
+        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
+        const bool pre = b + 1 < y1;
+        float nv[VEC];
+        if (pre) xprime<VEC>(X, Xc, W, H, Wc, Hc, N, a, b + 2, L.col, nv);
+        if (out_lane) {
+            const size_t node = (size_t)b * W + a;
+            A7 c, m;
+            load_coef(A.coef, node, A.cm, A.cl, c, m);
+            float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], o[VEC];
+            lds<VEC>(srow<VEC>(ring, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(ring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(ring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(ring, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(ring, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(ring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(ring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            ldg_vec<float, VEC>(B + node * N + L.col, bv);
+            const float w = omega / c.c;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
+                                 c.ne * xne[v] + c.sw * xsw[v];
+                o[v] = xc[v] + w * (bv[v] - ax);
+            }
+            st_vec<float, VEC>(Out + node * N + L.col, o);
+            if constexpr (DOTS > 0) {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    acc[0][v] += bv[v] * o[v];
+                    if constexpr (NQ == 2) acc[1][v] += bv[v] * bv[v];
+                }
+            }
+        }
+        if (pre) sts<VEC>(srow<VEC>(ring, (k + 3) & 3, L.ln, L.sx, TT, L.lc), nv);
+        __syncthreads();
+    }
+    if constexpr (DOTS == 1) tile_reduce_finish<VEC, 2, FIN_RZ_FIRST>(acc, L, TT, N, ring, cr);
+    if constexpr (DOTS == 2) tile_reduce_finish<VEC, 1, FIN_RZ_NEXT>(acc, L, TT, N, ring, cr);
+}
+
+// ---------------------------------------------------------------------------
+// PCG step length: alpha = rho / (p . A p) per column, A p not written
+// ---------------------------------------------------------------------------
+template <int VEC>
+__global__ void __launch_bounds__(kStBlock)
+k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __restrict__ P,
+               ColRed<float> cr, Skip sk) {
+    pdl_enter();
+    if (skip_now(sk)) return;
+    extern __shared__ float4 smem4[];
+    float* ring = reinterpret_cast<float*>(smem4);
+    const Lanes L = lanes<VEC>(TT);
+    const int W = A.W, H = A.H;
+    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int a0 = seg * (L.sx - 2) - 1;
+    const int y0 = strip * sy, y1 = min(H, y0 + sy);
+    const int a = a0 + L.ln;
+    {
+        float v[VEC];
+        for (int r = 0; r < 3; ++r) {
+            gload<VEC>(P, W, H, N, a, y0 - 1 + r, L.col, v);
+            sts<VEC>(srow<VEC>(ring, r, L.ln, L.sx, TT, L.lc), v);
+        }
+    }
+    __syncthreads();
+    float acc[1][VEC];
+    zero_vec<VEC>(acc[0]);
+    const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
+    for (int b = y0; b < y1; ++b) {
+        const int k = b - y0;
+        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
+        const bool pre = b + 1 < y1;
+        float nv[VEC];
+        if (pre) gload<VEC>(P, W, H, N, a, b + 2, L.col, nv);
+        if (out_lane) {
+            const size_t node = (size_t)b * W + a;
+            A7 c, m;
+            load_coef(A.coef, node, A.cm, A.cl, c, m);
+            float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
+            lds<VEC>(srow<VEC>(ring, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(ring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(ring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(ring, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(ring, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(ring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(ring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
+                                 c.ne * xne[v] + c.sw * xsw[v];
+                acc[0][v] += xc[v] * ax;
+            }
+        }
+        if (pre) sts<VEC>(srow<VEC>(ring, (k + 3) & 3, L.ln, L.sx, TT, L.lc), nv);
+        __syncthreads();
+    }
+    tile_reduce_finish<VEC, 1, FIN_ALPHA>(acc, L, TT, N, ring, cr);
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes
+// ---------------------------------------------------------------------------
+
+inline bool al(const void* p, size_t a) { return p == nullptr || ((uintptr_t)p % a) == 0; }
+
+// VEC (floats per thread) and TT (columns per time tile) for N columns
+struct Shape {
+    int vec, TT, tpn, sx, block;
+};
+
+Shape st_shape(int N, std::initializer_list<const void*> ptrs, bool need_even) {
+    Shape s{};
+    s.vec = 1;
+    for (int v : {4, 2}) {
+        if (N % v) continue;
+        bool ok = true;
+        for (const void* p : ptrs) ok = ok && al(p, v * sizeof(float));
+        if (ok) { s.vec = v; break; }
+    }
+    if (need_even && s.vec < 2) throw Error(PTP_EINVAL, "stencil time restriction needs an even, aligned N");
+    // the largest divisor of N up to 32 that VEC divides
+    s.TT = s.vec;
+    for (int d = std::min(N, 32); d >= s.vec; --d)
+        if (N % d == 0 && d % s.vec == 0) { s.TT = d; break; }
+    s.tpn = s.TT / s.vec;
+    s.sx = kStBlock / s.tpn;
+    s.block = s.sx * s.tpn;
+    return s;
+}
+
+// rows per block strip: enough blocks for about three per SM, 2..32 rows
+int strip_rows(int H, int nseg, int nch) {
+    const long want = 3L * num_sms();
+    long sy = ((long)H * nseg * nch) / std::max(1L, want);
+    return (int)std::max(2L, std::min(32L, sy));
+}
+
+}  // namespace
+
+#define PTP_ST_VEC(vec, ...)                                     \
+    switch (vec) {                                               \
+        case 4: { constexpr int VEC = 4; __VA_ARGS__; } break;   \
+        case 2: { constexpr int VEC = 2; __VA_ARGS__; } break;   \
+        default: { constexpr int VEC = 1; __VA_ARGS__; } break;  \
+    }
+
+template <typename... KArgs, typename... Args>
+static void st_launch(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args&&... args) {
+    static thread_local std::vector<const void*> raised;
+    const void* k = (const void*)kernel;
+    if (smem > 48 * 1024 && std::find(raised.begin(), raised.end(), k) == raised.end()) {
+        PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        raised.push_back(k);
+    }
+    launch_k_smem(kernel, grid, dim3(block), smem, s, std::forward<Args>(args)...);
+}
+
+int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
+                     float omega, bool time_restrict, Skip sk, cudaStream_t s) {
+    const Shape sh = st_shape(N, {X, B, R, Z0}, time_restrict);
+    const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
+    const int nch = N / sh.TT;
+    const int sy = strip_rows(A.H, nseg, nch);
+    const int nstrip = (A.H + sy - 1) / sy;
+    const size_t smem = (4 * (size_t)sh.sx * sh.TT + 4 * (size_t)sh.sx) * sizeof(float);
+    const dim3 grid(nseg * nstrip, nch);
+    if (time_restrict) {
+        if (sh.vec == 4) st_launch(k_st_presid<4, 1>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk);
+        else st_launch(k_st_presid<2, 1>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk);
+    } else {
+        PTP_ST_VEC(sh.vec, st_launch(k_st_presid<VEC, 0>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R,
+                                     Z0, omega, sk));
+    }
+    return 1;
+}
+
+int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
+                             const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s) {
+    PTP_REQUIRE(Af.W == 2 * Ac.W + 1 && Af.H == 2 * Ac.H + 1, "stencil restriction: grids are not nested");
+    const Shape sh = st_shape(N, {Xf, Bf, Bc, Xc}, false);
+    const int cxo = (sh.sx - 3) / 2;
+    PTP_REQUIRE(cxo >= 1, "stencil restriction: block too narrow");
+    const int nseg = (Ac.W + cxo - 1) / cxo;
+    const int nch = N / sh.TT;
+    const int cy = std::max(1, strip_rows(Ac.H, nseg, nch) / 2);
+    const int nstrip = (Ac.H + cy - 1) / cy;
+    const size_t smem = 7 * (size_t)sh.sx * sh.TT * sizeof(float);
+    const dim3 grid(nseg * nstrip, nch);
+    PTP_ST_VEC(sh.vec, st_launch(k_st_resid_restrict<VEC>, grid, sh.block, smem, s, Af, Ac, N, sh.TT, cy, nseg, Xf,
+                                 Bf, Bc, Xc, omega, sk));
+    return 1;
+}
+
+int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
+                           const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
+                           cudaStream_t s) {
+    PTP_REQUIRE(A.W == 2 * Wc + 1 && A.H == 2 * Hc + 1, "stencil interpolation: grids are not nested");
+    const Shape sh = st_shape(N, {Xc, X, B, Out}, false);
+    const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
+    const int nch = N / sh.TT;
+    const int sy = strip_rows(A.H, nseg, nch);
+    const int nstrip = (A.H + sy - 1) / sy;
+    const size_t smem = 4 * (size_t)sh.sx * sh.TT * sizeof(float);
+    const dim3 grid(nseg * nstrip, nch);
+    if (dots) {
+        const size_t need = (size_t)grid.x * grid.y * 2 * sh.TT;
+        PTP_REQUIRE(cr.partials != nullptr && need <= cr.capacity, "stencil reduction: partial buffer too small");
+        PTP_REQUIRE(nch <= 254, "stencil reduction: too many time tiles");
+    }
+    if (dots == 1) {
+        PTP_ST_VEC(sh.vec, st_launch(k_st_interp_sweep<VEC, 1>, grid, sh.block, smem, s, A, Wc, Hc, N, sh.TT, sy, nseg,
+                                     Xc, X, B, Out, omega, cr, sk));
+    } else if (dots == 2) {
+        PTP_ST_VEC(sh.vec, st_launch(k_st_interp_sweep<VEC, 2>, grid, sh.block, smem, s, A, Wc, Hc, N, sh.TT, sy, nseg,
+                                     Xc, X, B, Out, omega, cr, sk));
+    } else {
+        PTP_ST_VEC(sh.vec, st_launch(k_st_interp_sweep<VEC, 0>, grid, sh.block, smem, s, A, Wc, Hc, N, sh.TT, sy, nseg,
+                                     Xc, X, B, Out, omega, cr, sk));
+    }
+    return 1;
+}
+
+int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s) {
+    const Shape sh = st_shape(N, {P}, false);
+    const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
+    const int nch = N / sh.TT;
+    const int sy = strip_rows(A.H, nseg, nch);
+    const int nstrip = (A.H + sy - 1) / sy;
+    const size_t smem = 4 * (size_t)sh.sx * sh.TT * sizeof(float);
+    const dim3 grid(nseg * nstrip, nch);
+    const size_t need = (size_t)grid.x * grid.y * sh.TT;
+    PTP_REQUIRE(cr.partials != nullptr && need <= cr.capacity, "stencil reduction: partial buffer too small");
+    PTP_REQUIRE(nch <= 254, "stencil reduction: too many time tiles");
+    PTP_ST_VEC(sh.vec, st_launch(k_st_apply_dot<VEC>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, P, cr, sk));
+    return 1;
+}
+
+}  // namespace ptp

@@ -159,6 +159,7 @@ struct Op {             // cm * v1 + cl * v2 on a CSR pattern
 template <typename T>
 struct ColRed {         // per-column reduction workspace
     T* partials = nullptr;   // grid * N * 2
+    size_t capacity = 0;     // entries of `partials`
     unsigned* counter = nullptr;
     T* col = nullptr;        // per-column scalars, 8 x N: rho alpha beta rr bb . . .
     int* pdone = nullptr;    // PCG early-exit flag
@@ -217,6 +218,32 @@ int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip s
 template <typename T>
 int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, ColRed<T> cr, Skip sk,
                        cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Structured-grid stencil kernels of the float inner solve (k_stencil.cu).
+// Level grid: W free nodes per row, H rows, free node (a, b) at b W + a;
+// coef: 4 float4 per node (M {C,E,W,N}, M {S,NE,SW,0}, L {..}, L {..}).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct StencilOp {      // cm M + cl L as a 7-point stencil
+    int W = 0, H = 0;
+    const float4* coef = nullptr;
+    T cm = 1, cl = 0;
+};
+// R = B - (A X^n - M X^{n-1}) and Z0 = omega D^-1 R (Z0 may be null); with
+// time_restrict R instead receives the pair sums over (2m, 2m+1) (N/2 columns)
+int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
+                     float omega, bool time_restrict, Skip sk, cudaStream_t s);
+// Bc = P^T (Bf - Af Xf); Xc = omega Dc^-1 Bc if Xc is set
+int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
+                             const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s);
+// Out = x' + omega D^-1 (B - A x'), x' = X + P Xc; dots 1: rho = B.Out, bb = rr = B.B;
+// dots 2: beta = B.Out / rho, rho = B.Out (per column, cr)
+int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
+                           const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
+                           cudaStream_t s);
+// alpha = rho / (P . A P) per column
+int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s);
 
 // dense coarse-level apply Y = Ainv B  (n x n, row-major)
 template <typename T>

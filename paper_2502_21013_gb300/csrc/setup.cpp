@@ -471,6 +471,44 @@ void build_problem(Ctx& c) {
     c.coil_sin.upload(csin, s);
 }
 
+// The operators M and L of a structured level as per-node 7-point stencils:
+// for free node (a, b) (index b W + a) the coefficients of the neighbours
+// C (a, b), E (a+1, b), W (a-1, b), N (a, b+1), S (a, b-1), NE (a+1, b+1),
+// SW (a-1, b-1) -- the P1 pattern of the grid whose cells are split along
+// (i, j)-(i+1, j+1).  Layout per node: M {C, E, W, N}, M {S, NE, SW, 0},
+// L {C, E, W, N}, L {S, NE, SW, 0}.  Returns false if an entry lies outside
+// the pattern (then the level has no stencil form).
+static bool stencil_coefficients(const HostCSR& M, const HostCSR& L, int W, int H, std::vector<float>& out) {
+    const int n = W * H;
+    out.assign(16 * (size_t)n, 0.0f);
+    auto slot = [&](int i, int j) -> int {
+        const int ai = i % W, bi = i / W, aj = j % W, bj = j / W;
+        const int da = aj - ai, db = bj - bi;
+        if (da == 0 && db == 0) return 0;
+        if (da == 1 && db == 0) return 1;
+        if (da == -1 && db == 0) return 2;
+        if (da == 0 && db == 1) return 3;
+        if (da == 0 && db == -1) return 4;
+        if (da == 1 && db == 1) return 5;
+        if (da == -1 && db == -1) return 6;
+        return -1;
+    };
+    for (int part = 0; part < 2; ++part) {
+        const HostCSR& A = part == 0 ? M : L;
+        if (A.rows != n) return false;
+        for (int i = 0; i < n; ++i)
+            for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+                const int sl = slot(i, A.idx[k]);
+                if (sl < 0) {
+                    if (A.val[k] != 0.0) return false;
+                    continue;
+                }
+                out[16 * (size_t)i + 8 * part + sl] = (float)A.val[k];
+            }
+    }
+    return true;
+}
+
 void build_hierarchy(Ctx& c) {
     cudaStream_t s = c.stream;
     const ptp_opts& o = c.opts;
@@ -528,6 +566,23 @@ void build_hierarchy(Ctx& c) {
             upload_csr(L.R, transpose(L.hP), nullptr, false, s);
         }
     }
+
+    // ---- the same operators as 7-point stencils (structured hierarchy) ----
+    c.stencil_ok = c.structured && o.spatial_prec == PTP_PREC_GMG && c.sl.size() > 1;
+    for (auto& L : c.sl) {
+        L.st_ok = false;
+        L.st_coef.release();
+        if (!c.stencil_ok) continue;
+        if (L.nx < 3 || L.ny < 3 || (L.nx - 2) * (L.ny - 2) != L.n) { c.stencil_ok = false; continue; }
+        std::vector<float> coef;
+        if (!stencil_coefficients(L.hM, L.hL, L.nx - 2, L.ny - 2, coef)) { c.stencil_ok = false; continue; }
+        std::vector<float4> packed(coef.size() / 4);
+        std::memcpy(packed.data(), coef.data(), coef.size() * sizeof(float));
+        L.st_coef.upload(packed, s);
+        L.st_ok = true;
+    }
+    if (!c.stencil_ok)
+        for (auto& L : c.sl) { L.st_ok = false; L.st_coef.release(); }
 
     // ---- time levels: coarsen by 2 while N_l is even and above N_c ----
     c.tl.clear();

@@ -105,9 +105,11 @@ ColRed<T> make_cr(Ctx& c) {
     ColRed<T> r;
     if constexpr (sizeof(T) == 8) {
         r.partials = c.part_d.p;
+        r.capacity = c.part_d.n;
         r.col = c.col_d.p;
     } else {
         r.partials = c.part_f.p;
+        r.capacity = c.part_f.n;
         r.col = c.col_f.p;
     }
     r.counter = c.counter.p;
@@ -117,6 +119,29 @@ ColRed<T> make_cr(Ctx& c) {
 bool use_gmg(const Ctx& c) {
     return c.opts.spatial_prec == PTP_PREC_GMG &&
            (c.sl.size() > 1 || c.ops[0].inv_d.p != nullptr);
+}
+
+// The float inner solve runs the structured-grid stencil kernels
+// (k_stencil.cu): every spatial level has its 7-point stencil, GMG with one
+// sweep per level, and the option is on.
+template <typename T>
+bool use_stencil(const Ctx& c) {
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+        return c.stencil_ok && c.opts.stencil != 0 && use_gmg(c) && std::max(1, c.opts.gmg_smooth) == 1;
+    }
+}
+
+// operator cm M + cl L of op pair opi on spatial level s as a stencil
+StencilOp<float> st_op(const Ctx& c, int s, int opi) {
+    StencilOp<float> o;
+    o.W = c.sl[s].nx - 2;
+    o.H = c.sl[s].ny - 2;
+    o.coef = c.sl[s].st_coef.p;
+    o.cm = (float)c.ops[opi].cm;
+    o.cl = (float)c.ops[opi].cl;
+    return o;
 }
 
 // Aux for a fused first damped-Jacobi sweep of spatial level s under op pair opi
@@ -146,7 +171,68 @@ Aux<T> sweep_aux(Ctx& c, int s, int opi, T* Y2) {
 // for level 0 the caller's producer of b0 when first_done).  Returns the
 // buffer that holds z (xa or xb).
 template <typename T>
-T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool first_done) {
+T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool first_done, int dots = 0);
+
+// The same V-cycle with the stencil kernels: the residual and its
+// restriction in one pass per level (with the coarse level's first sweep),
+// the interpolation and the post-smoothing sweep in one pass per level, and
+// on the finest level the PCG dot products of b0 and z (dots 1: rho, bb, rr;
+// dots 2: beta, rho) in that same pass.
+float* gmg_vcycle_stencil(Ctx& c, int opi, int N, const float* b0, float* xa, float* xb, Skip sk, bool first_done,
+                          int dots) {
+    const int S = (int)c.sl.size();
+    const float w = (float)c.opts.gmg_omega;
+    cudaStream_t st = c.stream;
+    std::vector<const float*> b(S);
+    std::vector<float*> cur(S), oth(S);
+    b[0] = b0;
+    cur[0] = xa;
+    oth[0] = xb;
+    for (int s = 1; s < S; ++s) {
+        b[s] = gb<float>(c, s);
+        cur[s] = gx<float>(c, s);
+        oth[s] = gr<float>(c, s);
+    }
+    if (!first_done) {
+        Op<float> A = level_op<float>(c, 0, opi);
+        c.launches += launch_spmm<float>(SP_JACOBI, A, N, nullptr, b[0], cur[0], w, sk, st);
+    }
+    for (int s = 0; s < S - 1; ++s) {
+        // the next level's first sweep rides on the restriction unless it is the dense level
+        float* x_next = (s + 1 < S - 1) ? cur[s + 1] : nullptr;
+        c.launches += launch_st_resid_restrict(st_op(c, s, opi), st_op(c, s + 1, opi), N, cur[s], b[s],
+                                               const_cast<float*>(b[s + 1]), x_next, w, sk, st);
+    }
+    {
+        const int s = S - 1;
+        const float* inv = c.ops[opi].inv_f.p;
+        if (inv) {
+            c.launches += launch_dense_apply<float>(c.sl[s].n, N, inv, b[s], cur[s], sk, st);
+        } else {
+            Op<float> A = level_op<float>(c, s, opi);
+            c.launches += launch_spmm<float>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
+            for (int k = 1; k < 4; ++k) {
+                c.launches += launch_spmm<float>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
+                std::swap(cur[s], oth[s]);
+            }
+        }
+    }
+    ColRed<float> cr = make_cr<float>(c);
+    for (int s = S - 2; s >= 0; --s) {
+        const int d = s == 0 ? dots : 0;
+        c.launches += launch_st_interp_sweep(st_op(c, s, opi), c.sl[s + 1].nx - 2, c.sl[s + 1].ny - 2, N, cur[s + 1],
+                                             cur[s], b[s], oth[s], w, cr, d, sk, st);
+        std::swap(cur[s], oth[s]);
+    }
+    return cur[0];
+}
+
+template <typename T>
+T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool first_done, int dots) {
+    if constexpr (sizeof(T) == 4) {
+        if (use_stencil<T>(c)) return gmg_vcycle_stencil(c, opi, N, b0, xa, xb, sk, first_done, dots);
+    }
+    if (dots) throw Error(PTP_EINVAL, "fused dot products need the stencil V-cycle");
     const int S = (int)c.sl.size();
     const double cm = c.ops[opi].cm, cl = c.ops[opi].cl;
     const int nu = std::max(1, c.opts.gmg_smooth);
@@ -253,8 +339,10 @@ struct PCG {
             p = wbuf<T>(c, 2);
             c.launches += launch_pcg_init_jacobi<T>(A, N, r, z, p, cr, sk2, st);
         } else {
-            T* zr = gmg_vcycle<T>(c, opi, N, r, wbuf<T>(c, 1), wbuf<T>(c, 4), sk2, j0_done);
-            c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, zr, cr, 1, sk2, st);
+            // the stencil V-cycle forms rho = r.z and bb = rr = r.r in its last pass
+            const bool fused = use_stencil<T>(c);
+            T* zr = gmg_vcycle<T>(c, opi, N, r, wbuf<T>(c, 1), wbuf<T>(c, 4), sk2, j0_done, fused ? 1 : 0);
+            if (!fused) c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, zr, cr, 1, sk2, st);
             p = zr;
             pa = zr == wbuf<T>(c, 1) ? wbuf<T>(c, 4) : wbuf<T>(c, 1);
             pb = wbuf<T>(c, 5);
@@ -263,21 +351,31 @@ struct PCG {
 
     void iterate(bool last) {
         cudaStream_t st = c.stream;
-        c.launches += launch_pcg_apply_alpha<T>(A, N, p, q, cr, sk2, st);
         const int assign = (assign_first && iter == 0) ? 1 : 0;
-        ++iter;
         if (last && !cr.pdone) {   // no tolerance: the final r and its norm are never read
+            ++iter;
+            if constexpr (sizeof(T) == 4) {
+                if (use_stencil<T>(c)) {   // q = A p is not needed: only p.(A p) for alpha
+                    c.launches += launch_st_apply_dot(st_op(c, 0, opi), N, p, cr, sk2, st);
+                    c.launches += launch_pcg_xupdate<T>(A.rows, N, xscale, assign, x, p, cr, sk2, st);
+                    return;
+                }
+            }
+            c.launches += launch_pcg_apply_alpha<T>(A, N, p, q, cr, sk2, st);
             c.launches += launch_pcg_xupdate<T>(A.rows, N, xscale, assign, x, p, cr, sk2, st);
             return;
         }
+        c.launches += launch_pcg_apply_alpha<T>(A, N, p, q, cr, sk2, st);
+        ++iter;
         // the next V-cycle's first sweep rides on the residual update
         Aux<T> aux = (gmg && !last) ? sweep_aux<T>(c, 0, opi, pa) : Aux<T>();
         c.launches += launch_pcg_update<T>(A, N, xscale, assign, x, p, r, q, gmg ? nullptr : z, gmg ? 0 : 1, cr,
                                            sk2, st, aux);
         if (last) return;
         if (gmg) {
-            z = gmg_vcycle<T>(c, opi, N, r, pa, pb, sk2, true);
-            c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, z, cr, 0, sk2, st);
+            const bool fused = use_stencil<T>(c);
+            z = gmg_vcycle<T>(c, opi, N, r, pa, pb, sk2, true, fused ? 2 : 0);
+            if (!fused) c.launches += launch_pcg_dot_rz<T>(A.rows, N, r, z, cr, 0, sk2, st);
         }
         c.launches += launch_pcg_direction<T>(A.rows, N, z, p, cr, sk2, st);
     }
@@ -298,6 +396,9 @@ void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
             c.launches += launch_spmm<T>(SP_COPY, A, t.N, nullptr, b, r, T(0), sk, c.stream, aux);
         else
             PTP_CUDA(cudaMemcpyAsync(r, b, cnt * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
+    } else if (use_stencil<T>(c)) {
+        if constexpr (sizeof(T) == 4)
+            c.launches += launch_st_presid(st_op(c, 0, t.op), t.N, x, b, r, aux.Y2, aux.omega, false, sk, c.stream);
     } else {
         c.launches += launch_spmm<T>(SP_PRESID, A, t.N, x, b, r, T(0), sk, c.stream, aux);
     }
@@ -431,8 +532,17 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
         bj_sweep<T>(c, l, x, b, zero, sk);
         zero = false;
     }
-    Op<T> A = level_op<T>(c, 0, t.op);
-    c.launches += launch_spmm<T>(SP_PRESID_RESTRICT, A, t.N, x, b, mgb<T>(c, l + 1), T(0), sk, st);
+    bool restricted = false;
+    if constexpr (sizeof(T) == 4) {
+        if (use_stencil<T>(c) && t.N % 2 == 0) {
+            c.launches += launch_st_presid(st_op(c, 0, t.op), t.N, x, b, mgb<T>(c, l + 1), nullptr, 0.f, true, sk, st);
+            restricted = true;
+        }
+    }
+    if (!restricted) {
+        Op<T> A = level_op<T>(c, 0, t.op);
+        c.launches += launch_spmm<T>(SP_PRESID_RESTRICT, A, t.N, x, b, mgb<T>(c, l + 1), T(0), sk, st);
+    }
     mgt_vcycle<T>(c, l + 1, true, sk, full);
     c.launches += launch_time_prolong_add<T>(c.n, c.tl[l + 1].N, mgx<T>(c, l + 1), x, sk, st);
     for (int k = 0; k < post; ++k) bj_sweep<T>(c, l, x, b, false, sk);
@@ -767,8 +877,9 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
     };
-    const int ints[11] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
-                          o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it};
+    const int ints[12] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+                          o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it,
+                          o.stencil};
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));
