@@ -191,6 +191,11 @@ struct Ctx {
     DBuf<double> coil_s;        // n_coils x N: amp sin(2 pi t^n/T + phase)
     std::vector<int> coil_rows; // nodes with a nonzero coil load (host)
     DBuf<double> Qx, Qy;        // iron element flux scratch, n_iron x N each
+    // structured grid, saturating law: the residual in one fused pass
+    bool k1_struct = false;
+    double k1_ihx2 = 0, k1_ihy2 = 0, k1_At = 0, k1_Bt = 0;
+    DBuf<uint8_t> k1_cell, k1_flag;
+    DBuf<double> k1_mass, k1_lin;
     // adjoint data
     DBuf<double> e_area;        // |T| per iron element
     DBuf<int> mj_ptr, mj_idx;   // loss mass sum_iron sigma_e M1_e

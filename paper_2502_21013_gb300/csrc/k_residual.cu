@@ -18,6 +18,7 @@
 //      applies the stopping rule.
 // Threads are mapped with the time index fastest, so every load of a node's
 // N values is a contiguous, coalesced run.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 
@@ -68,6 +69,69 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Block reduction of ||R||^2 (every thread passes its partial sum), then
+// the last block to finish (atomic ticket, no waiting) sums the block
+// partials in a fixed order, writes ||R|| and applies the stopping rule of
+// Section 4 to the solve status.  Called by every thread of every block.
+__device__ void residual_norm_finish(double local, const ResidualArgs& a) {
+    __shared__ double sm[32];
+    __shared__ bool last;
+    const int nw = (blockDim.x + 31) / 32;
+    local = warp_sum(local);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (int)threadIdx.x < nw ? sm[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) {
+            const unsigned nblk = gridDim.x * gridDim.y;
+            const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+            a.partials[bid] = v;
+            __threadfence();
+            const unsigned ticket = atomicAdd(a.counter, 1u);
+            last = ticket == nblk - 1;
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    const int nblk = (int)(gridDim.x * gridDim.y);
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(a.partials + b);
+    s = warp_sum(s);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += sm[w];
+        const double nrm = sqrt(tot);
+        if (a.norm_out) *a.norm_out = nrm;
+        Status* st = a.status;
+        if (!st) {
+            *a.counter = 0u;
+            return;
+        }
+        st->bscale_used = st->bscale;
+        if (isfinite(nrm) && nrm > 0.0) st->bscale = nrm;
+        if (a.check) {
+            const int it = st->iteration;
+            if (it == 0) st->res0 = nrm;
+            st->res = nrm;
+            st->iteration = it + 1;
+            if (!isfinite(nrm)) {
+                st->done = 2;
+                if (a.done) *a.done = 1;
+            } else if (nrm <= st->tol * st->res0) {
+                st->done = 1;
+                if (a.done) *a.done = 1;
+            }
+        } else {
+            st->res = nrm;
+        }
+        *a.counter = 0u;
+    }
+}
+
 __global__ void __launch_bounds__(kBlock)
 k_node_residual(ResidualArgs a) {
     pdl_enter();
@@ -112,58 +176,192 @@ k_node_residual(ResidualArgs a) {
         if (a.b_f) a.b_f[g] = (float)(fscale * r);
         local += r * r;
     }
-    // block reduction of ||R||^2, then the last block finishes the sum
-    __shared__ double sm[kBlock / 32];
-    __shared__ bool last;
-    local = warp_sum(local);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < kBlock / 32 ? sm[threadIdx.x] : 0.0;
-        v = warp_sum(v);
-        if (threadIdx.x == 0) {
-            a.partials[blockIdx.x] = v;
-            __threadfence();
-            const unsigned ticket = atomicAdd(a.counter, 1u);
-            last = ticket == gridDim.x - 1;
-        }
-    }
-    __syncthreads();
-    if (!last) return;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += __ldcg(a.partials + b);
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) tot += sm[w];
-        const double nrm = sqrt(tot);
-        if (a.norm_out) *a.norm_out = nrm;
-        Status* st = a.status;
-        if (!st) {
-            *a.counter = 0u;
-            return;
-        }
-        st->bscale_used = st->bscale;
-        if (isfinite(nrm) && nrm > 0.0) st->bscale = nrm;
-        if (a.check) {
-            const int it = st->iteration;
-            if (it == 0) st->res0 = nrm;
-            st->res = nrm;
-            st->iteration = it + 1;
-            if (!isfinite(nrm)) {
-                st->done = 2;
-                if (a.done) *a.done = 1;
-            } else if (nrm <= st->tol * st->res0) {
-                st->done = 1;
-                if (a.done) *a.done = 1;
-            }
+    residual_norm_finish(local, a);
+}
+
+// ---------------------------------------------------------------------------
+// K1 on a structured grid with the saturating law: one fused pass.
+//
+// The grid's cells are split along (i, j)-(i+1, j+1) into the triangles
+// T_a = {(i,j), (i+1,j), (i+1,j+1)} and T_b = {(i,j), (i+1,j+1), (i,j+1)}, all
+// with area |T| = hx hy / 2 and axis-parallel legs, so on an iron triangle
+//   T_a: dx = u(i+1,j) - u(i,j),     dy = u(i+1,j+1) - u(i+1,j)
+//   T_b: dx = u(i+1,j+1) - u(i,j+1), dy = u(i,j+1) - u(i,j)
+//   s^2 = dx^2 / hx^2 + dy^2 / hy^2,  nu |T| = |T| nu_max - |T| dnu s_sat^2 / (s^2 + s_sat^2)
+//   Qx = nu |T| dx / hx^2, Qy = nu |T| dy / hy^2
+// and the element's contributions nu |T| g . grad(phi_k) to its vertices are
+//   T_a: (i,j) -Qx, (i+1,j) Qx - Qy, (i+1,j+1) Qy
+//   T_b: (i,j) -Qy, (i+1,j+1) Qx,     (i,j+1) Qy - Qx.
+// A block owns a time tile of TT columns, a segment of a grid row and a strip
+// of rows, and marches up the strip with shared-memory rings of U and of
+// u^n - u^{n-1} (four rows each) and of the iron fluxes (two cell rows):
+// each iron flux is computed once per block, and U is read once (plus the
+// halo).  The mass (M / tau) and the linear-element stiffness act as
+// per-node stencils; the source, the outputs and ||R|| are as in the
+// two-pass kernels.
+constexpr int kK1TT = 16;                  // time columns per block (double2 per thread)
+constexpr int kK1TPN = kK1TT / 2;          // threads per node
+constexpr int kK1SX = kBlock / kK1TPN;     // node slots per block row (32)
+constexpr size_t kK1Smem = (size_t)(8 + 8) * kK1SX * kK1TT * sizeof(double);   // 64 KB
+
+__device__ __forceinline__ double* k1_u(double* base, int slot, int node) {
+    return base + ((size_t)slot * kK1SX + node) * kK1TT;
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_k1_structured(ResidualArgs a, int sy, int nseg) {
+    pdl_enter();
+    if (skip_now(a.done)) return;
+    extern __shared__ double2 k1_smem[];
+    double* su = reinterpret_cast<double*>(k1_smem);           // U rows
+    double* sd = su + 4 * kK1SX * kK1TT;                       // u^n - u^{n-1} rows
+    double* sq = sd + 4 * kK1SX * kK1TT;                       // cell fluxes Qx_a, Qy_a, Qx_b, Qy_b
+    const int N = a.N, W = a.st_W, H = a.st_H, nxc = W + 1;    // cells per grid row
+    const int lc = threadIdx.x % kK1TPN, ln = threadIdx.x / kK1TPN;
+    const int col = blockIdx.y * kK1TT + 2 * lc;
+    const int colm = col == 0 ? N - 1 : col - 1;
+    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int a0 = seg * (kK1SX - 2) - 1;
+    const int y0 = strip * sy, y1 = min(H, y0 + sy);
+    const int an = a0 + ln;                                     // this thread's free column
+    const bool in_x = an >= 0 && an < W;
+    const double fscale = a.b_f ? a.scale / a.status->bscale : 0.0;
+    auto fetch = [&](int b, double2& v, double& pv) {
+        if (in_x && b >= 0 && b < H) {
+            const double* p = a.U + ((size_t)b * W + an) * N;
+            v = __ldg(reinterpret_cast<const double2*>(p + col));
+            pv = __ldg(p + colm);
         } else {
-            st->res = nrm;
+            v = make_double2(0.0, 0.0);
+            pv = 0.0;
         }
-        *a.counter = 0u;
+    };
+    auto stash = [&](int slot, double2 v, double pv) {
+        *reinterpret_cast<double2*>(k1_u(su, slot, ln) + 2 * lc) = v;
+        *reinterpret_cast<double2*>(k1_u(sd, slot, ln) + 2 * lc) = make_double2(v.x - pv, v.y - v.x);
+    };
+    // fluxes of grid cell row cj (free rows cj - 1 = slot sS, cj = slot sN) into flux slot q
+    auto cell_row = [&](int cj, int sS, int sN, int q) {
+        // cell slot cs = ln covers grid cell ci = a0 + 1 + cs, free columns ci - 1, ci = slots ln, ln + 1
+        if (ln > kK1SX - 2) return;
+        const int ci = a0 + 1 + ln;
+        double* out = sq + ((size_t)q * kK1SX + ln) * 4 * kK1TT + 2 * lc;
+        uint8_t f = 0;
+        if (ci >= 0 && ci < nxc && cj >= 0 && cj <= H) f = __ldg(a.st_cell + (size_t)cj * nxc + ci);
+        double2 r0 = make_double2(0.0, 0.0), r1 = r0, r2 = r0, r3 = r0;
+        if (f) {
+            const double2 u00 = *reinterpret_cast<const double2*>(k1_u(su, sS, ln) + 2 * lc);      // (i, j)
+            const double2 u10 = *reinterpret_cast<const double2*>(k1_u(su, sS, ln + 1) + 2 * lc);  // (i+1, j)
+            const double2 u01 = *reinterpret_cast<const double2*>(k1_u(su, sN, ln) + 2 * lc);      // (i, j+1)
+            const double2 u11 = *reinterpret_cast<const double2*>(k1_u(su, sN, ln + 1) + 2 * lc);  // (i+1, j+1)
+            auto flux = [&](double dx, double dy, double& qx, double& qy) {
+                const double d = fma(dx * dx, a.st_ihx2, fma(dy * dy, a.st_ihy2, a.s2sat));
+                const double nuT = fma(-a.st_Bt, recip_newton(d), a.st_At);
+                qx = nuT * a.st_ihx2 * dx;
+                qy = nuT * a.st_ihy2 * dy;
+            };
+            if (f & 1) {
+                flux(u10.x - u00.x, u11.x - u10.x, r0.x, r1.x);
+                flux(u10.y - u00.y, u11.y - u10.y, r0.y, r1.y);
+            }
+            if (f & 2) {
+                flux(u11.x - u01.x, u01.x - u00.x, r2.x, r3.x);
+                flux(u11.y - u01.y, u01.y - u00.y, r2.y, r3.y);
+            }
+        }
+        *reinterpret_cast<double2*>(out) = r0;
+        *reinterpret_cast<double2*>(out + kK1TT) = r1;
+        *reinterpret_cast<double2*>(out + 2 * kK1TT) = r2;
+        *reinterpret_cast<double2*>(out + 3 * kK1TT) = r3;
+    };
+    {
+        double2 v;
+        double pv;
+        for (int r = 0; r < 3; ++r) {
+            fetch(y0 - 1 + r, v, pv);
+            stash(r, v, pv);
+        }
     }
+    __syncthreads();
+    cell_row(y0, 0, 1, y0 & 1);
+    double local = 0.0;
+    const bool out_lane = ln >= 1 && ln <= kK1SX - 2 && in_x;
+    for (int b = y0; b < y1; ++b) {
+        const int k = b - y0;
+        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
+        const bool pre = b + 1 < y1;
+        double2 nv;
+        double npv;
+        if (pre) fetch(b + 2, nv, npv);
+        cell_row(b + 1, sC, sN, (b + 1) & 1);
+        __syncthreads();
+        if (out_lane) {
+            const size_t node = (size_t)b * W + an;
+            // iron: cells (a, b) [this node is vertex (i+1, j+1) of both], (a+1, b) [(i, j+1) of T_b],
+            // (a, b+1) [(i+1, j) of T_a], (a+1, b+1) [(i, j) of both], grid cell coordinates
+            const double* qS = sq + ((size_t)(b & 1) * kK1SX) * 4 * kK1TT + 2 * lc;
+            const double* qN = sq + ((size_t)((b + 1) & 1) * kK1SX) * 4 * kK1TT + 2 * lc;
+            auto Q = [&](const double* base, int cs, int comp) {
+                return *reinterpret_cast<const double2*>(base + ((size_t)cs * 4 + comp) * kK1TT);
+            };
+            const double2 sw_ya = Q(qS, ln - 1, 1), sw_xb = Q(qS, ln - 1, 2);
+            const double2 se_xb = Q(qS, ln, 2), se_yb = Q(qS, ln, 3);
+            const double2 nw_xa = Q(qN, ln - 1, 0), nw_ya = Q(qN, ln - 1, 1);
+            const double2 ne_xa = Q(qN, ln, 0), ne_yb = Q(qN, ln, 3);
+            double kv0 = (sw_ya.x + sw_xb.x) + (se_yb.x - se_xb.x) + (nw_xa.x - nw_ya.x) - (ne_xa.x + ne_yb.x);
+            double kv1 = (sw_ya.y + sw_xb.y) + (se_yb.y - se_xb.y) + (nw_xa.y - nw_ya.y) - (ne_xa.y + ne_yb.y);
+            const uint8_t fl = __ldg(a.st_flag + node);
+            if (fl & 2) {   // linear elements: nu_linear stiffness, five-point
+                const double* L = a.st_lin + 8 * node;
+                const double2 c0 = __ldg(reinterpret_cast<const double2*>(L));      // C, E
+                const double2 c1 = __ldg(reinterpret_cast<const double2*>(L + 2));  // W, N
+                const double cS = __ldg(L + 4);
+                const double2 uc = *reinterpret_cast<const double2*>(k1_u(su, sC, ln) + 2 * lc);
+                const double2 ue = *reinterpret_cast<const double2*>(k1_u(su, sC, ln + 1) + 2 * lc);
+                const double2 uw = *reinterpret_cast<const double2*>(k1_u(su, sC, ln - 1) + 2 * lc);
+                const double2 un = *reinterpret_cast<const double2*>(k1_u(su, sN, ln) + 2 * lc);
+                const double2 us = *reinterpret_cast<const double2*>(k1_u(su, sS, ln) + 2 * lc);
+                kv0 = fma(c0.x, uc.x, fma(c0.y, ue.x, fma(c1.x, uw.x, fma(c1.y, un.x, fma(cS, us.x, kv0)))));
+                kv1 = fma(c0.x, uc.y, fma(c0.y, ue.y, fma(c1.x, uw.y, fma(c1.y, un.y, fma(cS, us.y, kv1)))));
+            }
+            double mv0 = 0.0, mv1 = 0.0;
+            if ((fl & 1) && !a.st_no_mass) {   // (M / tau)(u^n - u^{n-1}), seven-point
+                const double* Mr = a.st_mass + 8 * node;
+                const double2 m0 = __ldg(reinterpret_cast<const double2*>(Mr));      // C, E
+                const double2 m1 = __ldg(reinterpret_cast<const double2*>(Mr + 2));  // W, N
+                const double2 m2 = __ldg(reinterpret_cast<const double2*>(Mr + 4));  // S, NE
+                const double mSW = __ldg(Mr + 6);
+                const double2 dc = *reinterpret_cast<const double2*>(k1_u(sd, sC, ln) + 2 * lc);
+                const double2 de = *reinterpret_cast<const double2*>(k1_u(sd, sC, ln + 1) + 2 * lc);
+                const double2 dw = *reinterpret_cast<const double2*>(k1_u(sd, sC, ln - 1) + 2 * lc);
+                const double2 dn = *reinterpret_cast<const double2*>(k1_u(sd, sN, ln) + 2 * lc);
+                const double2 ds = *reinterpret_cast<const double2*>(k1_u(sd, sS, ln) + 2 * lc);
+                const double2 dne = *reinterpret_cast<const double2*>(k1_u(sd, sN, ln + 1) + 2 * lc);
+                const double2 dsw = *reinterpret_cast<const double2*>(k1_u(sd, sS, ln - 1) + 2 * lc);
+                mv0 = fma(m0.x, dc.x, fma(m0.y, de.x, fma(m1.x, dw.x, fma(m1.y, dn.x, fma(m2.x, ds.x,
+                          fma(m2.y, dne.x, mSW * dsw.x))))));
+                mv1 = fma(m0.x, dc.y, fma(m0.y, de.y, fma(m1.x, dw.y, fma(m1.y, dn.y, fma(m2.x, ds.y,
+                          fma(m2.y, dne.y, mSW * dsw.y))))));
+            }
+            double f0 = 0.0, f1 = 0.0;
+            for (int cc = 0; cc < a.n_coils; ++cc) {
+                const double cb = __ldg(a.coil_b + (size_t)cc * a.n + node);
+                if (cb != 0.0) {
+                    f0 = fma(cb, __ldg(a.coil_s + (size_t)cc * N + col), f0);
+                    f1 = fma(cb, __ldg(a.coil_s + (size_t)cc * N + col + 1), f1);
+                }
+            }
+            const double r0 = f0 - mv0 - kv0, r1 = f1 - mv1 - kv1;
+            const size_t g = node * N + col;
+            if (a.R) *reinterpret_cast<double2*>(a.R + g) = make_double2(r0, r1);
+            if (a.b_d) *reinterpret_cast<double2*>(a.b_d + g) = make_double2(a.scale * r0, a.scale * r1);
+            if (a.b_f) *reinterpret_cast<float2*>(a.b_f + g) = make_float2((float)(fscale * r0), (float)(fscale * r1));
+            local = fma(r0, r0, fma(r1, r1, local));
+        }
+        if (pre) stash((k + 3) & 3, nv, npv);
+        __syncthreads();
+    }
+    residual_norm_finish(local, a);
 }
 
 __global__ void k_source(int n, int N, int n_coils, const double* __restrict__ coil_b,
@@ -210,6 +408,32 @@ int num_sms() {
 int residual_grid(size_t total) { return grid_for(total, 8); }
 
 int launch_residual(const ResidualArgs& a, cudaStream_t s) {
+    // structured grid, saturating law, the outer residual with its own source
+    // and iron fluxes: one fused pass when its blocks fit the partial sums
+    if (a.st_cell && !a.Fext && !a.skip_flux && a.N % kK1TT == 0 &&
+        ((uintptr_t)a.U % 16) == 0 && ((uintptr_t)a.R % 16) == 0 && ((uintptr_t)a.b_d % 16) == 0 &&
+        ((uintptr_t)a.b_f % 8) == 0) {
+        const int nseg = (a.st_W + kK1SX - 3) / (kK1SX - 2);
+        const int nch = a.N / kK1TT;
+        const long want = 3L * num_sms();
+        int sy = (int)std::max(2L, std::min(32L, ((long)a.st_H * nseg * nch) / std::max(1L, want)));
+        long blocks = (long)nseg * ((a.st_H + sy - 1) / sy) * nch;
+        while (blocks > (long)a.partials_cap && sy < a.st_H) {
+            sy *= 2;
+            blocks = (long)nseg * ((a.st_H + sy - 1) / sy) * nch;
+        }
+        if (blocks <= (long)a.partials_cap) {
+            const int nstrip = (a.st_H + sy - 1) / sy;
+            static thread_local int smem_set = -1;
+            if (smem_set < 0) {
+                PTP_CUDA(cudaFuncSetAttribute(k_k1_structured, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kK1Smem));
+                smem_set = 1;
+            }
+            launch_k_smem(k_k1_structured, dim3(nseg * nstrip, nch), dim3(kBlock), kK1Smem, s, a, sy, nseg);
+            return 1;
+        }
+    }
     int launched = 0;
     if (a.n_iron > 0 && !a.skip_flux) {
         const size_t te = (size_t)a.n_iron * a.N;

@@ -93,6 +93,17 @@ struct ResidualArgs {
     double* norm_out;         // if set, the last block also writes ||R|| here
     int* done;                // outer early-exit flag (may be null)
     int check;                // apply the stopping rule in the last block
+    size_t partials_cap;      // entries of `partials`
+    // structured grid with the saturating law (set: one fused pass, see
+    // launch_residual): W x H free nodes, cells (nx-1) x (ny-1)
+    int st_W, st_H;
+    const uint8_t* st_cell;   // per grid cell: bit 0 lower-right triangle iron, bit 1 upper-left
+    const uint8_t* st_flag;   // per free node: bit 0 mass row nonzero, bit 1 linear stiffness row nonzero
+    const double* st_mass;    // per free node 8: M / tau at C, E, W, N, S, NE, SW, 0
+    const double* st_lin;     // per free node 8: nu_linear stiffness at C, E, W, N, S, 0, 0, 0
+    double st_ihx2, st_ihy2;  // 1 / hx^2, 1 / hy^2
+    double st_At, st_Bt;      // |T| nu_max, |T| (nu_max - nu_min) s_sat^2
+    int st_no_mass;           // sigma = 0 (static problems)
 };
 int launch_residual(const ResidualArgs& a, cudaStream_t s);  // returns kernels launched
 // the same, with the iron fluxes of the exponential law of Section 4 when e_law

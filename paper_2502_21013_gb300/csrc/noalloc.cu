@@ -120,6 +120,7 @@ extern "C" int ptp_residual_noalloc_dev(ptp_ctx* h, const double* U, double* R, 
         ResidualArgs a = residual_args(c, U, R);
         a.counter = reinterpret_cast<unsigned*>(base);
         a.partials = base + kCounterDoubles;
+        a.partials_cap = kPartialDoubles;
         a.Qx = base + kFluxOffset;
         a.Qy = a.Qx + (size_t)c.n_iron * c.N;
         a.status = nullptr;

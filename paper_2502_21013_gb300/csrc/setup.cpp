@@ -301,6 +301,9 @@ void make_structured_mesh(Ctx& c, int nx, int ny, double x0, double y0, double x
     c.gnx = nx; c.gny = ny; c.gx0 = x0; c.gy0 = y0; c.gx1 = x1; c.gy1 = y1;
 }
 
+static void build_k1_structured(Ctx& c, const HostCSR& M, const std::vector<double>& mval, const HostCSR& Ll,
+                                const std::vector<int>& iron_of, cudaStream_t s);
+
 void build_problem(Ctx& c) {
     PTP_REQUIRE(c.n_nodes > 0 && c.n_tri > 0, "no mesh");
     PTP_REQUIRE(c.have_materials, "materials not set");
@@ -439,6 +442,7 @@ void build_problem(Ctx& c) {
         c.l_ptr.upload(Ll.ptr, s);
         c.l_idx.upload(Ll.idx, s);
         c.l_val.upload(Ll.val, s);
+        build_k1_structured(c, M, mv, Ll, iron_of, s);
     }
     // K_hat: nu_max A, or sum_T khat_T A_T with the per-element weights
     HostCSR L = A;
@@ -469,6 +473,60 @@ void build_problem(Ctx& c) {
     c.coil_b.upload(cb, s);
     c.coil_s.upload(cs, s);
     c.coil_sin.upload(csin, s);
+}
+
+// Data of the fused residual on a structured grid with the saturating law:
+// per grid cell which of its two triangles are iron, per free node the rows
+// of M / tau and of the linear-element stiffness as stencils (the P1 pattern
+// of the grid), and the element constants, which are equal on every iron
+// triangle of the uniform grid.  Leaves k1_struct false on any other mesh.
+static void build_k1_structured(Ctx& c, const HostCSR& M, const std::vector<double>& mval, const HostCSR& Ll,
+                                const std::vector<int>& iron_of, cudaStream_t s) {
+    c.k1_struct = false;
+    c.k1_cell.release(); c.k1_flag.release(); c.k1_mass.release(); c.k1_lin.release();
+    if (!c.structured || c.law_exp || c.gnx < 3 || c.gny < 3) return;
+    const int nx = c.gnx, ny = c.gny, W = nx - 2, H = ny - 2;
+    if ((int64_t)W * H != c.n) return;
+    const double hx = (c.gx1 - c.gx0) / (nx - 1), hy = (c.gy1 - c.gy0) / (ny - 1);
+    std::vector<uint8_t> cell((size_t)(nx - 1) * (ny - 1), 0);
+    for (int j = 0; j < ny - 1; ++j)
+        for (int i = 0; i < nx - 1; ++i) {
+            const size_t e = 2 * ((size_t)j * (nx - 1) + i);
+            cell[(size_t)j * (nx - 1) + i] = (uint8_t)((iron_of[e] >= 0 ? 1 : 0) | (iron_of[e + 1] >= 0 ? 2 : 0));
+        }
+    auto slot = [&](int i, int j) -> int {
+        const int da = j % W - i % W, db = j / W - i / W;
+        const int off[7][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}};
+        for (int k = 0; k < 7; ++k)
+            if (off[k][0] == da && off[k][1] == db) return k;
+        return -1;
+    };
+    std::vector<double> mass(8 * (size_t)c.n, 0.0), lin(8 * (size_t)c.n, 0.0);
+    std::vector<uint8_t> flag(c.n, 0);
+    for (int i = 0; i < c.n; ++i) {
+        for (int k = M.ptr[i]; k < M.ptr[i + 1]; ++k) {
+            const int sl = slot(i, M.idx[k]);
+            if (sl < 0) return;
+            mass[8 * (size_t)i + sl] = mval[k];
+            if (mval[k] != 0.0) flag[i] |= 1;
+        }
+        for (int k = Ll.ptr[i]; k < Ll.ptr[i + 1]; ++k) {
+            const int sl = slot(i, Ll.idx[k]);
+            if (sl < 0 || sl > 4) return;   // right triangles: no diagonal coupling in the stiffness
+            lin[8 * (size_t)i + sl] = Ll.val[k];
+            if (Ll.val[k] != 0.0) flag[i] |= 2;
+        }
+    }
+    const double area = 0.5 * hx * hy;
+    c.k1_ihx2 = 1.0 / (hx * hx);
+    c.k1_ihy2 = 1.0 / (hy * hy);
+    c.k1_At = area * c.nu_max;
+    c.k1_Bt = area * (c.nu_max - c.nu_min) * c.s_sat * c.s_sat;
+    c.k1_cell.upload(cell, s);
+    c.k1_flag.upload(flag, s);
+    c.k1_mass.upload(mass, s);
+    c.k1_lin.upload(lin, s);
+    c.k1_struct = true;
 }
 
 // The operators M and L of a structured level as per-node 7-point stencils:

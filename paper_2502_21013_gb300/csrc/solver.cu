@@ -571,7 +571,10 @@ void outer_step(Ctx& c, Skip sk, int kind) {
         a.Fext = c.Gadj.p;
         a.skip_flux = 1;
     }
-    if (kind == STEP_STATIC) a.m_ptr = c.zero_ptr.p;   // every mass row empty
+    if (kind == STEP_STATIC) {   // every mass row empty
+        a.m_ptr = c.zero_ptr.p;
+        a.st_no_mass = 1;
+    }
     c.launches += launch_residual_law(a, law_data(c), c.stream);
     if (kind == STEP_STATIC) {
         PCG<T> pcg(c, c.coarse_ops[0], c.N, mgb<T>(c, 0), mgx<T>(c, 0), T(1), 0.0, sk, true);
@@ -597,7 +600,10 @@ void final_residual(Ctx& c, int kind) {
         a.Fext = c.Gadj.p;
         a.skip_flux = 1;
     }
-    if (kind == STEP_STATIC) a.m_ptr = c.zero_ptr.p;
+    if (kind == STEP_STATIC) {
+        a.m_ptr = c.zero_ptr.p;
+        a.st_no_mass = 1;
+    }
     c.launches += launch_residual_law(a, law_data(c), c.stream);
 }
 
@@ -640,8 +646,21 @@ ResidualArgs residual_args(Ctx& c, const double* U, double* R) {
     a.Qy = c.Qy.p;
     a.R = R;
     a.partials = c.part_d.p;
+    a.partials_cap = c.part_d.n;
     a.counter = c.counter.p;
     a.status = c.status.p;
+    if (c.k1_struct) {
+        a.st_W = c.gnx - 2;
+        a.st_H = c.gny - 2;
+        a.st_cell = c.k1_cell.p;
+        a.st_flag = c.k1_flag.p;
+        a.st_mass = c.k1_mass.p;
+        a.st_lin = c.k1_lin.p;
+        a.st_ihx2 = c.k1_ihx2;
+        a.st_ihy2 = c.k1_ihy2;
+        a.st_At = c.k1_At;
+        a.st_Bt = c.k1_Bt;
+    }
     return a;
 }
 

@@ -46,6 +46,10 @@ PROBLEMS = {
     "transformer33x17_N8": lambda: W.transformer_problem(33, 17, 8),
     "square9_N4_strong": lambda: W.unit_square_problem(9, 4, amps=(3000.0,)),
     "square17_N6": lambda: W.unit_square_problem(17, 6),
+    # structured grids whose N is a multiple of 16 take the fused one-pass K1
+    # (time tiles of 16 columns): three tiles, a rectangle, saturated iron
+    "square33_N48_strong": lambda: W.unit_square_problem(33, 48, amps=(500.0,)),
+    "transformer65x33_N16": lambda: W.transformer_problem(65, 33, 16),
 }
 
 
