@@ -126,6 +126,9 @@ typedef struct ptp_opts {
                             kernels (fused residual + restriction,
                             interpolation + sweep + dot products; default),
                             0 = the padded-ELL row kernels                   */
+    int    k1_fused;     /* structured grids, saturating law: 1 = the outer
+                            residual in one fused pass (shared-memory element
+                            fluxes), 0 = element pass + node pass (default)  */
 } ptp_opts;
 
 /* Statistics of the last solve. */

@@ -132,6 +132,7 @@ void ptp_default_opts(ptp_opts* o) {
     o->newton_eta = 1e-2;
     o->krylov_dim = 20;
     o->stencil = 1;
+    o->k1_fused = 0;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }

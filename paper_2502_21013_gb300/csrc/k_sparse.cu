@@ -401,19 +401,45 @@ k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Sk
     }
 }
 
-// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv)
+// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600):
+// one warp per output row i and chunk of up to 32 columns.  With at least 32
+// columns the lanes take one column each and walk j with four independent
+// partial sums (Ainv[i][j] is a broadcast, B[j][c..c+31] one coalesced load);
+// with fewer columns the lanes split j and the partial sums meet in a
+// fixed-order shuffle reduction.
 template <typename T>
 __global__ void k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Y,
                               Skip sk) {
     pdl_enter();
     if (skip_now(sk)) return;
-    const size_t total = (size_t)n * N;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(g / N), c = (int)(g - (size_t)i * N);
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int cchunks = (N + 31) / 32;
+    const long items = (long)n * cchunks;
+    for (long w = (long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < items; w += warps) {
+        const int i = (int)(w / cchunks), c0 = (int)(w - (long)i * cchunks) * 32;
         const T* a = A + (size_t)i * n;
-        T s = T(0);
-        for (int j = 0; j < n; ++j) s += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
-        Y[g] = s;
+        if (N >= 32) {
+            const int c = c0 + lane;
+            if (c >= N) continue;
+            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            int j = 0;
+            for (; j + 4 <= n; j += 4) {
+                s0 += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
+                s1 += __ldg(a + j + 1) * __ldg(B + (size_t)(j + 1) * N + c);
+                s2 += __ldg(a + j + 2) * __ldg(B + (size_t)(j + 2) * N + c);
+                s3 += __ldg(a + j + 3) * __ldg(B + (size_t)(j + 3) * N + c);
+            }
+            for (; j < n; ++j) s0 += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
+            Y[(size_t)i * N + c] = (s0 + s1) + (s2 + s3);
+        } else {
+            for (int c = 0; c < N; ++c) {
+                T s = 0;
+                for (int j = lane; j < n; j += 32) s += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) Y[(size_t)i * N + c] = s;
+            }
+        }
     }
 }
 
@@ -710,7 +736,9 @@ int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip s
 
 template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    launch_k(k_dense_apply<T>, flat_grid((size_t)n * N), 256, s, n, N, Ainv, B, Y, sk);
+    const size_t warps = (size_t)n * ((N + 31) / 32);
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>((warps + 7) / 8, (size_t)num_sms() * 8));
+    launch_k(k_dense_apply<T>, grid, 256, s, n, N, Ainv, B, Y, sk);
     return 1;
 }
 

@@ -153,9 +153,21 @@ __device__ void tile_reduce_finish(float (&acc)[NQ][VEC], const Lanes& L, int TT
     }
     __syncthreads();
     if (!last) return;
-    for (int e = threadIdx.x; e < NQ * TT; e += blockDim.x) {
+    // all threads of the last block: P = blockDim / (NQ TT) threads per sum,
+    // each over a strided subset of the tiles, then P-way partials in order
+    const int E = NQ * TT;
+    const int P = max(1, (int)blockDim.x / E);
+    float* red = scratch + E;   // P x E partial sums
+    if ((int)threadIdx.x < P * E) {
+        const int e = threadIdx.x % E, p = threadIdx.x / E;
         float s = 0.f;
-        for (int b = 0; b < tiles; ++b) s += __ldcg(part + (size_t)b * NQ * TT + e);
+        for (int b = p; b < tiles; b += P) s += __ldcg(part + (size_t)b * E + e);
+        red[p * E + e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        float s = 0.f;
+        for (int p = 0; p < P; ++p) s += red[p * E + e];
         scratch[e] = s;
     }
     __syncthreads();
@@ -177,10 +189,48 @@ __device__ void tile_reduce_finish(float (&acc)[NQ][VEC], const Lanes& L, int TT
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous row pipeline.  Rows are copied global -> shared by cp.async
+// (zero-filled outside the grid) into rings of kNS slots, kLA rows ahead of
+// the row being computed, one commit group per row: at every step the block
+// waits (a hardware wait on its own copies) until the rows it needs have
+// landed, so about kLA rows per thread are in flight.
+// ---------------------------------------------------------------------------
+constexpr int kNS = 8;   // ring slots (power of two)
+constexpr int kLA = 4;   // rows in flight beyond the three being used: kNS >= 3 + kLA + 1
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? BYTES : 0;   // 0: nothing is read, the destination is zero-filled
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// async copy of this thread's VEC values of free node (a, b), zero outside the grid
+template <int VEC>
+__device__ __forceinline__ void issue(float* dst, const float* __restrict__ X, int W, int H, int N, int a, int b,
+                                      int col) {
+    const bool ok = a >= 0 && a < W && b >= 0 && b < H;
+    const float* src = ok ? X + ((size_t)b * W + a) * N + col : X;
+    cp_async<VEC * 4>(dst, src, ok);
+}
+
+__device__ __forceinline__ int sl8(int q) { return q & (kNS - 1); }
+
+// ---------------------------------------------------------------------------
 // periodic residual (+ first GMG sweep), or its time restriction
 // ---------------------------------------------------------------------------
 // MODE 0: R = B - (A X^n - M X^{n-1}), Z0 = omega D^-1 R (if Z0 set)
 // MODE 1: Yc^m = sum over n in {2m, 2m+1} of the same residual (N/2 columns)
+// Rings: X rows y0-1 .. y1 (q = row - y0 + 1), with column col0 - 1 of each
+// node (the tile's previous column, for X^{n-1}); B row q - 1 travels with X
+// row q.
 template <int VEC, int MODE>
 __global__ void __launch_bounds__(kStBlock)
 k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __restrict__ X,
@@ -188,60 +238,58 @@ k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    float* ring = reinterpret_cast<float*>(smem4);
     const Lanes L = lanes<VEC>(TT);
-    float* prev = ring + 4 * (size_t)L.sx * TT;   // column col0 - 1 of each node, lc == 0 lanes
+    float* xr = reinterpret_cast<float*>(smem4);
+    float* br = xr + kNS * (size_t)L.sx * TT;
+    float* prev = br + kNS * (size_t)L.sx * TT;
     const int W = A.W, H = A.H;
     const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
     const int a0 = seg * (L.sx - 2) - 1;          // node slot 0 is a0; outputs at slots 1..sx-2
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
     const int pcol = (blockIdx.y * TT == 0 ? N : blockIdx.y * TT) - 1;   // previous column of the tile
-    auto fetch = [&](int b, float (&v)[VEC], float& pv) {
-        gload<VEC>(X, W, H, N, a, b, L.col, v);
-        pv = 0.f;
-        if (L.lc == 0 && a >= 0 && a < W && b >= 0 && b < H) pv = __ldg(X + ((size_t)b * W + a) * N + pcol);
-    };
-    auto stash = [&](int slot, const float (&v)[VEC], float pv) {
-        sts<VEC>(srow<VEC>(ring, slot, L.ln, L.sx, TT, L.lc), v);
-        if (L.lc == 0) prev[slot * L.sx + L.ln] = pv;
-    };
-    {
-        float v[VEC], pv;
-        for (int r = 0; r < 3; ++r) {
-            fetch(y0 - 1 + r, v, pv);
-            stash(r, v, pv);
+    const int nrows = y1 - y0 + 2;
+    auto issue_q = [&](int q) {
+        if (q < nrows) {
+            const int r = y0 - 1 + q;
+            issue<VEC>(srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc), X, W, H, N, a, r, L.col);
+            if (L.lc == 0) {
+                const bool ok = a >= 0 && a < W && r >= 0 && r < H;
+                cp_async<4>(prev + sl8(q) * L.sx + L.ln, ok ? X + ((size_t)r * W + a) * N + pcol : X, ok);
+            }
+            if (q >= 2) issue<VEC>(srow<VEC>(br, sl8(q), L.ln, L.sx, TT, L.lc), B, W, H, N, a, r - 1, L.col);
         }
-    }
-    __syncthreads();
+        cp_commit();
+    };
+    for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
     for (int b = y0; b < y1; ++b) {
-        const int k = b - y0;
-        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
-        const bool pre = b + 1 < y1;
-        float nv[VEC], npv;
-        if (pre) fetch(b + 2, nv, npv);
+        const int i = b - y0;
+        issue_q(i + kLA + 2);
+        cp_wait<kLA>();
+        __syncthreads();
         if (out_lane) {
+            const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
             const size_t node = (size_t)b * W + a;
             A7 c, m;
             load_coef(A.coef, node, A.cm, A.cl, c, m);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
-            lds<VEC>(srow<VEC>(ring, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(ring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(ring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(ring, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(ring, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(ring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(ring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(xr, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(xr, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(xr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(xr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
             // column col - 1 of the seven nodes: from the lane to the left, or the tile's previous column
             auto before = [&](int slot, int nd) -> float {
-                return L.lc > 0 ? ring[((size_t)slot * L.sx + nd) * TT + L.lc * VEC - 1] : prev[slot * L.sx + nd];
+                return L.lc > 0 ? xr[((size_t)slot * L.sx + nd) * TT + L.lc * VEC - 1] : prev[slot * L.sx + nd];
             };
             float p_c = before(sC, L.ln), p_e = before(sC, L.ln + 1), p_w = before(sC, L.ln - 1);
             float p_n = before(sN, L.ln), p_s = before(sS, L.ln), p_ne = before(sN, L.ln + 1),
                   p_sw = before(sS, L.ln - 1);
             float bv[VEC], r[VEC];
-            ldg_vec<float, VEC>(B + node * N + L.col, bv);
+            lds<VEC>(srow<VEC>(br, sN, L.ln, L.sx, TT, L.lc), bv);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
@@ -268,9 +316,8 @@ k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __
                 st_vec<float, HV>(R + node * (N / 2) + L.col / 2, o);
             }
         }
-        if (pre) stash((k + 3) & 3, nv, npv);
-        __syncthreads();
     }
+    cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -280,6 +327,8 @@ k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __
 //   coarse free node (A, B) sits on fine free node (2A+1, 2B+1) and takes the
 //   fine residual there plus half of it at the six pattern neighbours.
 // Xc = omega Dc^-1 Bc (the coarse level's first sweep from zero) if Xc is set.
+// Rings: Xf rows f0-1 .. f1+1 (q = row - f0 + 1); Bf row q - 1 travels with
+// Xf row q; the fine residual t in three rows.
 template <int VEC>
 __global__ void __launch_bounds__(kStBlock)
 k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int cy, int nseg,
@@ -288,9 +337,10 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    float* zring = reinterpret_cast<float*>(smem4);
     const Lanes L = lanes<VEC>(TT);
-    float* tring = zring + 4 * (size_t)L.sx * TT;
+    float* zr = reinterpret_cast<float*>(smem4);
+    float* br = zr + kNS * (size_t)L.sx * TT;
+    float* tr = br + kNS * (size_t)L.sx * TT;
     const int W = Af.W, H = Af.H, Wc = Ac.W, Hc = Ac.H;
     const int cxo = (L.sx - 3) / 2;                 // coarse nodes per block row segment
     const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
@@ -298,47 +348,44 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
     const int a = 2 * A0 - 1 + L.ln;                // fine node of slot ln
     const int B0 = strip * cy, B1 = min(Hc, B0 + cy);
     const int f0 = 2 * B0, f1 = 2 * B1;             // fine rows whose residual is needed: f0..f1
-    {
-        float v[VEC];
-        for (int r = 0; r < 3; ++r) {
-            gload<VEC>(Xf, W, H, N, a, f0 - 1 + r, L.col, v);
-            sts<VEC>(srow<VEC>(zring, r, L.ln, L.sx, TT, L.lc), v);
+    const int nrows = f1 - f0 + 3;                  // Xf rows f0-1 .. f1+1
+    auto issue_q = [&](int q) {
+        if (q < nrows) {
+            const int r = f0 - 1 + q;
+            issue<VEC>(srow<VEC>(zr, sl8(q), L.ln, L.sx, TT, L.lc), Xf, W, H, N, a, r, L.col);
+            if (q >= 2) issue<VEC>(srow<VEC>(br, sl8(q), L.ln, L.sx, TT, L.lc), Bf, W, H, N, a, r - 1, L.col);
         }
-    }
-    __syncthreads();
+        cp_commit();
+    };
+    for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool t_lane = L.ln >= 1 && L.ln <= 2 * cxo + 1 && a < W;
     for (int f = f0; f <= f1; ++f) {
         const int k = f - f0;
-        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
-        const bool pre = f < f1;
-        float nv[VEC];
-        if (pre) gload<VEC>(Xf, W, H, N, a, f + 2, L.col, nv);
-        if (t_lane) {
-            float t[VEC];
-            if (f < H) {
-                const size_t node = (size_t)f * W + a;
-                A7 c, m;
-                load_coef(Af.coef, node, Af.cm, Af.cl, c, m);
-                float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC];
-                lds<VEC>(srow<VEC>(zring, sC, L.ln, L.sx, TT, L.lc), xc);
-                lds<VEC>(srow<VEC>(zring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-                lds<VEC>(srow<VEC>(zring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-                lds<VEC>(srow<VEC>(zring, sN, L.ln, L.sx, TT, L.lc), xn);
-                lds<VEC>(srow<VEC>(zring, sS, L.ln, L.sx, TT, L.lc), xs);
-                lds<VEC>(srow<VEC>(zring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-                lds<VEC>(srow<VEC>(zring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
-                ldg_vec<float, VEC>(Bf + node * N + L.col, bv);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v)
-                    t[v] = bv[v] - (c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
-                                    c.ne * xne[v] + c.sw * xsw[v]);
-            } else {
-                zero_vec<VEC>(t);
-            }
-            sts<VEC>(srow<VEC>(tring, k % 3, L.ln, L.sx, TT, L.lc), t);
-        }
+        issue_q(k + kLA + 2);
+        cp_wait<kLA>();
         __syncthreads();
+        if (t_lane) {
+            const int sS = sl8(k), sC = sl8(k + 1), sN = sl8(k + 2);
+            const size_t node = (size_t)f * W + a;
+            A7 c, m;
+            load_coef(Af.coef, node, Af.cm, Af.cl, c, m);
+            float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], t[VEC];
+            lds<VEC>(srow<VEC>(zr, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(zr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(zr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(zr, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(zr, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(zr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(zr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            lds<VEC>(srow<VEC>(br, sN, L.ln, L.sx, TT, L.lc), bv);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+                t[v] = bv[v] - (c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
+                                c.ne * xne[v] + c.sw * xsw[v]);
+            sts<VEC>(srow<VEC>(tr, k % 3, L.ln, L.sx, TT, L.lc), t);
+        }
         if (k >= 2 && (k & 1) == 0) {
+            __syncthreads();
             // coarse row Bq: fine rows f-2 (S), f-1 (centre), f (N)
             const int Bq = B0 + (k - 2) / 2;
             const int Aq = A0 + L.ln;
@@ -346,13 +393,13 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
                 const int tS = (k - 2) % 3, tC = (k - 1) % 3, tN = k % 3;
                 const int sl = 2 * L.ln + 2;   // slot of the fine centre node 2 Aq + 1
                 float vc[VEC], ve[VEC], vw[VEC], vn[VEC], vs[VEC], vne[VEC], vsw[VEC], o[VEC];
-                lds<VEC>(srow<VEC>(tring, tC, sl, L.sx, TT, L.lc), vc);
-                lds<VEC>(srow<VEC>(tring, tC, sl + 1, L.sx, TT, L.lc), ve);
-                lds<VEC>(srow<VEC>(tring, tC, sl - 1, L.sx, TT, L.lc), vw);
-                lds<VEC>(srow<VEC>(tring, tN, sl, L.sx, TT, L.lc), vn);
-                lds<VEC>(srow<VEC>(tring, tS, sl, L.sx, TT, L.lc), vs);
-                lds<VEC>(srow<VEC>(tring, tN, sl + 1, L.sx, TT, L.lc), vne);
-                lds<VEC>(srow<VEC>(tring, tS, sl - 1, L.sx, TT, L.lc), vsw);
+                lds<VEC>(srow<VEC>(tr, tC, sl, L.sx, TT, L.lc), vc);
+                lds<VEC>(srow<VEC>(tr, tC, sl + 1, L.sx, TT, L.lc), ve);
+                lds<VEC>(srow<VEC>(tr, tC, sl - 1, L.sx, TT, L.lc), vw);
+                lds<VEC>(srow<VEC>(tr, tN, sl, L.sx, TT, L.lc), vn);
+                lds<VEC>(srow<VEC>(tr, tS, sl, L.sx, TT, L.lc), vs);
+                lds<VEC>(srow<VEC>(tr, tN, sl + 1, L.sx, TT, L.lc), vne);
+                lds<VEC>(srow<VEC>(tr, tS, sl - 1, L.sx, TT, L.lc), vsw);
 #pragma unroll
                 for (int v = 0; v < VEC; ++v)
                     o[v] = vc[v] + 0.5f * (ve[v] + vw[v] + vn[v] + vs[v] + vne[v] + vsw[v]);
@@ -366,9 +413,8 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
                 }
             }
         }
-        if (pre) sts<VEC>(srow<VEC>(zring, (k + 3) & 3, L.ln, L.sx, TT, L.lc), nv);
-        __syncthreads();
     }
+    cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -377,33 +423,11 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
 // x' = X + P Xc on the fine level, Out = x' + omega D^-1 (B - A x').
 // DOTS 1: (B.Out, B.B) per column -> rho, bb, rr (first PCG direction);
 // DOTS 2: B.Out -> beta, rho (later directions).  B is the PCG residual there.
-template <int VEC>
-__device__ __forceinline__ void xprime(const float* __restrict__ X, const float* __restrict__ Xc, int W, int H,
-                                       int Wc, int Hc, int N, int a, int f, int col, float (&v)[VEC]) {
-    gload<VEC>(X, W, H, N, a, f, col, v);
-    if (a < 0 || a >= W || f < 0 || f >= H) return;
-    float c1[VEC], c2[VEC];
-    const bool ao = a & 1, fo = f & 1;
-    if (ao && fo) {                       // on a coarse node
-        gload<VEC>(Xc, Wc, Hc, N, (a - 1) / 2, (f - 1) / 2, col, c1);
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) v[k] += c1[k];
-        return;
-    }
-    if (!ao && fo) {                      // horizontal edge midpoint
-        gload<VEC>(Xc, Wc, Hc, N, a / 2 - 1, (f - 1) / 2, col, c1);
-        gload<VEC>(Xc, Wc, Hc, N, a / 2, (f - 1) / 2, col, c2);
-    } else if (ao && !fo) {               // vertical edge midpoint
-        gload<VEC>(Xc, Wc, Hc, N, (a - 1) / 2, f / 2 - 1, col, c1);
-        gload<VEC>(Xc, Wc, Hc, N, (a - 1) / 2, f / 2, col, c2);
-    } else {                              // midpoint of the diagonal (i,j)-(i+1,j+1)
-        gload<VEC>(Xc, Wc, Hc, N, a / 2 - 1, f / 2 - 1, col, c1);
-        gload<VEC>(Xc, Wc, Hc, N, a / 2, f / 2, col, c2);
-    }
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) v[k] += 0.5f * (c1[k] + c2[k]);
-}
-
+// Rings: X rows y0-1 .. y1 (q = row - y0 + 1), turned into x' in place once
+// they have landed; B row q - 1 travels with X row q; coarse rows by their
+// own index c (slot c mod kNS), each issued with the first fine row that
+// needs it.  Fine free row f uses coarse rows (f-1)/2 (f odd) or f/2 - 1 and
+// f/2 (f even); fine free column a likewise.
 template <int VEC, int DOTS>
 __global__ void __launch_bounds__(kStBlock)
 k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int nseg,
@@ -412,45 +436,90 @@ k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    float* ring = reinterpret_cast<float*>(smem4);
     const Lanes L = lanes<VEC>(TT);
+    const int cw = L.sx / 2 + 2;                    // coarse nodes per ring row
+    float* xr = reinterpret_cast<float*>(smem4);
+    float* br = xr + kNS * (size_t)L.sx * TT;
+    float* cr8 = br + kNS * (size_t)L.sx * TT;      // coarse ring: kNS x cw x TT
     const int W = A.W, H = A.H;
     const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
     const int a0 = seg * (L.sx - 2) - 1;
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
-    {
-        float v[VEC];
-        for (int r = 0; r < 3; ++r) {
-            xprime<VEC>(X, Xc, W, H, Wc, Hc, N, a, y0 - 1 + r, L.col, v);
-            sts<VEC>(srow<VEC>(ring, r, L.ln, L.sx, TT, L.lc), v);
+    const int cA0 = (a0 >> 1) - 1;                  // first coarse column of the ring rows (a0 >= -1)
+    const int nrows = y1 - y0 + 2;
+    // the newest coarse row fine row r needs: floor(r / 2); the oldest (first row only)
+    auto cnew = [](int r) { return r >= 0 ? r / 2 : -1; };
+    int cnext = ((y0 - 1) >= 0 ? (y0 - 1) / 2 : 0) - 1;   // next coarse row to issue
+    auto issue_q = [&](int q) {
+        if (q < nrows) {
+            const int r = y0 - 1 + q;
+            issue<VEC>(srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc), X, W, H, N, a, r, L.col);
+            if (q >= 2) issue<VEC>(srow<VEC>(br, sl8(q), L.ln, L.sx, TT, L.lc), B, W, H, N, a, r - 1, L.col);
+            const int last = cnew(r);
+            for (; cnext <= last; ++cnext)
+                if (L.ln < cw)
+                    issue<VEC>(cr8 + ((size_t)sl8(cnext) * cw + L.ln) * TT + L.lc * VEC, Xc, Wc, Hc, N, cA0 + L.ln,
+                               cnext, L.col);
         }
-    }
+        cp_commit();
+    };
+    // x' = x + P xc in place for ring row q (fine row r)
+    auto to_xprime = [&](int q) {
+        const int r = y0 - 1 + q;
+        if (a < 0 || a >= W || r < 0 || r >= H) return;
+        float* xp = srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc);
+        float v[VEC], c1[VEC], c2[VEC];
+        lds<VEC>(xp, v);
+        auto cval = [&](int Acol, int Brow, float (&o)[VEC]) {
+            if (Acol < 0 || Acol >= Wc || Brow < 0 || Brow >= Hc) { zero_vec<VEC>(o); return; }
+            lds<VEC>(cr8 + ((size_t)sl8(Brow) * cw + (Acol - cA0)) * TT + L.lc * VEC, o);
+        };
+        const bool ao = a & 1, fo = r & 1;
+        if (ao && fo) {
+            cval((a - 1) / 2, (r - 1) / 2, c1);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[k] += c1[k];
+        } else {
+            if (!ao && fo) { cval(a / 2 - 1, (r - 1) / 2, c1); cval(a / 2, (r - 1) / 2, c2); }
+            else if (ao && !fo) { cval((a - 1) / 2, r / 2 - 1, c1); cval((a - 1) / 2, r / 2, c2); }
+            else { cval(a / 2 - 1, r / 2 - 1, c1); cval(a / 2, r / 2, c2); }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v[k] += 0.5f * (c1[k] + c2[k]);
+        }
+        sts<VEC>(xp, v);
+    };
+    for (int q = 0; q < kLA + 2; ++q) issue_q(q);
+    cp_wait<kLA>();          // rows q = 0, 1 and their coarse rows have landed
     __syncthreads();
+    to_xprime(0);
+    to_xprime(1);
     constexpr int NQ = DOTS == 1 ? 2 : 1;
     float acc[NQ][VEC];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) zero_vec<VEC>(acc[q]);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
     for (int b = y0; b < y1; ++b) {
-        const int k = b - y0;
-        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
-        const bool pre = b + 1 < y1;
-        float nv[VEC];
-        if (pre) xprime<VEC>(X, Xc, W, H, Wc, Hc, N, a, b + 2, L.col, nv);
+        const int i = b - y0;
+        issue_q(i + kLA + 2);
+        cp_wait<kLA>();
+        __syncthreads();
+        to_xprime(i + 2);
+        __syncthreads();
         if (out_lane) {
+            const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
             const size_t node = (size_t)b * W + a;
             A7 c, m;
             load_coef(A.coef, node, A.cm, A.cl, c, m);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], o[VEC];
-            lds<VEC>(srow<VEC>(ring, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(ring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(ring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(ring, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(ring, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(ring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(ring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
-            ldg_vec<float, VEC>(B + node * N + L.col, bv);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(xr, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(xr, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(xr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(xr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            lds<VEC>(srow<VEC>(br, sN, L.ln, L.sx, TT, L.lc), bv);
             const float w = omega / c.c;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
@@ -467,11 +536,11 @@ k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int
                 }
             }
         }
-        if (pre) sts<VEC>(srow<VEC>(ring, (k + 3) & 3, L.ln, L.sx, TT, L.lc), nv);
-        __syncthreads();
     }
-    if constexpr (DOTS == 1) tile_reduce_finish<VEC, 2, FIN_RZ_FIRST>(acc, L, TT, N, ring, cr);
-    if constexpr (DOTS == 2) tile_reduce_finish<VEC, 1, FIN_RZ_NEXT>(acc, L, TT, N, ring, cr);
+    cp_wait<0>();
+    __syncthreads();
+    if constexpr (DOTS == 1) tile_reduce_finish<VEC, 2, FIN_RZ_FIRST>(acc, L, TT, N, xr, cr);
+    if constexpr (DOTS == 2) tile_reduce_finish<VEC, 1, FIN_RZ_NEXT>(acc, L, TT, N, xr, cr);
 }
 
 // ---------------------------------------------------------------------------
@@ -484,42 +553,40 @@ k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float*
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    float* ring = reinterpret_cast<float*>(smem4);
     const Lanes L = lanes<VEC>(TT);
+    float* xr = reinterpret_cast<float*>(smem4);
     const int W = A.W, H = A.H;
     const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
     const int a0 = seg * (L.sx - 2) - 1;
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
-    {
-        float v[VEC];
-        for (int r = 0; r < 3; ++r) {
-            gload<VEC>(P, W, H, N, a, y0 - 1 + r, L.col, v);
-            sts<VEC>(srow<VEC>(ring, r, L.ln, L.sx, TT, L.lc), v);
-        }
-    }
-    __syncthreads();
+    const int nrows = y1 - y0 + 2;
+    auto issue_q = [&](int q) {
+        if (q < nrows) issue<VEC>(srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc), P, W, H, N, a, y0 - 1 + q, L.col);
+        cp_commit();
+    };
+    for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     float acc[1][VEC];
     zero_vec<VEC>(acc[0]);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
     for (int b = y0; b < y1; ++b) {
-        const int k = b - y0;
-        const int sS = k & 3, sC = (k + 1) & 3, sN = (k + 2) & 3;
-        const bool pre = b + 1 < y1;
-        float nv[VEC];
-        if (pre) gload<VEC>(P, W, H, N, a, b + 2, L.col, nv);
+        const int i = b - y0;
+        issue_q(i + kLA + 2);
+        cp_wait<kLA>();
+        __syncthreads();
         if (out_lane) {
+            const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
             const size_t node = (size_t)b * W + a;
             A7 c, m;
             load_coef(A.coef, node, A.cm, A.cl, c, m);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
-            lds<VEC>(srow<VEC>(ring, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(ring, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(ring, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(ring, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(ring, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(ring, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(ring, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln, L.sx, TT, L.lc), xc);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
+            lds<VEC>(srow<VEC>(xr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
+            lds<VEC>(srow<VEC>(xr, sN, L.ln, L.sx, TT, L.lc), xn);
+            lds<VEC>(srow<VEC>(xr, sS, L.ln, L.sx, TT, L.lc), xs);
+            lds<VEC>(srow<VEC>(xr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
+            lds<VEC>(srow<VEC>(xr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
                 const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
@@ -527,10 +594,10 @@ k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float*
                 acc[0][v] += xc[v] * ax;
             }
         }
-        if (pre) sts<VEC>(srow<VEC>(ring, (k + 3) & 3, L.ln, L.sx, TT, L.lc), nv);
-        __syncthreads();
     }
-    tile_reduce_finish<VEC, 1, FIN_ALPHA>(acc, L, TT, N, ring, cr);
+    cp_wait<0>();
+    __syncthreads();
+    tile_reduce_finish<VEC, 1, FIN_ALPHA>(acc, L, TT, N, xr, cr);
 }
 
 // ---------------------------------------------------------------------------
@@ -598,7 +665,7 @@ int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const flo
     const int nch = N / sh.TT;
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
-    const size_t smem = (4 * (size_t)sh.sx * sh.TT + 4 * (size_t)sh.sx) * sizeof(float);
+    const size_t smem = (2 * kNS * (size_t)sh.sx * sh.TT + kNS * (size_t)sh.sx) * sizeof(float);
     const dim3 grid(nseg * nstrip, nch);
     if (time_restrict) {
         if (sh.vec == 4) st_launch(k_st_presid<4, 1>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk);
@@ -620,7 +687,7 @@ int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>&
     const int nch = N / sh.TT;
     const int cy = std::max(1, strip_rows(Ac.H, nseg, nch) / 2);
     const int nstrip = (Ac.H + cy - 1) / cy;
-    const size_t smem = 7 * (size_t)sh.sx * sh.TT * sizeof(float);
+    const size_t smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
     const dim3 grid(nseg * nstrip, nch);
     PTP_ST_VEC(sh.vec, st_launch(k_st_resid_restrict<VEC>, grid, sh.block, smem, s, Af, Ac, N, sh.TT, cy, nseg, Xf,
                                  Bf, Bc, Xc, omega, sk));
@@ -636,7 +703,7 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
     const int nch = N / sh.TT;
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
-    const size_t smem = 4 * (size_t)sh.sx * sh.TT * sizeof(float);
+    const size_t smem = (2 * kNS * (size_t)sh.sx + kNS * (size_t)(sh.sx / 2 + 2)) * sh.TT * sizeof(float);
     const dim3 grid(nseg * nstrip, nch);
     if (dots) {
         const size_t need = (size_t)grid.x * grid.y * 2 * sh.TT;
@@ -662,7 +729,7 @@ int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed
     const int nch = N / sh.TT;
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
-    const size_t smem = 4 * (size_t)sh.sx * sh.TT * sizeof(float);
+    const size_t smem = kNS * (size_t)sh.sx * sh.TT * sizeof(float);
     const dim3 grid(nseg * nstrip, nch);
     const size_t need = (size_t)grid.x * grid.y * sh.TT;
     PTP_REQUIRE(cr.partials != nullptr && need <= cr.capacity, "stencil reduction: partial buffer too small");

@@ -649,7 +649,7 @@ ResidualArgs residual_args(Ctx& c, const double* U, double* R) {
     a.partials_cap = c.part_d.n;
     a.counter = c.counter.p;
     a.status = c.status.p;
-    if (c.k1_struct) {
+    if (c.k1_struct && c.opts.k1_fused) {
         a.st_W = c.gnx - 2;
         a.st_H = c.gny - 2;
         a.st_cell = c.k1_cell.p;
@@ -896,9 +896,9 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
     };
-    const int ints[12] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+    const int ints[13] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
                           o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it,
-                          o.stencil};
+                          o.stencil, o.k1_fused};
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));

@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
         ("use_graph", ctypes.c_int), ("check_every", ctypes.c_int), ("coarse_cycles", ctypes.c_int),
         ("coarse_solver", ctypes.c_int), ("dft_max_it", ctypes.c_int), ("init_tol", ctypes.c_double),
         ("init_static", ctypes.c_int), ("newton_eta", ctypes.c_double), ("krylov_dim", ctypes.c_int),
-        ("stencil", ctypes.c_int),
+        ("stencil", ctypes.c_int), ("k1_fused", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -58,11 +58,13 @@ PROBLEMS = {
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
-@pytest.mark.parametrize("structured", [True, False])
-def test_source_and_residual(name, structured):
+@pytest.mark.parametrize("structured,k1_fused", [(True, 0), (True, 1), (False, 0)])
+def test_source_and_residual(name, structured, k1_fused):
+    """k1_fused = 1 takes the one-pass structured kernel where N is a multiple
+    of 16 (the others fall back to the element and node passes)."""
     prob = PROBLEMS[name]()
     d = P.assemble(prob)
-    c, _ = make_ctx(prob, structured, precision=ptp.PTP_FP64)
+    c, _ = make_ctx(prob, structured, precision=ptp.PTP_FP64, k1_fused=k1_fused)
     F = c.source()
     assert rel(F, P.source(prob, d)) < 1e-14
     rng = np.random.default_rng(1)

@@ -104,3 +104,15 @@ def test_stencil_path_launches_fewer_kernels():
         st, rc = c.solve_dev(U, o)
         counts.append(st.kernel_launches / max(1, st.outer_iterations + 1))
     assert counts[1] < 0.8 * counts[0], counts
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(ptp.PTP_FP64, 1e-13, 1e-10), (ptp.PTP_MIXED, 1e-11, 1e-8)])
+def test_fixed_point_with_the_fused_residual_reaches_the_oracle(precision, tol, bar):
+    """The one-pass structured outer residual (k1_fused) inside the fixed
+    point: the 33x33, N = 32 solve reaches the stored oracle solution."""
+    prob = W.unit_square_problem(33, 32)
+    Uo = np.load(os.path.join(GOLDEN, "square33_N32_oracle.npz"))["U"]
+    c, o = _ctx(prob, precision=precision, tol=tol, max_outer=20000, k1_fused=1)
+    U, st, rc = c.solve(o)
+    assert rc == ptp.PTP_OK
+    assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) < bar
