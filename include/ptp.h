@@ -129,6 +129,11 @@ typedef struct ptp_opts {
     int    k1_fused;     /* structured grids, saturating law: 1 = the outer
                             residual in one fused pass (shared-memory element
                             fluxes), 0 = element pass + node pass (default)  */
+    int    coarse_direct;/* 1 (default): on a uniform structured grid with
+                            K_hat = nu_max * stiffness and (nx - 1), (ny - 1)
+                            powers of two, the tau_c L solve of the coarsest
+                            time level is direct (sine transforms, exact up
+                            to rounding) instead of coarse_tol PCG; 0 = PCG */
 } ptp_opts;
 
 /* Statistics of the last solve. */

@@ -133,6 +133,7 @@ void ptp_default_opts(ptp_opts* o) {
     o->krylov_dim = 20;
     o->stencil = 1;
     o->k1_fused = 0;
+    o->coarse_direct = 1;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }

@@ -217,6 +217,11 @@ struct Ctx {
     std::vector<OpPair> ops;
     std::vector<TimeLevel> tl;
     int coarse_ops[2] = {-1, -1};  // ops of the coarsest time level (N_c = 1 or 2)
+    // exact tau_c L solve by sine transforms (uniform structured grid, K_hat = nu_max A)
+    bool dst_ok = false;
+    int dst_logx = 0, dst_logy = 0;
+    DBuf<double2> dst_wx, dst_wy;
+    DBuf<double> dst_scale, dst_tmp, dst_tmp2;
     bool coarse_ok = false;        // the coarsest time level has 1 or 2 steps
     int active_levels = 0;         // levels of the V-cycle (opts.time_levels)
     // exact periodic solve of one time level by a DFT in time (opts.coarse_solver)

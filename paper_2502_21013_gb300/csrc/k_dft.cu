@@ -19,6 +19,7 @@
 // Transforms: radix-2 FFT in shared memory per node (N a power of two, one
 // block holds 512 / N nodes), otherwise a direct sum over the N steps.
 // N <= 1022, so the K <= 512 complex columns of a row fit one block.
+#include "dev_fft.cuh"
 #include "dev_util.cuh"
 
 namespace ptp {
@@ -26,37 +27,6 @@ namespace ptp {
 namespace {
 
 constexpr int kFftThreads = 256;
-
-__device__ __forceinline__ int bit_reverse(int t, int logN) {
-    return logN == 0 ? 0 : (int)(__brev((unsigned)t) >> (32 - logN));
-}
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// In-place iterative radix-2 FFT (decimation in time) of nb rows of length N
-// held in shared memory in bit-reversed order; W[j] = e^{-2 pi i j / N}, the
-// inverse uses conj(W).
-template <bool INV>
-__device__ void fft_stages(double2* sh, int nb, int N, const double2* __restrict__ W) {
-    const int half = N / 2;
-    for (int len = 2; len <= N; len <<= 1) {
-        const int h = len >> 1, stride = N / len;
-        for (int b = threadIdx.x; b < nb * half; b += blockDim.x) {
-            const int j = b / half, bb = b - j * half;
-            const int grp = bb / h, pos = bb - grp * h;
-            const int i0 = j * N + grp * len + pos, i1 = i0 + h;
-            double2 w = __ldg(W + pos * stride);
-            if (INV) w.y = -w.y;
-            const double2 u = sh[i0];
-            const double2 t = cmul(w, sh[i1]);
-            sh[i0] = make_double2(u.x + t.x, u.y + t.y);
-            sh[i1] = make_double2(u.x - t.x, u.y - t.y);
-        }
-        __syncthreads();
-    }
-}
 
 // forward: H[i][k] = sum_t x[i][t] e^{-2 pi i k t / N}, k < K (N a power of two)
 template <typename T>

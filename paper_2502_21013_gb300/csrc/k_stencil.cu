@@ -30,6 +30,8 @@
 // in a fixed order by the last block of each time tile (atomic ticket, no
 // waiting).
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "dev_util.cuh"
 
@@ -647,13 +649,20 @@ int strip_rows(int H, int nseg, int nch) {
         default: { constexpr int VEC = 1; __VA_ARGS__; } break;  \
     }
 
+// Launch with `smem` bytes of dynamic shared memory; the kernel's limit is
+// raised whenever a launch needs more than it was last granted (the ring
+// sizes depend on the columns of the level).
 template <typename... KArgs, typename... Args>
 static void st_launch(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args&&... args) {
-    static thread_local std::vector<const void*> raised;
-    const void* k = (const void*)kernel;
-    if (smem > 48 * 1024 && std::find(raised.begin(), raised.end(), k) == raised.end()) {
-        PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        raised.push_back(k);
+    static std::mutex mu;
+    static std::map<const void*, size_t> granted;
+    if (smem > 48 * 1024) {
+        std::lock_guard<std::mutex> lock(mu);
+        size_t& g = granted[(const void*)kernel];
+        if (smem > g) {
+            PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            g = smem;
+        }
     }
     launch_k_smem(kernel, grid, dim3(block), smem, s, std::forward<Args>(args)...);
 }

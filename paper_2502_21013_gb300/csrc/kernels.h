@@ -39,7 +39,7 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
     attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
 // the same with dynamic shared memory
@@ -56,7 +56,7 @@ inline void launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +255,22 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
                            cudaStream_t s);
 // alpha = rho / (P . A P) per column
 int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Exact solve of tau_c L x = b on a uniform structured grid by discrete sine
+// transforms along rows and columns (k_poisson.cu), double arithmetic.
+// ---------------------------------------------------------------------------
+struct DstSolve {
+    int W = 0, H = 0;              // free nodes per row, rows; W + 1 and H + 1 powers of two
+    int logx = 0, logy = 0;        // log2 of the FFT lengths 2 (W + 1), 2 (H + 1)
+    const double2* wx = nullptr;   // e^{-2 pi i j / (2 (W + 1))}, j < W + 1
+    const double2* wy = nullptr;
+    const double* scale = nullptr; // [k][l]: (2 / m_x)(2 / m_y) / (tau_c nu_max lambda_kl)
+    double* tmp = nullptr;         // W x H work arrays
+    double* tmp2 = nullptr;
+};
+template <typename T>   // x = (tau_c L)^{-1} b, both [W x H] node order (one column)
+int launch_dst_solve(const DstSolve& d, const T* b, T* x, Skip sk, cudaStream_t s);
 
 // dense coarse-level apply Y = Ainv B  (n x n, row-major)
 template <typename T>

@@ -303,6 +303,7 @@ void make_structured_mesh(Ctx& c, int nx, int ny, double x0, double y0, double x
 
 static void build_k1_structured(Ctx& c, const HostCSR& M, const std::vector<double>& mval, const HostCSR& Ll,
                                 const std::vector<int>& iron_of, cudaStream_t s);
+static void build_dst(Ctx& c, cudaStream_t s);
 
 void build_problem(Ctx& c) {
     PTP_REQUIRE(c.n_nodes > 0 && c.n_tri > 0, "no mesh");
@@ -529,6 +530,45 @@ static void build_k1_structured(Ctx& c, const HostCSR& M, const std::vector<doub
     c.k1_struct = true;
 }
 
+// The exact tau_c L solve of the coarsest time level by sine transforms
+// (k_poisson.cu): on a uniform structured grid with K_hat = nu_max A, and
+// (nx - 1), (ny - 1) powers of two, the FFT twiddles, the inverse
+// eigenvalues (with the transforms' normalisation) and two work arrays.
+static void build_dst(Ctx& c, cudaStream_t s) {
+    c.dst_ok = false;
+    c.dst_wx.release(); c.dst_wy.release(); c.dst_scale.release(); c.dst_tmp.release(); c.dst_tmp2.release();
+    if (!c.opts.coarse_direct || !c.structured || !c.khat.empty() || !c.coarse_ok || c.coarse_ops[0] < 0) return;
+    const int W = c.gnx - 2, H = c.gny - 2;
+    if (W < 1 || H < 1 || (int64_t)W * H != c.n) return;
+    const int mx = W + 1, my = H + 1;
+    if ((mx & (mx - 1)) || (my & (my - 1)) || 2 * mx > 65536 || 2 * my > 65536) return;
+    const double hx = (c.gx1 - c.gx0) / (c.gnx - 1), hy = (c.gy1 - c.gy0) / (c.gny - 1);
+    const double coef = c.ops[c.coarse_ops[0]].cl * c.nu_max;   // tau_c nu_max
+    auto twiddles = [](int L) {
+        std::vector<double2> w(L / 2);
+        for (int j = 0; j < L / 2; ++j) w[j] = make_double2(std::cos(2.0 * M_PI * j / L), -std::sin(2.0 * M_PI * j / L));
+        return w;
+    };
+    std::vector<double> sc((size_t)W * H);
+    for (int k = 1; k <= W; ++k)
+        for (int l = 1; l <= H; ++l) {
+            const double lam = hy / hx * (2.0 - 2.0 * std::cos(M_PI * k / mx)) +
+                               hx / hy * (2.0 - 2.0 * std::cos(M_PI * l / my));
+            sc[(size_t)(k - 1) * H + (l - 1)] = (2.0 / mx) * (2.0 / my) / (coef * lam);
+        }
+    int lx = 0, ly = 0;
+    while ((1 << lx) < 2 * mx) ++lx;
+    while ((1 << ly) < 2 * my) ++ly;
+    c.dst_wx.upload(twiddles(2 * mx), s);
+    c.dst_wy.upload(twiddles(2 * my), s);
+    c.dst_scale.upload(sc, s);
+    c.dst_tmp.alloc((size_t)W * H);
+    c.dst_tmp2.alloc((size_t)W * H);
+    c.dst_logx = lx;
+    c.dst_logy = ly;
+    c.dst_ok = true;
+}
+
 // The operators M and L of a structured level as per-node 7-point stencils:
 // for free node (a, b) (index b W + a) the coefficients of the neighbours
 // C (a, b), E (a+1, b), W (a-1, b), N (a, b+1), S (a, b-1), NE (a+1, b+1),
@@ -669,6 +709,7 @@ void build_hierarchy(Ctx& c) {
     c.coarse_ops[0] = add_op(0.0, tc);            // sum mode:        tau_c L
     c.coarse_ops[1] = Nc == 2 ? add_op(2.0, tc) : -1;  // difference:  2M + tau_c L
     c.coarse_ok = Nc == 1 || Nc == 2;
+    build_dst(c, s);
     const int full = (int)c.tl.size();
     c.active_levels = o.time_levels > 0 ? std::min(o.time_levels, full) : full;
     // DFT in time on the last level used: preconditioner tau_l L, twiddles and mode shifts

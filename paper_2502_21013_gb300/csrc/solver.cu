@@ -407,7 +407,22 @@ void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
     for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
 }
 
-// exact (to coarse_tol) solve on the coarsest time level, in double
+DstSolve dst_of(Ctx& c) {
+    DstSolve d;
+    d.W = c.gnx - 2;
+    d.H = c.gny - 2;
+    d.logx = c.dst_logx;
+    d.logy = c.dst_logy;
+    d.wx = c.dst_wx.p;
+    d.wy = c.dst_wy.p;
+    d.scale = c.dst_scale.p;
+    d.tmp = c.dst_tmp.p;
+    d.tmp2 = c.dst_tmp2.p;
+    return d;
+}
+
+// exact solve on the coarsest time level, in double: direct by sine
+// transforms where the grid allows, else PCG to coarse_tol
 template <typename T>
 void coarse_solve(Ctx& c, Skip sk) {
     const int L = (int)c.tl.size();
@@ -427,6 +442,10 @@ void coarse_solve(Ctx& c, Skip sk) {
         pcg.init();
         for (int k = 0; k < maxit; ++k) pcg.iterate(k == maxit - 1);
     };
+    if (Nc == 1 && c.dst_ok) {   // direct: tau_c L x = b by sine transforms, in double
+        c.launches += launch_dst_solve<T>(dst_of(c), bc, xc, sk, st);
+        return;
+    }
     if (Nc == 1) {
         if constexpr (sizeof(T) == 8)
             PTP_CUDA(cudaMemcpyAsync(cb, bc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -443,7 +462,8 @@ void coarse_solve(Ctx& c, Skip sk) {
         double* xs = cx;
         double* xd = cx + n;
         c.launches += launch_split2<T>(n, bc, bs, bd, sk, st);
-        run(c.coarse_ops[0], bs, xs);
+        if (c.dst_ok) c.launches += launch_dst_solve<double>(dst_of(c), bs, xs, sk, st);
+        else run(c.coarse_ops[0], bs, xs);
         run(c.coarse_ops[1], bd, xd);
         c.launches += launch_combine2<T>(n, xs, xd, xc, sk, st);
     }
@@ -896,9 +916,9 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
     };
-    const int ints[13] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+    const int ints[14] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
                           o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it,
-                          o.stencil, o.k1_fused};
+                          o.stencil, o.k1_fused, o.coarse_direct};
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));
