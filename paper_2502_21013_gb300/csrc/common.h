@@ -120,6 +120,8 @@ struct OpPair {
     // per spatial level, double: padded-ELL values cm M + cl L and its diagonal,
     // formed once so the double row kernels spend no FMA on the combination
     std::vector<DBuf<double>> comb, dcomb;
+    // per spatial level, float stencil of cm M + cl L (structured hierarchies)
+    std::vector<DBuf<float4>> st_a;
 };
 
 struct TimeLevel {

@@ -45,23 +45,30 @@ struct A7 {
     float c, e, w, n, s, ne, sw;
 };
 
-// coefficients of node `node`: a = cm M + cl L and m = M
-__device__ __forceinline__ void load_coef(const float4* __restrict__ coef, size_t node, float cm, float cl,
-                                          A7& a, A7& m) {
-    const float4 m0 = __ldg(coef + 4 * node), m1 = __ldg(coef + 4 * node + 1);
-    const float4 l0 = __ldg(coef + 4 * node + 2), l1 = __ldg(coef + 4 * node + 3);
-    m = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z};
-    a.c = cm * m0.x + cl * l0.x;
-    a.e = cm * m0.y + cl * l0.y;
-    a.w = cm * m0.z + cl * l0.z;
-    a.n = cm * m0.w + cl * l0.w;
-    a.s = cm * m1.x + cl * l1.x;
-    a.ne = cm * m1.y + cl * l1.y;
-    a.sw = cm * m1.z + cl * l1.z;
+// cm M + cl L of node `node` from the precombined array (2 float4 per node:
+// {C, E, W, N}, {S, NE, SW, 1 / C}); idiag receives 1 / C
+__device__ __forceinline__ void load_a(const float4* __restrict__ ac, size_t node, A7& a, float& idiag) {
+    const float4 a0 = __ldg(ac + 2 * node), a1 = __ldg(ac + 2 * node + 1);
+    a = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z};
+    idiag = a1.w;
 }
 
-__device__ __forceinline__ float diag_coef(const float4* __restrict__ coef, size_t node, float cm, float cl) {
-    return cm * __ldg(&coef[4 * node].x) + cl * __ldg(&coef[4 * node + 2].x);
+// M alone (the first two float4 of the level's 4 per node)
+__device__ __forceinline__ void load_m(const float4* __restrict__ coef, size_t node, A7& m) {
+    const float4 m0 = __ldg(coef + 4 * node), m1 = __ldg(coef + 4 * node + 1);
+    m = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z};
+}
+
+__global__ void k_st_combine(int n, const float4* __restrict__ coef, float cm, float cl, float4* __restrict__ out) {
+    pdl_enter();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 m0 = coef[4 * (size_t)i], m1 = coef[4 * (size_t)i + 1];
+        const float4 l0 = coef[4 * (size_t)i + 2], l1 = coef[4 * (size_t)i + 3];
+        const float c = cm * m0.x + cl * l0.x;
+        out[2 * (size_t)i] = make_float4(c, cm * m0.y + cl * l0.y, cm * m0.z + cl * l0.z, cm * m0.w + cl * l0.w);
+        out[2 * (size_t)i + 1] = make_float4(cm * m1.x + cl * l1.x, cm * m1.y + cl * l1.y, cm * m1.z + cl * l1.z,
+                                             c != 0.f ? 1.0f / c : 0.f);
+    }
 }
 
 // thread geometry of a block: TPN = TT / VEC threads per node (a time tile),
@@ -115,16 +122,6 @@ __device__ __forceinline__ void sts(float* p, const float (&v)[VEC]) {
     } else {
         p[0] = v[0];
     }
-}
-
-// global value block of free node (a, b) at this thread's columns, zero outside the grid
-template <int VEC>
-__device__ __forceinline__ void gload(const float* __restrict__ X, int W, int H, int N, int a, int b, int col,
-                                      float (&v)[VEC]) {
-    if (a >= 0 && a < W && b >= 0 && b < H)
-        ldg_vec<float, VEC>(X + ((size_t)b * W + a) * N + col, v);
-    else
-        zero_vec<VEC>(v);
 }
 
 // Per-column sums of NQ quantities over the block, then over the blocks of
@@ -214,16 +211,55 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// async copy of this thread's VEC values of free node (a, b), zero outside the grid
-template <int VEC>
-__device__ __forceinline__ void issue(float* dst, const float* __restrict__ X, int W, int H, int N, int a, int b,
-                                      int col) {
-    const bool ok = a >= 0 && a < W && b >= 0 && b < H;
-    const float* src = ok ? X + ((size_t)b * W + a) * N + col : X;
-    cp_async<VEC * 4>(dst, src, ok);
+__device__ __forceinline__ int sl8(int q) { return q & (kNS - 1); }
+
+// Per-thread cursor over the rows of one [W x H][N] array at this thread's
+// node column a and columns col..col+VEC: element offset of row r, and
+// whether (a, r) lies on the grid.
+struct Cursor {
+    long base;   // offset of row 0 (may be off the grid; only used when valid)
+    long rs;     // elements per grid row
+    int H;
+    bool a_ok;
+    __device__ __forceinline__ long off(int r) const { return base + (long)r * rs; }
+    __device__ __forceinline__ bool ok(int r) const { return a_ok && r >= 0 && r < H; }
+};
+
+__device__ __forceinline__ Cursor cursor(int W, int H, int N, int a, int col) {
+    Cursor c;
+    c.base = (long)a * N + col;
+    c.rs = (long)W * N;
+    c.H = H;
+    c.a_ok = a >= 0 && a < W;
+    return c;
 }
 
-__device__ __forceinline__ int sl8(int q) { return q & (kNS - 1); }
+template <int VEC>
+__device__ __forceinline__ void issue_row(float* dst, const float* __restrict__ X, const Cursor& c, int r) {
+    const bool ok = c.ok(r);
+    cp_async<VEC * 4>(dst, ok ? X + c.off(r) : X, ok);
+}
+
+// the seven stencil neighbours of node slot ln at the rows in slots sS, sC, sN
+template <int VEC>
+__device__ __forceinline__ void nbrs(float* ring, int sS, int sC, int sN, int ln, int sx, int TT, int lc,
+                                     float (&xc)[VEC], float (&xe)[VEC], float (&xw)[VEC], float (&xn)[VEC],
+                                     float (&xs)[VEC], float (&xne)[VEC], float (&xsw)[VEC]) {
+    lds<VEC>(srow<VEC>(ring, sC, ln, sx, TT, lc), xc);
+    lds<VEC>(srow<VEC>(ring, sC, ln + 1, sx, TT, lc), xe);
+    lds<VEC>(srow<VEC>(ring, sC, ln - 1, sx, TT, lc), xw);
+    lds<VEC>(srow<VEC>(ring, sN, ln, sx, TT, lc), xn);
+    lds<VEC>(srow<VEC>(ring, sS, ln, sx, TT, lc), xs);
+    lds<VEC>(srow<VEC>(ring, sN, ln + 1, sx, TT, lc), xne);
+    lds<VEC>(srow<VEC>(ring, sS, ln - 1, sx, TT, lc), xsw);
+}
+
+template <int VEC>
+__device__ __forceinline__ float apply7(const A7& c, const float (&xc)[VEC], const float (&xe)[VEC],
+                                        const float (&xw)[VEC], const float (&xn)[VEC], const float (&xs)[VEC],
+                                        const float (&xne)[VEC], const float (&xsw)[VEC], int v) {
+    return c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] + c.ne * xne[v] + c.sw * xsw[v];
+}
 
 // ---------------------------------------------------------------------------
 // periodic residual (+ first GMG sweep), or its time restriction
@@ -250,21 +286,27 @@ k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
     const int pcol = (blockIdx.y * TT == 0 ? N : blockIdx.y * TT) - 1;   // previous column of the tile
+    const Cursor cx = cursor(W, H, N, a, L.col);
+    const long pdelta = (long)pcol - L.col;       // from this thread's column to the tile's previous one
     const int nrows = y1 - y0 + 2;
+    float* xslot0 = srow<VEC>(xr, 0, L.ln, L.sx, TT, L.lc);
+    float* bslot0 = srow<VEC>(br, 0, L.ln, L.sx, TT, L.lc);
+    const size_t sstride = (size_t)L.sx * TT;     // floats per ring slot
     auto issue_q = [&](int q) {
         if (q < nrows) {
             const int r = y0 - 1 + q;
-            issue<VEC>(srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc), X, W, H, N, a, r, L.col);
+            issue_row<VEC>(xslot0 + sl8(q) * sstride, X, cx, r);
             if (L.lc == 0) {
-                const bool ok = a >= 0 && a < W && r >= 0 && r < H;
-                cp_async<4>(prev + sl8(q) * L.sx + L.ln, ok ? X + ((size_t)r * W + a) * N + pcol : X, ok);
+                const bool ok = cx.ok(r);
+                cp_async<4>(prev + sl8(q) * L.sx + L.ln, ok ? X + cx.off(r) + pdelta : X, ok);
             }
-            if (q >= 2) issue<VEC>(srow<VEC>(br, sl8(q), L.ln, L.sx, TT, L.lc), B, W, H, N, a, r - 1, L.col);
+            if (q >= 2) issue_row<VEC>(bslot0 + sl8(q) * sstride, B, cx, r - 1);
         }
         cp_commit();
     };
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
+    const float* pre_base = xr + (size_t)L.lc * VEC - 1;       // column col - 1 within a slot row (lc > 0)
     for (int b = y0; b < y1; ++b) {
         const int i = b - y0;
         issue_q(i + kLA + 2);
@@ -274,41 +316,37 @@ k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __
             const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
             const size_t node = (size_t)b * W + a;
             A7 c, m;
-            load_coef(A.coef, node, A.cm, A.cl, c, m);
+            float idiag;
+            load_a(A.acoef, node, c, idiag);
+            load_m(A.coef, node, m);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
-            lds<VEC>(srow<VEC>(xr, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(xr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(xr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(xr, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(xr, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(xr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(xr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
             // column col - 1 of the seven nodes: from the lane to the left, or the tile's previous column
             auto before = [&](int slot, int nd) -> float {
-                return L.lc > 0 ? xr[((size_t)slot * L.sx + nd) * TT + L.lc * VEC - 1] : prev[slot * L.sx + nd];
+                return L.lc > 0 ? pre_base[((size_t)slot * L.sx + nd) * TT] : prev[slot * L.sx + nd];
             };
             float p_c = before(sC, L.ln), p_e = before(sC, L.ln + 1), p_w = before(sC, L.ln - 1);
             float p_n = before(sN, L.ln), p_s = before(sS, L.ln), p_ne = before(sN, L.ln + 1),
                   p_sw = before(sS, L.ln - 1);
             float bv[VEC], r[VEC];
-            lds<VEC>(srow<VEC>(br, sN, L.ln, L.sx, TT, L.lc), bv);
+            lds<VEC>(bslot0 + sN * sstride, bv);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
-                                 c.ne * xne[v] + c.sw * xsw[v];
+                const float ax = apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
                 const float mx = m.c * p_c + m.e * p_e + m.w * p_w + m.n * p_n + m.s * p_s + m.ne * p_ne +
                                  m.sw * p_sw;
                 r[v] = bv[v] - (ax - mx);
                 p_c = xc[v]; p_e = xe[v]; p_w = xw[v]; p_n = xn[v]; p_s = xs[v]; p_ne = xne[v]; p_sw = xsw[v];
             }
             if constexpr (MODE == 0) {
-                st_vec<float, VEC>(R + node * N + L.col, r);
+                const long o = cx.off(b);
+                st_vec<float, VEC>(R + o, r);
                 if (Z0) {
-                    const float w = omega / c.c;
+                    const float w = omega * idiag;
                     float z[VEC];
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) z[v] = w * r[v];
-                    st_vec<float, VEC>(Z0 + node * N + L.col, z);
+                    st_vec<float, VEC>(Z0 + o, z);
                 }
             } else {
                 constexpr int HV = VEC / 2;
@@ -351,16 +389,25 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
     const int B0 = strip * cy, B1 = min(Hc, B0 + cy);
     const int f0 = 2 * B0, f1 = 2 * B1;             // fine rows whose residual is needed: f0..f1
     const int nrows = f1 - f0 + 3;                  // Xf rows f0-1 .. f1+1
+    const Cursor cf = cursor(W, H, N, a, L.col);
+    const size_t sstride = (size_t)L.sx * TT;
+    float* zslot0 = srow<VEC>(zr, 0, L.ln, L.sx, TT, L.lc);
+    float* bslot0 = srow<VEC>(br, 0, L.ln, L.sx, TT, L.lc);
     auto issue_q = [&](int q) {
         if (q < nrows) {
             const int r = f0 - 1 + q;
-            issue<VEC>(srow<VEC>(zr, sl8(q), L.ln, L.sx, TT, L.lc), Xf, W, H, N, a, r, L.col);
-            if (q >= 2) issue<VEC>(srow<VEC>(br, sl8(q), L.ln, L.sx, TT, L.lc), Bf, W, H, N, a, r - 1, L.col);
+            issue_row<VEC>(zslot0 + sl8(q) * sstride, Xf, cf, r);
+            if (q >= 2) issue_row<VEC>(bslot0 + sl8(q) * sstride, Bf, cf, r - 1);
         }
         cp_commit();
     };
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool t_lane = L.ln >= 1 && L.ln <= 2 * cxo + 1 && a < W;
+    // coarse output of this thread (slot ln < cxo): node (A0 + ln, Bq), fine centre slot 2 ln + 2
+    const int Aq = A0 + L.ln;
+    const bool c_lane = L.ln < cxo && Aq < Wc;
+    const Cursor cc = cursor(Wc, Hc, N, Aq, L.col);
+    const int sl = 2 * L.ln + 2;
     for (int f = f0; f <= f1; ++f) {
         const int k = f - f0;
         issue_q(k + kLA + 2);
@@ -369,49 +416,35 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
         if (t_lane) {
             const int sS = sl8(k), sC = sl8(k + 1), sN = sl8(k + 2);
             const size_t node = (size_t)f * W + a;
-            A7 c, m;
-            load_coef(Af.coef, node, Af.cm, Af.cl, c, m);
+            A7 c;
+            float idiag;
+            load_a(Af.acoef, node, c, idiag);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], t[VEC];
-            lds<VEC>(srow<VEC>(zr, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(zr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(zr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(zr, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(zr, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(zr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(zr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
-            lds<VEC>(srow<VEC>(br, sN, L.ln, L.sx, TT, L.lc), bv);
+            nbrs<VEC>(zr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
+            lds<VEC>(bslot0 + sN * sstride, bv);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v)
-                t[v] = bv[v] - (c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
-                                c.ne * xne[v] + c.sw * xsw[v]);
+            for (int v = 0; v < VEC; ++v) t[v] = bv[v] - apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
             sts<VEC>(srow<VEC>(tr, k % 3, L.ln, L.sx, TT, L.lc), t);
         }
         if (k >= 2 && (k & 1) == 0) {
             __syncthreads();
             // coarse row Bq: fine rows f-2 (S), f-1 (centre), f (N)
             const int Bq = B0 + (k - 2) / 2;
-            const int Aq = A0 + L.ln;
-            if (L.ln < cxo && Aq < Wc && Bq < Hc) {
+            if (c_lane && Bq < Hc) {
                 const int tS = (k - 2) % 3, tC = (k - 1) % 3, tN = k % 3;
-                const int sl = 2 * L.ln + 2;   // slot of the fine centre node 2 Aq + 1
                 float vc[VEC], ve[VEC], vw[VEC], vn[VEC], vs[VEC], vne[VEC], vsw[VEC], o[VEC];
-                lds<VEC>(srow<VEC>(tr, tC, sl, L.sx, TT, L.lc), vc);
-                lds<VEC>(srow<VEC>(tr, tC, sl + 1, L.sx, TT, L.lc), ve);
-                lds<VEC>(srow<VEC>(tr, tC, sl - 1, L.sx, TT, L.lc), vw);
-                lds<VEC>(srow<VEC>(tr, tN, sl, L.sx, TT, L.lc), vn);
-                lds<VEC>(srow<VEC>(tr, tS, sl, L.sx, TT, L.lc), vs);
-                lds<VEC>(srow<VEC>(tr, tN, sl + 1, L.sx, TT, L.lc), vne);
-                lds<VEC>(srow<VEC>(tr, tS, sl - 1, L.sx, TT, L.lc), vsw);
+                nbrs<VEC>(tr, tS, tC, tN, sl, L.sx, TT, L.lc, vc, ve, vw, vn, vs, vne, vsw);
 #pragma unroll
                 for (int v = 0; v < VEC; ++v)
                     o[v] = vc[v] + 0.5f * (ve[v] + vw[v] + vn[v] + vs[v] + vne[v] + vsw[v]);
-                const size_t cn = (size_t)Bq * Wc + Aq;
-                st_vec<float, VEC>(Bc + cn * N + L.col, o);
+                const long co = cc.off(Bq);
+                st_vec<float, VEC>(Bc + co, o);
                 if (Xc) {
-                    const float w = omega / diag_coef(Ac.coef, cn, Ac.cm, Ac.cl);
+                    const size_t cn = (size_t)Bq * Wc + Aq;
+                    const float w = omega * __ldg(&Ac.acoef[2 * cn + 1].w);
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) o[v] *= w;
-                    st_vec<float, VEC>(Xc + cn * N + L.col, o);
+                    st_vec<float, VEC>(Xc + co, o);
                 }
             }
         }
@@ -450,42 +483,57 @@ k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int
     const int a = a0 + L.ln;
     const int cA0 = (a0 >> 1) - 1;                  // first coarse column of the ring rows (a0 >= -1)
     const int nrows = y1 - y0 + 2;
-    // the newest coarse row fine row r needs: floor(r / 2); the oldest (first row only)
-    auto cnew = [](int r) { return r >= 0 ? r / 2 : -1; };
+    const Cursor cx = cursor(W, H, N, a, L.col);
+    const Cursor cc = cursor(Wc, Hc, N, cA0 + L.ln, L.col);   // coarse loads by lanes ln < cw
+    const bool c_issuer = L.ln < cw;
+    const size_t sstride = (size_t)L.sx * TT, cstride = (size_t)cw * TT;
+    float* xslot0 = srow<VEC>(xr, 0, L.ln, L.sx, TT, L.lc);
+    float* bslot0 = srow<VEC>(br, 0, L.ln, L.sx, TT, L.lc);
+    float* cslot0 = cr8 + (size_t)L.ln * TT + L.lc * VEC;
     int cnext = ((y0 - 1) >= 0 ? (y0 - 1) / 2 : 0) - 1;   // next coarse row to issue
     auto issue_q = [&](int q) {
         if (q < nrows) {
             const int r = y0 - 1 + q;
-            issue<VEC>(srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc), X, W, H, N, a, r, L.col);
-            if (q >= 2) issue<VEC>(srow<VEC>(br, sl8(q), L.ln, L.sx, TT, L.lc), B, W, H, N, a, r - 1, L.col);
-            const int last = cnew(r);
+            issue_row<VEC>(xslot0 + sl8(q) * sstride, X, cx, r);
+            if (q >= 2) issue_row<VEC>(bslot0 + sl8(q) * sstride, B, cx, r - 1);
+            const int last = r >= 0 ? r / 2 : -1;
             for (; cnext <= last; ++cnext)
-                if (L.ln < cw)
-                    issue<VEC>(cr8 + ((size_t)sl8(cnext) * cw + L.ln) * TT + L.lc * VEC, Xc, Wc, Hc, N, cA0 + L.ln,
-                               cnext, L.col);
+                if (c_issuer) issue_row<VEC>(cslot0 + sl8(cnext) * cstride, Xc, cc, cnext);
         }
         cp_commit();
     };
+    // this thread's coarse columns for x': a odd -> (a-1)/2; a even -> a/2 - 1 and a/2
+    const bool ao = a & 1;
+    const int A1 = ao ? (a - 1) / 2 : a / 2 - 1, A2 = ao ? A1 : a / 2;
+    const bool A1ok = A1 >= 0 && A1 < Wc, A2ok = A2 >= 0 && A2 < Wc;
+    const float* c1base = cr8 + (size_t)(A1 - cA0) * TT + L.lc * VEC;
+    const float* c2base = cr8 + (size_t)(A2 - cA0) * TT + L.lc * VEC;
     // x' = x + P xc in place for ring row q (fine row r)
     auto to_xprime = [&](int q) {
         const int r = y0 - 1 + q;
-        if (a < 0 || a >= W || r < 0 || r >= H) return;
-        float* xp = srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc);
+        if (!cx.ok(r)) return;
+        float* xp = xslot0 + sl8(q) * sstride;
         float v[VEC], c1[VEC], c2[VEC];
         lds<VEC>(xp, v);
-        auto cval = [&](int Acol, int Brow, float (&o)[VEC]) {
-            if (Acol < 0 || Acol >= Wc || Brow < 0 || Brow >= Hc) { zero_vec<VEC>(o); return; }
-            lds<VEC>(cr8 + ((size_t)sl8(Brow) * cw + (Acol - cA0)) * TT + L.lc * VEC, o);
+        auto cval = [&](const float* base, bool aok, int Brow, float (&o)[VEC]) {
+            if (!aok || Brow < 0 || Brow >= Hc) { zero_vec<VEC>(o); return; }
+            lds<VEC>(base + sl8(Brow) * cstride, o);
         };
-        const bool ao = a & 1, fo = r & 1;
-        if (ao && fo) {
-            cval((a - 1) / 2, (r - 1) / 2, c1);
+        if (r & 1) {                    // fine row on a coarse row: (r - 1) / 2
+            const int Bo = (r - 1) / 2;
+            cval(c1base, A1ok, Bo, c1);
+            if (ao) {
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] += c1[k];
-        } else {
-            if (!ao && fo) { cval(a / 2 - 1, (r - 1) / 2, c1); cval(a / 2, (r - 1) / 2, c2); }
-            else if (ao && !fo) { cval((a - 1) / 2, r / 2 - 1, c1); cval((a - 1) / 2, r / 2, c2); }
-            else { cval(a / 2 - 1, r / 2 - 1, c1); cval(a / 2, r / 2, c2); }
+                for (int k = 0; k < VEC; ++k) v[k] += c1[k];
+            } else {
+                cval(c2base, A2ok, Bo, c2);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) v[k] += 0.5f * (c1[k] + c2[k]);
+            }
+        } else {                        // between coarse rows r/2 - 1 and r/2
+            cval(c1base, A1ok, r / 2 - 1, c1);
+            if (ao) cval(c1base, A1ok, r / 2, c2);           // vertical edge midpoint
+            else cval(c2base, A2ok, r / 2, c2);              // diagonal midpoint
 #pragma unroll
             for (int k = 0; k < VEC; ++k) v[k] += 0.5f * (c1[k] + c2[k]);
         }
@@ -511,25 +559,16 @@ k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int
         if (out_lane) {
             const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
             const size_t node = (size_t)b * W + a;
-            A7 c, m;
-            load_coef(A.coef, node, A.cm, A.cl, c, m);
+            A7 c;
+            float idiag;
+            load_a(A.acoef, node, c, idiag);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], o[VEC];
-            lds<VEC>(srow<VEC>(xr, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(xr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(xr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(xr, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(xr, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(xr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(xr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
-            lds<VEC>(srow<VEC>(br, sN, L.ln, L.sx, TT, L.lc), bv);
-            const float w = omega / c.c;
+            nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
+            lds<VEC>(bslot0 + sN * sstride, bv);
+            const float w = omega * idiag;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
-                                 c.ne * xne[v] + c.sw * xsw[v];
-                o[v] = xc[v] + w * (bv[v] - ax);
-            }
-            st_vec<float, VEC>(Out + node * N + L.col, o);
+            for (int v = 0; v < VEC; ++v) o[v] = xc[v] + w * (bv[v] - apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v));
+            st_vec<float, VEC>(Out + cx.off(b), o);
             if constexpr (DOTS > 0) {
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
@@ -563,8 +602,11 @@ k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float*
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
     const int nrows = y1 - y0 + 2;
+    const Cursor cx = cursor(W, H, N, a, L.col);
+    const size_t sstride = (size_t)L.sx * TT;
+    float* xslot0 = srow<VEC>(xr, 0, L.ln, L.sx, TT, L.lc);
     auto issue_q = [&](int q) {
-        if (q < nrows) issue<VEC>(srow<VEC>(xr, sl8(q), L.ln, L.sx, TT, L.lc), P, W, H, N, a, y0 - 1 + q, L.col);
+        if (q < nrows) issue_row<VEC>(xslot0 + sl8(q) * sstride, P, cx, y0 - 1 + q);
         cp_commit();
     };
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
@@ -579,22 +621,13 @@ k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float*
         if (out_lane) {
             const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
             const size_t node = (size_t)b * W + a;
-            A7 c, m;
-            load_coef(A.coef, node, A.cm, A.cl, c, m);
+            A7 c;
+            float idiag;
+            load_a(A.acoef, node, c, idiag);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
-            lds<VEC>(srow<VEC>(xr, sC, L.ln, L.sx, TT, L.lc), xc);
-            lds<VEC>(srow<VEC>(xr, sC, L.ln + 1, L.sx, TT, L.lc), xe);
-            lds<VEC>(srow<VEC>(xr, sC, L.ln - 1, L.sx, TT, L.lc), xw);
-            lds<VEC>(srow<VEC>(xr, sN, L.ln, L.sx, TT, L.lc), xn);
-            lds<VEC>(srow<VEC>(xr, sS, L.ln, L.sx, TT, L.lc), xs);
-            lds<VEC>(srow<VEC>(xr, sN, L.ln + 1, L.sx, TT, L.lc), xne);
-            lds<VEC>(srow<VEC>(xr, sS, L.ln - 1, L.sx, TT, L.lc), xsw);
+            nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const float ax = c.c * xc[v] + c.e * xe[v] + c.w * xw[v] + c.n * xn[v] + c.s * xs[v] +
-                                 c.ne * xne[v] + c.sw * xsw[v];
-                acc[0][v] += xc[v] * ax;
-            }
+            for (int v = 0; v < VEC; ++v) acc[0][v] += xc[v] * apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
         }
     }
     cp_wait<0>();
@@ -665,6 +698,11 @@ static void st_launch(void (*kernel)(KArgs...), dim3 grid, int block, size_t sme
         }
     }
     launch_k_smem(kernel, grid, dim3(block), smem, s, std::forward<Args>(args)...);
+}
+
+void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* out, cudaStream_t s) {
+    if (n <= 0) return;
+    launch_k(k_st_combine, dim3(std::min(4096, (n + 255) / 256)), dim3(256), s, n, coef, cm, cl, out);
 }
 
 int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,

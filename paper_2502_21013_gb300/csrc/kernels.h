@@ -238,9 +238,12 @@ int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, 
 template <typename T>
 struct StencilOp {      // cm M + cl L as a 7-point stencil
     int W = 0, H = 0;
-    const float4* coef = nullptr;
+    const float4* coef = nullptr;    // the level's M and L (4 float4 per node)
+    const float4* acoef = nullptr;   // cm M + cl L precombined: {C, E, W, N}, {S, NE, SW, 1 / C}
     T cm = 1, cl = 0;
 };
+// out (2 float4 per node) = cm M + cl L of coef, with 1 / diagonal in the last slot
+void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* out, cudaStream_t s);
 // R = B - (A X^n - M X^{n-1}) and Z0 = omega D^-1 R (Z0 may be null); with
 // time_restrict R instead receives the pair sums over (2m, 2m+1) (N/2 columns)
 int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,

@@ -754,6 +754,16 @@ void build_hierarchy(Ctx& c) {
             launch_lincomb((size_t)d.rows, p.cm, d.d1d.p, p.cl, d.d2d.p, p.dcomb[k].p, s);
         }
     }
+    // precombined float stencils cm M + cl L per op pair and structured level
+    for (auto& p : c.ops) {
+        p.st_a.clear();
+        p.st_a.resize(c.sl.size());
+        if (!c.stencil_ok) continue;
+        for (size_t k = 0; k < c.sl.size(); ++k) {
+            p.st_a[k].alloc((size_t)2 * c.sl[k].n);
+            launch_st_combine(c.sl[k].n, c.sl[k].st_coef.p, (float)p.cm, (float)p.cl, p.st_a[k].p, s);
+        }
+    }
     // dense inverses on the coarsest spatial level
     const SpatialLevel& cs = c.sl.back();
     if (cs.n <= COARSE_MAX) {

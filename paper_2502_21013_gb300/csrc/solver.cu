@@ -139,6 +139,7 @@ StencilOp<float> st_op(const Ctx& c, int s, int opi) {
     o.W = c.sl[s].nx - 2;
     o.H = c.sl[s].ny - 2;
     o.coef = c.sl[s].st_coef.p;
+    o.acoef = c.ops[opi].st_a[s].p;
     o.cm = (float)c.ops[opi].cm;
     o.cl = (float)c.ops[opi].cl;
     return o;
