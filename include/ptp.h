@@ -92,13 +92,15 @@ typedef struct ptp_opts {
                             N_l > coarse_steps); see coarse_cycles           */
     int    coarse_steps; /* N_c of the coarsest level: 1 or 2 (exact solve)  */
     int    vcycles;      /* multigrid-in-time V-cycles per outer step        */
-    int    pre_smooth;   /* damped block-Jacobi sweeps before coarsening     */
-    int    post_smooth;  /* ... and after                                    */
-    double omega_t;      /* block-Jacobi damping                             */
+    int    pre_smooth;   /* damped block-Jacobi sweeps before coarsening
+                            (default 1)                                      */
+    int    post_smooth;  /* ... and after (default 0: a V(1,0) cycle, which
+                            reaches the exact inner solve's outer count)     */
+    double omega_t;      /* block-Jacobi damping (default 0.95)              */
     int    pcg_iters;    /* PCG iterations per block-Jacobi spatial solve    */
     int    spatial_prec; /* PTP_PREC_JACOBI or PTP_PREC_GMG                  */
     int    gmg_smooth;   /* damped-Jacobi sweeps per GMG level (pre = post)  */
-    double gmg_omega;    /* damping of those sweeps                          */
+    double gmg_omega;    /* damping of those sweeps (default 0.7)            */
     double coarse_tol;   /* relative tolerance of the coarsest-level PCG     */
     int    coarse_max_it;/* iteration cap of the coarsest-level PCG          */
     int    use_graph;    /* capture one outer step in a CUDA graph           */

@@ -114,12 +114,12 @@ void ptp_default_opts(ptp_opts* o) {
     o->coarse_steps = 1;
     o->vcycles = 1;
     o->pre_smooth = 1;
-    o->post_smooth = 1;
-    o->omega_t = 0.5;
+    o->post_smooth = 0;
+    o->omega_t = 0.95;
     o->pcg_iters = 1;
     o->spatial_prec = PTP_PREC_GMG;
     o->gmg_smooth = 1;
-    o->gmg_omega = 0.8;
+    o->gmg_omega = 0.7;
     o->coarse_tol = 1e-6;
     o->coarse_max_it = 4;
     o->use_graph = 1;

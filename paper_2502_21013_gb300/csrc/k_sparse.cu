@@ -401,46 +401,46 @@ k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Sk
     }
 }
 
-// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600):
-// one warp per output row i and chunk of up to 32 columns.  With at least 32
-// columns the lanes take one column each and walk j with four independent
-// partial sums (Ainv[i][j] is a broadcast, B[j][c..c+31] one coalesced load);
-// with fewer columns the lanes split j and the partial sums meet in a
-// fixed-order shuffle reduction.
+// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600),
+// tiled through shared memory: a block computes a 32 x 32 tile of Y
+// (rows i, columns c; four rows per thread) from 32-wide panels of Ainv and
+// B, so each Ainv and B value is read once per tile instead of once per
+// output.  Out-of-range rows, columns and panel entries read as zero.
+constexpr int kDT = 32;
 template <typename T>
-__global__ void k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Y,
-                              Skip sk) {
+__global__ void __launch_bounds__(256)
+k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Y, Skip sk) {
     pdl_enter();
     if (skip_now(sk)) return;
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    const int cchunks = (N + 31) / 32;
-    const long items = (long)n * cchunks;
-    for (long w = (long)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < items; w += warps) {
-        const int i = (int)(w / cchunks), c0 = (int)(w - (long)i * cchunks) * 32;
-        const T* a = A + (size_t)i * n;
-        if (N >= 32) {
-            const int c = c0 + lane;
-            if (c >= N) continue;
-            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            int j = 0;
-            for (; j + 4 <= n; j += 4) {
-                s0 += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
-                s1 += __ldg(a + j + 1) * __ldg(B + (size_t)(j + 1) * N + c);
-                s2 += __ldg(a + j + 2) * __ldg(B + (size_t)(j + 2) * N + c);
-                s3 += __ldg(a + j + 3) * __ldg(B + (size_t)(j + 3) * N + c);
-            }
-            for (; j < n; ++j) s0 += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
-            Y[(size_t)i * N + c] = (s0 + s1) + (s2 + s3);
-        } else {
-            for (int c = 0; c < N; ++c) {
-                T s = 0;
-                for (int j = lane; j < n; j += 32) s += __ldg(a + j) * __ldg(B + (size_t)j * N + c);
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) Y[(size_t)i * N + c] = s;
-            }
+    __shared__ T As[kDT][kDT + 1];
+    __shared__ T Bs[kDT][kDT];
+    const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row group (8 groups of 4 rows)
+    const int c0 = blockIdx.x * kDT, i0 = blockIdx.y * kDT;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int k0 = 0; k0 < n; k0 += kDT) {
+        for (int e = threadIdx.x; e < kDT * kDT; e += blockDim.x) {
+            const int r = e / kDT, q = e - r * kDT;
+            const int ia = i0 + r, ka = k0 + q;
+            As[r][q] = (ia < n && ka < n) ? __ldg(A + (size_t)ia * n + ka) : T(0);
+            const int kb = k0 + r, cb = c0 + q;
+            Bs[r][q] = (kb < n && cb < N) ? __ldg(B + (size_t)kb * N + cb) : T(0);
         }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kDT; ++kk) {
+            const T b = Bs[kk][tx];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r] += As[ty * 4 + r][kk] * b;
+        }
+        __syncthreads();
     }
+    const int c = c0 + tx;
+    if (c < N)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + ty * 4 + r;
+            if (i < n) Y[(size_t)i * N + c] = acc[r];
+        }
 }
 
 template <typename T>
@@ -736,9 +736,7 @@ int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip s
 
 template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    const size_t warps = (size_t)n * ((N + 31) / 32);
-    const int grid = (int)std::max<size_t>(1, std::min<size_t>((warps + 7) / 8, (size_t)num_sms() * 8));
-    launch_k(k_dense_apply<T>, grid, 256, s, n, N, Ainv, B, Y, sk);
+    launch_k(k_dense_apply<T>, dim3((N + kDT - 1) / kDT, (n + kDT - 1) / kDT), dim3(256), s, n, N, Ainv, B, Y, sk);
     return 1;
 }
 

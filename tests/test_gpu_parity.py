@@ -240,8 +240,9 @@ def test_linear_material_converges_in_one_step_and_zero_source():
     prob = W.unit_square_problem(17, 8)
     lin = prob.replace(nonlinear_e=np.zeros(prob.n_tri, np.uint8), nu_linear=prob.nu_max)
     d, Uo = _oracle_solution(lin)
-    c, o = make_ctx(lin, precision=ptp.PTP_FP64, tol=1e-9, max_outer=50, vcycles=40,
-                    coarse_tol=1e-13, coarse_max_it=60)
+    # 40 V(1,1) cycles per step: the inner periodic solve is exact to rounding
+    c, o = make_ctx(lin, precision=ptp.PTP_FP64, tol=1e-9, max_outer=50, vcycles=40, pre_smooth=1, post_smooth=1,
+                    omega_t=0.5, coarse_tol=1e-13, coarse_max_it=60)
     U, st, rc = c.solve(o)
     assert rc == ptp.PTP_OK and st.outer_iterations == 1
     assert rel(U, Uo) < 1e-9
