@@ -94,9 +94,20 @@ typedef struct ptp_opts {
     int    vcycles;      /* multigrid-in-time V-cycles per outer step        */
     int    pre_smooth;   /* damped block-Jacobi sweeps before coarsening
                             (default 1)                                      */
-    int    post_smooth;  /* ... and after (default 0: a V(1,0) cycle, which
-                            reaches the exact inner solve's outer count)     */
-    double omega_t;      /* block-Jacobi damping (default 0.95)              */
+    int    post_smooth;  /* ... and after; < 0 (default): chosen with
+                            omega_t, see below                               */
+    double omega_t;      /* block-Jacobi damping; <= 0 (default): chosen per
+                            problem.  On a spatial mode with eigenvalue
+                            lambda of L x = lambda M x the periodic system of
+                            level l is (1 + kappa_l) x^n - x^{n-1} with
+                            kappa_l = tau_l lambda; the V(pre, post) cycle
+                            with omega near 1 contracts fast for kappa >= 1
+                            but amplifies slow modes with kappa -> 0.  Set-up
+                            estimates lambda_min by inverse iteration and
+                            takes the cheapest (post, omega) whose cycle has
+                            a model spectral radius <= 0.6 for every
+                            kappa >= 0.9 tau_0 lambda_min (ptp_stats reports
+                            the choice)                                      */
     int    pcg_iters;    /* PCG iterations per block-Jacobi spatial solve    */
     int    spatial_prec; /* PTP_PREC_JACOBI or PTP_PREC_GMG                  */
     int    gmg_smooth;   /* damped-Jacobi sweeps per GMG level (pre = post)  */
@@ -154,9 +165,26 @@ typedef struct ptp_stats {
     double init_ms;           /* wall time of the static initialisation      */
     int    init_iterations;   /* its fixed-point steps (0: not run)          */
     int    inner_iterations;  /* Newton: Krylov iterations of all steps      */
+    double omega_t;           /* time smoother used: damping ...             */
+    int    post_smooth;       /* ... and post-smoothing sweeps               */
+    double kappa_min;         /* tau_0 lambda_min(L, M) behind an automatic
+                                 choice (0 if none was made)                 */
 } ptp_stats;
 
 void        ptp_default_opts(ptp_opts* opts);
+
+/* Host-only model of the multigrid-in-time cycle (no GPU is used).  On the
+   scalar periodic system (1 + kappa_l) x^n - x^{n-1} = b^n of each level
+   (N_l = Nl[l] steps, Nl[l] = 2 Nl[l+1], the last level solved exactly,
+   kappa_l = kappa0 Nl[0] / Nl[l]): damped Jacobi (omega), pair-sum
+   restriction, injection.  ptp_time_cycle_rho writes the spectral radius of
+   the V(pre, post) cycle's error propagation (power iteration);
+   ptp_choose_time_smoother the choice that the automatic omega_t and
+   post_smooth make for kappa >= kappa_min (post < 0 / omega <= 0: free).
+   Both return PTP_EINVAL for bad sizes or a hierarchy that does not halve. */
+int ptp_time_cycle_rho(const int* Nl, int levels, double kappa0, int pre, int post, double omega, double* rho);
+int ptp_choose_time_smoother(const int* Nl, int levels, double kappa_min, int pre, int post, double omega,
+                             int* post_out, double* omega_out, double* rho_out);
 const char* ptp_version(void);
 /* sizeof(ptp_opts) and sizeof(ptp_stats) as compiled into the library, so a
    binding can check its own struct layouts.  Either pointer may be NULL. */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libptp.so")
-SOURCES = ["k_residual.cu", "k_sparse.cu", "solver.cu", "setup.cpp", "api.cpp", "noalloc.cu", "k_adjoint.cu", "batch.cu", "k_dft.cu", "k_law.cu", "k_krylov.cu", "newton.cpp", "probe.cu", "k_stencil.cu", "k_poisson.cu"]
+SOURCES = ["k_residual.cu", "k_sparse.cu", "solver.cu", "setup.cpp", "api.cpp", "noalloc.cu", "k_adjoint.cu", "batch.cu", "k_dft.cu", "k_law.cu", "k_krylov.cu", "newton.cpp", "probe.cu", "k_stencil.cu", "k_poisson.cu", "tsmooth.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 

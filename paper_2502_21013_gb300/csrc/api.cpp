@@ -81,6 +81,7 @@ void invalidate(Ctx& c) {
         c.newton_exec = nullptr;
     }
     c.newton_key = -1;
+    c.lambda_min = -1.0;
 }
 
 // device copies for the host-pointer entry points
@@ -114,8 +115,8 @@ void ptp_default_opts(ptp_opts* o) {
     o->coarse_steps = 1;
     o->vcycles = 1;
     o->pre_smooth = 1;
-    o->post_smooth = 0;
-    o->omega_t = 0.95;
+    o->post_smooth = -1;   // chosen per problem (with omega_t)
+    o->omega_t = 0.0;
     o->pcg_iters = 1;
     o->spatial_prec = PTP_PREC_GMG;
     o->gmg_smooth = 1;
@@ -334,6 +335,8 @@ int ptp_setup(ptp_ctx* h, const ptp_opts* opts) {
             c.f_norm = ptp::norm_dev(c, F, cnt);
             PTP_CUDA(cudaFreeAsync(F, c.stream));
         }
+        // the smallest kappa that selects an automatic time smoother
+        if ((o.omega_t <= 0 || o.post_smooth < 0) && c.coarse_ops[0] >= 0) c.lambda_min = ptp::estimate_lambda_min(c);
         PTP_CUDA(cudaStreamSynchronize(c.stream));
         c.ready = true;
         c.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

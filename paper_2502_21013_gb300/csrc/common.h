@@ -262,6 +262,11 @@ struct Ctx {
     int row_block = 256;         // threads per block of the row kernels (autotuned)
     bool stencil_ok = false;     // every spatial level has a 7-point stencil (structured GMG hierarchy)
     int64_t buf_gen = 0;         // bumped when a buffer a captured graph may use is reallocated
+    // smallest eigenvalue of L x = lambda M x (inverse iteration, on first need;
+    // < 0: not yet estimated) and the time smoother it selected
+    double lambda_min = -1.0;
+    double kappa_min = 0.0;      // tau lambda_min on the finest time level
+    double rho_time = 0.0;       // model spectral radius of the chosen cycle
 
     ~Ctx();
 };
@@ -302,6 +307,19 @@ int autotune(Ctx& c, double* best_us);     // picks c.row_block by timing the le
 void require_coarse(const Ctx& c);         // the time hierarchy has an exact last-level solve
 void alloc_adjoint(Ctx& c);                // Jacobian coefficients and adjoint work
 void mg_precondition(Ctx& c, const double* v, double* z);   // z = inner periodic solve of v
+double estimate_lambda_min(Ctx& c);        // smallest eigenvalue of L x = lambda M x
+
+// ---- tsmooth.cpp ----
+struct TimeSmoother {
+    int post;       // post-smoothing sweeps
+    double omega;   // block-Jacobi damping
+    double rho;     // worst model spectral radius over kappa >= kappa_min
+};
+// spectral radius of the V(pre, post) cycle on the scalar periodic model
+// (1 + kappa_l) x^n - x^{n-1}, levels Nl (halving, last one exact), kappa_0 = kappa0
+double tmg_cycle_rho(const std::vector<int>& Nl, double kappa0, int pre, int post, double omega);
+// post < 0 / omega <= 0: free choices; the cheapest candidate with rho <= 0.6
+TimeSmoother choose_time_smoother(const std::vector<int>& Nl, double kappa_min, int pre, int post, double omega);
 
 // ---- api.cpp ----
 // Runs f on the context of h (which must be set up) with the error handling

@@ -37,15 +37,19 @@ __device__ __forceinline__ bool skip_now(const int* done) {
 
 // Iron elements only: q = nu(|g|^2) |T| g with
 // nu |T| = |T| nu_max - |T| (nu_max - nu_min) s_sat^2 / (|g|^2 + s_sat^2).
-__global__ void __launch_bounds__(kBlock)
-k_elem_flux(int n_iron, int N, const int* __restrict__ e_nodes, const double* __restrict__ e_geo,
-            const double* __restrict__ U, double* __restrict__ Qx, double* __restrict__ Qy,
-            double s2sat, const int* done) {
+__device__ __forceinline__ void elem_flux_body(const ElemFluxArgs& p, const VGrid& vg) {
     pdl_enter();
-    if (skip_now(done)) return;
+    if (skip_now(p.done)) return;
+    const int n_iron = p.n_iron, N = p.N;
+    const int* __restrict__ e_nodes = p.e_nodes;
+    const double* __restrict__ e_geo = p.e_geo;
+    const double* __restrict__ U = p.U;
+    double* __restrict__ Qx = p.Qx;
+    double* __restrict__ Qy = p.Qy;
+    const double s2sat = p.s2sat;
     const size_t total = (size_t)n_iron * N;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (size_t)gridDim.x * blockDim.x) {
+    for (size_t g = (size_t)vg.bx * blockDim.x + threadIdx.x; g < total;
+         g += (size_t)vg.gx * blockDim.x) {
         const int e = (int)(g / N);
         const int t = (int)(g - (size_t)e * N);
         const int a = __ldg(e_nodes + 3 * e), b = __ldg(e_nodes + 3 * e + 1),
@@ -73,7 +77,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // the last block to finish (atomic ticket, no waiting) sums the block
 // partials in a fixed order, writes ||R|| and applies the stopping rule of
 // Section 4 to the solve status.  Called by every thread of every block.
-__device__ void residual_norm_finish(double local, const ResidualArgs& a) {
+__device__ void residual_norm_finish(double local, const ResidualArgs& a, const VGrid& vg) {
     __shared__ double sm[32];
     __shared__ bool last;
     const int nw = (blockDim.x + 31) / 32;
@@ -84,8 +88,8 @@ __device__ void residual_norm_finish(double local, const ResidualArgs& a) {
         double v = (int)threadIdx.x < nw ? sm[threadIdx.x] : 0.0;
         v = warp_sum(v);
         if (threadIdx.x == 0) {
-            const unsigned nblk = gridDim.x * gridDim.y;
-            const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+            const unsigned nblk = (unsigned)(vg.gx * vg.gy);
+            const unsigned bid = (unsigned)(vg.by * vg.gx + vg.bx);
             a.partials[bid] = v;
             __threadfence();
             const unsigned ticket = atomicAdd(a.counter, 1u);
@@ -94,7 +98,7 @@ __device__ void residual_norm_finish(double local, const ResidualArgs& a) {
     }
     __syncthreads();
     if (!last) return;
-    const int nblk = (int)(gridDim.x * gridDim.y);
+    const int nblk = vg.gx * vg.gy;
     double s = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(a.partials + b);
     s = warp_sum(s);
@@ -132,8 +136,7 @@ __device__ void residual_norm_finish(double local, const ResidualArgs& a) {
     }
 }
 
-__global__ void __launch_bounds__(kBlock)
-k_node_residual(ResidualArgs a) {
+__device__ __forceinline__ void node_residual_body(const ResidualArgs& a, const VGrid& vg) {
     pdl_enter();
     if (skip_now(a.done)) return;
     const int N = a.N;
@@ -143,8 +146,8 @@ k_node_residual(ResidualArgs a) {
     // (Every block reads s before the last block replaces it below.)
     const double fscale = a.b_f ? a.scale / a.status->bscale : 0.0;
     double local = 0.0;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (size_t)gridDim.x * blockDim.x) {
+    for (size_t g = (size_t)vg.bx * blockDim.x + threadIdx.x; g < total;
+         g += (size_t)vg.gx * blockDim.x) {
         const int i = (int)(g / N);
         const int t = (int)(g - (size_t)i * N);
         const int tm = t == 0 ? N - 1 : t - 1;
@@ -176,7 +179,22 @@ k_node_residual(ResidualArgs a) {
         if (a.b_f) a.b_f[g] = (float)(fscale * r);
         local += r * r;
     }
-    residual_norm_finish(local, a);
+    residual_norm_finish(local, a, vg);
+}
+
+__global__ void __launch_bounds__(kBlock) k_elem_flux(ElemFluxArgs p) { elem_flux_body(p, native_grid()); }
+__global__ void __launch_bounds__(kBlock) k_elem_flux_b(const ElemFluxArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) elem_flux_body(ps[i], g);
+}
+__global__ void __launch_bounds__(kBlock) k_node_residual(ResidualArgs a) { node_residual_body(a, native_grid()); }
+__global__ void __launch_bounds__(kBlock) k_node_residual_b(const ResidualArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) node_residual_body(ps[i], g);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,7 +379,7 @@ k_k1_structured(ResidualArgs a, int sy, int nseg) {
         if (pre) stash((k + 3) & 3, nv, npv);
         __syncthreads();
     }
-    residual_norm_finish(local, a);
+    residual_norm_finish(local, a, native_grid());
 }
 
 __global__ void k_source(int n, int N, int n_coils, const double* __restrict__ coil_b,
@@ -434,16 +452,32 @@ int launch_residual(const ResidualArgs& a, cudaStream_t s) {
             return 1;
         }
     }
-    int launched = 0;
-    if (a.n_iron > 0 && !a.skip_flux) {
-        const size_t te = (size_t)a.n_iron * a.N;
-        launch_k(k_elem_flux, dim3(grid_for(te, 8)), dim3(kBlock), s, a.n_iron, a.N, a.e_nodes, a.e_geo, a.U,
-                 a.Qx, a.Qy, a.s2sat, (const int*)a.done);
-        ++launched;
-    }
-    const size_t tn = (size_t)a.n * a.N;
-    launch_k(k_node_residual, dim3(grid_for(tn, 8)), dim3(kBlock), s, a);
-    return launched + 1;
+    ElemFluxArgs ef;
+    KShape kef, knr;
+    const bool flux = plan_residual(a, ef, kef, knr);
+    if (flux) launch_k(k_elem_flux, dim3(kef.gx), dim3(kBlock), s, ef);
+    launch_k(k_node_residual, dim3(knr.gx), dim3(kBlock), s, a);
+    return flux ? 2 : 1;
+}
+
+// the element and node passes of the two-pass residual: arguments and shapes
+bool plan_residual(const ResidualArgs& a, ElemFluxArgs& ef, KShape& kef, KShape& knr) {
+    const bool flux = a.n_iron > 0 && !a.skip_flux;
+    ef = ElemFluxArgs{a.n_iron, a.N, a.e_nodes, a.e_geo, a.U, a.Qx, a.Qy, a.s2sat, (const int*)a.done};
+    kef = KShape{};
+    if (flux) kef = KShape{grid_for((size_t)a.n_iron * a.N, 8), 1, kBlock, 0, 1, 0};
+    knr = KShape{grid_for((size_t)a.n * a.N, 8), 1, kBlock, 0, 1, 0};
+    return flux;
+}
+
+int launch_elem_flux_batch(const ElemFluxArgs* args, BatchMap m, int blocks, cudaStream_t s) {
+    launch_k(k_elem_flux_b, dim3(blocks), dim3(kBlock), s, args, m);
+    return 1;
+}
+
+int launch_node_residual_batch(const ResidualArgs* args, BatchMap m, int blocks, cudaStream_t s) {
+    launch_k(k_node_residual_b, dim3(blocks), dim3(kBlock), s, args, m);
+    return 1;
 }
 
 void launch_source(int n, int N, int n_coils, const double* coil_b, const double* coil_s,

@@ -78,13 +78,13 @@ struct Lanes {
 };
 
 template <int VEC>
-__device__ __forceinline__ Lanes lanes(int TT) {
+__device__ __forceinline__ Lanes lanes(int TT, int by) {
     Lanes L;
     L.tpn = TT / VEC;
     L.lc = threadIdx.x % L.tpn;
     L.ln = threadIdx.x / L.tpn;
     L.sx = blockDim.x / L.tpn;
-    L.col = blockIdx.y * TT + L.lc * VEC;
+    L.col = by * TT + L.lc * VEC;
     return L;
 }
 
@@ -130,19 +130,19 @@ __device__ __forceinline__ void sts(float* p, const float (&v)[VEC]) {
 // free (the caller synchronised after its last use).
 template <int VEC, int NQ, int FIN>
 __device__ void tile_reduce_finish(float (&acc)[NQ][VEC], const Lanes& L, int TT, int N, float* scratch,
-                                   ColRed<float> cr) {
+                                   const ColRed<float>& cr, const VGrid& g) {
     __shared__ int last;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) sts<VEC>(scratch + ((size_t)q * L.sx + L.ln) * TT + L.lc * VEC, acc[q]);
     __syncthreads();
-    const int tiles = gridDim.x;
-    const int chunk = blockIdx.y;
+    const int tiles = g.gx;
+    const int chunk = g.by;
     float* part = cr.partials + ((size_t)chunk * tiles) * NQ * TT;
     for (int e = threadIdx.x; e < NQ * TT; e += blockDim.x) {
         const int q = e / TT, j = e - q * TT;
         float s = 0.f;
         for (int r = 0; r < L.sx; ++r) s += scratch[((size_t)q * L.sx + r) * TT + j];
-        part[(size_t)blockIdx.x * NQ * TT + e] = s;
+        part[(size_t)g.bx * NQ * TT + e] = s;
     }
     __threadfence();
     __syncthreads();
@@ -270,22 +270,28 @@ __device__ __forceinline__ float apply7(const A7& c, const float (&xc)[VEC], con
 // node (the tile's previous column, for X^{n-1}); B row q - 1 travels with X
 // row q.
 template <int VEC, int MODE>
-__global__ void __launch_bounds__(kStBlock)
-k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __restrict__ X,
-            const float* __restrict__ B, float* __restrict__ R, float* __restrict__ Z0, float omega, Skip sk) {
+__device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGrid& g) {
+    const StencilOp<float>& A = p.A;
+    const int N = p.N, TT = p.TT, sy = p.sy, nseg = p.nseg;
+    const float* __restrict__ X = p.X;
+    const float* __restrict__ B = p.B;
+    float* __restrict__ R = p.R;
+    float* __restrict__ Z0 = p.Z0;
+    const float omega = p.omega;
+    const Skip& sk = p.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    const Lanes L = lanes<VEC>(TT);
+    const Lanes L = lanes<VEC>(TT, g.by);
     float* xr = reinterpret_cast<float*>(smem4);
     float* br = xr + kNS * (size_t)L.sx * TT;
     float* prev = br + kNS * (size_t)L.sx * TT;
     const int W = A.W, H = A.H;
-    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int seg = g.bx % nseg, strip = g.bx / nseg;
     const int a0 = seg * (L.sx - 2) - 1;          // node slot 0 is a0; outputs at slots 1..sx-2
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
-    const int pcol = (blockIdx.y * TT == 0 ? N : blockIdx.y * TT) - 1;   // previous column of the tile
+    const int pcol = (g.by * TT == 0 ? N : g.by * TT) - 1;   // previous column of the tile
     const Cursor cx = cursor(W, H, N, a, L.col);
     const long pdelta = (long)pcol - L.col;       // from this thread's column to the tile's previous one
     const int nrows = y1 - y0 + 2;
@@ -370,20 +376,26 @@ k_st_presid(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __
 // Rings: Xf rows f0-1 .. f1+1 (q = row - f0 + 1); Bf row q - 1 travels with
 // Xf row q; the fine residual t in three rows.
 template <int VEC>
-__global__ void __launch_bounds__(kStBlock)
-k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int cy, int nseg,
-                    const float* __restrict__ Xf, const float* __restrict__ Bf, float* __restrict__ Bc,
-                    float* __restrict__ Xc, float omega, Skip sk) {
+__device__ __forceinline__ void st_resid_restrict_body(const StRestrictArgs& p, const VGrid& g) {
+    const StencilOp<float>& Af = p.Af;
+    const StencilOp<float>& Ac = p.Ac;
+    const int N = p.N, TT = p.TT, cy = p.cy, nseg = p.nseg;
+    const float* __restrict__ Xf = p.Xf;
+    const float* __restrict__ Bf = p.Bf;
+    float* __restrict__ Bc = p.Bc;
+    float* __restrict__ Xc = p.Xc;
+    const float omega = p.omega;
+    const Skip& sk = p.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    const Lanes L = lanes<VEC>(TT);
+    const Lanes L = lanes<VEC>(TT, g.by);
     float* zr = reinterpret_cast<float*>(smem4);
     float* br = zr + kNS * (size_t)L.sx * TT;
     float* tr = br + kNS * (size_t)L.sx * TT;
     const int W = Af.W, H = Af.H, Wc = Ac.W, Hc = Ac.H;
     const int cxo = (L.sx - 3) / 2;                 // coarse nodes per block row segment
-    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int seg = g.bx % nseg, strip = g.bx / nseg;
     const int A0 = seg * cxo;
     const int a = 2 * A0 - 1 + L.ln;                // fine node of slot ln
     const int B0 = strip * cy, B1 = min(Hc, B0 + cy);
@@ -464,20 +476,26 @@ k_st_resid_restrict(StencilOp<float> Af, StencilOp<float> Ac, int N, int TT, int
 // needs it.  Fine free row f uses coarse rows (f-1)/2 (f odd) or f/2 - 1 and
 // f/2 (f even); fine free column a likewise.
 template <int VEC, int DOTS>
-__global__ void __launch_bounds__(kStBlock)
-k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int nseg,
-                  const float* __restrict__ Xc, const float* __restrict__ X, const float* __restrict__ B,
-                  float* __restrict__ Out, float omega, ColRed<float> cr, Skip sk) {
+__device__ __forceinline__ void st_interp_sweep_body(const StInterpArgs& p, const VGrid& g) {
+    const StencilOp<float>& A = p.A;
+    const int Wc = p.Wc, Hc = p.Hc, N = p.N, TT = p.TT, sy = p.sy, nseg = p.nseg;
+    const float* __restrict__ Xc = p.Xc;
+    const float* __restrict__ X = p.X;
+    const float* __restrict__ B = p.B;
+    float* __restrict__ Out = p.Out;
+    const float omega = p.omega;
+    const ColRed<float>& cr = p.cr;
+    const Skip& sk = p.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    const Lanes L = lanes<VEC>(TT);
+    const Lanes L = lanes<VEC>(TT, g.by);
     const int cw = L.sx / 2 + 2;                    // coarse nodes per ring row
     float* xr = reinterpret_cast<float*>(smem4);
     float* br = xr + kNS * (size_t)L.sx * TT;
     float* cr8 = br + kNS * (size_t)L.sx * TT;      // coarse ring: kNS x cw x TT
     const int W = A.W, H = A.H;
-    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int seg = g.bx % nseg, strip = g.bx / nseg;
     const int a0 = seg * (L.sx - 2) - 1;
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
@@ -580,24 +598,27 @@ k_st_interp_sweep(StencilOp<float> A, int Wc, int Hc, int N, int TT, int sy, int
     }
     cp_wait<0>();
     __syncthreads();
-    if constexpr (DOTS == 1) tile_reduce_finish<VEC, 2, FIN_RZ_FIRST>(acc, L, TT, N, xr, cr);
-    if constexpr (DOTS == 2) tile_reduce_finish<VEC, 1, FIN_RZ_NEXT>(acc, L, TT, N, xr, cr);
+    if constexpr (DOTS == 1) tile_reduce_finish<VEC, 2, FIN_RZ_FIRST>(acc, L, TT, N, xr, cr, g);
+    if constexpr (DOTS == 2) tile_reduce_finish<VEC, 1, FIN_RZ_NEXT>(acc, L, TT, N, xr, cr, g);
 }
 
 // ---------------------------------------------------------------------------
 // PCG step length: alpha = rho / (p . A p) per column, A p not written
 // ---------------------------------------------------------------------------
 template <int VEC>
-__global__ void __launch_bounds__(kStBlock)
-k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float* __restrict__ P,
-               ColRed<float> cr, Skip sk) {
+__device__ __forceinline__ void st_apply_dot_body(const StApplyDotArgs& p, const VGrid& g) {
+    const StencilOp<float>& A = p.A;
+    const int N = p.N, TT = p.TT, sy = p.sy, nseg = p.nseg;
+    const float* __restrict__ P = p.P;
+    const ColRed<float>& cr = p.cr;
+    const Skip& sk = p.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     extern __shared__ float4 smem4[];
-    const Lanes L = lanes<VEC>(TT);
+    const Lanes L = lanes<VEC>(TT, g.by);
     float* xr = reinterpret_cast<float*>(smem4);
     const int W = A.W, H = A.H;
-    const int seg = blockIdx.x % nseg, strip = blockIdx.x / nseg;
+    const int seg = g.bx % nseg, strip = g.bx / nseg;
     const int a0 = seg * (L.sx - 2) - 1;
     const int y0 = strip * sy, y1 = min(H, y0 + sy);
     const int a = a0 + L.ln;
@@ -632,7 +653,7 @@ k_st_apply_dot(StencilOp<float> A, int N, int TT, int sy, int nseg, const float*
     }
     cp_wait<0>();
     __syncthreads();
-    tile_reduce_finish<VEC, 1, FIN_ALPHA>(acc, L, TT, N, xr, cr);
+    tile_reduce_finish<VEC, 1, FIN_ALPHA>(acc, L, TT, N, xr, cr, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -705,27 +726,71 @@ void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* ou
     launch_k(k_st_combine, dim3(std::min(4096, (n + 255) / 256)), dim3(256), s, n, coef, cm, cl, out);
 }
 
-int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
-                     float omega, bool time_restrict, Skip sk, cudaStream_t s) {
+// ---- kernels: one single-instance and one batched entry per body ----
+template <int VEC, int MODE>
+__global__ void __launch_bounds__(kStBlock) k_st_presid(StPresidArgs p) {
+    st_presid_body<VEC, MODE>(p, native_grid());
+}
+template <int VEC, int MODE>
+__global__ void __launch_bounds__(kStBlock) k_st_presid_b(const StPresidArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) st_presid_body<VEC, MODE>(ps[i], g);
+}
+template <int VEC>
+__global__ void __launch_bounds__(kStBlock) k_st_resid_restrict(StRestrictArgs p) {
+    st_resid_restrict_body<VEC>(p, native_grid());
+}
+template <int VEC>
+__global__ void __launch_bounds__(kStBlock) k_st_resid_restrict_b(const StRestrictArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) st_resid_restrict_body<VEC>(ps[i], g);
+}
+template <int VEC, int DOTS>
+__global__ void __launch_bounds__(kStBlock) k_st_interp_sweep(StInterpArgs p) {
+    st_interp_sweep_body<VEC, DOTS>(p, native_grid());
+}
+template <int VEC, int DOTS>
+__global__ void __launch_bounds__(kStBlock) k_st_interp_sweep_b(const StInterpArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) st_interp_sweep_body<VEC, DOTS>(ps[i], g);
+}
+template <int VEC>
+__global__ void __launch_bounds__(kStBlock) k_st_apply_dot(StApplyDotArgs p) {
+    st_apply_dot_body<VEC>(p, native_grid());
+}
+template <int VEC>
+__global__ void __launch_bounds__(kStBlock) k_st_apply_dot_b(const StApplyDotArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) st_apply_dot_body<VEC>(ps[i], g);
+}
+
+// ---- plans: arguments and shape of one call ----
+StPresidArgs plan_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
+                            float omega, bool time_restrict, Skip sk, KShape& ks) {
     const Shape sh = st_shape(N, {X, B, R, Z0}, time_restrict);
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
-    const size_t smem = (2 * kNS * (size_t)sh.sx * sh.TT + kNS * (size_t)sh.sx) * sizeof(float);
-    const dim3 grid(nseg * nstrip, nch);
-    if (time_restrict) {
-        if (sh.vec == 4) st_launch(k_st_presid<4, 1>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk);
-        else st_launch(k_st_presid<2, 1>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk);
-    } else {
-        PTP_ST_VEC(sh.vec, st_launch(k_st_presid<VEC, 0>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, X, B, R,
-                                     Z0, omega, sk));
-    }
-    return 1;
+    ks.gx = nseg * nstrip;
+    ks.gy = nch;
+    ks.block = sh.block;
+    ks.smem = (2 * kNS * (size_t)sh.sx * sh.TT + kNS * (size_t)sh.sx) * sizeof(float);
+    ks.vec = sh.vec;
+    ks.variant = time_restrict ? 1 : 0;
+    return StPresidArgs{A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk};
 }
 
-int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
-                             const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s) {
+StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
+                                      const float* Bf, float* Bc, float* Xc, float omega, Skip sk, KShape& ks) {
     PTP_REQUIRE(Af.W == 2 * Ac.W + 1 && Af.H == 2 * Ac.H + 1, "stencil restriction: grids are not nested");
     const Shape sh = st_shape(N, {Xf, Bf, Bc, Xc}, false);
     const int cxo = (sh.sx - 3) / 2;
@@ -734,54 +799,127 @@ int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>&
     const int nch = N / sh.TT;
     const int cy = std::max(1, strip_rows(Ac.H, nseg, nch) / 2);
     const int nstrip = (Ac.H + cy - 1) / cy;
-    const size_t smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
-    const dim3 grid(nseg * nstrip, nch);
-    PTP_ST_VEC(sh.vec, st_launch(k_st_resid_restrict<VEC>, grid, sh.block, smem, s, Af, Ac, N, sh.TT, cy, nseg, Xf,
-                                 Bf, Bc, Xc, omega, sk));
-    return 1;
+    ks.gx = nseg * nstrip;
+    ks.gy = nch;
+    ks.block = sh.block;
+    ks.smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
+    ks.vec = sh.vec;
+    ks.variant = 0;
+    return StRestrictArgs{Af, Ac, N, sh.TT, cy, nseg, Xf, Bf, Bc, Xc, omega, sk};
 }
 
-int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
-                           const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
-                           cudaStream_t s) {
+StInterpArgs plan_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
+                                  const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
+                                  KShape& ks) {
     PTP_REQUIRE(A.W == 2 * Wc + 1 && A.H == 2 * Hc + 1, "stencil interpolation: grids are not nested");
     const Shape sh = st_shape(N, {Xc, X, B, Out}, false);
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
-    const size_t smem = (2 * kNS * (size_t)sh.sx + kNS * (size_t)(sh.sx / 2 + 2)) * sh.TT * sizeof(float);
-    const dim3 grid(nseg * nstrip, nch);
+    ks.gx = nseg * nstrip;
+    ks.gy = nch;
+    ks.block = sh.block;
+    ks.smem = (2 * kNS * (size_t)sh.sx + kNS * (size_t)(sh.sx / 2 + 2)) * sh.TT * sizeof(float);
+    ks.vec = sh.vec;
+    ks.variant = dots;
     if (dots) {
-        const size_t need = (size_t)grid.x * grid.y * 2 * sh.TT;
+        const size_t need = (size_t)ks.gx * ks.gy * 2 * sh.TT;
         PTP_REQUIRE(cr.partials != nullptr && need <= cr.capacity, "stencil reduction: partial buffer too small");
         PTP_REQUIRE(nch <= 254, "stencil reduction: too many time tiles");
     }
-    if (dots == 1) {
-        PTP_ST_VEC(sh.vec, st_launch(k_st_interp_sweep<VEC, 1>, grid, sh.block, smem, s, A, Wc, Hc, N, sh.TT, sy, nseg,
-                                     Xc, X, B, Out, omega, cr, sk));
-    } else if (dots == 2) {
-        PTP_ST_VEC(sh.vec, st_launch(k_st_interp_sweep<VEC, 2>, grid, sh.block, smem, s, A, Wc, Hc, N, sh.TT, sy, nseg,
-                                     Xc, X, B, Out, omega, cr, sk));
-    } else {
-        PTP_ST_VEC(sh.vec, st_launch(k_st_interp_sweep<VEC, 0>, grid, sh.block, smem, s, A, Wc, Hc, N, sh.TT, sy, nseg,
-                                     Xc, X, B, Out, omega, cr, sk));
-    }
-    return 1;
+    return StInterpArgs{A, Wc, Hc, N, sh.TT, sy, nseg, Xc, X, B, Out, omega, cr, sk};
 }
 
-int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s) {
+StApplyDotArgs plan_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk,
+                                 KShape& ks) {
     const Shape sh = st_shape(N, {P}, false);
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
-    const size_t smem = kNS * (size_t)sh.sx * sh.TT * sizeof(float);
-    const dim3 grid(nseg * nstrip, nch);
-    const size_t need = (size_t)grid.x * grid.y * sh.TT;
+    ks.gx = nseg * nstrip;
+    ks.gy = nch;
+    ks.block = sh.block;
+    ks.smem = kNS * (size_t)sh.sx * sh.TT * sizeof(float);
+    ks.vec = sh.vec;
+    ks.variant = 0;
+    const size_t need = (size_t)ks.gx * ks.gy * sh.TT;
     PTP_REQUIRE(cr.partials != nullptr && need <= cr.capacity, "stencil reduction: partial buffer too small");
     PTP_REQUIRE(nch <= 254, "stencil reduction: too many time tiles");
-    PTP_ST_VEC(sh.vec, st_launch(k_st_apply_dot<VEC>, grid, sh.block, smem, s, A, N, sh.TT, sy, nseg, P, cr, sk));
+    return StApplyDotArgs{A, N, sh.TT, sy, nseg, P, cr, sk};
+}
+
+// ---- single launches ----
+int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
+                     float omega, bool time_restrict, Skip sk, cudaStream_t s) {
+    KShape ks;
+    const StPresidArgs a = plan_st_presid(A, N, X, B, R, Z0, omega, time_restrict, sk, ks);
+    const dim3 grid(ks.gx, ks.gy);
+    if (time_restrict) {
+        if (ks.vec == 4) st_launch(k_st_presid<4, 1>, grid, ks.block, ks.smem, s, a);
+        else st_launch(k_st_presid<2, 1>, grid, ks.block, ks.smem, s, a);
+    } else {
+        PTP_ST_VEC(ks.vec, st_launch(k_st_presid<VEC, 0>, grid, ks.block, ks.smem, s, a));
+    }
+    return 1;
+}
+
+int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
+                             const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s) {
+    KShape ks;
+    const StRestrictArgs a = plan_st_resid_restrict(Af, Ac, N, Xf, Bf, Bc, Xc, omega, sk, ks);
+    PTP_ST_VEC(ks.vec, st_launch(k_st_resid_restrict<VEC>, dim3(ks.gx, ks.gy), ks.block, ks.smem, s, a));
+    return 1;
+}
+
+int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
+                           const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
+                           cudaStream_t s) {
+    KShape ks;
+    const StInterpArgs a = plan_st_interp_sweep(A, Wc, Hc, N, Xc, X, B, Out, omega, cr, dots, sk, ks);
+    const dim3 grid(ks.gx, ks.gy);
+    if (dots == 1) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 1>, grid, ks.block, ks.smem, s, a))
+    else if (dots == 2) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 2>, grid, ks.block, ks.smem, s, a))
+    else PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 0>, grid, ks.block, ks.smem, s, a))
+    return 1;
+}
+
+int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s) {
+    KShape ks;
+    const StApplyDotArgs a = plan_st_apply_dot(A, N, P, cr, sk, ks);
+    PTP_ST_VEC(ks.vec, st_launch(k_st_apply_dot<VEC>, dim3(ks.gx, ks.gy), ks.block, ks.smem, s, a));
+    return 1;
+}
+
+// ---- batched launches: every instance's blocks in one 1-D grid ----
+int launch_st_presid_batch(const StPresidArgs* args, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    const dim3 grid(blocks);
+    if (ks.variant == 1) {
+        if (ks.vec == 4) st_launch(k_st_presid_b<4, 1>, grid, ks.block, ks.smem, s, args, m);
+        else st_launch(k_st_presid_b<2, 1>, grid, ks.block, ks.smem, s, args, m);
+    } else {
+        PTP_ST_VEC(ks.vec, st_launch(k_st_presid_b<VEC, 0>, grid, ks.block, ks.smem, s, args, m));
+    }
+    return 1;
+}
+
+int launch_st_resid_restrict_batch(const StRestrictArgs* args, BatchMap m, int blocks, const KShape& ks,
+                                   cudaStream_t s) {
+    PTP_ST_VEC(ks.vec, st_launch(k_st_resid_restrict_b<VEC>, dim3(blocks), ks.block, ks.smem, s, args, m));
+    return 1;
+}
+
+int launch_st_interp_sweep_batch(const StInterpArgs* args, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    const dim3 grid(blocks);
+    if (ks.variant == 1) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep_b<VEC, 1>, grid, ks.block, ks.smem, s, args, m))
+    else if (ks.variant == 2) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep_b<VEC, 2>, grid, ks.block, ks.smem, s, args, m))
+    else PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep_b<VEC, 0>, grid, ks.block, ks.smem, s, args, m))
+    return 1;
+}
+
+int launch_st_apply_dot_batch(const StApplyDotArgs* args, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    PTP_ST_VEC(ks.vec, st_launch(k_st_apply_dot_b<VEC>, dim3(blocks), ks.block, ks.smem, s, args, m));
     return 1;
 }
 

@@ -60,6 +60,49 @@ inline void launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
 }
 
 // ---------------------------------------------------------------------------
+// Virtual grids.  Kernel bodies index blocks through a VGrid so that one
+// launch can serve many instances (the batched step): a single launch passes
+// the native grid; a batched launch gives instance i the blocks
+// [start[i], start[i+1]) of a 1-D grid and maps them onto its own gx x gy.
+// ---------------------------------------------------------------------------
+struct VGrid {
+    int bx, by, gx, gy;
+};
+struct BatchMap {
+    const int* start;   // n + 1 block offsets
+    const int* gx;      // virtual grid of each instance
+    const int* gy;
+    int n;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ VGrid native_grid() {
+    return VGrid{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
+}
+// instance and virtual block of this block in a batched launch
+__device__ __forceinline__ bool batch_block(const BatchMap& m, int& inst, VGrid& g) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = m.n - 1;
+    while (lo < hi) {   // largest i with start[i] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(m.start + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    inst = lo;
+    const int local = b - __ldg(m.start + lo);
+    const int gx = __ldg(m.gx + lo), gy = __ldg(m.gy + lo);
+    if (local >= gx * gy) return false;
+    g = VGrid{local % gx, local / gx, gx, gy};
+    return true;
+}
+#endif
+
+// Launch shape of one kernel call: virtual grid gx x gy of `block` threads,
+// dynamic shared memory, vector width and kernel variant.
+struct KShape {
+    int gx = 0, gy = 0, block = 0;
+    size_t smem = 0;
+    int vec = 0, variant = 0;
+};
+// ---------------------------------------------------------------------------
 // K1: outer residual R = F - A(U), double (fused source, mass, K(u), norm)
 // ---------------------------------------------------------------------------
 struct ResidualArgs {
@@ -106,6 +149,20 @@ struct ResidualArgs {
     int st_no_mass;           // sigma = 0 (static problems)
 };
 int launch_residual(const ResidualArgs& a, cudaStream_t s);  // returns kernels launched
+struct ElemFluxArgs {         // iron element fluxes of the two-pass residual
+    int n_iron, N;
+    const int* e_nodes;
+    const double* e_geo;
+    const double* U;
+    double* Qx;
+    double* Qy;
+    double s2sat;
+    const int* done;
+};
+// the two-pass residual's element pass (returned: whether it runs) and node pass
+bool plan_residual(const ResidualArgs& a, ElemFluxArgs& ef, KShape& kef, KShape& knr);
+int launch_elem_flux_batch(const ElemFluxArgs* args, BatchMap m, int blocks, cudaStream_t s);
+int launch_node_residual_batch(const ResidualArgs* args, BatchMap m, int blocks, cudaStream_t s);
 // the same, with the iron fluxes of the exponential law of Section 4 when e_law
 // (4 per iron element: |T| a, b, ln c, |T| d) is set (k_law.cu)
 int launch_residual_law(const ResidualArgs& a, const double* e_law, cudaStream_t s);
@@ -244,20 +301,75 @@ struct StencilOp {      // cm M + cl L as a 7-point stencil
 };
 // out (2 float4 per node) = cm M + cl L of coef, with 1 / diagonal in the last slot
 void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* out, cudaStream_t s);
+struct StPresidArgs {
+    StencilOp<float> A;
+    int N, TT, sy, nseg;
+    const float* X;
+    const float* B;
+    float* R;
+    float* Z0;
+    float omega;
+    Skip sk;
+};
+struct StRestrictArgs {
+    StencilOp<float> Af, Ac;
+    int N, TT, cy, nseg;
+    const float* Xf;
+    const float* Bf;
+    float* Bc;
+    float* Xc;
+    float omega;
+    Skip sk;
+};
+struct StInterpArgs {
+    StencilOp<float> A;
+    int Wc, Hc, N, TT, sy, nseg;
+    const float* Xc;
+    const float* X;
+    const float* B;
+    float* Out;
+    float omega;
+    ColRed<float> cr;
+    Skip sk;
+};
+struct StApplyDotArgs {
+    StencilOp<float> A;
+    int N, TT, sy, nseg;
+    const float* P;
+    ColRed<float> cr;
+    Skip sk;
+};
 // R = B - (A X^n - M X^{n-1}) and Z0 = omega D^-1 R (Z0 may be null); with
 // time_restrict R instead receives the pair sums over (2m, 2m+1) (N/2 columns)
+StPresidArgs plan_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
+                            float omega, bool time_restrict, Skip sk, KShape& sh);
 int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
                      float omega, bool time_restrict, Skip sk, cudaStream_t s);
 // Bc = P^T (Bf - Af Xf); Xc = omega Dc^-1 Bc if Xc is set
+StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
+                                      const float* Bf, float* Bc, float* Xc, float omega, Skip sk, KShape& sh);
 int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
                              const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s);
 // Out = x' + omega D^-1 (B - A x'), x' = X + P Xc; dots 1: rho = B.Out, bb = rr = B.B;
 // dots 2: beta = B.Out / rho, rho = B.Out (per column, cr)
+StInterpArgs plan_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
+                                  const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
+                                  KShape& sh);
 int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, const float* Xc, const float* X,
                            const float* B, float* Out, float omega, ColRed<float> cr, int dots, Skip sk,
                            cudaStream_t s);
 // alpha = rho / (P . A P) per column
+StApplyDotArgs plan_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk,
+                                 KShape& sh);
 int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s);
+// One launch of a kernel kind for many instances: `args` (device array, one
+// per instance), the batch map (device arrays) and the common shape (vec,
+// variant, block and the largest smem); `blocks` = the sum of gx * gy.
+int launch_st_presid_batch(const StPresidArgs* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+int launch_st_resid_restrict_batch(const StRestrictArgs* args, BatchMap m, int blocks, const KShape& sh,
+                                   cudaStream_t s);
+int launch_st_interp_sweep_batch(const StInterpArgs* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+int launch_st_apply_dot_batch(const StApplyDotArgs* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Exact solve of tau_c L x = b on a uniform structured grid by discrete sine

@@ -966,6 +966,88 @@ int autotune(Ctx& c, double* best_us) {
     return bestb;
 }
 
+// Smallest eigenvalue of the pencil L x = lambda M x (M the sigma-weighted
+// mass, singular on non-conducting nodes) by inverse iteration
+// x <- (tau_c L)^{-1} M x with the double spatial PCG of the coarsest time
+// level; the Rayleigh quotient x.Lx / x.Mx decreases to lambda_min.
+double estimate_lambda_min(Ctx& c) {
+    const int n = c.n;
+    cudaStream_t st = c.stream;
+    const int oL = c.coarse_ops[0];
+    PTP_REQUIRE(oL >= 0, "no tau_c L operator");
+    const double tc = c.ops[oL].cl;
+    Op<double> Mop = make_op<double>(c.sl[0].op, 1.0, 0.0);
+    Op<double> Lop = level_op<double>(c, 0, oL);
+    DBuf<double> x, Mx, Lx;
+    x.alloc(n);
+    Mx.alloc(n);
+    Lx.alloc(n);
+    std::vector<double> hx(n), hm(n), hl(n);
+    c.launches += launch_fill<double>((size_t)n, 1.0, x.p, Skip{}, st);
+    double lam = -1.0;
+    const int max_pcg = 200;
+    for (int k = 0; k < 30; ++k) {
+        double* r = c.w_d[0].p;   // M x, destroyed by the PCG
+        c.launches += launch_spmm<double>(SP_APPLY, Mop, 1, x.p, nullptr, r, 0.0, Skip{}, st);
+        c.launches += launch_fill<double>((size_t)n, 0.0, x.p, Skip{}, st);
+        PCG<double> pcg(c, oL, 1, r, x.p, 1.0, 1e-10, Skip{}, false);
+        pcg.init();
+        for (int it = 0; it < max_pcg; ++it) {
+            pcg.iterate(it == max_pcg - 1);
+            if (it % 8 == 7) {
+                int done = 0;
+                PTP_CUDA(cudaMemcpyAsync(&done, c.flag.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+                PTP_CUDA(cudaStreamSynchronize(st));
+                if (done) break;
+            }
+        }
+        c.launches += launch_spmm<double>(SP_APPLY, Mop, 1, x.p, nullptr, Mx.p, 0.0, Skip{}, st);
+        c.launches += launch_spmm<double>(SP_APPLY, Lop, 1, x.p, nullptr, Lx.p, 0.0, Skip{}, st);
+        PTP_CUDA(cudaMemcpyAsync(hx.data(), x.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaMemcpyAsync(hm.data(), Mx.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaMemcpyAsync(hl.data(), Lx.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PTP_CUDA(cudaStreamSynchronize(st));
+        double xm = 0.0, xl = 0.0;
+        for (int i = 0; i < n; ++i) {
+            xm += hx[i] * hm[i];
+            xl += hx[i] * hl[i];
+        }
+        if (!(xm > 0.0)) return 1e300;   // M = 0: no time coupling, kappa is infinite
+        if (!std::isfinite(xl)) return 0.0;
+        const double now = xl / tc / xm;
+        const bool settled = lam > 0 && std::fabs(lam - now) <= 1e-4 * now;
+        lam = now;
+        if (settled) break;
+        const double sc = 1.0 / std::sqrt(xm);
+        for (int i = 0; i < n; ++i) hx[i] *= sc;
+        PTP_CUDA(cudaMemcpyAsync(x.p, hx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    PTP_CUDA(cudaStreamSynchronize(st));
+    return lam;
+}
+
+// Resolves omega_t <= 0 and post_smooth < 0 (automatic) from the smallest
+// kappa = tau lambda_min of the problem (tsmooth.cpp).
+static void resolve_time_smoother(Ctx& c) {
+    ptp_opts& o = c.opts;
+    if (o.omega_t > 0 && o.post_smooth >= 0) return;
+    if (c.lambda_min < 0) c.lambda_min = estimate_lambda_min(c);
+    c.kappa_min = std::min(1e6, c.tl[0].tau * c.lambda_min);
+    // the model's hierarchy: the levels down to the one solved exactly
+    int last = (int)c.tl.size() - 1;
+    if (c.dft_level >= 0) last = std::min(last, c.dft_level);
+    last = std::min(last, std::max(0, c.active_levels - 1));
+    std::vector<int> Nl;
+    for (int l = 0; l <= last; ++l) Nl.push_back(c.tl[l].N);
+    // a 10% margin below the estimate (a Rayleigh quotient, which approaches
+    // lambda_min from above; smaller kappa is the harder case)
+    const TimeSmoother t = choose_time_smoother(Nl, 0.9 * c.kappa_min, std::max(0, o.pre_smooth), o.post_smooth,
+                                                o.omega_t);
+    o.post_smooth = t.post;
+    o.omega_t = t.omega;
+    c.rho_time = t.rho;
+}
+
 void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, int kind) {
     const bool adjoint = kind == STEP_ADJOINT;
     if (kind != STEP_STATIC) require_coarse(c);   // the static step has no time hierarchy
@@ -974,6 +1056,7 @@ void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, int kind) {
                     o.coarse_solver == c.opts.coarse_solver,
                 "precision / preconditioner / hierarchy options differ from ptp_setup");
     c.opts = o;
+    if (kind != STEP_STATIC) resolve_time_smoother(c);
     cudaStream_t st = c.stream;
     double* X = adjoint ? c.Lam.p : c.U.p;
     const size_t cnt = (size_t)c.n * c.N;
@@ -1026,6 +1109,9 @@ int solve_end(Ctx& c, ptp_stats* stats, int kind, int64_t step_launches, double 
         stats->kernel_launches = step_launches;
         stats->time_levels = c.active_levels;
         stats->spatial_levels = (int)c.sl.size();
+        stats->omega_t = c.opts.omega_t;
+        stats->post_smooth = c.opts.post_smooth;
+        stats->kappa_min = c.kappa_min;
     }
     if (fs.done == 2) return PTP_ENAN;
     return conv ? PTP_OK : PTP_ENOTCONV;
@@ -1042,7 +1128,7 @@ static int run_fixed_point(Ctx& c, const ptp_opts& o, const double* X0, double* 
     cudaStream_t st = c.stream;
     const size_t cnt = (size_t)c.n * c.N;
     // graph of one outer step, re-captured when the options change
-    const int64_t key = step_key(c, o);
+    const int64_t key = step_key(c, c.opts);
     if (o.use_graph && (c.graph_exec[gi] == nullptr || c.graph_key[gi] != key)) {
         if (c.graph_exec[gi]) { cudaGraphExecDestroy(c.graph_exec[gi]); c.graph_exec[gi] = nullptr; }
         cudaGraph_t g;

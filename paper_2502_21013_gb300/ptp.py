@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
         ("res_final", ctypes.c_double), ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
         ("residual_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("time_levels", ctypes.c_int),
         ("spatial_levels", ctypes.c_int), ("init_ms", ctypes.c_double), ("init_iterations", ctypes.c_int),
-        ("inner_iterations", ctypes.c_int),
+        ("inner_iterations", ctypes.c_int), ("omega_t", ctypes.c_double), ("post_smooth", ctypes.c_int),
+        ("kappa_min", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -115,6 +116,8 @@ def _load():
         "ptp_adjoint_gradient": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
         "ptp_probe_fma": (I, [I, I, pD]),
         "ptp_probe_recip_dev": (I, [I, P, P, ctypes.c_int64, P]),
+        "ptp_time_cycle_rho": (I, [pI, I, D, I, I, D, pD]),
+        "ptp_choose_time_smoother": (I, [pI, I, D, I, I, D, pI, pD, pD]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -143,7 +146,29 @@ EXPORTED = [
     "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient", "ptp_autotune",
     "ptp_batch_create", "ptp_batch_destroy", "ptp_batch_last_error", "ptp_batch_add", "ptp_batch_size",
     "ptp_batch_solve", "ptp_batch_result_dev", "ptp_probe_fma", "ptp_probe_recip_dev",
+    "ptp_time_cycle_rho", "ptp_choose_time_smoother",
 ]
+
+
+def time_cycle_rho(Nl, kappa0, pre, post, omega):
+    """Model spectral radius of the V(pre, post) time cycle (ptp_time_cycle_rho; host only)."""
+    arr = (ctypes.c_int * len(Nl))(*[int(v) for v in Nl])
+    r = ctypes.c_double()
+    rc = lib.ptp_time_cycle_rho(arr, len(Nl), float(kappa0), int(pre), int(post), float(omega), ctypes.byref(r))
+    if rc != PTP_OK:
+        raise PtpError(rc, "ptp_time_cycle_rho: bad arguments")
+    return r.value
+
+
+def choose_time_smoother(Nl, kappa_min, pre=1, post=-1, omega=0.0):
+    """(post, omega, rho) that the automatic time smoother takes (ptp_choose_time_smoother; host only)."""
+    arr = (ctypes.c_int * len(Nl))(*[int(v) for v in Nl])
+    q, w, r = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.ptp_choose_time_smoother(arr, len(Nl), float(kappa_min), int(pre), int(post), float(omega),
+                                      ctypes.byref(q), ctypes.byref(w), ctypes.byref(r))
+    if rc != PTP_OK:
+        raise PtpError(rc, "ptp_choose_time_smoother: bad arguments")
+    return q.value, w.value, r.value
 
 
 def probe_fma(device=0, fp64=True):

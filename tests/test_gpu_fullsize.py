@@ -104,8 +104,11 @@ def test_adjoint_full_size_every_parameter_class():
     removes the h^2 term.  A single element's conductivity moves J by 1e-7 to
     1e-5 of itself per unit relative change, while J of a state solved to the
     double residual's floor (2.5e-13 relative on this workload) reproduces to
-    about 5e-12 of itself; so each sampled sigma_e is checked to 1e-5 relative
-    plus that noise floor (1e-11 J / h), and the directional derivative along a
+    about eps = 5e-12 of itself.  The Richardson value (4 D(h/2) - D(h)) / 3
+    of the central differences D(h/2) = (J+ - J-) / h and D(h) =
+    (J++ - J--) / (2 h) carries at most (4 * 2 + 1) / 3 = 3 eps J / h of that
+    noise; so each sampled sigma_e is checked to 1e-5 relative plus the floor
+    3 eps J / h, and the directional derivative along a
     seeded random combination of every iron conductivity, whose change of J
     is far above the noise, to 1e-5 relative.  The base state is solved to
     1e-12."""
@@ -160,7 +163,7 @@ def test_adjoint_full_size_every_parameter_class():
         h = hrel * abs(p0) if hrel is not None else 1e-3
         fd = central(setter, p0, h) if kind == "central" else richardson(setter, p0, h)
         err = abs(fd - grad) / abs(fd)
-        floor = 1e-11 * abs(J) / h if name.startswith("sigma[") else 0.0
+        floor = 3 * 5e-12 * abs(J) / h if name.startswith("sigma[") else 0.0
         print(f"adjoint FD {name}: adjoint {grad:.10e} FD {fd:.10e} rel. diff {err:.2e} "
               f"(noise floor {floor / abs(fd):.1e} relative)")
         if not abs(fd - grad) <= 1e-5 * abs(fd) + floor:
