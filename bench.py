@@ -21,6 +21,10 @@ Also reported on the same line:
             algorithmic bytes / duration against the measured HBM copy peak;
             traffic: DRAM bytes per launch from the ncu capture in profiles/
             while the kernel source is unchanged since it, else null
+  transformer   config 3 (1025x513 nodes, N = 512) solved to 1e-8, with its
+            own e2e and rooflines
+  batched   uneven instances in one merged graph launch per step (a bounded
+            sample of the 64-instance draw; see its `sample`)
   cpu_baseline  the CPU oracle on a bounded sample (see `sample`)
 
 Multi-GPU: every rank solves its own seeded instance (independent replicas,
@@ -406,6 +410,65 @@ def transformer_leg(args, local, dev, stream, world, hbm_peak):
                             "traffic": None}}
 
 
+def batched_leg(args, local, dev, world):
+    """Batched uneven instances (meshes drawn from {65,129,257,513}^2 nodes,
+    N from {64..512}, J0 ~ U[20,80], s_sat ~ U[0.5,2]), mixed precision to
+    1e-8 from U = 0, every instance in one merged CUDA-graph launch per
+    fixed-point step.  Bounded sample: the first `batched_count` instances of
+    the seeded 64-instance draw (the whole draw is a separate workload,
+    --workload batched64).  Also timed: the same batch with every instance
+    as a graph branch of its own (its launches unmerged), over a fixed
+    number of steps, for the per-step cost of merging."""
+    import torch
+    from paper_2502_21013_gb300 import ptp
+    rank = int(os.environ.get("RANK", "0"))
+    probs = W.config_batched(seed=rank, count=64)[:args.batched_count]
+    t0 = time.perf_counter()
+    ctxs = []
+    for p in probs:
+        c = ptp.Context(local)
+        ptp.load_problem(c, p)
+        c.setup(ptp.default_opts(precision=ptp.PTP_MIXED))
+        ctxs.append(c)
+    setup_s = time.perf_counter() - t0
+    batch = ptp.Batch(local)
+    for c in ctxs:
+        batch.add(c)
+    batch.solve(ptp.default_opts(precision=ptp.PTP_MIXED, tol=TOL, max_outer=2))   # plan and capture
+    opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=TOL, max_outer=args.max_outer)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    stats, nconv, rc = batch.solve(opts)
+    torch.cuda.synchronize()
+    el = reduce_scalar(time.perf_counter() - t, "max", dev, world)
+    lps, merged, nmerged = batch.plan_info()
+    dofs = sum(p.n_free * p.N for p in probs)
+    steps = max(s.outer_iterations for s in stats) + 1
+    # per-step time, merged against one graph branch per instance, over a fixed step count
+    fixed = ptp.default_opts(precision=ptp.PTP_MIXED, tol=0.0, max_outer=64)
+    per_step = {}
+    for mode, name in ((ptp.PTP_BATCH_MERGED, "merged"), (ptp.PTP_BATCH_BRANCHES, "branches")):
+        batch.set_mode(mode)
+        batch.solve(ptp.default_opts(precision=ptp.PTP_MIXED, tol=0.0, max_outer=2))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        batch.solve(fixed)
+        torch.cuda.synchronize()
+        per_step[name] = {"ms_per_step": (time.perf_counter() - t) * 1e3 / fixed.max_outer,
+                          "launches_per_step": batch.plan_info()[0]}
+    batch.close()
+    del ctxs
+    torch.cuda.empty_cache()
+    return {"workload": "batched_uneven", "value": reduce_scalar(dofs, "sum", dev, world) / el, "unit": UNIT,
+            "sample": f"the first {len(probs)} of the 64 seeded instances", "instances": len(probs),
+            "space_time_dofs": dofs, "converged": nconv, "tol": TOL, "precision": "mixed",
+            "seconds": el, "setup_s": setup_s, "batched_steps": steps,
+            "outer_iterations": [s.outer_iterations for s in stats],
+            "grids_and_steps": [f"{int(round(math.sqrt(p.n_nodes)))}^2 N={p.N}" for p in probs],
+            "launches_per_step": lps, "merged_instances": merged, "merged_launches": nmerged,
+            "per_step_64": per_step, "gpu_launches": int(lps * steps)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -541,6 +604,10 @@ def run_ours(args):
     if args.transformer_steps > 0:
         transformer = transformer_leg(args, local, dev, stream, world, hbm_peak)
 
+    batched = None
+    if args.batched_count > 0:
+        batched = batched_leg(args, local, dev, world)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_to_tolerance()
@@ -587,6 +654,7 @@ def run_ours(args):
                                                         "paper_2502_21013_gb300/csrc/k_sparse.cu"),
                             "algorithmic_bytes": k2["bytes"], "duration_us": k2["seconds"] * 1e6},
             "transformer": transformer,
+            "batched": batched,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }
@@ -637,7 +705,8 @@ def run_batched(args):
                        "outer_iterations": [s.outer_iterations for s in stats],
                        "largest_instance_dofs": max(p.n_free * p.N for p in probs),
                        "row_block_choices": {str(b): tuned.count(b) for b in sorted(set(tuned))},
-                       "gpu_launches": int(sum(s.kernel_launches for s in stats))},
+                       "launches_per_step": batch.plan_info()[0], "merged_instances": batch.plan_info()[1],
+                       "gpu_launches": int(stats[0].kernel_launches)},
             "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -780,6 +849,8 @@ def main():
     ap.add_argument("--dft-max-it", type=int, default=None,
                     help="COCG iterations per DFT-in-time solve (library default 30)")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batched-count", type=int, default=16,
+                    help="instances of the batched leg of the default line (0: skip)")
     ap.add_argument("--allow-unconverged", action="store_true",
                     help="profiling only: accept solves cut short by --max-outer")
     ap.add_argument("--ref-iterations", type=int, default=EXTRAP_ITERATIONS,

@@ -286,10 +286,19 @@ int ptp_autotune(ptp_ctx* ctx, int* block_threads, double* best_us);
 /* ---- batched independent instances ----------------------------------- */
 
 /* A batch advances many set-up contexts (uneven meshes and N allowed) with
-   one CUDA-graph launch per fixed-point step: the outer step of every
-   instance is a parallel branch of the graph, so their kernels run
-   concurrently.  The batch does not own the contexts; they must stay alive
-   and set up while the batch is used.  Same device only. */
+   one CUDA-graph launch per fixed-point step.  In PTP_BATCH_MERGED mode (the
+   default) the outer step of every instance is recorded and the recordings
+   are merged: launches of the same kernel kind at aligned positions of the
+   instances' steps become one launch over a work-list of (instance, its
+   blocks), so the kernels per step do not grow with the number of
+   instances.  An instance whose step has work without a batched form (the
+   exponential law, the ELL kernels of unstructured meshes, the DFT time
+   solver, the fused K1 option) runs as a parallel branch of the same graph;
+   PTP_BATCH_BRANCHES runs every instance that way.  The batch does not own
+   the contexts; they must stay alive and set up while the batch is used.
+   Same device only. */
+#define PTP_BATCH_MERGED   0
+#define PTP_BATCH_BRANCHES 1
 typedef struct ptp_batch ptp_batch;
 int  ptp_batch_create(ptp_batch** out, int device);
 void ptp_batch_destroy(ptp_batch* batch);
@@ -301,11 +310,20 @@ int  ptp_batch_size(const ptp_batch* batch);
    ptp_setup).  stats: array of ptp_batch_size entries (may be NULL);
    *n_converged (may be NULL) counts instances that met the stopping rule.
    Each instance's iterate stays in its context (read with ptp_residual_dev
-   or a later ptp_solve); results are identical to solving the instance
-   alone.  Returns PTP_OK if all converged, else PTP_ENOTCONV or PTP_ENAN. */
+   or a later ptp_solve); results are bitwise identical to solving the
+   instance alone (each instance's blocks compute what its own launch would,
+   in the same order).  The stats of every instance count the kernels of
+   the whole batch.  Returns PTP_OK if all converged, else PTP_ENOTCONV or PTP_ENAN. */
 int  ptp_batch_solve(ptp_batch* batch, const ptp_opts* opts, ptp_stats* stats, int* n_converged);
 /* Copies instance i's current iterate (device U, [n_free][N]). */
 int  ptp_batch_result_dev(ptp_batch* batch, int i, double* U);
+/* PTP_BATCH_MERGED or PTP_BATCH_BRANCHES (takes effect at the next solve). */
+int  ptp_batch_set_mode(ptp_batch* batch, int mode);
+/* The captured step of the last ptp_batch_solve: kernels per step (merged
+   launches plus those of branch instances), instances merged, merged
+   launches.  Pointers may be NULL; PTP_ESTATE before the first solve. */
+int  ptp_batch_plan_info(const ptp_batch* batch, int64_t* launches_per_step, int* merged_instances,
+                         int* merged_launches);
 
 /* ---- the hot path ---------------------------------------------------- */
 

@@ -336,7 +336,10 @@ int ptp_setup(ptp_ctx* h, const ptp_opts* opts) {
             PTP_CUDA(cudaFreeAsync(F, c.stream));
         }
         // the smallest kappa that selects an automatic time smoother
-        if ((o.omega_t <= 0 || o.post_smooth < 0) && c.coarse_ops[0] >= 0) c.lambda_min = ptp::estimate_lambda_min(c);
+        if ((o.omega_t <= 0 || o.post_smooth < 0) && c.coarse_ops[0] >= 0) {
+            c.lambda_min = ptp::estimate_lambda_min(c);
+            ptp::resolve_time_smoother(c);   // c.opts as the entry points without options use it
+        }
         PTP_CUDA(cudaStreamSynchronize(c.stream));
         c.ready = true;
         c.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -504,6 +507,7 @@ int ptp_periodic_solve_dev(ptp_ctx* h, const ptp_opts* opts, const double* B, do
                         "ptp_periodic_solve: hierarchy options differ from ptp_setup");
             c.opts = *opts;
         }
+        ptp::resolve_time_smoother(c);
         ptp::periodic_mg_solve(c, B, X, cycles, relres);
         PTP_CUDA(cudaGetLastError());
         return PTP_OK;

@@ -1,23 +1,107 @@
 // Batched solve of many independent instances (uneven mesh sizes and N).
 //
-// Each instance is a set-up context with its own stream and buffers.  One
-// outer fixed-point step of every instance is captured into a single CUDA
-// graph as parallel branches forked from, and joined back into, the batch
-// stream, so one graph launch advances all instances by one step and their
-// kernels run concurrently (small instances fill the SMs that a large one
-// leaves idle).  An instance that has met its stopping rule keeps launching
-// inside the graph but every kernel of it returns at once (its device flag),
-// so its iterate is the one that converged.  The host reads all statuses
-// every check_every steps and stops when every instance is done.
+// Each instance is a set-up context with its own buffers.  One outer
+// fixed-point step of every instance is first RECORDED: its launchers append
+// (kernel kind, launch shape, argument struct) instead of launching.  The
+// recorded programs are then merged into one: each instance's launches keep
+// their order, and launches of the same kind (same batched kernel, block size,
+// vector width and variant) at aligned positions become ONE launch over the
+// work-list of those instances, every instance getting its own virtual grid
+// (a contiguous range of the launch's blocks).  The alignment is a shortest
+// common supersequence built instance by instance from longest common
+// subsequences of the kind sequences, so instances of the same hierarchy
+// share every launch and deeper ones add only their extra levels; the number
+// of launches per step does not grow with the number of instances.  The
+// merged program is captured into one CUDA graph per step.  An instance whose
+// step has work without a batched form (another residual law, the ELL path,
+// the DFT solver) runs as a parallel branch of the same graph instead.
+//
+// An instance that has met its stopping rule keeps its entries, but every
+// kernel body of it returns at once (its device flag), so its iterate is the
+// one that converged.  The host reads all statuses every check_every steps
+// and stops when every instance is done.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <numeric>
 #include <vector>
 
 #include "common.h"
+#include "kernels.h"
 
 namespace ptp {
 Ctx* ctx_of(ptp_ctx* h);
+
+Recorder*& active_recorder() {
+    static thread_local Recorder* r = nullptr;
+    return r;
 }
+}  // namespace ptp
+
+namespace {
+
+using ptp::BatchLaunch;
+using ptp::KShape;
+using ptp::RecordedLaunch;
+
+struct MergedOp {
+    BatchLaunch fn = nullptr;
+    KShape shape;                              // common kind; the largest dynamic shared memory
+    std::vector<int> inst;                     // instance of each entry
+    std::vector<const RecordedLaunch*> rec;    // its recorded launch
+    size_t off_args = 0, off_start = 0, off_gx = 0, off_gy = 0;
+    int blocks = 0;
+};
+
+bool same_kind(const MergedOp& m, const RecordedLaunch& r) {
+    return m.fn == r.fn && m.shape.block == r.shape.block && m.shape.vec == r.shape.vec &&
+           m.shape.variant == r.shape.variant && m.rec.front()->args.size() == r.args.size();
+}
+
+MergedOp single(int inst, const RecordedLaunch& r) {
+    MergedOp m;
+    m.fn = r.fn;
+    m.shape = r.shape;
+    m.inst.push_back(inst);
+    m.rec.push_back(&r);
+    return m;
+}
+
+// merges program `ops` of instance `inst` into `seq` (longest common subsequence of kinds)
+std::vector<MergedOp> merge(std::vector<MergedOp>&& seq, int inst, const std::vector<RecordedLaunch>& ops) {
+    const size_t A = seq.size(), B = ops.size();
+    std::vector<int> dp((A + 1) * (B + 1), 0);
+    auto at = [&](size_t a, size_t b) -> int& { return dp[a * (B + 1) + b]; };
+    for (size_t a = 1; a <= A; ++a)
+        for (size_t b = 1; b <= B; ++b)
+            at(a, b) = same_kind(seq[a - 1], ops[b - 1]) ? at(a - 1, b - 1) + 1 : std::max(at(a - 1, b), at(a, b - 1));
+    std::vector<MergedOp> out;
+    out.reserve(A + B);
+    size_t a = A, b = B;
+    while (a > 0 || b > 0) {
+        if (a > 0 && b > 0 && same_kind(seq[a - 1], ops[b - 1]) && at(a, b) == at(a - 1, b - 1) + 1) {
+            MergedOp m = std::move(seq[a - 1]);
+            m.inst.push_back(inst);
+            m.rec.push_back(&ops[b - 1]);
+            m.shape.smem = std::max(m.shape.smem, ops[b - 1].shape.smem);
+            out.push_back(std::move(m));
+            --a;
+            --b;
+        } else if (a > 0 && (b == 0 || at(a - 1, b) >= at(a, b - 1))) {
+            out.push_back(std::move(seq[a - 1]));
+            --a;
+        } else {
+            out.push_back(single(inst, ops[b - 1]));
+            --b;
+        }
+    }
+    std::reverse(out.begin(), out.end());
+    return out;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
 
 struct ptp_batch {
     int device = 0;
@@ -28,6 +112,14 @@ struct ptp_batch {
     std::vector<int64_t> per_step;
     std::vector<cudaEvent_t> events;
     std::string err;
+    int mode = PTP_BATCH_MERGED;
+    // the merged program
+    std::vector<ptp::Recorder> recs;
+    std::vector<MergedOp> merged;
+    std::vector<int> branch;        // instances that run as graph branches
+    unsigned char* blob = nullptr;  // device work-lists (argument structs and virtual grids)
+    int64_t step_launches = 0;      // kernels per batched step
+    int merged_instances = 0;
 };
 
 namespace {
@@ -36,6 +128,11 @@ void drop_graph(ptp_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->keys.clear();
+    if (b->blob) cudaFree(b->blob);
+    b->blob = nullptr;
+    b->merged.clear();
+    b->recs.clear();
+    b->branch.clear();
 }
 
 template <typename F>
@@ -52,6 +149,98 @@ int batch_guard(ptp_batch* b, F&& f) {
         b->err = e.what();
         return PTP_EINVAL;
     }
+}
+
+struct RecordGuard {
+    explicit RecordGuard(ptp::Recorder* r) { ptp::active_recorder() = r; }
+    ~RecordGuard() { ptp::active_recorder() = nullptr; }
+};
+
+// records every instance's step and merges those without foreign work
+void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
+    const int K = (int)cs.size();
+    b->recs.assign(K, ptp::Recorder{});
+    b->per_step.assign(K, 0);
+    std::vector<int> mergeable;
+    for (int i = 0; i < K; ++i) {
+        if (b->mode != PTP_BATCH_MERGED) {
+            b->branch.push_back(i);
+            continue;
+        }
+        ptp::set_row_block(cs[i]->row_block);
+        {
+            RecordGuard g(&b->recs[i]);
+            b->per_step[i] = ptp::enqueue_step(*cs[i], ptp::STEP_FORWARD);
+        }
+        if (b->recs[i].foreign == 0 && !b->recs[i].ops.empty()) mergeable.push_back(i);
+        else b->branch.push_back(i);
+    }
+    // longest programs first: they form the backbone of the alignment
+    std::stable_sort(mergeable.begin(), mergeable.end(),
+                     [&](int x, int y) { return b->recs[x].ops.size() > b->recs[y].ops.size(); });
+    std::vector<MergedOp> seq;
+    for (int i : mergeable) seq = merge(std::move(seq), i, b->recs[i].ops);
+    // work-lists: argument structs, block offsets and virtual grids of every merged launch
+    size_t bytes = 0;
+    for (MergedOp& m : seq) {
+        const size_t k = m.inst.size();
+        m.off_args = bytes = align_up(bytes, 256);
+        bytes += k * m.rec.front()->args.size();
+        m.off_start = bytes = align_up(bytes, 16);
+        bytes += (k + 1) * sizeof(int);
+        m.off_gx = bytes = align_up(bytes, 16);
+        bytes += k * sizeof(int);
+        m.off_gy = bytes = align_up(bytes, 16);
+        bytes += k * sizeof(int);
+    }
+    std::vector<unsigned char> host(std::max<size_t>(bytes, 1), 0);
+    for (MergedOp& m : seq) {
+        const size_t k = m.inst.size(), asz = m.rec.front()->args.size();
+        int* start = reinterpret_cast<int*>(host.data() + m.off_start);
+        int* gx = reinterpret_cast<int*>(host.data() + m.off_gx);
+        int* gy = reinterpret_cast<int*>(host.data() + m.off_gy);
+        long total = 0;
+        for (size_t j = 0; j < k; ++j) {
+            std::memcpy(host.data() + m.off_args + j * asz, m.rec[j]->args.data(), asz);
+            start[j] = (int)total;
+            gx[j] = m.rec[j]->shape.gx;
+            gy[j] = std::max(1, m.rec[j]->shape.gy);
+            total += (long)gx[j] * gy[j];
+        }
+        PTP_REQUIRE(total < (1L << 31), "batched launch: too many blocks");
+        start[k] = (int)total;
+        m.blocks = (int)total;
+    }
+    if (!seq.empty()) {
+        PTP_CUDA(cudaMalloc((void**)&b->blob, bytes));
+        PTP_CUDA(cudaMemcpy(b->blob, host.data(), bytes, cudaMemcpyHostToDevice));
+    }
+    b->merged = std::move(seq);
+    b->merged_instances = (int)mergeable.size();
+}
+
+// the step of every instance: merged launches on the batch stream, branches on their own
+void enqueue_batched_step(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
+    const int K = (int)cs.size();
+    PTP_CUDA(cudaEventRecord(b->events[K], b->stream));
+    int64_t launches = 0;
+    for (int i : b->branch) {
+        PTP_CUDA(cudaStreamWaitEvent(cs[i]->stream, b->events[K], 0));
+        ptp::set_row_block(cs[i]->row_block);
+        b->per_step[i] = ptp::enqueue_step(*cs[i], ptp::STEP_FORWARD);
+        launches += b->per_step[i];
+        PTP_CUDA(cudaEventRecord(b->events[i], cs[i]->stream));
+    }
+    for (const MergedOp& m : b->merged) {
+        ptp::BatchMap map;
+        map.start = reinterpret_cast<const int*>(b->blob + m.off_start);
+        map.gx = reinterpret_cast<const int*>(b->blob + m.off_gx);
+        map.gy = reinterpret_cast<const int*>(b->blob + m.off_gy);
+        map.n = (int)m.inst.size();
+        launches += m.fn(b->blob + m.off_args, map, m.blocks, m.shape, b->stream);
+    }
+    for (int i : b->branch) PTP_CUDA(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+    b->step_launches = launches;
 }
 
 }  // namespace
@@ -103,6 +292,24 @@ int ptp_batch_add(ptp_batch* b, ptp_ctx* h) {
 
 int ptp_batch_size(const ptp_batch* b) { return b ? (int)b->items.size() : PTP_EINVAL; }
 
+int ptp_batch_set_mode(ptp_batch* b, int mode) {
+    return batch_guard(b, [&]() {
+        PTP_REQUIRE(mode == PTP_BATCH_MERGED || mode == PTP_BATCH_BRANCHES, "ptp_batch_set_mode: bad mode");
+        if (mode != b->mode) drop_graph(b);
+        b->mode = mode;
+        return PTP_OK;
+    });
+}
+
+int ptp_batch_plan_info(const ptp_batch* b, int64_t* launches_per_step, int* merged_instances, int* merged_launches) {
+    if (!b) return PTP_EINVAL;
+    if (!b->exec) return PTP_ESTATE;
+    if (launches_per_step) *launches_per_step = b->step_launches;
+    if (merged_instances) *merged_instances = b->merged_instances;
+    if (merged_launches) *merged_launches = (int)b->merged.size();
+    return PTP_OK;
+}
+
 int ptp_batch_result_dev(ptp_batch* b, int i, double* U) {
     return batch_guard(b, [&]() {
         PTP_REQUIRE(i >= 0 && i < (int)b->items.size() && U, "ptp_batch_result_dev: bad index or pointer");
@@ -144,18 +351,11 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
                 PTP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
                 b->events.push_back(e);
             }
-            b->per_step.assign(K, 0);
+            plan(b, cs);
             cudaGraph_t g;
             PTP_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
             try {
-                PTP_CUDA(cudaEventRecord(b->events[K], b->stream));
-                for (int i = 0; i < K; ++i) {
-                    PTP_CUDA(cudaStreamWaitEvent(cs[i]->stream, b->events[K], 0));
-                    ptp::set_row_block(cs[i]->row_block);
-                    b->per_step[i] = ptp::enqueue_step(*cs[i], ptp::STEP_FORWARD);
-                    PTP_CUDA(cudaEventRecord(b->events[i], cs[i]->stream));
-                    PTP_CUDA(cudaStreamWaitEvent(b->stream, b->events[i], 0));
-                }
+                enqueue_batched_step(b, cs);
             } catch (...) {
                 cudaStreamEndCapture(b->stream, &g);
                 throw;
@@ -208,7 +408,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
             ptp::set_row_block(cs[i]->row_block);
             ptp_stats st;
             std::memset(&st, 0, sizeof(st));
-            const int rc = ptp::solve_end(*cs[i], &st, ptp::STEP_FORWARD, (int64_t)launched * b->per_step[i], wall, ms);
+            const int rc = ptp::solve_end(*cs[i], &st, ptp::STEP_FORWARD, (int64_t)launched * b->step_launches, wall, ms);
             if (stats) stats[i] = st;
             if (rc == PTP_OK) ++conv;
             else if (worst == PTP_OK || rc == PTP_ENAN) worst = rc;

@@ -308,6 +308,9 @@ void require_coarse(const Ctx& c);         // the time hierarchy has an exact la
 void alloc_adjoint(Ctx& c);                // Jacobian coefficients and adjoint work
 void mg_precondition(Ctx& c, const double* v, double* z);   // z = inner periodic solve of v
 double estimate_lambda_min(Ctx& c);        // smallest eigenvalue of L x = lambda M x
+// replaces an automatic omega_t (<= 0) / post_smooth (< 0) in c.opts by the
+// choice for the problem's smallest kappa (estimating lambda_min on first need)
+void resolve_time_smoother(Ctx& c);
 
 // ---- tsmooth.cpp ----
 struct TimeSmoother {

@@ -89,6 +89,14 @@ __device__ __forceinline__ void st_vec(T* p, const T (&o)[VEC]) {
     for (int rg_ = blockIdx.x; rg_ * (rpb) < (rows); rg_ += gridDim.x)                  \
         for (int row = rg_ * (rpb) + rsub_; row < (rows) && rsub_ < (rpb); row = (rows))
 
+// the same walk over the blocks of a virtual grid g
+#define PTP_ROW_LOOP_G(rows, NC, rpb, g)                                               \
+    const int chunk_ = threadIdx.x % (NC);                                             \
+    const int rsub_ = threadIdx.x / (NC);                                              \
+    const int col0 = chunk_ * VEC;                                                     \
+    for (int rg_ = (g).bx; rg_ * (rpb) < (rows); rg_ += (g).gx)                        \
+        for (int row = rg_ * (rpb) + rsub_; row < (rows) && rsub_ < (rpb); row = (rows))
+
 // ---------------------------------------------------------------------------
 // per-column reductions with a last-block finish
 // ---------------------------------------------------------------------------

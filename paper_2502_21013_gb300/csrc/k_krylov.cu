@@ -105,17 +105,19 @@ __global__ void k_sqrt_or_one(double* x) {
 // used again: x = xscale alpha p (assign) or x += xscale alpha p, with the
 // per-column alpha of the ColRed scalars (the same arithmetic as the full update).
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kMaxBlock)
-k_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* __restrict__ p, const T* __restrict__ alpha,
-              Skip sk) {
+__device__ __forceinline__ void pcg_xupdate_body(const XUpdateArgs<T>& a, const VGrid& g) {
     pdl_enter();
-    if (skip_now(sk)) return;
-    const int NC = N / VEC, rpb = blockDim.x / NC;
-    PTP_ROW_LOOP(rows, NC, rpb) {
+    if (skip_now(a.sk)) return;
+    const int N = a.N, NC = N / VEC, rpb = blockDim.x / NC;
+    const T xscale = a.xscale;
+    const T* __restrict__ p = a.p;
+    const T* __restrict__ alpha = a.alpha;
+    T* x = a.x;
+    PTP_ROW_LOOP_G(a.rows, NC, rpb, g) {
         const size_t o = (size_t)row * N + col0;
         T pv[VEC], xv[VEC];
         ldg_vec<T, VEC>(p + o, pv);
-        if (assign) {
+        if (a.assign) {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) xv[v] = T(0);
         } else {
@@ -125,6 +127,18 @@ k_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* __restrict__
         for (int v = 0; v < VEC; ++v) xv[v] += xscale * alpha[col0 + v] * pv[v];
         st_vec<T, VEC>(x + o, xv);
     }
+}
+
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock) k_pcg_xupdate(XUpdateArgs<T> a) {
+    pcg_xupdate_body<T, VEC>(a, native_grid());
+}
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kMaxBlock) k_pcg_xupdate_b(const XUpdateArgs<T>* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) pcg_xupdate_body<T, VEC>(ps[i], g);
 }
 
 int grid_of(size_t count) {
@@ -160,16 +174,45 @@ int launch_div_scalar(size_t count, const double* x, const double* h, double* y,
 }
 
 template <typename T>
+int launch_pcg_xupdate_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {
+    const XUpdateArgs<T>* a = static_cast<const XUpdateArgs<T>*>(args);
+    if (sh.vec == 4) {
+        if constexpr (sizeof(T) == 4) launch_k(k_pcg_xupdate_b<T, 4>, dim3(blocks), dim3(sh.block), s, a, m);
+    } else if (sh.vec == 2) {
+        launch_k(k_pcg_xupdate_b<T, 2>, dim3(blocks), dim3(sh.block), s, a, m);
+    } else {
+        launch_k(k_pcg_xupdate_b<T, 1>, dim3(blocks), dim3(sh.block), s, a, m);
+    }
+    return 1;
+}
+
+template <typename T>
 int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, ColRed<T> cr, Skip sk,
                        cudaStream_t s) {
-    const T* alpha = cr.col + S_ALPHA * N;
+    const XUpdateArgs<T> a{rows, N, xscale, assign, x, p, cr.col + S_ALPHA * N, sk};
     auto al = [](const void* q, size_t b) { return ((uintptr_t)q % b) == 0; };
+    int vec = 1;
+    const void* kern = (const void*)k_pcg_xupdate<T, 1>;
     if (sizeof(T) == 4 && N % 4 == 0 && al(x, 16) && al(p, 16)) {
-        if constexpr (sizeof(T) == 4) launch_rows(k_pcg_xupdate<T, 4>, rows, N, 4, s, rows, N, xscale, assign, x, p, alpha, sk);
+        vec = 4;
+        if constexpr (sizeof(T) == 4) kern = (const void*)k_pcg_xupdate<T, 4>;
     } else if (N % 2 == 0 && al(x, 2 * sizeof(T)) && al(p, 2 * sizeof(T))) {
-        launch_rows(k_pcg_xupdate<T, 2>, rows, N, 2, s, rows, N, xscale, assign, x, p, alpha, sk);
+        vec = 2;
+        kern = (const void*)k_pcg_xupdate<T, 2>;
+    }
+    const Launch l = row_launch(rows, N, vec, kern);
+    KShape sh;
+    sh.gx = l.grid;
+    sh.gy = 1;
+    sh.block = l.block;
+    sh.vec = vec;
+    if (record_launch(launch_pcg_xupdate_batch<T>, a, sh)) return 1;
+    if (vec == 4) {
+        if constexpr (sizeof(T) == 4) launch_k(k_pcg_xupdate<T, 4>, dim3(l.grid), dim3(l.block), s, a);
+    } else if (vec == 2) {
+        launch_k(k_pcg_xupdate<T, 2>, dim3(l.grid), dim3(l.block), s, a);
     } else {
-        launch_rows(k_pcg_xupdate<T, 1>, rows, N, 1, s, rows, N, xscale, assign, x, p, alpha, sk);
+        launch_k(k_pcg_xupdate<T, 1>, dim3(l.grid), dim3(l.block), s, a);
     }
     return 1;
 }

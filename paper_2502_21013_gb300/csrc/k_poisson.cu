@@ -64,18 +64,21 @@ __device__ __forceinline__ void dst_load(double2* sh, int p, int ntr, int n, int
 // transform is scaled elementwise by scale[t][k] and transformed again
 // (S (scale * S in)), in one pass over shared memory.
 template <typename TI, typename TO, bool TWICE>
-__global__ void __launch_bounds__(kDstThreads)
-k_dst(int ntr, int n, int logM2, const TI* __restrict__ in, long in_tr, long in_el, TO* __restrict__ out,
-      long out_tr, long out_el, const double* __restrict__ scale, const double2* __restrict__ Wt, Skip sk) {
+__device__ __forceinline__ void dst_body(const DstArgs& p, const VGrid& g) {
     pdl_enter();
-    if (skip_now(sk)) return;
+    if (skip_now(p.sk)) return;
+    const int ntr = p.ntr, n = p.n, logM2 = p.logM2;
+    const TI* __restrict__ in = static_cast<const TI*>(p.in);
+    TO* __restrict__ out = static_cast<TO*>(p.out);
+    const double* __restrict__ scale = p.scale;
+    const double2* __restrict__ Wt = p.Wt;
     extern __shared__ double2 dsm[];
     const int m = n + 1, M2 = 2 * m;
     double2* sh = dsm;
     double2* sh2 = dsm + M2;
-    for (int p = blockIdx.x; 2 * p < ntr; p += gridDim.x) {
-        const int t1 = 2 * p, t2 = 2 * p + 1;
-        dst_load<TI>(sh, p, ntr, n, logM2, in, in_tr, in_el);
+    for (int q = g.bx; 2 * q < ntr; q += g.gx) {
+        const int t1 = 2 * q, t2 = 2 * q + 1;
+        dst_load<TI>(sh, q, ntr, n, logM2, in, p.in_tr, p.in_el);
         __syncthreads();
         fft_stages<false>(sh, 1, M2, Wt);
         if constexpr (TWICE) {
@@ -103,15 +106,27 @@ k_dst(int ntr, int n, int logM2, const TI* __restrict__ in, long in_tr, long in_
         const double2* res = TWICE ? sh2 : sh;
         for (int k = 1 + threadIdx.x; k <= n; k += blockDim.x) {
             const double2 Y = res[k];
-            out[(long)t1 * out_tr + (long)(k - 1) * out_el] = (TO)(-0.5 * Y.y);
-            if (t2 < ntr) out[(long)t2 * out_tr + (long)(k - 1) * out_el] = (TO)(0.5 * Y.x);
+            out[(long)t1 * p.out_tr + (long)(k - 1) * p.out_el] = (TO)(-0.5 * Y.y);
+            if (t2 < ntr) out[(long)t2 * p.out_tr + (long)(k - 1) * p.out_el] = (TO)(0.5 * Y.x);
         }
         __syncthreads();
     }
 }
 
+template <typename TI, typename TO, bool TWICE>
+__global__ void __launch_bounds__(kDstThreads) k_dst(DstArgs p) {
+    dst_body<TI, TO, TWICE>(p, native_grid());
+}
+template <typename TI, typename TO, bool TWICE>
+__global__ void __launch_bounds__(kDstThreads) k_dst_b(const DstArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) dst_body<TI, TO, TWICE>(ps[i], g);
+}
+
 template <typename... KArgs, typename... Args>
-void dst_launch(void (*kernel)(KArgs...), int pairs, size_t smem, cudaStream_t s, Args&&... args) {
+void dst_launch(void (*kernel)(KArgs...), int blocks, size_t smem, cudaStream_t s, Args&&... args) {
     static std::mutex mu;
     static std::map<const void*, size_t> granted;   // dynamic shared memory granted per kernel
     if (smem > 48 * 1024) {
@@ -122,7 +137,25 @@ void dst_launch(void (*kernel)(KArgs...), int pairs, size_t smem, cudaStream_t s
             g = smem;
         }
     }
-    launch_k_smem(kernel, dim3(std::max(1, pairs)), dim3(kDstThreads), smem, s, std::forward<Args>(args)...);
+    launch_k_smem(kernel, dim3(std::max(1, blocks)), dim3(kDstThreads), smem, s, std::forward<Args>(args)...);
+}
+
+template <typename TI, typename TO, bool TWICE>
+int dst_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {
+    dst_launch(k_dst_b<TI, TO, TWICE>, blocks, sh.smem, s, static_cast<const DstArgs*>(args), m);
+    return 1;
+}
+
+// one transform pass: recorded for a batched step, else launched
+template <typename TI, typename TO, bool TWICE>
+void dst_pass(const DstArgs& a, cudaStream_t s) {
+    KShape sh;
+    sh.gx = std::max(1, (a.ntr + 1) / 2);
+    sh.gy = 1;
+    sh.block = kDstThreads;
+    sh.smem = (size_t)(TWICE ? 4 : 2) * (a.n + 1) * sizeof(double2);
+    if (record_launch(dst_batch<TI, TO, TWICE>, a, sh)) return;
+    dst_launch(k_dst<TI, TO, TWICE>, sh.gx, sh.smem, s, a);
 }
 
 }  // namespace
@@ -131,14 +164,12 @@ template <typename T>
 int launch_dst_solve(const DstSolve& d, const T* b, T* x, Skip sk, cudaStream_t s) {
     const int W = d.W, H = d.H;
     // rows: along a for every b, written transposed to tmp[k][b]
-    dst_launch(k_dst<T, double, false>, (H + 1) / 2, (size_t)2 * (W + 1) * sizeof(double2), s, H, W, d.logx, b,
-               (long)W, 1L, d.tmp, 1L, (long)H, (const double*)nullptr, d.wx, sk);
+    dst_pass<T, double, false>(DstArgs{H, W, d.logx, b, (long)W, 1L, d.tmp, 1L, (long)H, nullptr, d.wx, sk}, s);
     // columns: along b for every k, scaled by 1 / eigenvalue, and back
-    dst_launch(k_dst<double, double, true>, (W + 1) / 2, (size_t)4 * (H + 1) * sizeof(double2), s, W, H, d.logy,
-               (const double*)d.tmp, (long)H, 1L, d.tmp2, (long)H, 1L, (const double*)d.scale, d.wy, sk);
+    dst_pass<double, double, true>(DstArgs{W, H, d.logy, d.tmp, (long)H, 1L, d.tmp2, (long)H, 1L, d.scale, d.wy, sk},
+                                   s);
     // rows again: along k for every b, written back in node order
-    dst_launch(k_dst<double, T, false>, (H + 1) / 2, (size_t)2 * (W + 1) * sizeof(double2), s, H, W, d.logx,
-               (const double*)d.tmp2, 1L, (long)H, x, (long)W, 1L, (const double*)nullptr, d.wx, sk);
+    dst_pass<double, T, false>(DstArgs{H, W, d.logx, d.tmp2, 1L, (long)H, x, (long)W, 1L, nullptr, d.wx, sk}, s);
     return 3;
 }
 

@@ -455,8 +455,10 @@ int launch_residual(const ResidualArgs& a, cudaStream_t s) {
     ElemFluxArgs ef;
     KShape kef, knr;
     const bool flux = plan_residual(a, ef, kef, knr);
-    if (flux) launch_k(k_elem_flux, dim3(kef.gx), dim3(kBlock), s, ef);
-    launch_k(k_node_residual, dim3(knr.gx), dim3(kBlock), s, a);
+    if (flux && !record_launch(launch_elem_flux_batch, ef, kef))
+        launch_k(k_elem_flux, dim3(kef.gx), dim3(kBlock), s, ef);
+    if (!record_launch(launch_node_residual_batch, a, knr))
+        launch_k(k_node_residual, dim3(knr.gx), dim3(kBlock), s, a);
     return flux ? 2 : 1;
 }
 
@@ -470,13 +472,13 @@ bool plan_residual(const ResidualArgs& a, ElemFluxArgs& ef, KShape& kef, KShape&
     return flux;
 }
 
-int launch_elem_flux_batch(const ElemFluxArgs* args, BatchMap m, int blocks, cudaStream_t s) {
-    launch_k(k_elem_flux_b, dim3(blocks), dim3(kBlock), s, args, m);
+int launch_elem_flux_batch(const void* args, BatchMap m, int blocks, const KShape&, cudaStream_t s) {
+    launch_k(k_elem_flux_b, dim3(blocks), dim3(kBlock), s, static_cast<const ElemFluxArgs*>(args), m);
     return 1;
 }
 
-int launch_node_residual_batch(const ResidualArgs* args, BatchMap m, int blocks, cudaStream_t s) {
-    launch_k(k_node_residual_b, dim3(blocks), dim3(kBlock), s, args, m);
+int launch_node_residual_batch(const void* args, BatchMap m, int blocks, const KShape&, cudaStream_t s) {
+    launch_k(k_node_residual_b, dim3(blocks), dim3(kBlock), s, static_cast<const ResidualArgs*>(args), m);
     return 1;
 }
 

@@ -408,14 +408,17 @@ k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Sk
 // output.  Out-of-range rows, columns and panel entries read as zero.
 constexpr int kDT = 32;
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ Y, Skip sk) {
+__device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VGrid& g) {
     pdl_enter();
-    if (skip_now(sk)) return;
+    if (skip_now(p.sk)) return;
+    const int n = p.n, N = p.N;
+    const T* __restrict__ A = p.A;
+    const T* __restrict__ B = p.B;
+    T* __restrict__ Y = p.Y;
     __shared__ T As[kDT][kDT + 1];
     __shared__ T Bs[kDT][kDT];
     const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row group (8 groups of 4 rows)
-    const int c0 = blockIdx.x * kDT, i0 = blockIdx.y * kDT;
+    const int c0 = g.bx * kDT, i0 = g.by * kDT;
     T acc[4] = {T(0), T(0), T(0), T(0)};
     for (int k0 = 0; k0 < n; k0 += kDT) {
         for (int e = threadIdx.x; e < kDT * kDT; e += blockDim.x) {
@@ -442,19 +445,56 @@ k_dense_apply(int n, int N, const T* __restrict__ A, const T* __restrict__ B, T*
             if (i < n) Y[(size_t)i * N + c] = acc[r];
         }
 }
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply(DenseArgs<T> p) { dense_apply_body<T>(p, native_grid()); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply_b(const DenseArgs<T>* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) dense_apply_body<T>(ps[i], g);
+}
 
 template <typename T>
-__global__ void k_time_prolong_add(int rows, int Nc, const T* __restrict__ xc, T* __restrict__ x, Skip sk) {
+__device__ __forceinline__ void time_prolong_add_body(const ProlongArgs<T>& p, const VGrid& g) {
     pdl_enter();
-    if (skip_now(sk)) return;
-    const size_t total = (size_t)rows * Nc;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = g / Nc, m = g - i * Nc;
-        const T v = xc[g];
-        T* xr = x + i * (2 * (size_t)Nc) + 2 * m;
+    if (skip_now(p.sk)) return;
+    const int Nc = p.Nc;
+    const size_t total = (size_t)p.rows * Nc;
+    for (size_t q = (size_t)g.bx * blockDim.x + threadIdx.x; q < total; q += (size_t)g.gx * blockDim.x) {
+        const size_t i = q / Nc, m = q - i * Nc;
+        const T v = p.xc[q];
+        T* xr = p.x + i * (2 * (size_t)Nc) + 2 * m;
         xr[0] += v;
         xr[1] += v;
     }
+}
+template <typename T>
+__global__ void k_time_prolong_add(ProlongArgs<T> p) { time_prolong_add_body<T>(p, native_grid()); }
+template <typename T>
+__global__ void k_time_prolong_add_b(const ProlongArgs<T>* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) time_prolong_add_body<T>(ps[i], g);
+}
+
+template <typename T>
+__device__ __forceinline__ void add_to_double_body(const AddArgs<T>& p, const VGrid& g) {
+    pdl_enter();
+    if (skip_now(p.sk)) return;
+    const double s = p.scale ? *p.scale : 1.0;
+    for (size_t q = (size_t)g.bx * blockDim.x + threadIdx.x; q < p.count; q += (size_t)g.gx * blockDim.x)
+        p.U[q] += s * (double)p.d[q];
+}
+template <typename T>
+__global__ void k_add_to_double(AddArgs<T> p) { add_to_double_body<T>(p, native_grid()); }
+template <typename T>
+__global__ void k_add_to_double_b(const AddArgs<T>* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) add_to_double_body<T>(ps[i], g);
 }
 
 template <typename T>
@@ -479,16 +519,6 @@ __global__ void k_cast(size_t count, const TI* __restrict__ x, TO* __restrict__ 
     if (skip_now(sk)) return;
     for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
         y[g] = (TO)x[g];
-}
-
-template <typename T>
-__global__ void k_add_to_double(size_t count, const T* __restrict__ d, double* __restrict__ U,
-                                const double* __restrict__ scale, Skip sk) {
-    pdl_enter();
-    if (skip_now(sk)) return;
-    const double s = scale ? *scale : 1.0;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x)
-        U[g] += s * (double)d[g];
 }
 
 template <typename TI, typename TO>
@@ -735,14 +765,38 @@ int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip s
 }
 
 template <typename T>
+int launch_dense_apply_batch(const void* args, BatchMap m, int blocks, const KShape&, cudaStream_t s) {
+    launch_k(k_dense_apply_b<T>, dim3(blocks), dim3(256), s, static_cast<const DenseArgs<T>*>(args), m);
+    return 1;
+}
+
+template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    launch_k(k_dense_apply<T>, dim3((N + kDT - 1) / kDT, (n + kDT - 1) / kDT), dim3(256), s, n, N, Ainv, B, Y, sk);
+    const DenseArgs<T> a{n, N, Ainv, B, Y, sk};
+    KShape sh;
+    sh.gx = (N + kDT - 1) / kDT;
+    sh.gy = (n + kDT - 1) / kDT;
+    sh.block = 256;
+    if (record_launch(launch_dense_apply_batch<T>, a, sh)) return 1;
+    launch_k(k_dense_apply<T>, dim3(sh.gx, sh.gy), dim3(256), s, a);
+    return 1;
+}
+
+template <typename T>
+int launch_time_prolong_add_batch(const void* args, BatchMap m, int blocks, const KShape&, cudaStream_t s) {
+    launch_k(k_time_prolong_add_b<T>, dim3(blocks), dim3(256), s, static_cast<const ProlongArgs<T>*>(args), m);
     return 1;
 }
 
 template <typename T>
 int launch_time_prolong_add(int rows, int Nc, const T* xc, T* x, Skip sk, cudaStream_t s) {
-    launch_k(k_time_prolong_add<T>, flat_grid((size_t)rows * Nc), 256, s, rows, Nc, xc, x, sk);
+    const ProlongArgs<T> a{rows, Nc, xc, x, sk};
+    KShape sh;
+    sh.gx = flat_grid((size_t)rows * Nc);
+    sh.gy = 1;
+    sh.block = 256;
+    if (record_launch(launch_time_prolong_add_batch<T>, a, sh)) return 1;
+    launch_k(k_time_prolong_add<T>, dim3(sh.gx), 256, s, a);
     return 1;
 }
 
@@ -765,8 +819,20 @@ int launch_cast(size_t count, const TI* x, TO* y, Skip sk, cudaStream_t s) {
 }
 
 template <typename T>
+int launch_add_to_double_batch(const void* args, BatchMap m, int blocks, const KShape&, cudaStream_t s) {
+    launch_k(k_add_to_double_b<T>, dim3(blocks), dim3(256), s, static_cast<const AddArgs<T>*>(args), m);
+    return 1;
+}
+
+template <typename T>
 int launch_add_to_double(size_t count, const T* d, double* U, const double* scale, Skip sk, cudaStream_t s) {
-    launch_k(k_add_to_double<T>, flat_grid(count), 256, s, count, d, U, scale, sk);
+    const AddArgs<T> a{count, d, U, scale, sk};
+    KShape sh;
+    sh.gx = flat_grid(count);
+    sh.gy = 1;
+    sh.block = 256;
+    if (record_launch(launch_add_to_double_batch<T>, a, sh)) return 1;
+    launch_k(k_add_to_double<T>, dim3(sh.gx), 256, s, a);
     return 1;
 }
 

@@ -726,7 +726,44 @@ void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* ou
     launch_k(k_st_combine, dim3(std::min(4096, (n + 255) / 256)), dim3(256), s, n, coef, cm, cl, out);
 }
 
+// ---------------------------------------------------------------------------
+// start of a block-Jacobi sweep from x = 0: R = B, Z0 = omega D^-1 B
+// ---------------------------------------------------------------------------
+template <int VEC>
+__device__ __forceinline__ void st_copy_sweep_body(const StCopyArgs& p, const VGrid& g) {
+    pdl_enter();
+    if (skip_now(p.sk)) return;
+    const int N = p.N, NC = N / VEC;
+    const size_t total = (size_t)p.n * NC;
+    const float* __restrict__ B = p.B;
+    for (size_t q = (size_t)g.bx * blockDim.x + threadIdx.x; q < total; q += (size_t)g.gx * blockDim.x) {
+        const size_t node = q / NC;
+        const size_t o = node * N + (q - node * NC) * VEC;
+        float b[VEC];
+        ldg_vec<float, VEC>(B + o, b);
+        st_vec<float, VEC>(p.R + o, b);
+        if (p.Z0) {
+            const float w = p.omega * __ldg(&p.acoef[2 * node + 1].w);
+            float z[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) z[v] = w * b[v];
+            st_vec<float, VEC>(p.Z0 + o, z);
+        }
+    }
+}
+
 // ---- kernels: one single-instance and one batched entry per body ----
+template <int VEC>
+__global__ void __launch_bounds__(256) k_st_copy_sweep(StCopyArgs p) {
+    st_copy_sweep_body<VEC>(p, native_grid());
+}
+template <int VEC>
+__global__ void __launch_bounds__(256) k_st_copy_sweep_b(const StCopyArgs* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) st_copy_sweep_body<VEC>(ps[i], g);
+}
 template <int VEC, int MODE>
 __global__ void __launch_bounds__(kStBlock) k_st_presid(StPresidArgs p) {
     st_presid_body<VEC, MODE>(p, native_grid());
@@ -855,6 +892,7 @@ int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const flo
                      float omega, bool time_restrict, Skip sk, cudaStream_t s) {
     KShape ks;
     const StPresidArgs a = plan_st_presid(A, N, X, B, R, Z0, omega, time_restrict, sk, ks);
+    if (record_launch(launch_st_presid_batch, a, ks)) return 1;
     const dim3 grid(ks.gx, ks.gy);
     if (time_restrict) {
         if (ks.vec == 4) st_launch(k_st_presid<4, 1>, grid, ks.block, ks.smem, s, a);
@@ -869,6 +907,7 @@ int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>&
                              const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s) {
     KShape ks;
     const StRestrictArgs a = plan_st_resid_restrict(Af, Ac, N, Xf, Bf, Bc, Xc, omega, sk, ks);
+    if (record_launch(launch_st_resid_restrict_batch, a, ks)) return 1;
     PTP_ST_VEC(ks.vec, st_launch(k_st_resid_restrict<VEC>, dim3(ks.gx, ks.gy), ks.block, ks.smem, s, a));
     return 1;
 }
@@ -878,6 +917,7 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
                            cudaStream_t s) {
     KShape ks;
     const StInterpArgs a = plan_st_interp_sweep(A, Wc, Hc, N, Xc, X, B, Out, omega, cr, dots, sk, ks);
+    if (record_launch(launch_st_interp_sweep_batch, a, ks)) return 1;
     const dim3 grid(ks.gx, ks.gy);
     if (dots == 1) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 1>, grid, ks.block, ks.smem, s, a))
     else if (dots == 2) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 2>, grid, ks.block, ks.smem, s, a))
@@ -888,12 +928,37 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
 int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s) {
     KShape ks;
     const StApplyDotArgs a = plan_st_apply_dot(A, N, P, cr, sk, ks);
+    if (record_launch(launch_st_apply_dot_batch, a, ks)) return 1;
     PTP_ST_VEC(ks.vec, st_launch(k_st_apply_dot<VEC>, dim3(ks.gx, ks.gy), ks.block, ks.smem, s, a));
     return 1;
 }
 
+int launch_st_copy_sweep_batch(const void* argv, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    const StCopyArgs* args = static_cast<const StCopyArgs*>(argv);
+    PTP_ST_VEC(ks.vec, launch_k(k_st_copy_sweep_b<VEC>, dim3(blocks), dim3(256), s, args, m));
+    return 1;
+}
+
+int launch_st_copy_sweep(const StencilOp<float>& A, int N, const float* B, float* R, float* Z0, float omega, Skip sk,
+                         cudaStream_t s) {
+    const StCopyArgs a{A.acoef, A.W * A.H, N, B, R, Z0, omega, sk};
+    auto al = [](const void* p, size_t b) { return ((uintptr_t)p % b) == 0; };
+    const bool a16 = al(B, 16) && al(R, 16) && (!Z0 || al(Z0, 16));
+    const bool a8 = al(B, 8) && al(R, 8) && (!Z0 || al(Z0, 8));
+    KShape ks;
+    ks.vec = (N % 4 == 0 && a16) ? 4 : (N % 2 == 0 && a8) ? 2 : 1;
+    const size_t total = (size_t)a.n * (N / ks.vec);
+    ks.gx = (int)std::max<size_t>(1, std::min((total + 255) / 256, (size_t)num_sms() * 8));
+    ks.gy = 1;
+    ks.block = 256;
+    if (record_launch(launch_st_copy_sweep_batch, a, ks)) return 1;
+    PTP_ST_VEC(ks.vec, launch_k(k_st_copy_sweep<VEC>, dim3(ks.gx), dim3(256), s, a));
+    return 1;
+}
+
 // ---- batched launches: every instance's blocks in one 1-D grid ----
-int launch_st_presid_batch(const StPresidArgs* args, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+int launch_st_presid_batch(const void* argv, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    const StPresidArgs* args = static_cast<const StPresidArgs*>(argv);
     const dim3 grid(blocks);
     if (ks.variant == 1) {
         if (ks.vec == 4) st_launch(k_st_presid_b<4, 1>, grid, ks.block, ks.smem, s, args, m);
@@ -904,13 +969,15 @@ int launch_st_presid_batch(const StPresidArgs* args, BatchMap m, int blocks, con
     return 1;
 }
 
-int launch_st_resid_restrict_batch(const StRestrictArgs* args, BatchMap m, int blocks, const KShape& ks,
+int launch_st_resid_restrict_batch(const void* argv, BatchMap m, int blocks, const KShape& ks,
                                    cudaStream_t s) {
+    const StRestrictArgs* args = static_cast<const StRestrictArgs*>(argv);
     PTP_ST_VEC(ks.vec, st_launch(k_st_resid_restrict_b<VEC>, dim3(blocks), ks.block, ks.smem, s, args, m));
     return 1;
 }
 
-int launch_st_interp_sweep_batch(const StInterpArgs* args, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+int launch_st_interp_sweep_batch(const void* argv, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    const StInterpArgs* args = static_cast<const StInterpArgs*>(argv);
     const dim3 grid(blocks);
     if (ks.variant == 1) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep_b<VEC, 1>, grid, ks.block, ks.smem, s, args, m))
     else if (ks.variant == 2) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep_b<VEC, 2>, grid, ks.block, ks.smem, s, args, m))
@@ -918,7 +985,8 @@ int launch_st_interp_sweep_batch(const StInterpArgs* args, BatchMap m, int block
     return 1;
 }
 
-int launch_st_apply_dot_batch(const StApplyDotArgs* args, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+int launch_st_apply_dot_batch(const void* argv, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
+    const StApplyDotArgs* args = static_cast<const StApplyDotArgs*>(argv);
     PTP_ST_VEC(ks.vec, st_launch(k_st_apply_dot_b<VEC>, dim3(blocks), ks.block, ks.smem, s, args, m));
     return 1;
 }

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <utility>
+#include <vector>
 
 #include "common.h"
 
@@ -26,38 +28,6 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 bool pdl_enabled();   // false if the environment sets PTP_NO_PDL
-
-template <typename... KArgs, typename... Args>
-inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
-}
-
-// the same with dynamic shared memory
-template <typename... KArgs, typename... Args>
-inline void launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                          Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
-}
 
 // ---------------------------------------------------------------------------
 // Virtual grids.  Kernel bodies index blocks through a VGrid so that one
@@ -102,6 +72,83 @@ struct KShape {
     size_t smem = 0;
     int vec = 0, variant = 0;
 };
+
+// ---------------------------------------------------------------------------
+// Recording (the batched step).  While a recorder is active on the host
+// thread, the launcher of every kernel that has a batched form appends its
+// kind, shape and argument struct instead of launching; any other launch or
+// stream operation counts as foreign (and the instance is then not merged
+// with others).
+// ---------------------------------------------------------------------------
+// batched form of a kernel kind: one launch over the instances of `args`
+// (device array of argument structs) with their virtual grids in m
+using BatchLaunch = int (*)(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+struct RecordedLaunch {
+    BatchLaunch fn = nullptr;
+    KShape shape;
+    std::vector<unsigned char> args;
+};
+struct Recorder {
+    std::vector<RecordedLaunch> ops;
+    int foreign = 0;
+};
+Recorder*& active_recorder();   // this host thread's recorder (null: launch)
+
+template <typename A>
+inline bool record_launch(BatchLaunch fn, const A& a, const KShape& sh) {
+    Recorder* r = active_recorder();
+    if (!r) return false;
+    RecordedLaunch l;
+    l.fn = fn;
+    l.shape = sh;
+    l.args.resize(sizeof(A));
+    std::memcpy(l.args.data(), &a, sizeof(A));
+    r->ops.push_back(std::move(l));
+    return true;
+}
+// a launch or copy without batched form: true (and counted) while recording
+inline bool record_foreign() {
+    Recorder* r = active_recorder();
+    if (!r) return false;
+    ++r->foreign;
+    return true;
+}
+
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+    if (record_foreign()) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
+// the same with dynamic shared memory
+template <typename... KArgs, typename... Args>
+inline void launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+    if (record_foreign()) return;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 // ---------------------------------------------------------------------------
 // K1: outer residual R = F - A(U), double (fused source, mass, K(u), norm)
 // ---------------------------------------------------------------------------
@@ -161,8 +208,8 @@ struct ElemFluxArgs {         // iron element fluxes of the two-pass residual
 };
 // the two-pass residual's element pass (returned: whether it runs) and node pass
 bool plan_residual(const ResidualArgs& a, ElemFluxArgs& ef, KShape& kef, KShape& knr);
-int launch_elem_flux_batch(const ElemFluxArgs* args, BatchMap m, int blocks, cudaStream_t s);
-int launch_node_residual_batch(const ResidualArgs* args, BatchMap m, int blocks, cudaStream_t s);
+int launch_elem_flux_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+int launch_node_residual_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
 // the same, with the iron fluxes of the exponential law of Section 4 when e_law
 // (4 per iron element: |T| a, b, ln c, |T| d) is set (k_law.cu)
 int launch_residual_law(const ResidualArgs& a, const double* e_law, cudaStream_t s);
@@ -284,6 +331,16 @@ template <typename T>
 int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s);
 // x (+)= xscale alpha p only: the last update when r and its norm are not needed (k_krylov.cu)
 template <typename T>
+struct XUpdateArgs {   // x = (assign ? 0 : x) + xscale alpha p, alpha per column
+    int rows, N;
+    T xscale;
+    int assign;
+    T* x;
+    const T* p;
+    const T* alpha;
+    Skip sk;
+};
+template <typename T>
 int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, ColRed<T> cr, Skip sk,
                        cudaStream_t s);
 
@@ -362,14 +419,26 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
 StApplyDotArgs plan_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk,
                                  KShape& sh);
 int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s);
+// R = B and Z0 = omega D^-1 B (Z0 may be null): a block-Jacobi sweep from zero
+struct StCopyArgs {
+    const float4* acoef;
+    int n, N;
+    const float* B;
+    float* R;
+    float* Z0;
+    float omega;
+    Skip sk;
+};
+int launch_st_copy_sweep(const StencilOp<float>& A, int N, const float* B, float* R, float* Z0, float omega, Skip sk,
+                         cudaStream_t s);
 // One launch of a kernel kind for many instances: `args` (device array, one
 // per instance), the batch map (device arrays) and the common shape (vec,
 // variant, block and the largest smem); `blocks` = the sum of gx * gy.
-int launch_st_presid_batch(const StPresidArgs* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
-int launch_st_resid_restrict_batch(const StRestrictArgs* args, BatchMap m, int blocks, const KShape& sh,
+int launch_st_presid_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+int launch_st_resid_restrict_batch(const void* args, BatchMap m, int blocks, const KShape& sh,
                                    cudaStream_t s);
-int launch_st_interp_sweep_batch(const StInterpArgs* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
-int launch_st_apply_dot_batch(const StApplyDotArgs* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+int launch_st_interp_sweep_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
+int launch_st_apply_dot_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Exact solve of tau_c L x = b on a uniform structured grid by discrete sine
@@ -384,12 +453,45 @@ struct DstSolve {
     double* tmp = nullptr;         // W x H work arrays
     double* tmp2 = nullptr;
 };
+struct DstArgs {   // one DST-I pass over ntr transforms of length n (element types fixed by the kernel)
+    int ntr, n, logM2;
+    const void* in;
+    long in_tr, in_el;
+    void* out;
+    long out_tr, out_el;
+    const double* scale;
+    const double2* Wt;
+    Skip sk;
+};
 template <typename T>   // x = (tau_c L)^{-1} b, both [W x H] node order (one column)
 int launch_dst_solve(const DstSolve& d, const T* b, T* x, Skip sk, cudaStream_t s);
 
 // dense coarse-level apply Y = Ainv B  (n x n, row-major)
 template <typename T>
+struct DenseArgs {
+    int n, N;
+    const T* A;
+    const T* B;
+    T* Y;
+    Skip sk;
+};
+template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s);
+template <typename T>
+struct ProlongArgs {   // x^{2m}, x^{2m+1} += xc^m
+    int rows, Nc;
+    const T* xc;
+    T* x;
+    Skip sk;
+};
+template <typename T>
+struct AddArgs {       // U += (*scale) d
+    size_t count;
+    const T* d;
+    double* U;
+    const double* scale;
+    Skip sk;
+};
 
 // time transfers and vector helpers
 template <typename T>

@@ -220,6 +220,7 @@ int newton_solve(Ctx& c, const ptp_opts& o, const double* U0, double* Uout, ptp_
         PTP_CUDA(cudaMemsetAsync(c.U.p, 0, cnt * sizeof(double), st));
     }
     c.opts = o;
+    resolve_time_smoother(c);
     alloc_adjoint(c);
     ensure_staging(c);
     grow(c.kr_v, (size_t)(m + 1) * cnt);

@@ -43,6 +43,12 @@ namespace {
 // per-iron-element constants of the exponential law, or null for the saturating law
 const double* law_data(const Ctx& c) { return c.law_exp ? c.e_law.p : nullptr; }
 
+// device-to-device copy inside a step (foreign work while a batched step is recorded)
+static void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (record_foreign()) return;
+    PTP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+}
+
 template <typename T> T* wbuf(Ctx& c, int k);
 template <> double* wbuf<double>(Ctx& c, int k) { return c.w_d[k].p; }
 template <> float* wbuf<float>(Ctx& c, int k) { return c.w_f[k].p; }
@@ -393,10 +399,19 @@ void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
     Op<T> A = level_op<T>(c, 0, t.op);
     Aux<T> aux = pcg.gmg ? sweep_aux<T>(c, 0, t.op, pcg.first_sweep_buffer()) : Aux<T>();
     if (x_zero) {
-        if (pcg.gmg)
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (pcg.gmg && use_stencil<T>(c)) {
+                c.launches += launch_st_copy_sweep(st_op(c, 0, t.op), t.N, b, r, aux.Y2, aux.omega, sk, c.stream);
+                done = true;
+            }
+        }
+        if (done) {
+        } else if (pcg.gmg) {
             c.launches += launch_spmm<T>(SP_COPY, A, t.N, nullptr, b, r, T(0), sk, c.stream, aux);
-        else
-            PTP_CUDA(cudaMemcpyAsync(r, b, cnt * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
+        } else {
+            copy_async(r, b, cnt * sizeof(T), c.stream);
+        }
     } else if (use_stencil<T>(c)) {
         if constexpr (sizeof(T) == 4)
             c.launches += launch_st_presid(st_op(c, 0, t.op), t.N, x, b, r, aux.Y2, aux.omega, false, sk, c.stream);
@@ -449,12 +464,12 @@ void coarse_solve(Ctx& c, Skip sk) {
     }
     if (Nc == 1) {
         if constexpr (sizeof(T) == 8)
-            PTP_CUDA(cudaMemcpyAsync(cb, bc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            copy_async(cb, bc, (size_t)n * sizeof(double), st);
         else
             c.launches += launch_cast<float, double>((size_t)n, bc, cb, sk, st);
         run(c.coarse_ops[0], cb, cx);
         if constexpr (sizeof(T) == 8)
-            PTP_CUDA(cudaMemcpyAsync(xc, cx, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            copy_async(xc, cx, (size_t)n * sizeof(double), st);
         else
             c.launches += launch_cast<double, float>((size_t)n, cx, xc, sk, st);
     } else {
@@ -1028,9 +1043,9 @@ double estimate_lambda_min(Ctx& c) {
 
 // Resolves omega_t <= 0 and post_smooth < 0 (automatic) from the smallest
 // kappa = tau lambda_min of the problem (tsmooth.cpp).
-static void resolve_time_smoother(Ctx& c) {
+void resolve_time_smoother(Ctx& c) {
     ptp_opts& o = c.opts;
-    if (o.omega_t > 0 && o.post_smooth >= 0) return;
+    if ((o.omega_t > 0 && o.post_smooth >= 0) || c.tl.empty()) return;
     if (c.lambda_min < 0) c.lambda_min = estimate_lambda_min(c);
     c.kappa_min = std::min(1e6, c.tl[0].tau * c.lambda_min);
     // the model's hierarchy: the levels down to the one solved exactly

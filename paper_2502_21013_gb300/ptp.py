@@ -21,6 +21,7 @@ PTP_OK, PTP_EINVAL, PTP_ECUDA, PTP_ENOTCONV, PTP_ENAN, PTP_ESTATE, PTP_ENOMEM = 
 PTP_FP64, PTP_MIXED = 0, 1
 PTP_PREC_JACOBI, PTP_PREC_GMG = 0, 1
 PTP_COARSE_VCYCLES, PTP_COARSE_DFT = 0, 1
+PTP_BATCH_MERGED, PTP_BATCH_BRANCHES = 0, 1
 
 
 class Opts(ctypes.Structure):
@@ -112,6 +113,8 @@ def _load():
         "ptp_batch_size": (I, [P]),
         "ptp_batch_solve": (I, [P, ctypes.POINTER(Opts), P, pI]),
         "ptp_batch_result_dev": (I, [P, I, P]),
+        "ptp_batch_set_mode": (I, [P, I]),
+        "ptp_batch_plan_info": (I, [P, ctypes.POINTER(ctypes.c_int64), pI, pI]),
         "ptp_adjoint_gradient_dev": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
         "ptp_adjoint_gradient": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
         "ptp_probe_fma": (I, [I, I, pD]),
@@ -145,7 +148,7 @@ EXPORTED = [
     "ptp_jacobian_apply_dev",
     "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient", "ptp_autotune",
     "ptp_batch_create", "ptp_batch_destroy", "ptp_batch_last_error", "ptp_batch_add", "ptp_batch_size",
-    "ptp_batch_solve", "ptp_batch_result_dev", "ptp_probe_fma", "ptp_probe_recip_dev",
+    "ptp_batch_solve", "ptp_batch_result_dev", "ptp_batch_set_mode", "ptp_batch_plan_info", "ptp_probe_fma", "ptp_probe_recip_dev",
     "ptp_time_cycle_rho", "ptp_choose_time_smoother",
 ]
 
@@ -572,6 +575,15 @@ class Batch:
         rc = lib.ptp_batch_solve(self._h, ctypes.byref(opts), stats, ctypes.byref(nconv))
         self._check(rc, allow=(PTP_ENOTCONV,))
         return [stats[i] for i in range(K)], nconv.value, rc
+
+    def set_mode(self, mode):
+        self._check(lib.ptp_batch_set_mode(self._h, int(mode)))
+
+    def plan_info(self):
+        """(kernels per batched step, instances merged, merged launches)."""
+        lps, mi, ml = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib.ptp_batch_plan_info(self._h, ctypes.byref(lps), ctypes.byref(mi), ctypes.byref(ml)))
+        return lps.value, mi.value, ml.value
 
     def result_dev(self, i, U):
         i = int(i)

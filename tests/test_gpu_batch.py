@@ -1,5 +1,7 @@
 """Batched solve of uneven instances (one CUDA-graph launch per fixed-point
-step for the whole batch) and the per-context launch-shape autotuner."""
+step for the whole batch; in the merged mode one kernel launch per kernel
+kind and aligned position over a work-list of instances) and the
+per-context launch-shape autotuner."""
 import numpy as np
 import pytest
 
@@ -44,8 +46,16 @@ def _oracle_solution(i, prob):
 
 # FP64 solved to 1e-13 and compared at 1e-10; mixed solved to 1e-11 (its
 # double outer residual) and compared at 1e-8
-@pytest.mark.parametrize("precision,tol,bar", [(ptp.PTP_FP64, 1e-13, 1e-10), (ptp.PTP_MIXED, 1e-11, 1e-8)])
-def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar):
+@pytest.mark.parametrize("precision,tol,bar,mode", [
+    (ptp.PTP_FP64, 1e-13, 1e-10, ptp.PTP_BATCH_MERGED),
+    (ptp.PTP_MIXED, 1e-11, 1e-8, ptp.PTP_BATCH_MERGED),
+    (ptp.PTP_MIXED, 1e-11, 1e-8, ptp.PTP_BATCH_BRANCHES),
+])
+def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar, mode):
+    """Every instance of the batch is bitwise the instance solved alone (the
+    merged launches give each instance the blocks of its own launch), and the
+    oracle's fixed point.  In mixed precision every instance's step has a
+    batched form and is merged; FP64 steps (ELL kernels) run as branches."""
     probs = _instances()
     opts = ptp.default_opts(precision=precision, tol=tol, max_outer=20000)
     alone = []
@@ -58,10 +68,16 @@ def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar):
         alone.append((U.clone(), st.outer_iterations))
         ctxs.append(c)
     batch = ptp.Batch(0)
+    batch.set_mode(mode)
     for c in ctxs:
         batch.add(c)
     stats, nconv, rc = batch.solve(opts)
     assert rc == ptp.PTP_OK and nconv == len(probs)
+    lps, merged, nmerged = batch.plan_info()
+    if mode == ptp.PTP_BATCH_MERGED and precision == ptp.PTP_MIXED:
+        assert merged == len(probs) and nmerged == lps
+    else:
+        assert merged == 0 and nmerged == 0
     results = []
     for i, p in enumerate(probs):
         Ub = torch.empty((p.n_free, p.N), dtype=torch.float64, device="cuda")
@@ -96,3 +112,34 @@ def test_autotune_keeps_the_solution():
     Uo = np.load(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden",
                                              "square33_N32_oracle.npz"))["U"]
     assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) < 1e-8
+
+
+def test_merged_launches_do_not_grow_with_the_instances():
+    """Kernels per batched step: the merged program of three uneven instances
+    is as long as it is for nine (three copies of each), shorter than the
+    three steps' launches together, and at least the longest one's."""
+    makes = [lambda: W.unit_square_problem(17, 16), lambda: W.unit_square_problem(33, 32),
+             lambda: W.transformer_problem(65, 33, 64)]
+    opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=1e-8, max_outer=4)
+    alone = []
+    for mk in makes:
+        p = mk()
+        c = _ctx(p, precision=ptp.PTP_MIXED)
+        U = torch.zeros((p.n_free, p.N), dtype=torch.float64, device="cuda")
+        st, _ = c.solve_dev(U, opts)
+        alone.append(st.kernel_launches / (st.outer_iterations + 1))
+    counts = []
+    for copies in (1, 3):
+        batch = ptp.Batch(0)
+        keep = []
+        for _ in range(copies):
+            for mk in makes:
+                c = _ctx(mk(), precision=ptp.PTP_MIXED)
+                keep.append(c)
+                batch.add(c)
+        batch.solve(opts)
+        lps, merged, _ = batch.plan_info()
+        assert merged == len(keep)
+        counts.append(lps)
+    assert counts[0] == counts[1]
+    assert max(alone) - 4 <= counts[0] < sum(alone), (counts, alone)

@@ -24,10 +24,12 @@ def lambda_min(prob):
     return 1.0 / abs(mu[0]), d
 
 
+# (name, problem, expected choice: "fast" = V(1,0) with omega 0.95, "robust" =
+# damping <= 0.6, where V(1,0) with omega 0.95 would amplify the slow modes)
 CASES = [
-    ("square33_N32", lambda: W.unit_square_problem(33, 32), (0, 0.95)),
+    ("square33_N32", lambda: W.unit_square_problem(33, 32), "fast"),
     ("transformer65x33_N32", lambda: W.transformer_problem(65, 33, 32), None),
-    ("paper41x53_N16", lambda: W.paper_transformer_problem(41, 53, 16), (1, 0.5)),
+    ("paper41x53_N16", lambda: W.paper_transformer_problem(41, 53, 16), "robust"),
 ]
 
 
@@ -47,8 +49,11 @@ def test_kappa_estimate_and_choice(name, make, expect):
     levels = [prob.N >> k for k in range(st.time_levels)]
     post, omega, _ = ptp.choose_time_smoother(levels, 0.9 * st.kappa_min)
     assert (st.post_smooth, st.omega_t) == (post, omega)
-    if expect is not None:
-        assert (st.post_smooth, st.omega_t) == expect
+    if expect == "fast":
+        assert (st.post_smooth, st.omega_t) == (0, 0.95)
+    elif expect == "robust":
+        assert st.omega_t <= 0.6
+        assert ptp.time_cycle_rho(levels, 0.9 * st.kappa_min, 1, 0, 0.95) > 1.0
 
 
 def test_explicit_values_are_kept():
@@ -77,5 +82,5 @@ def test_paper_transformer_converges_with_the_default_cycle(precision, tol, bar)
     c.setup(o)
     U, st, rc = c.solve(o)
     assert rc == ptp.PTP_OK
-    assert st.post_smooth == 1
+    assert st.omega_t <= 0.6
     assert np.linalg.norm(U - ref.U) / np.linalg.norm(ref.U) < bar
