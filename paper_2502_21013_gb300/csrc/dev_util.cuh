@@ -143,7 +143,7 @@ __device__ __forceinline__ double2 safe_cdiv(double2 a, double2 b) {
 constexpr int kGroup = 32;
 
 template <typename T, int VEC, int NQ, int FIN>
-__device__ void col_reduce_finish(T (&acc)[NQ][VEC], int N, int NC, int rpb, ColRed<T> cr) {
+__device__ void col_reduce_finish(T (&acc)[NQ][VEC], int N, int NC, int rpb, const ColRed<T>& cr, const VGrid& vg) {
     __shared__ T sm[NQ * kMaxBlock * VEC];
     __shared__ int stage;
     __shared__ int all_conv;
@@ -152,19 +152,19 @@ __device__ void col_reduce_finish(T (&acc)[NQ][VEC], int N, int NC, int rpb, Col
 #pragma unroll
         for (int v = 0; v < VEC; ++v) sm[(q * blockDim.x + threadIdx.x) * VEC + v] = acc[q][v];
     __syncthreads();
-    const int G = gridDim.x;
+    const int G = vg.gx;
     const int QN = NQ * N;
     for (int e = threadIdx.x; e < QN; e += blockDim.x) {
         const int q = e / N, col = e - q * N;
         const int chunk = col / VEC, v = col - chunk * VEC;
         T s = T(0);
         for (int r = 0; r < rpb; ++r) s += sm[(q * blockDim.x + r * NC + chunk) * VEC + v];
-        cr.partials[(size_t)blockIdx.x * QN + e] = s;
+        cr.partials[(size_t)vg.bx * QN + e] = s;
     }
     __threadfence();
     __syncthreads();
     const int ng = (G + kGroup - 1) / kGroup;
-    const int g = blockIdx.x / kGroup;
+    const int g = vg.bx / kGroup;
     const int b0 = g * kGroup;
     const int gsz = min(kGroup, G - b0);
     T* part2 = cr.partials + (size_t)G * QN;

@@ -193,7 +193,7 @@ k_capply_alpha(Op<double> op, int D, const double2* __restrict__ ck, double tau,
         acc[0][0] += pv.x * y.x - pv.y * y.y;
         acc[0][1] += pv.x * y.y + pv.y * y.x;
     }
-    col_reduce_finish<double, VEC, 1, FIN_C_ALPHA>(acc, D, NC, rpb, cr);
+    col_reduce_finish<double, VEC, 1, FIN_C_ALPHA>(acc, D, NC, rpb, cr, native_grid());
 }
 
 // x += alpha p (x = alpha p when assign) ; r -= alpha q ; rr = |r|^2 and the convergence test
@@ -220,7 +220,7 @@ k_cupdate(int rows, int D, int assign, double* x, const double* __restrict__ p, 
         acc[0][0] += rv.x * rv.x;
         acc[0][1] += rv.y * rv.y;
     }
-    col_reduce_finish<double, VEC, 1, FIN_C_UPDATE>(acc, D, NC, rpb, cr);
+    col_reduce_finish<double, VEC, 1, FIN_C_UPDATE>(acc, D, NC, rpb, cr, native_grid());
 }
 
 // first: rho = r^T z, bb = rr = |r|^2 ; else beta = (r^T z) / rho, rho = r^T z
@@ -245,7 +245,7 @@ k_cdot_rz(int rows, int D, const double* __restrict__ r, const double* __restric
             acc[1][1] += rv.y * rv.y;
         }
     }
-    col_reduce_finish<double, VEC, NQ, FIRST ? FIN_C_RZ_FIRST : FIN_C_RZ_NEXT>(acc, D, NC, rpb, cr);
+    col_reduce_finish<double, VEC, NQ, FIRST ? FIN_C_RZ_FIRST : FIN_C_RZ_NEXT>(acc, D, NC, rpb, cr, native_grid());
 }
 
 // p = z + beta p

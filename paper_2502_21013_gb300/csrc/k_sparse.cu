@@ -17,6 +17,7 @@
 #include <map>
 #include <mutex>
 
+#include "dev_async.cuh"
 #include "dev_util.cuh"
 
 namespace ptp {
@@ -181,15 +182,85 @@ __device__ __forceinline__ void fused_sweep(const Aux<T>& aux, int N, int row, i
 }
 
 
+// argument structs of the row kernels (one per launch; arrays of them in a batched launch)
+template <typename T>
+struct SpmmArgs {
+    Op<T> op;
+    int N;
+    const T* X;
+    const T* B;
+    T* Y;
+    T omega;
+    Skip sk;
+    Aux<T> aux;
+};
+template <typename T>
+struct AlphaArgs {
+    Op<T> op;
+    int N;
+    const T* p;
+    T* q;
+    ColRed<T> cr;
+    Skip sk;
+};
+template <typename T>
+struct UpdateArgs {
+    Op<T> op;
+    int N;
+    T xscale;
+    int assign;
+    T* x;
+    const T* p;
+    T* r;
+    const T* q;
+    T* z;
+    ColRed<T> cr;
+    Skip sk;
+    Aux<T> aux;
+};
+template <typename T>
+struct InitJacArgs {
+    Op<T> op;
+    int N;
+    const T* r;
+    T* z;
+    T* p;
+    ColRed<T> cr;
+    Skip sk;
+};
+template <typename T>
+struct DotRzArgs {
+    int rows, N;
+    const T* r;
+    const T* z;
+    ColRed<T> cr;
+    int first;
+    Skip sk;
+};
+template <typename T>
+struct DirArgs {
+    int rows, N;
+    const T* z;
+    T* p;
+    ColRed<T> cr;
+    Skip sk;
+};
+
 template <typename T, int VEC, int MODE>
-__global__ void __launch_bounds__(kMaxBlock)
-k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, T omega, Skip sk,
-       Aux<T> aux) {
+__device__ __forceinline__ void spmm_body(const SpmmArgs<T>& a_, const VGrid& g_) {
+    const Op<T>& op = a_.op;
+    const int N = a_.N;
+    const T* __restrict__ X = a_.X;
+    const T* __restrict__ B = a_.B;
+    T* Y = a_.Y;
+    const T omega = a_.omega;
+    const Skip& sk = a_.sk;
+    const Aux<T>& aux = a_.aux;
     pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC;
     const int rpb = blockDim.x / NC;
-    PTP_ROW_LOOP(op.rows, NC, rpb) {
+    PTP_ROW_LOOP_G(op.rows, NC, rpb, g_) {
         if constexpr (MODE == SP_APPLY || MODE == SP_RESTRICT) {
             T acc[VEC];
             row_apply<T, VEC>(op, N, row, col0, X, acc);
@@ -253,15 +324,20 @@ k_spmm(Op<T> op, int N, const T* __restrict__ X, const T* __restrict__ B, T* Y, 
 
 // q = A p ; alpha = rho / (p . q)
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kMaxBlock)
-k_pcg_apply_alpha(Op<T> op, int N, const T* __restrict__ p, T* __restrict__ q, ColRed<T> cr, Skip sk) {
+__device__ __forceinline__ void apply_alpha_body(const AlphaArgs<T>& a_, const VGrid& g_) {
+    const Op<T>& op = a_.op;
+    const int N = a_.N;
+    const T* __restrict__ p = a_.p;
+    T* __restrict__ q = a_.q;
+    const ColRed<T>& cr = a_.cr;
+    const Skip& sk = a_.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     T acc[1][VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[0][v] = T(0);
-    PTP_ROW_LOOP(op.rows, NC, rpb) {
+    PTP_ROW_LOOP_G(op.rows, NC, rpb, g_) {
         T y[VEC], x[VEC];
         row_apply<T, VEC>(op, N, row, col0, p, y);
         ldg_vec<T, VEC>(p + (size_t)row * N + col0, x);
@@ -269,14 +345,24 @@ k_pcg_apply_alpha(Op<T> op, int N, const T* __restrict__ p, T* __restrict__ q, C
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[0][v] += x[v] * y[v];
     }
-    col_reduce_finish<T, VEC, 1, FIN_ALPHA>(acc, N, NC, rpb, cr);
+    col_reduce_finish<T, VEC, 1, FIN_ALPHA>(acc, N, NC, rpb, cr, g_);
 }
 
 // x += xscale alpha p ; r -= alpha q ; (jacobi) z = r / D ; dots (rz, rr) or (rr)
 template <typename T, int VEC, bool JAC>
-__global__ void __launch_bounds__(kMaxBlock)
-k_pcg_update(Op<T> op, int N, T xscale, int assign, T* x, const T* __restrict__ p, T* r,
-             const T* __restrict__ q, T* z, ColRed<T> cr, Skip sk, Aux<T> aux) {
+__device__ __forceinline__ void pcg_update_body(const UpdateArgs<T>& a_, const VGrid& g_) {
+    const Op<T>& op = a_.op;
+    const int N = a_.N;
+    const T xscale = a_.xscale;
+    const int assign = a_.assign;
+    T* x = a_.x;
+    const T* __restrict__ p = a_.p;
+    T* r = a_.r;
+    const T* __restrict__ q = a_.q;
+    T* z = a_.z;
+    const ColRed<T>& cr = a_.cr;
+    const Skip& sk = a_.sk;
+    const Aux<T>& aux = a_.aux;
     pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
@@ -287,7 +373,7 @@ k_pcg_update(Op<T> op, int N, T xscale, int assign, T* x, const T* __restrict__ 
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[qq][v] = T(0);
     const T* alpha = cr.col + S_ALPHA * N;
-    PTP_ROW_LOOP(op.rows, NC, rpb) {
+    PTP_ROW_LOOP_G(op.rows, NC, rpb, g_) {
         const size_t o = (size_t)row * N + col0;
         T pv[VEC], qv[VEC], xv[VEC], rv[VEC], al[VEC];
         ldg_vec<T, VEC>(p + o, pv);
@@ -324,21 +410,26 @@ k_pcg_update(Op<T> op, int N, T xscale, int assign, T* x, const T* __restrict__ 
             fused_sweep<T, VEC>(aux, N, row, col0, rv);
         }
     }
-    col_reduce_finish<T, VEC, NQ, JAC ? FIN_UPDATE_JACOBI : FIN_UPDATE_RR>(acc, N, NC, rpb, cr);
+    col_reduce_finish<T, VEC, NQ, JAC ? FIN_UPDATE_JACOBI : FIN_UPDATE_RR>(acc, N, NC, rpb, cr, g_);
 }
 
 // z = r / D ; p = z ; rho = r.z ; bb = rr = r.r
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kMaxBlock)
-k_pcg_init_jacobi(Op<T> op, int N, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
-                  ColRed<T> cr, Skip sk) {
+__device__ __forceinline__ void init_jacobi_body(const InitJacArgs<T>& a_, const VGrid& g_) {
+    const Op<T>& op = a_.op;
+    const int N = a_.N;
+    const T* __restrict__ r = a_.r;
+    T* __restrict__ z = a_.z;
+    T* __restrict__ p = a_.p;
+    const ColRed<T>& cr = a_.cr;
+    const Skip& sk = a_.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     T acc[2][VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[0][v] = acc[1][v] = T(0);
-    PTP_ROW_LOOP(op.rows, NC, rpb) {
+    PTP_ROW_LOOP_G(op.rows, NC, rpb, g_) {
         const size_t o = (size_t)row * N + col0;
         T rv[VEC], zv[VEC];
         ldg_vec<T, VEC>(r + o, rv);
@@ -352,20 +443,25 @@ k_pcg_init_jacobi(Op<T> op, int N, const T* __restrict__ r, T* __restrict__ z, T
         st_vec<T, VEC>(z + o, zv);
         st_vec<T, VEC>(p + o, zv);
     }
-    col_reduce_finish<T, VEC, 2, FIN_RZ_FIRST>(acc, N, NC, rpb, cr);
+    col_reduce_finish<T, VEC, 2, FIN_RZ_FIRST>(acc, N, NC, rpb, cr, g_);
 }
 
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kMaxBlock)
-k_pcg_dot_rz(int rows, int N, const T* __restrict__ r, const T* __restrict__ z, ColRed<T> cr, int first,
-             Skip sk) {
+__device__ __forceinline__ void dot_rz_body(const DotRzArgs<T>& a_, const VGrid& g_) {
+    const int rows = a_.rows;
+    const int N = a_.N;
+    const T* __restrict__ r = a_.r;
+    const T* __restrict__ z = a_.z;
+    const ColRed<T>& cr = a_.cr;
+    const int first = a_.first;
+    const Skip& sk = a_.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     T acc[2][VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[0][v] = acc[1][v] = T(0);
-    PTP_ROW_LOOP(rows, NC, rpb) {
+    PTP_ROW_LOOP_G(rows, NC, rpb, g_) {
         const size_t o = (size_t)row * N + col0;
         T rv[VEC], zv[VEC];
         ldg_vec<T, VEC>(r + o, rv);
@@ -377,20 +473,25 @@ k_pcg_dot_rz(int rows, int N, const T* __restrict__ r, const T* __restrict__ z, 
         }
     }
     if (first)
-        col_reduce_finish<T, VEC, 2, FIN_RZ_FIRST>(acc, N, NC, rpb, cr);
+        col_reduce_finish<T, VEC, 2, FIN_RZ_FIRST>(acc, N, NC, rpb, cr, g_);
     else
-        col_reduce_finish<T, VEC, 2, FIN_RZ_NEXT>(acc, N, NC, rpb, cr);
+        col_reduce_finish<T, VEC, 2, FIN_RZ_NEXT>(acc, N, NC, rpb, cr, g_);
 }
 
 // p = z + beta p
 template <typename T, int VEC>
-__global__ void __launch_bounds__(kMaxBlock)
-k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Skip sk) {
+__device__ __forceinline__ void direction_body(const DirArgs<T>& a_, const VGrid& g_) {
+    const int rows = a_.rows;
+    const int N = a_.N;
+    const T* __restrict__ z = a_.z;
+    T* p = a_.p;
+    const ColRed<T>& cr = a_.cr;
+    const Skip& sk = a_.sk;
     pdl_enter();
     if (skip_now(sk)) return;
     const int NC = N / VEC, rpb = blockDim.x / NC;
     const T* beta = cr.col + S_BETA * N;
-    PTP_ROW_LOOP(rows, NC, rpb) {
+    PTP_ROW_LOOP_G(rows, NC, rpb, g_) {
         const size_t o = (size_t)row * N + col0;
         T zv[VEC], pv[VEC];
         ldg_vec<T, VEC>(z + o, zv);
@@ -401,39 +502,81 @@ k_pcg_direction(int rows, int N, const T* __restrict__ z, T* p, ColRed<T> cr, Sk
     }
 }
 
-// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600),
-// tiled through shared memory: a block computes a 32 x 32 tile of Y
-// (rows i, columns c; four rows per thread) from 32-wide panels of Ainv and
-// B, so each Ainv and B value is read once per tile instead of once per
-// output.  Out-of-range rows, columns and panel entries read as zero.
+
+// ---- kernels: one single-instance and one batched entry per body ----
+#define PTP_ROW_KERNELS(NAME, BODY, ARGS, TPARAMS, TARGS)                                            \
+    template <TPARAMS>                                                                              \
+    __global__ void __launch_bounds__(kMaxBlock) NAME(ARGS a) { BODY<TARGS>(a, native_grid()); }    \
+    template <TPARAMS>                                                                              \
+    __global__ void __launch_bounds__(kMaxBlock) NAME##_b(const ARGS* __restrict__ ps, BatchMap m) { \
+        pdl_enter();                                                                                \
+        int i;                                                                                      \
+        VGrid g;                                                                                    \
+        if (batch_block(m, i, g)) BODY<TARGS>(ps[i], g);                                            \
+    }
+#define PTP_COMMA ,
+PTP_ROW_KERNELS(k_spmm, spmm_body, SpmmArgs<T>, typename T PTP_COMMA int VEC PTP_COMMA int MODE, T PTP_COMMA VEC PTP_COMMA MODE)
+PTP_ROW_KERNELS(k_pcg_apply_alpha, apply_alpha_body, AlphaArgs<T>, typename T PTP_COMMA int VEC, T PTP_COMMA VEC)
+PTP_ROW_KERNELS(k_pcg_update, pcg_update_body, UpdateArgs<T>, typename T PTP_COMMA int VEC PTP_COMMA bool JAC,
+                T PTP_COMMA VEC PTP_COMMA JAC)
+PTP_ROW_KERNELS(k_pcg_init_jacobi, init_jacobi_body, InitJacArgs<T>, typename T PTP_COMMA int VEC, T PTP_COMMA VEC)
+PTP_ROW_KERNELS(k_pcg_dot_rz, dot_rz_body, DotRzArgs<T>, typename T PTP_COMMA int VEC, T PTP_COMMA VEC)
+PTP_ROW_KERNELS(k_pcg_direction, direction_body, DirArgs<T>, typename T PTP_COMMA int VEC, T PTP_COMMA VEC)
+#undef PTP_ROW_KERNELS
+#undef PTP_COMMA
+
+// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600).
+// A block computes a 32 x 32 tile of Y (rows i, columns c; four rows per
+// thread) from the 32 rows of Ainv and the 32 columns of B it needs, copied
+// to shared memory kc values of k at a time (kc = n when it fits, so one
+// chunk in float).  Every copy of a chunk is in flight at once (cp.async,
+// zero-filled outside the matrices): this small product is bound by latency,
+// and one round trip per chunk replaces one per 32-wide panel.
 constexpr int kDT = 32;
+constexpr size_t kDenseSmem = 96 * 1024;
+template <typename T>
+int dense_chunk(int n) {   // k values per chunk
+    const int fit = (int)((kDenseSmem / sizeof(T) - kDT) / (2 * kDT));
+    return std::max(1, std::min(n, fit));
+}
+template <typename T>
+size_t dense_smem(int kc) { return (size_t)(kDT * (kc + 1) + kc * kDT) * sizeof(T); }
+
 template <typename T>
 __device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VGrid& g) {
     pdl_enter();
     if (skip_now(p.sk)) return;
-    const int n = p.n, N = p.N;
+    const int n = p.n, N = p.N, kc = p.kc;
     const T* __restrict__ A = p.A;
     const T* __restrict__ B = p.B;
     T* __restrict__ Y = p.Y;
-    __shared__ T As[kDT][kDT + 1];
-    __shared__ T Bs[kDT][kDT];
+    extern __shared__ __align__(16) unsigned char dense_smem_raw[];
+    T* As = reinterpret_cast<T*>(dense_smem_raw);   // [32][kc + 1]
+    T* Bs = As + kDT * (kc + 1);                    // [kc][32]
     const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row group (8 groups of 4 rows)
     const int c0 = g.bx * kDT, i0 = g.by * kDT;
     T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int k0 = 0; k0 < n; k0 += kDT) {
-        for (int e = threadIdx.x; e < kDT * kDT; e += blockDim.x) {
-            const int r = e / kDT, q = e - r * kDT;
-            const int ia = i0 + r, ka = k0 + q;
-            As[r][q] = (ia < n && ka < n) ? __ldg(A + (size_t)ia * n + ka) : T(0);
-            const int kb = k0 + r, cb = c0 + q;
-            Bs[r][q] = (kb < n && cb < N) ? __ldg(B + (size_t)kb * N + cb) : T(0);
+    for (int k0 = 0; k0 < n; k0 += kc) {
+        const int kk = min(kc, n - k0);
+        for (int e = threadIdx.x; e < kDT * kc; e += blockDim.x) {
+            const int r = e / kc, q = e - r * kc;
+            const bool ok = i0 + r < n && q < kk;
+            cp_async<sizeof(T)>(As + r * (kc + 1) + q, ok ? A + (size_t)(i0 + r) * n + (k0 + q) : A, ok);
         }
+        for (int e = threadIdx.x; e < kc * kDT; e += blockDim.x) {
+            const int r = e / kDT, q = e - r * kDT;
+            const bool ok = r < kk && c0 + q < N;
+            cp_async<sizeof(T)>(Bs + r * kDT + q, ok ? B + (size_t)(k0 + r) * N + (c0 + q) : B, ok);
+        }
+        cp_commit();
+        cp_wait<0>();
         __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < kDT; ++kk) {
-            const T b = Bs[kk][tx];
+        const T* ar = As + (ty * 4) * (kc + 1);
+#pragma unroll 4
+        for (int k = 0; k < kk; ++k) {
+            const T b = Bs[k * kDT + tx];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) acc[r] += As[ty * 4 + r][kk] * b;
+            for (int r = 0; r < 4; ++r) acc[r] += ar[r * (kc + 1) + k] * b;
         }
         __syncthreads();
     }
@@ -675,6 +818,85 @@ size_t reduction_partials(int Nmax) { return (size_t)num_sms() * 9 * 2 * (size_t
         default: { constexpr int VEC = 1; __VA_ARGS__; } break;  \
     }
 
+// launch shape of a row kernel as a KShape (variant: the template's mode)
+template <typename... KArgs>
+KShape row_shape(void (*kernel)(KArgs...), int rows, int N, int vec, int variant) {
+    const Launch l = row_launch(rows, N, vec, (const void*)kernel);
+    KShape sh;
+    sh.gx = l.grid;
+    sh.gy = 1;
+    sh.block = l.block;
+    sh.vec = vec;
+    sh.variant = variant;
+    return sh;
+}
+
+// recorded for a batched step, else launched
+template <typename A, typename... KArgs>
+void row_go(void (*kernel)(KArgs...), BatchLaunch bfn, int rows, int N, int vec, int variant, cudaStream_t s,
+            const A& a) {
+    const KShape sh = row_shape(kernel, rows, N, vec, variant);
+    if (record_launch(bfn, a, sh)) return;
+    launch_k(kernel, dim3(sh.gx), dim3(sh.block), s, a);
+}
+
+// batched launch of a row-kernel family: VEC from the shape (4 only in float;
+// the time restriction needs VEC >= 2)
+#define PTP_ROW_BATCH(FN, KB, ARGS, TPARAMS, ...)                                                   \
+    template <TPARAMS>                                                                              \
+    int FN(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {             \
+        const ARGS* a = static_cast<const ARGS*>(args);                                             \
+        const dim3 g(blocks), b(sh.block);                                                          \
+        if (sh.vec == 4) {                                                                          \
+            if constexpr (sizeof(T) == 4) launch_k(KB<T, 4, ##__VA_ARGS__>, g, b, s, a, m);         \
+        } else if (sh.vec == 2) {                                                                   \
+            launch_k(KB<T, 2, ##__VA_ARGS__>, g, b, s, a, m);                                       \
+        } else {                                                                                    \
+            one_vec<T>(KB<T, 1, ##__VA_ARGS__>, g, b, s, a, m);                                     \
+        }                                                                                           \
+        return 1;                                                                                   \
+    }
+
+template <typename T, typename... KArgs, typename... Args>
+void one_vec(void (*kernel)(KArgs...), dim3 g, dim3 b, cudaStream_t s, Args&&... args) {
+    launch_k(kernel, g, b, s, std::forward<Args>(args)...);
+}
+
+#define PTP_COMMA ,
+PTP_ROW_BATCH(alpha_batch, k_pcg_apply_alpha_b, AlphaArgs<T>, typename T)
+PTP_ROW_BATCH(init_jacobi_batch, k_pcg_init_jacobi_b, InitJacArgs<T>, typename T)
+PTP_ROW_BATCH(dot_rz_batch, k_pcg_dot_rz_b, DotRzArgs<T>, typename T)
+PTP_ROW_BATCH(direction_batch, k_pcg_direction_b, DirArgs<T>, typename T)
+PTP_ROW_BATCH(update_batch, k_pcg_update_b, UpdateArgs<T>, typename T PTP_COMMA bool JAC, JAC)
+#undef PTP_COMMA
+#undef PTP_ROW_BATCH
+
+template <typename T, int MODE>
+int spmm_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {
+    const SpmmArgs<T>* a = static_cast<const SpmmArgs<T>*>(args);
+    const dim3 g(blocks), b(sh.block);
+    if (sh.vec == 4) {
+        if constexpr (sizeof(T) == 4) launch_k(k_spmm_b<T, 4, MODE>, g, b, s, a, m);
+    } else if (sh.vec == 2) {
+        launch_k(k_spmm_b<T, 2, MODE>, g, b, s, a, m);
+    } else {
+        if constexpr (MODE != SP_PRESID_RESTRICT) launch_k(k_spmm_b<T, 1, MODE>, g, b, s, a, m);
+    }
+    return 1;
+}
+
+template <typename T, int MODE>
+void spmm_go(const SpmmArgs<T>& a, int vec, cudaStream_t s) {
+    const int rows = a.op.rows, N = a.N;
+    if (vec == 4) {
+        if constexpr (sizeof(T) == 4) row_go(k_spmm<T, 4, MODE>, spmm_batch<T, MODE>, rows, N, 4, MODE, s, a);
+    } else if (vec == 2) {
+        row_go(k_spmm<T, 2, MODE>, spmm_batch<T, MODE>, rows, N, 2, MODE, s, a);
+    } else {
+        if constexpr (MODE != SP_PRESID_RESTRICT) row_go(k_spmm<T, 1, MODE>, spmm_batch<T, MODE>, rows, N, 1, MODE, s, a);
+    }
+}
+
 template <typename T>
 int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* Y, T omega, Skip sk,
                 cudaStream_t s, Aux<T> aux) {
@@ -682,41 +904,37 @@ int launch_spmm(SpMode mode, const Op<T>& op, int N, const T* X, const T* B, T* 
     int vec = pick_vec<T>(N, {X, B, Y, aux.Y2}, restrict_time);
     if (sizeof(T) == 8 && vec == 4) vec = 2;
     if (restrict_time && sizeof(T) == 4 && vec == 4 && !aligned(Y, 8)) vec = 2;
-#define PTP_SPMM_CASE(M)                                                                          \
-    case M:                                                                                       \
-        if constexpr (M == SP_PRESID_RESTRICT) {                                                  \
-            if (vec == 4) {                                                                       \
-                if constexpr (sizeof(T) == 4)                                                     \
-                    launch_rows(k_spmm<T, 4, M>, op.rows, N, vec, s, op, N, X, B, Y, omega, sk, aux);        \
-            } else                                                                                \
-                launch_rows(k_spmm<T, 2, M>, op.rows, N, vec, s, op, N, X, B, Y, omega, sk, aux);            \
-        } else {                                                                                  \
-            PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)                       \
-                                      launch_rows(k_spmm<T, VEC, M>, op.rows, N, vec, s, op, N, X, B, Y, \
-                                                                                 omega, sk, aux)); \
-        }                                                                                         \
-        break;
+    const SpmmArgs<T> a{op, N, X, B, Y, omega, sk, aux};
     switch (mode) {
-        PTP_SPMM_CASE(SP_APPLY)
-        PTP_SPMM_CASE(SP_RESID)
-        PTP_SPMM_CASE(SP_JACOBI)
-        PTP_SPMM_CASE(SP_PRESID)
-        PTP_SPMM_CASE(SP_PRESID_RESTRICT)
-        PTP_SPMM_CASE(SP_INTERP_ADD)
-        PTP_SPMM_CASE(SP_RESTRICT)
-        PTP_SPMM_CASE(SP_PAPPLY)
-        PTP_SPMM_CASE(SP_COPY)
+        case SP_APPLY: spmm_go<T, SP_APPLY>(a, vec, s); break;
+        case SP_RESID: spmm_go<T, SP_RESID>(a, vec, s); break;
+        case SP_JACOBI: spmm_go<T, SP_JACOBI>(a, vec, s); break;
+        case SP_PRESID: spmm_go<T, SP_PRESID>(a, vec, s); break;
+        case SP_PRESID_RESTRICT: spmm_go<T, SP_PRESID_RESTRICT>(a, vec, s); break;
+        case SP_INTERP_ADD: spmm_go<T, SP_INTERP_ADD>(a, vec, s); break;
+        case SP_RESTRICT: spmm_go<T, SP_RESTRICT>(a, vec, s); break;
+        case SP_PAPPLY: spmm_go<T, SP_PAPPLY>(a, vec, s); break;
+        case SP_COPY: spmm_go<T, SP_COPY>(a, vec, s); break;
     }
-#undef PTP_SPMM_CASE
     return 1;
 }
+
+// the PCG row kernels: vec 4 (float) / 2 / 1 as for the SpMM
+#define PTP_ROW_GO(K, BATCH, ROWS, VARIANT, ...)                                                   \
+    if (vec == 4) {                                                                                 \
+        if constexpr (sizeof(T) == 4) row_go(K<T, 4, ##__VA_ARGS__>, BATCH, ROWS, N, 4, VARIANT, s, a); \
+    } else if (vec == 2) {                                                                          \
+        row_go(K<T, 2, ##__VA_ARGS__>, BATCH, ROWS, N, 2, VARIANT, s, a);                           \
+    } else {                                                                                        \
+        row_go(K<T, 1, ##__VA_ARGS__>, BATCH, ROWS, N, 1, VARIANT, s, a);                           \
+    }
 
 template <typename T>
 int launch_pcg_init_jacobi(const Op<T>& op, int N, T* r, T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {r, z, p});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              launch_rows(k_pcg_init_jacobi<T, VEC>, op.rows, N, vec, s, op, N, r, z, p, cr, sk));
+    const InitJacArgs<T> a{op, N, r, z, p, cr, sk};
+    PTP_ROW_GO(k_pcg_init_jacobi, init_jacobi_batch<T>, op.rows, 0)
     return 1;
 }
 
@@ -724,8 +942,8 @@ template <typename T>
 int launch_pcg_dot_rz(int rows, int N, const T* r, const T* z, ColRed<T> cr, int first, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {r, z});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              launch_rows(k_pcg_dot_rz<T, VEC>, rows, N, vec, s, rows, N, r, z, cr, first, sk));
+    const DotRzArgs<T> a{rows, N, r, z, cr, first, sk};
+    PTP_ROW_GO(k_pcg_dot_rz, dot_rz_batch<T>, rows, 0)
     return 1;
 }
 
@@ -733,8 +951,8 @@ template <typename T>
 int launch_pcg_apply_alpha(const Op<T>& op, int N, const T* p, T* q, ColRed<T> cr, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {p, q});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              launch_rows(k_pcg_apply_alpha<T, VEC>, op.rows, N, vec, s, op, N, p, q, cr, sk));
+    const AlphaArgs<T> a{op, N, p, q, cr, sk};
+    PTP_ROW_GO(k_pcg_apply_alpha, alpha_batch<T>, op.rows, 0)
     return 1;
 }
 
@@ -743,14 +961,11 @@ int launch_pcg_update(const Op<T>& op, int N, T xscale, int assign, T* x, const 
                       int jacobi, ColRed<T> cr, Skip sk, cudaStream_t s, Aux<T> aux) {
     int vec = pick_vec<T>(N, {x, p, r, q, z, aux.Y2});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
+    const UpdateArgs<T> a{op, N, xscale, assign, x, p, r, q, z, cr, sk, aux};
     if (jacobi) {
-        PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                                  launch_rows(k_pcg_update<T, VEC, true>, op.rows, N, vec, s, op, N, xscale, assign, x, p,
-                                                                                       r, q, z, cr, sk, aux));
+        PTP_ROW_GO(k_pcg_update, (update_batch<T, true>), op.rows, 1, true)
     } else {
-        PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                                  launch_rows(k_pcg_update<T, VEC, false>, op.rows, N, vec, s, op, N, xscale, assign, x, p,
-                                                                                        r, q, z, cr, sk, aux));
+        PTP_ROW_GO(k_pcg_update, (update_batch<T, false>), op.rows, 0, false)
     }
     return 1;
 }
@@ -759,26 +974,46 @@ template <typename T>
 int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip sk, cudaStream_t s) {
     int vec = pick_vec<T>(N, {z, p});
     if (sizeof(T) == 8 && vec == 4) vec = 2;
-    PTP_VEC_DISPATCH(vec, if constexpr (sizeof(T) == 4 || VEC <= 2)
-                              launch_rows(k_pcg_direction<T, VEC>, rows, N, vec, s, rows, N, z, p, cr, sk));
+    const DirArgs<T> a{rows, N, z, p, cr, sk};
+    PTP_ROW_GO(k_pcg_direction, direction_batch<T>, rows, 0)
     return 1;
+}
+#undef PTP_ROW_GO
+
+// raises a kernel's dynamic shared memory limit to smem once per size
+template <typename... KArgs>
+void grant_smem(void (*kernel)(KArgs...), size_t smem) {
+    if (smem <= 48 * 1024) return;
+    static std::mutex mu;
+    static std::map<const void*, size_t> granted;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& g = granted[(const void*)kernel];
+    if (smem > g) {
+        PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        g = smem;
+    }
 }
 
 template <typename T>
-int launch_dense_apply_batch(const void* args, BatchMap m, int blocks, const KShape&, cudaStream_t s) {
-    launch_k(k_dense_apply_b<T>, dim3(blocks), dim3(256), s, static_cast<const DenseArgs<T>*>(args), m);
+int launch_dense_apply_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {
+    grant_smem(k_dense_apply_b<T>, sh.smem);
+    launch_k_smem(k_dense_apply_b<T>, dim3(blocks), dim3(256), sh.smem, s, static_cast<const DenseArgs<T>*>(args),
+                  m);
     return 1;
 }
 
 template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    const DenseArgs<T> a{n, N, Ainv, B, Y, sk};
+    const int kc = dense_chunk<T>(n);
+    const DenseArgs<T> a{n, N, kc, Ainv, B, Y, sk};
     KShape sh;
     sh.gx = (N + kDT - 1) / kDT;
     sh.gy = (n + kDT - 1) / kDT;
     sh.block = 256;
+    sh.smem = dense_smem<T>(kc);
     if (record_launch(launch_dense_apply_batch<T>, a, sh)) return 1;
-    launch_k(k_dense_apply<T>, dim3(sh.gx, sh.gy), dim3(256), s, a);
+    grant_smem(k_dense_apply<T>, sh.smem);
+    launch_k_smem(k_dense_apply<T>, dim3(sh.gx, sh.gy), dim3(256), sh.smem, s, a);
     return 1;
 }
 

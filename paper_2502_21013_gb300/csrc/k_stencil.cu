@@ -33,6 +33,7 @@
 #include <map>
 #include <mutex>
 
+#include "dev_async.cuh"
 #include "dev_util.cuh"
 
 namespace ptp {
@@ -197,19 +198,6 @@ __device__ void tile_reduce_finish(float (&acc)[NQ][VEC], const Lanes& L, int TT
 constexpr int kNS = 8;   // ring slots (power of two)
 constexpr int kLA = 4;   // rows in flight beyond the three being used: kNS >= 3 + kLA + 1
 
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool valid) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int n = valid ? BYTES : 0;   // 0: nothing is read, the destination is zero-filled
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem), "n"(BYTES), "r"(n)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ int sl8(int q) { return q & (kNS - 1); }
 

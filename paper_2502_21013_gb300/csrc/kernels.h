@@ -469,7 +469,7 @@ int launch_dst_solve(const DstSolve& d, const T* b, T* x, Skip sk, cudaStream_t 
 // dense coarse-level apply Y = Ainv B  (n x n, row-major)
 template <typename T>
 struct DenseArgs {
-    int n, N;
+    int n, N, kc;   // kc: k values staged in shared memory per chunk
     const T* A;
     const T* B;
     T* Y;

@@ -54,8 +54,9 @@ def _oracle_solution(i, prob):
 def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar, mode):
     """Every instance of the batch is bitwise the instance solved alone (the
     merged launches give each instance the blocks of its own launch), and the
-    oracle's fixed point.  In mixed precision every instance's step has a
-    batched form and is merged; FP64 steps (ELL kernels) run as branches."""
+    oracle's fixed point.  Every instance's step has a batched form (the
+    stencil kernels on multigrid hierarchies, the ELL kernels with the dense
+    inverse on single-level grids, in both precisions) and is merged."""
     probs = _instances()
     opts = ptp.default_opts(precision=precision, tol=tol, max_outer=20000)
     alone = []
@@ -74,7 +75,7 @@ def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar, mode
     stats, nconv, rc = batch.solve(opts)
     assert rc == ptp.PTP_OK and nconv == len(probs)
     lps, merged, nmerged = batch.plan_info()
-    if mode == ptp.PTP_BATCH_MERGED and precision == ptp.PTP_MIXED:
+    if mode == ptp.PTP_BATCH_MERGED:
         assert merged == len(probs) and nmerged == lps
     else:
         assert merged == 0 and nmerged == 0
