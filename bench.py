@@ -354,6 +354,7 @@ def transformer_leg(args, local, dev, stream, world, hbm_peak):
     ptp.load_problem(c, prob)
     o = ptp.default_opts(precision=ptp.PTP_MIXED, tol=TOL, max_outer=args.max_outer)
     c.setup(o)
+    c.autotune()
     info = c.info()
     n, N = info["n_free"], info["N"]
     dofs = n * N
@@ -399,6 +400,8 @@ def transformer_leg(args, local, dev, stream, world, hbm_peak):
             "steps": args.transformer_steps, "grid": "1025x513 nodes on [0,2]x[0,1], 1048576 triangles",
             "free_nodes": n, "time_steps": N, "space_time_dofs": dofs, "tol": TOL, "precision": "mixed",
             "outer_iterations": its, "final_rel_residual": res_rel, "gpu_launches": int(launches),
+            "schedule": {k: info[k] for k in ("row_block", "st_tile", "st_waves")},
+            "time_smoother": {"post_smooth": st.post_smooth, "omega_t": st.omega_t, "kappa_min": st.kappa_min},
             "l2": "inputs larger than L2 (U alone is 2.1 GB)", "e2e": e2e,
             "roofline": {"bound": "alu", "kernel": "K1 outer residual, double", "achieved": k1["tflops"],
                          "peak": fp64_peak, "unit": "TFLOP/s", "frac": k1["tflops"] / fp64_peak,
@@ -429,8 +432,10 @@ def batched_leg(args, local, dev, world):
         c = ptp.Context(local)
         ptp.load_problem(c, p)
         c.setup(ptp.default_opts(precision=ptp.PTP_MIXED))
+        c.autotune()
         ctxs.append(c)
     setup_s = time.perf_counter() - t0
+    schedules = [(c.info()["row_block"], c.info()["st_tile"], c.info()["st_waves"]) for c in ctxs]
     batch = ptp.Batch(local)
     for c in ctxs:
         batch.add(c)
@@ -466,7 +471,9 @@ def batched_leg(args, local, dev, world):
             "outer_iterations": [s.outer_iterations for s in stats],
             "grids_and_steps": [f"{int(round(math.sqrt(p.n_nodes)))}^2 N={p.N}" for p in probs],
             "launches_per_step": lps, "merged_instances": merged, "merged_launches": nmerged,
-            "per_step_64": per_step, "gpu_launches": int(lps * steps)}
+            "per_step_64": per_step, "gpu_launches": int(lps * steps),
+            "autotuned_schedules": {f"rows{b}_tile{t}_waves{w}": schedules.count((b, t, w))
+                                    for (b, t, w) in sorted(set(schedules))}}
 
 
 def run_ours(args):
@@ -503,6 +510,7 @@ def run_ours(args):
         ptp.load_problem(c, prob)
         o = ptp.default_opts(precision=precision, tol=TOL, max_outer=args.max_outer, **inner_opts(args))
         c.setup(o)
+        c.autotune()   # launch schedule of this context (set-up time, outside the timed region)
         return c, o
 
     ctx, opts = make(ptp.PTP_MIXED)
@@ -632,6 +640,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "grid": "257x257 nodes, 131072 triangles", "free_nodes": n,
                        "time_steps": N, "space_time_dofs": dofs, "tol": TOL, "precision": "mixed",
                        "inner_solver": inner["name"],
+                       "schedule": {k: info[k] for k in ("row_block", "st_tile", "st_waves")},
+                       "time_smoother": {"post_smooth": st.post_smooth, "omega_t": st.omega_t,
+                                         "kappa_min": st.kappa_min},
                        "dft_max_it": opts.dft_max_it if opts.coarse_solver == ptp.PTP_COARSE_DFT else None,
                        "outer_iterations": iters, "final_rel_residual": res_rel,
                        "l2": "inputs larger than L2 (U alone is 133 MB)", "parallelism": f"replicas{world}"},

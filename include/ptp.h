@@ -273,14 +273,20 @@ int ptp_sizes(const ptp_ctx* ctx, int* n_free, int* N, int* n_tri,
      4 iron element-node incidences    5 nonzeros of the linear-element
      stiffness      6 nonzeros of the mass (M/tau) rows  7 nonzeros of the
      level-0 spatial operator M + tau L                  8 spatial levels
-     9 time levels  10 coils  11 threads per block of the row kernels      */
-#define PTP_INFO_COUNT 12
+     9 time levels  10 coils  11 threads per block of the row kernels
+    12 largest time tile of the stencil kernels   13 their blocks per SM     */
+#define PTP_INFO_COUNT 14
 int ptp_info(const ptp_ctx* ctx, int64_t* counts, int n);
 
-/* Times the level-0 SpMM of this context with 128, 256 and 512 threads per
-   block (rows per block = threads / (N / vector width)) and keeps the
-   fastest for every row kernel of the context.  *block_threads and
-   *best_us (per launch) may be NULL.  Synchronises. */
+/* Launch-schedule autotuner of this context.  Times the level-0 SpMM with
+   128, 256 and 512 threads per block (rows per block = threads / (N /
+   vector width)) and keeps the fastest for every row kernel; on structured
+   grids with the stencil kernels it also times the level-0 stencil passes
+   (periodic residual, residual + restriction, interpolation + sweep, time
+   restriction) for time tiles of up to 8, 16, 32 and 64 columns and row
+   strips aiming at 2, 3, 4 and 6 blocks per SM, and keeps the fastest pair
+   (ptp_info entries 12 and 13).  *block_threads and *best_us (per launch of
+   the SpMM) may be NULL.  Synchronises. */
 int ptp_autotune(ptp_ctx* ctx, int* block_threads, double* best_us);
 
 /* ---- batched independent instances ----------------------------------- */

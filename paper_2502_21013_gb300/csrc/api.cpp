@@ -29,7 +29,7 @@ int guarded(ptp_ctx* h, F&& f, bool device = true) {
         h->c.err.clear();
         if (device) {
             PTP_CUDA(cudaSetDevice(h->c.device));
-            ptp::set_row_block(h->c.row_block);
+            ptp::apply_schedule(h->c);
             if (!h->c.own_stream) {
                 PTP_CUDA(cudaStreamCreateWithFlags(&h->c.own_stream, cudaStreamNonBlocking));
                 if (!h->c.stream) h->c.stream = h->c.own_stream;
@@ -373,7 +373,7 @@ int ptp_info(const ptp_ctx* h, int64_t* counts, int n) {
     if (!c.ready) return PTP_ESTATE;
     const int64_t v[PTP_INFO_COUNT] = {c.n, c.N, c.n_tri, c.n_iron, (int64_t)c.inc_elem.n, (int64_t)c.l_idx.n,
                                        (int64_t)c.m_idx.n, c.sl[0].op.nnz, (int64_t)c.sl.size(),
-                                       (int64_t)c.tl.size(), c.n_coils, c.row_block};
+                                       (int64_t)c.tl.size(), c.n_coils, c.row_block, c.st_tt, c.st_waves};
     const int m = n < PTP_INFO_COUNT ? n : PTP_INFO_COUNT;
     for (int k = 0; k < m; ++k) counts[k] = v[k];
     return m;

@@ -167,7 +167,7 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
             b->branch.push_back(i);
             continue;
         }
-        ptp::set_row_block(cs[i]->row_block);
+        ptp::apply_schedule(*cs[i]);
         {
             RecordGuard g(&b->recs[i]);
             b->per_step[i] = ptp::enqueue_step(*cs[i], ptp::STEP_FORWARD);
@@ -226,7 +226,7 @@ void enqueue_batched_step(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
     int64_t launches = 0;
     for (int i : b->branch) {
         PTP_CUDA(cudaStreamWaitEvent(cs[i]->stream, b->events[K], 0));
-        ptp::set_row_block(cs[i]->row_block);
+        ptp::apply_schedule(*cs[i]);
         b->per_step[i] = ptp::enqueue_step(*cs[i], ptp::STEP_FORWARD);
         launches += b->per_step[i];
         PTP_CUDA(cudaEventRecord(b->events[i], cs[i]->stream));
@@ -338,7 +338,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
             o.time_levels = cs[i]->opts.time_levels;
             o.coarse_steps = cs[i]->opts.coarse_steps;
             o.coarse_solver = cs[i]->opts.coarse_solver;
-            ptp::set_row_block(cs[i]->row_block);
+            ptp::apply_schedule(*cs[i]);
             ptp::solve_begin(*cs[i], o, nullptr, ptp::STEP_FORWARD);
         }
         // capture one step of every instance (re-captured when any step changes)
@@ -405,7 +405,7 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
         const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         int conv = 0, worst = PTP_OK;
         for (int i = 0; i < K; ++i) {
-            ptp::set_row_block(cs[i]->row_block);
+            ptp::apply_schedule(*cs[i]);
             ptp_stats st;
             std::memset(&st, 0, sizeof(st));
             const int rc = ptp::solve_end(*cs[i], &st, ptp::STEP_FORWARD, (int64_t)launched * b->step_launches, wall, ms);

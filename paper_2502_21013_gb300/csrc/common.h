@@ -260,6 +260,7 @@ struct Ctx {
     int64_t launches = 0;        // kernels issued (counting while capturing)
     int64_t launches_per_step[3] = {0, 0, 0};
     int row_block = 256;         // threads per block of the row kernels (autotuned)
+    int st_tt = 32, st_waves = 3;  // stencil schedule: largest time tile, blocks per SM (autotuned)
     bool stencil_ok = false;     // every spatial level has a 7-point stencil (structured GMG hierarchy)
     int64_t buf_gen = 0;         // bumped when a buffer a captured graph may use is reallocated
     // smallest eigenvalue of L x = lambda M x (inverse iteration, on first need;
@@ -303,7 +304,8 @@ void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, int kind);
 int64_t step_key(const Ctx& c, const ptp_opts& o);
 int64_t enqueue_step(Ctx& c, int kind);
 int solve_end(Ctx& c, ptp_stats* stats, int kind, int64_t step_launches, double solve_ms, float dev_ms);
-int autotune(Ctx& c, double* best_us);     // picks c.row_block by timing the level-0 SpMM
+int autotune(Ctx& c, double* best_us);     // picks c.row_block (and the stencil schedule) by timing
+void apply_schedule(const Ctx& c);         // the context's launch schedule for this host thread
 void require_coarse(const Ctx& c);         // the time hierarchy has an exact last-level solve
 void alloc_adjoint(Ctx& c);                // Jacobian coefficients and adjoint work
 void mg_precondition(Ctx& c, const double* v, double* z);   // z = inner periodic solve of v

@@ -655,6 +655,10 @@ struct Shape {
     int vec, TT, tpn, sx, block;
 };
 
+// schedule of this host thread's launches (each context sets its autotuned one)
+thread_local int g_st_tt = 32;      // largest time tile
+thread_local int g_st_waves = 3;    // blocks per SM the strips aim at
+
 Shape st_shape(int N, std::initializer_list<const void*> ptrs, bool need_even) {
     Shape s{};
     s.vec = 1;
@@ -665,9 +669,10 @@ Shape st_shape(int N, std::initializer_list<const void*> ptrs, bool need_even) {
         if (ok) { s.vec = v; break; }
     }
     if (need_even && s.vec < 2) throw Error(PTP_EINVAL, "stencil time restriction needs an even, aligned N");
-    // the largest divisor of N up to 32 that VEC divides
+    // the largest divisor of N up to the schedule's tile that VEC divides
     s.TT = s.vec;
-    for (int d = std::min(N, 32); d >= s.vec; --d)
+    const int cap = std::min(g_st_tt, 32 * s.vec);   // at least 8 nodes per block row
+    for (int d = std::min(N, cap); d >= s.vec; --d)
         if (N % d == 0 && d % s.vec == 0) { s.TT = d; break; }
     s.tpn = s.TT / s.vec;
     s.sx = kStBlock / s.tpn;
@@ -675,9 +680,9 @@ Shape st_shape(int N, std::initializer_list<const void*> ptrs, bool need_even) {
     return s;
 }
 
-// rows per block strip: enough blocks for about three per SM, 2..32 rows
+// rows per block strip: enough blocks for about g_st_waves per SM, 2..32 rows
 int strip_rows(int H, int nseg, int nch) {
-    const long want = 3L * num_sms();
+    const long want = (long)g_st_waves * num_sms();
     long sy = ((long)H * nseg * nch) / std::max(1L, want);
     return (int)std::max(2L, std::min(32L, sy));
 }
@@ -707,6 +712,11 @@ static void st_launch(void (*kernel)(KArgs...), dim3 grid, int block, size_t sme
         }
     }
     launch_k_smem(kernel, grid, dim3(block), smem, s, std::forward<Args>(args)...);
+}
+
+void set_stencil_schedule(int tt, int waves) {
+    g_st_tt = std::max(1, std::min(tt, 256));
+    g_st_waves = std::max(1, std::min(waves, 16));
 }
 
 void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* out, cudaStream_t s) {

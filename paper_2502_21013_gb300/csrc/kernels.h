@@ -356,6 +356,9 @@ struct StencilOp {      // cm M + cl L as a 7-point stencil
     const float4* acoef = nullptr;   // cm M + cl L precombined: {C, E, W, N}, {S, NE, SW, 1 / C}
     T cm = 1, cl = 0;
 };
+// schedule of the stencil launches from this host thread: the largest time
+// tile (columns per block) and the blocks per SM the row strips aim at
+void set_stencil_schedule(int tt, int waves);
 // out (2 float4 per node) = cm M + cl L of coef, with 1 / diagonal in the last slot
 void launch_st_combine(int n, const float4* coef, float cm, float cl, float4* out, cudaStream_t s);
 struct StPresidArgs {

@@ -932,9 +932,9 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
     };
-    const int ints[14] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+    const int ints[16] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
                           o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it,
-                          o.stencil, o.k1_fused, o.coarse_direct};
+                          o.stencil, o.k1_fused, o.coarse_direct, c.st_tt, c.st_waves};
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));
@@ -973,12 +973,65 @@ int autotune(Ctx& c, double* best_us) {
             bestb = cb;
         }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     c.row_block = bestb;
     set_row_block(bestb);
     if (best_us) *best_us = best;
+    // stencil schedule: the level-0 passes of one V-cycle step for every
+    // (largest time tile, blocks per SM); a candidate whose launch plan does
+    // not fit the reduction buffers is skipped
+    if (mixed && use_stencil<float>(c) && c.sl.size() > 1) {
+        const int opi = c.tl[0].op;
+        const StencilOp<float> A0 = st_op(c, 0, opi), A1 = st_op(c, 1, opi);
+        float* w[4] = {c.w_f[0].p, c.w_f[1].p, c.w_f[2].p, c.w_f[3].p};
+        for (int k = 1; k < 4; ++k) PTP_CUDA(cudaMemsetAsync(w[k], 0, cnt * sizeof(float), st));
+        const size_t cnt1 = (size_t)c.sl[1].n * c.N;
+        PTP_CUDA(cudaMemsetAsync(c.g_xf[1].p, 0, cnt1 * sizeof(float), st));
+        ColRed<float> cr = make_cr<float>(c);
+        const bool even = c.N % 2 == 0 && c.tl.size() > 1;
+        auto pass = [&]() {
+            launch_st_presid(A0, c.N, w[0], w[1], w[2], w[3], 0.7f, false, Skip{}, st);
+            launch_st_resid_restrict(A0, A1, c.N, w[0], w[1], c.g_bf[1].p, c.g_xf[1].p, 0.7f, Skip{}, st);
+            launch_st_interp_sweep(A0, c.sl[1].nx - 2, c.sl[1].ny - 2, c.N, c.g_xf[1].p, w[0], w[1], w[2], 0.7f, cr, 1,
+                                   Skip{}, st);
+            if (even) launch_st_presid(A0, c.N, w[0], w[1], mgb<float>(c, 1), nullptr, 0.f, true, Skip{}, st);
+        };
+        double best_st = 1e300;
+        int bt = c.st_tt, bw = c.st_waves;
+        for (int tt : {8, 16, 32, 64}) {
+            for (int wv : {2, 3, 4, 6}) {
+                set_stencil_schedule(tt, wv);
+                try {
+                    for (int r = 0; r < 2; ++r) pass();
+                    PTP_CUDA(cudaEventRecord(a, st));
+                    for (int r = 0; r < 5; ++r) pass();
+                    PTP_CUDA(cudaEventRecord(b, st));
+                    PTP_CUDA(cudaEventSynchronize(b));
+                } catch (const Error& e) {
+                    if (e.code != PTP_EINVAL) throw;
+                    PTP_CUDA(cudaStreamSynchronize(st));
+                    continue;
+                }
+                float ms = 0;
+                PTP_CUDA(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best_st) {
+                    best_st = ms;
+                    bt = tt;
+                    bw = wv;
+                }
+            }
+        }
+        c.st_tt = bt;
+        c.st_waves = bw;
+        apply_schedule(c);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
     return bestb;
+}
+
+void apply_schedule(const Ctx& c) {
+    set_row_block(c.row_block);
+    set_stencil_schedule(c.st_tt, c.st_waves);
 }
 
 // Smallest eigenvalue of the pencil L x = lambda M x (M the sigma-weighted

@@ -360,7 +360,7 @@ class Context:
         return tuple(x.value for x in v)
 
     INFO_KEYS = ("n_free", "N", "n_tri", "n_iron", "iron_incidences", "lin_nnz", "mass_nnz", "op_nnz",
-                 "spatial_levels", "time_levels", "n_coils", "row_block")
+                 "spatial_levels", "time_levels", "n_coils", "row_block", "st_tile", "st_waves")
 
     def autotune(self):
         b, us = ctypes.c_int(), ctypes.c_double()

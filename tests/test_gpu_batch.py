@@ -106,7 +106,9 @@ def test_autotune_keeps_the_solution():
     c = _ctx(prob, precision=ptp.PTP_MIXED)
     block, us = c.autotune()
     assert block in (128, 256, 512) and us > 0
-    assert c.info()["row_block"] == block
+    info = c.info()
+    assert info["row_block"] == block
+    assert info["st_tile"] in (8, 16, 32, 64) and info["st_waves"] in (2, 3, 4, 6)
     opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=1e-11, max_outer=20000)
     U, st, rc = c.solve(opts)
     assert rc == ptp.PTP_OK
