@@ -325,6 +325,13 @@ int  ptp_batch_solve(ptp_batch* batch, const ptp_opts* opts, ptp_stats* stats, i
 int  ptp_batch_result_dev(ptp_batch* batch, int i, double* U);
 /* PTP_BATCH_MERGED or PTP_BATCH_BRANCHES (takes effect at the next solve). */
 int  ptp_batch_set_mode(ptp_batch* batch, int mode);
+/* Merged mode: the instances are split into `groups` (1..64, default 4)
+   groups of about equal space-time size, each merged into its own program;
+   the programs run concurrently as branches of the step's graph, so kernels
+   of different kinds (the double K1 of one group, the float stencil passes
+   of another) overlap.  Kernels per step stay bounded by the groups, not the
+   instances.  Takes effect at the next solve. */
+int  ptp_batch_set_groups(ptp_batch* batch, int groups);
 /* The captured step of the last ptp_batch_solve: kernels per step (merged
    launches plus those of branch instances), instances merged, merged
    launches.  Pointers may be NULL; PTP_ESTATE before the first solve. */

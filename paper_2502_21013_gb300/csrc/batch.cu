@@ -113,9 +113,12 @@ struct ptp_batch {
     std::vector<cudaEvent_t> events;
     std::string err;
     int mode = PTP_BATCH_MERGED;
-    // the merged program
+    int groups = 4;                 // merged programs that run concurrently
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gevents;
+    // the merged programs, one per group of instances
     std::vector<ptp::Recorder> recs;
-    std::vector<MergedOp> merged;
+    std::vector<std::vector<MergedOp>> merged;
     std::vector<int> branch;        // instances that run as graph branches
     unsigned char* blob = nullptr;  // device work-lists (argument structs and virtual grids)
     int64_t step_launches = 0;      // kernels per batched step
@@ -175,13 +178,30 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
         if (b->recs[i].foreign == 0 && !b->recs[i].ops.empty()) mergeable.push_back(i);
         else b->branch.push_back(i);
     }
-    // longest programs first: they form the backbone of the alignment
-    std::stable_sort(mergeable.begin(), mergeable.end(),
-                     [&](int x, int y) { return b->recs[x].ops.size() > b->recs[y].ops.size(); });
-    std::vector<MergedOp> seq;
-    for (int i : mergeable) seq = merge(std::move(seq), i, b->recs[i].ops);
+    // groups balanced by space-time size (largest first onto the lightest
+    // group); inside a group the longest programs form the backbone
+    const int G = std::max(1, std::min(b->groups, (int)mergeable.size()));
+    std::vector<std::vector<int>> grp(G);
+    {
+        std::vector<int> order = mergeable;
+        auto size_of = [&](int i) { return (double)cs[i]->n * cs[i]->N; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return size_of(x) > size_of(y); });
+        std::vector<double> load(G, 0.0);
+        for (int i : order) {
+            const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            grp[g].push_back(i);
+            load[g] += size_of(i);
+        }
+    }
+    std::vector<std::vector<MergedOp>> seqs(G);
+    for (int g = 0; g < G; ++g) {
+        std::stable_sort(grp[g].begin(), grp[g].end(),
+                         [&](int x, int y) { return b->recs[x].ops.size() > b->recs[y].ops.size(); });
+        for (int i : grp[g]) seqs[g] = merge(std::move(seqs[g]), i, b->recs[i].ops);
+    }
     // work-lists: argument structs, block offsets and virtual grids of every merged launch
     size_t bytes = 0;
+    for (auto& seq : seqs)
     for (MergedOp& m : seq) {
         const size_t k = m.inst.size();
         m.off_args = bytes = align_up(bytes, 256);
@@ -194,6 +214,7 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
         bytes += k * sizeof(int);
     }
     std::vector<unsigned char> host(std::max<size_t>(bytes, 1), 0);
+    for (auto& seq : seqs)
     for (MergedOp& m : seq) {
         const size_t k = m.inst.size(), asz = m.rec.front()->args.size();
         int* start = reinterpret_cast<int*>(host.data() + m.off_start);
@@ -211,12 +232,20 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
         start[k] = (int)total;
         m.blocks = (int)total;
     }
-    if (!seq.empty()) {
+    if (bytes > 0) {
         PTP_CUDA(cudaMalloc((void**)&b->blob, bytes));
         PTP_CUDA(cudaMemcpy(b->blob, host.data(), bytes, cudaMemcpyHostToDevice));
     }
-    b->merged = std::move(seq);
+    b->merged = std::move(seqs);
     b->merged_instances = (int)mergeable.size();
+    while (b->gstreams.size() < b->merged.size()) {
+        cudaStream_t st;
+        PTP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->gstreams.push_back(st);
+        cudaEvent_t e;
+        PTP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->gevents.push_back(e);
+    }
 }
 
 // the step of every instance: merged launches on the batch stream, branches on their own
@@ -231,14 +260,22 @@ void enqueue_batched_step(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
         launches += b->per_step[i];
         PTP_CUDA(cudaEventRecord(b->events[i], cs[i]->stream));
     }
-    for (const MergedOp& m : b->merged) {
-        ptp::BatchMap map;
-        map.start = reinterpret_cast<const int*>(b->blob + m.off_start);
-        map.gx = reinterpret_cast<const int*>(b->blob + m.off_gx);
-        map.gy = reinterpret_cast<const int*>(b->blob + m.off_gy);
-        map.n = (int)m.inst.size();
-        launches += m.fn(b->blob + m.off_args, map, m.blocks, m.shape, b->stream);
+    // one group on the batch stream, the others forked onto their own streams
+    const int G = (int)b->merged.size();
+    for (int g = 0; g < G; ++g) {
+        cudaStream_t st = g == 0 ? b->stream : b->gstreams[g];
+        if (g > 0) PTP_CUDA(cudaStreamWaitEvent(st, b->events[K], 0));
+        for (const MergedOp& m : b->merged[g]) {
+            ptp::BatchMap map;
+            map.start = reinterpret_cast<const int*>(b->blob + m.off_start);
+            map.gx = reinterpret_cast<const int*>(b->blob + m.off_gx);
+            map.gy = reinterpret_cast<const int*>(b->blob + m.off_gy);
+            map.n = (int)m.inst.size();
+            launches += m.fn(b->blob + m.off_args, map, m.blocks, m.shape, st);
+        }
+        if (g > 0) PTP_CUDA(cudaEventRecord(b->gevents[g], st));
     }
+    for (int g = 1; g < G; ++g) PTP_CUDA(cudaStreamWaitEvent(b->stream, b->gevents[g], 0));
     for (int i : b->branch) PTP_CUDA(cudaStreamWaitEvent(b->stream, b->events[i], 0));
     b->step_launches = launches;
 }
@@ -271,6 +308,8 @@ void ptp_batch_destroy(ptp_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
     for (auto e : b->events) cudaEventDestroy(e);
+    for (auto e : b->gevents) cudaEventDestroy(e);
+    for (auto st : b->gstreams) cudaStreamDestroy(st);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -306,8 +345,21 @@ int ptp_batch_plan_info(const ptp_batch* b, int64_t* launches_per_step, int* mer
     if (!b->exec) return PTP_ESTATE;
     if (launches_per_step) *launches_per_step = b->step_launches;
     if (merged_instances) *merged_instances = b->merged_instances;
-    if (merged_launches) *merged_launches = (int)b->merged.size();
+    if (merged_launches) {
+        size_t m = 0;
+        for (const auto& seq : b->merged) m += seq.size();
+        *merged_launches = (int)m;
+    }
     return PTP_OK;
+}
+
+int ptp_batch_set_groups(ptp_batch* b, int groups) {
+    return batch_guard(b, [&]() {
+        PTP_REQUIRE(groups >= 1 && groups <= 64, "ptp_batch_set_groups: 1..64 groups");
+        if (groups != b->groups) drop_graph(b);
+        b->groups = groups;
+        return PTP_OK;
+    });
 }
 
 int ptp_batch_result_dev(ptp_batch* b, int i, double* U) {

@@ -114,6 +114,7 @@ def _load():
         "ptp_batch_solve": (I, [P, ctypes.POINTER(Opts), P, pI]),
         "ptp_batch_result_dev": (I, [P, I, P]),
         "ptp_batch_set_mode": (I, [P, I]),
+        "ptp_batch_set_groups": (I, [P, I]),
         "ptp_batch_plan_info": (I, [P, ctypes.POINTER(ctypes.c_int64), pI, pI]),
         "ptp_adjoint_gradient_dev": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
         "ptp_adjoint_gradient": (I, [P, ctypes.POINTER(Opts), P, pD, pD, pD, P, ctypes.POINTER(Stats)]),
@@ -148,7 +149,7 @@ EXPORTED = [
     "ptp_jacobian_apply_dev",
     "ptp_loss_dev", "ptp_adjoint_gradient_dev", "ptp_adjoint_gradient", "ptp_autotune",
     "ptp_batch_create", "ptp_batch_destroy", "ptp_batch_last_error", "ptp_batch_add", "ptp_batch_size",
-    "ptp_batch_solve", "ptp_batch_result_dev", "ptp_batch_set_mode", "ptp_batch_plan_info", "ptp_probe_fma", "ptp_probe_recip_dev",
+    "ptp_batch_solve", "ptp_batch_result_dev", "ptp_batch_set_mode", "ptp_batch_set_groups", "ptp_batch_plan_info", "ptp_probe_fma", "ptp_probe_recip_dev",
     "ptp_time_cycle_rho", "ptp_choose_time_smoother",
 ]
 
@@ -578,6 +579,9 @@ class Batch:
 
     def set_mode(self, mode):
         self._check(lib.ptp_batch_set_mode(self._h, int(mode)))
+
+    def set_groups(self, groups):
+        self._check(lib.ptp_batch_set_groups(self._h, int(groups)))
 
     def plan_info(self):
         """(kernels per batched step, instances merged, merged launches)."""

@@ -134,6 +134,7 @@ def test_merged_launches_do_not_grow_with_the_instances():
     counts = []
     for copies in (1, 3):
         batch = ptp.Batch(0)
+        batch.set_groups(1)
         keep = []
         for _ in range(copies):
             for mk in makes:
@@ -146,3 +147,36 @@ def test_merged_launches_do_not_grow_with_the_instances():
         counts.append(lps)
     assert counts[0] == counts[1]
     assert max(alone) - 4 <= counts[0] < sum(alone), (counts, alone)
+
+
+def test_groups_run_concurrently_and_keep_results():
+    """Merged programs in groups (concurrent graph branches): results equal
+    the single-program batch bitwise, and the kernels per step are at most
+    the groups times the longest instance's."""
+    makes = [lambda: W.unit_square_problem(17, 16), lambda: W.unit_square_problem(33, 32),
+             lambda: W.transformer_problem(65, 33, 64), lambda: W.unit_square_problem(33, 8, amps=(70.0,))]
+    opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=1e-9, max_outer=20000)
+    res = {}
+    for groups in (1, 2, 4):
+        batch = ptp.Batch(0)
+        batch.set_groups(groups)
+        keep = []
+        for mk in makes:
+            p = mk()
+            c = _ctx(p, precision=ptp.PTP_MIXED)
+            keep.append((c, p))
+            batch.add(c)
+        stats, nconv, rc = batch.solve(opts)
+        assert rc == ptp.PTP_OK and nconv == len(makes)
+        lps, merged, _ = batch.plan_info()
+        assert merged == len(makes)
+        out = []
+        for i, (c, p) in enumerate(keep):
+            U = torch.empty((p.n_free, p.N), dtype=torch.float64, device="cuda")
+            batch.result_dev(i, U)
+            out.append(U)
+        res[groups] = (out, lps)
+    for groups in (2, 4):
+        for a, b in zip(res[1][0], res[groups][0]):
+            assert torch.equal(a, b)
+    assert res[4][1] >= res[1][1]
