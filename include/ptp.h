@@ -281,9 +281,9 @@ int ptp_info(const ptp_ctx* ctx, int64_t* counts, int n);
 /* Launch-schedule autotuner of this context.  Times the level-0 SpMM with
    128, 256 and 512 threads per block (rows per block = threads / (N /
    vector width)) and keeps the fastest for every row kernel; on structured
-   grids with the stencil kernels it also times the level-0 stencil passes
-   (periodic residual, residual + restriction, interpolation + sweep, time
-   restriction) for time tiles of up to 8, 16, 32 and 64 columns and row
+   grids with the stencil kernels (PTP_MIXED) it also times whole outer
+   steps of the fixed point (from zero, stopping rule off; the iterate is
+   left undefined) for time tiles of up to 8, 16, 32 and 64 columns and row
    strips aiming at 2, 3, 4 and 6 blocks per SM, and keeps the fastest pair
    (ptp_info entries 12 and 13).  *block_threads and *best_us (per launch of
    the SpMM) may be NULL.  Synchronises. */
@@ -380,6 +380,12 @@ int ptp_residual_noalloc_dev(ptp_ctx* ctx, const double* U, double* R, double* n
    X^0 = X^{N_l} (eq. iter1 multiplied by tau_l), double.  X and Y are
    different buffers (PTP_EINVAL if equal). */
 int ptp_periodic_apply_dev(ptp_ctx* ctx, int level, const double* X, double* Y);
+/* Periodic residual of level l in float, the block-Jacobi smoother's pass:
+   R^n = B^n - [(M + tau_l L) X^n - M X^{n-1}], X^0 = X^{N_l}, operator
+   values rounded to float.  On structured grids with the stencil path this
+   is the 7-point stencil kernel of the inner solve, else the ELL kernel.
+   R differs from X and B (PTP_EINVAL otherwise); PTP_MIXED contexts only. */
+int ptp_periodic_residual_f32_dev(ptp_ctx* ctx, int level, const float* X, const float* B, float* R);
 
 /* Batched PCG: solve (M + tau_l L) X = B column by column (N_l columns),
    starting from X = 0, with the preconditioner chosen at setup, until every

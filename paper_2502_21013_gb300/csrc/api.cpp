@@ -469,6 +469,19 @@ int ptp_periodic_apply_dev(ptp_ctx* h, int level, const double* X, double* Y) {
     });
 }
 
+int ptp_periodic_residual_f32_dev(ptp_ctx* h, int level, const float* X, const float* B, float* R) {
+    return guarded(h, [&](Ctx& c) {
+        need_ready(c);
+        check_level(c, level);
+        PTP_REQUIRE(c.opts.precision == PTP_MIXED, "ptp_periodic_residual_f32: needs a PTP_MIXED context");
+        PTP_REQUIRE(X && B && R && (const void*)R != (const void*)X && (const void*)R != (const void*)B,
+                    "ptp_periodic_residual_f32: null or aliased pointers");
+        ptp::periodic_residual_f32(c, level, X, B, R);
+        PTP_CUDA(cudaGetLastError());
+        return PTP_OK;
+    });
+}
+
 int ptp_spatial_solve_dev(ptp_ctx* h, int level, const double* B, double* X, double tol, int max_it,
                           int* iters) {
     return guarded(h, [&](Ctx& c) {

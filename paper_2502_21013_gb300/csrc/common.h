@@ -293,6 +293,7 @@ template <typename T>
 void apply_op(Ctx& c, int s, int op, int N, const T* X, T* Y);
 template <typename T>
 void periodic_apply(Ctx& c, int level, const T* X, T* Y);
+void periodic_residual_f32(Ctx& c, int level, const float* X, const float* B, float* R);
 template <typename T>
 int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check);
 void periodic_mg_solve(Ctx& c, const double* B, double* X, int cycles, double* relres);

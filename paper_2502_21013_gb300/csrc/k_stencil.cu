@@ -300,38 +300,53 @@ __device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGri
     };
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
-    const float* pre_base = xr + (size_t)L.lc * VEC - 1;       // column col - 1 within a slot row (lc > 0)
+    // every lane computes (the column shuffles need the whole warp); halo
+    // lanes read an interior slot and store nothing
+    const int lnc = (L.ln >= 1 && L.ln <= L.sx - 2) ? L.ln : 1;
+    const bool from_left = L.lc > 0 && (threadIdx.x & 31) != 0;   // column col - 1 is in the lane to the left
+    const float* pre_base = xr + (size_t)L.lc * VEC - 1;         // the same from shared memory (lc > 0)
+    // this node's coefficients for the next row, loaded one row ahead
+    A7 cn{}, mn{};
+    float idn = 0.f;
+    if (out_lane && y0 < y1) {
+        load_a(A.acoef, (size_t)y0 * W + a, cn, idn);
+        load_m(A.coef, (size_t)y0 * W + a, mn);
+    }
     for (int b = y0; b < y1; ++b) {
         const int i = b - y0;
+        const A7 c = cn, m = mn;
+        const float idiag = idn;
+        if (out_lane && b + 1 < y1) {
+            load_a(A.acoef, (size_t)(b + 1) * W + a, cn, idn);
+            load_m(A.coef, (size_t)(b + 1) * W + a, mn);
+        }
         issue_q(i + kLA + 2);
         cp_wait<kLA>();
         __syncthreads();
-        if (out_lane) {
-            const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
-            const size_t node = (size_t)b * W + a;
-            A7 c, m;
-            float idiag;
-            load_a(A.acoef, node, c, idiag);
-            load_m(A.coef, node, m);
-            float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
-            nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
-            // column col - 1 of the seven nodes: from the lane to the left, or the tile's previous column
-            auto before = [&](int slot, int nd) -> float {
-                return L.lc > 0 ? pre_base[((size_t)slot * L.sx + nd) * TT] : prev[slot * L.sx + nd];
-            };
-            float p_c = before(sC, L.ln), p_e = before(sC, L.ln + 1), p_w = before(sC, L.ln - 1);
-            float p_n = before(sN, L.ln), p_s = before(sS, L.ln), p_ne = before(sN, L.ln + 1),
-                  p_sw = before(sS, L.ln - 1);
-            float bv[VEC], r[VEC];
-            lds<VEC>(bslot0 + sN * sstride, bv);
+        const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
+        float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
+        nbrs<VEC>(xr, sS, sC, sN, lnc, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
+        // column col - 1 of the seven nodes: the lane to the left's last column,
+        // else shared memory (a node split across warps), else the tile's previous column
+        auto before = [&](int slot, int nd, float mine) -> float {
+            const float up = __shfl_up_sync(0xffffffffu, mine, 1);
+            if (from_left) return up;
+            return L.lc > 0 ? pre_base[((size_t)slot * L.sx + nd) * TT] : prev[slot * L.sx + nd];
+        };
+        float p_c = before(sC, lnc, xc[VEC - 1]), p_e = before(sC, lnc + 1, xe[VEC - 1]),
+              p_w = before(sC, lnc - 1, xw[VEC - 1]), p_n = before(sN, lnc, xn[VEC - 1]),
+              p_s = before(sS, lnc, xs[VEC - 1]), p_ne = before(sN, lnc + 1, xne[VEC - 1]),
+              p_sw = before(sS, lnc - 1, xsw[VEC - 1]);
+        float bv[VEC], r[VEC];
+        lds<VEC>(srow<VEC>(br, sN, lnc, L.sx, TT, L.lc), bv);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                const float ax = apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
-                const float mx = m.c * p_c + m.e * p_e + m.w * p_w + m.n * p_n + m.s * p_s + m.ne * p_ne +
-                                 m.sw * p_sw;
-                r[v] = bv[v] - (ax - mx);
-                p_c = xc[v]; p_e = xe[v]; p_w = xw[v]; p_n = xn[v]; p_s = xs[v]; p_ne = xne[v]; p_sw = xsw[v];
-            }
+        for (int v = 0; v < VEC; ++v) {
+            const float ax = apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
+            const float mx = m.c * p_c + m.e * p_e + m.w * p_w + m.n * p_n + m.s * p_s + m.ne * p_ne + m.sw * p_sw;
+            r[v] = bv[v] - (ax - mx);
+            p_c = xc[v]; p_e = xe[v]; p_w = xw[v]; p_n = xn[v]; p_s = xs[v]; p_ne = xne[v]; p_sw = xsw[v];
+        }
+        if (out_lane) {
             if constexpr (MODE == 0) {
                 const long o = cx.off(b);
                 st_vec<float, VEC>(R + o, r);
@@ -347,6 +362,7 @@ __device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGri
                 float o[HV];
 #pragma unroll
                 for (int v = 0; v < HV; ++v) o[v] = r[2 * v] + r[2 * v + 1];
+                const size_t node = (size_t)b * W + a;
                 st_vec<float, HV>(R + node * (N / 2) + L.col / 2, o);
             }
         }
@@ -408,17 +424,23 @@ __device__ __forceinline__ void st_resid_restrict_body(const StRestrictArgs& p, 
     const bool c_lane = L.ln < cxo && Aq < Wc;
     const Cursor cc = cursor(Wc, Hc, N, Aq, L.col);
     const int sl = 2 * L.ln + 2;
+    // fine coefficients one row ahead (rows f0..f1 on the grid)
+    const bool t_ok = t_lane;
+    A7 cn{};
+    float idn = 0.f;
+    auto fetch = [&](int f) {
+        if (t_ok && f >= 0 && f < H) load_a(Af.acoef, (size_t)f * W + a, cn, idn);
+    };
+    fetch(f0);
     for (int f = f0; f <= f1; ++f) {
         const int k = f - f0;
+        const A7 c = cn;
+        if (f + 1 <= f1) fetch(f + 1);
         issue_q(k + kLA + 2);
         cp_wait<kLA>();
         __syncthreads();
         if (t_lane) {
             const int sS = sl8(k), sC = sl8(k + 1), sN = sl8(k + 2);
-            const size_t node = (size_t)f * W + a;
-            A7 c;
-            float idiag;
-            load_a(Af.acoef, node, c, idiag);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], t[VEC];
             nbrs<VEC>(zr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
             lds<VEC>(bslot0 + sN * sstride, bv);
@@ -517,7 +539,7 @@ __device__ __forceinline__ void st_interp_sweep_body(const StInterpArgs& p, cons
     // x' = x + P xc in place for ring row q (fine row r)
     auto to_xprime = [&](int q) {
         const int r = y0 - 1 + q;
-        if (!cx.ok(r)) return;
+        if (q >= nrows || !cx.ok(r)) return;
         float* xp = xslot0 + sl8(q) * sstride;
         float v[VEC], c1[VEC], c2[VEC];
         lds<VEC>(xp, v);
@@ -545,29 +567,33 @@ __device__ __forceinline__ void st_interp_sweep_body(const StInterpArgs& p, cons
         }
         sts<VEC>(xp, v);
     };
+    // x' runs three rows ahead of the row being swept: one barrier per row
+    // publishes x' of rows i..i+2 and frees slot i+3 for x' in the same phase
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
-    cp_wait<kLA>();          // rows q = 0, 1 and their coarse rows have landed
+    cp_wait<kLA - 1>();      // rows q = 0, 1, 2 and their coarse rows have landed
     __syncthreads();
     to_xprime(0);
     to_xprime(1);
+    to_xprime(2);
     constexpr int NQ = DOTS == 1 ? 2 : 1;
     float acc[NQ][VEC];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) zero_vec<VEC>(acc[q]);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
+    A7 cn{};
+    float idn = 0.f;
+    if (out_lane && y0 < y1) load_a(A.acoef, (size_t)y0 * W + a, cn, idn);
     for (int b = y0; b < y1; ++b) {
         const int i = b - y0;
+        const A7 c = cn;
+        const float idiag = idn;
+        if (out_lane && b + 1 < y1) load_a(A.acoef, (size_t)(b + 1) * W + a, cn, idn);
         issue_q(i + kLA + 2);
-        cp_wait<kLA>();
+        cp_wait<kLA - 1>();  // row q = i + 3 has landed
         __syncthreads();
-        to_xprime(i + 2);
-        __syncthreads();
+        to_xprime(i + 3);
         if (out_lane) {
             const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
-            const size_t node = (size_t)b * W + a;
-            A7 c;
-            float idiag;
-            load_a(A.acoef, node, c, idiag);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC], bv[VEC], o[VEC];
             nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
             lds<VEC>(bslot0 + sN * sstride, bv);
@@ -622,17 +648,18 @@ __device__ __forceinline__ void st_apply_dot_body(const StApplyDotArgs& p, const
     float acc[1][VEC];
     zero_vec<VEC>(acc[0]);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
+    A7 cn{};
+    float idn = 0.f;
+    if (out_lane && y0 < y1) load_a(A.acoef, (size_t)y0 * W + a, cn, idn);
     for (int b = y0; b < y1; ++b) {
         const int i = b - y0;
+        const A7 c = cn;
+        if (out_lane && b + 1 < y1) load_a(A.acoef, (size_t)(b + 1) * W + a, cn, idn);
         issue_q(i + kLA + 2);
         cp_wait<kLA>();
         __syncthreads();
         if (out_lane) {
             const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
-            const size_t node = (size_t)b * W + a;
-            A7 c;
-            float idiag;
-            load_a(A.acoef, node, c, idiag);
             float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
             nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
 #pragma unroll

@@ -829,6 +829,16 @@ void periodic_apply(Ctx& c, int level, const T* X, T* Y) {
     c.launches += launch_spmm<T>(SP_PAPPLY, A, t.N, X, nullptr, Y, T(0), Skip{}, c.stream);
 }
 
+void periodic_residual_f32(Ctx& c, int level, const float* X, const float* B, float* R) {
+    const TimeLevel& t = c.tl[level];
+    if (use_stencil<float>(c)) {
+        c.launches += launch_st_presid(st_op(c, 0, t.op), t.N, X, B, R, nullptr, 0.f, false, Skip{}, c.stream);
+    } else {
+        Op<float> A = level_op<float>(c, 0, t.op);
+        c.launches += launch_spmm<float>(SP_PRESID, A, t.N, X, B, R, 0.f, Skip{}, c.stream);
+    }
+}
+
 template <typename T>
 int spatial_pcg(Ctx& c, int op, int N, const T* B, T* X, double tol, int max_it, bool host_check) {
     ensure_work(c, sizeof(T) == 8);
@@ -976,34 +986,25 @@ int autotune(Ctx& c, double* best_us) {
     c.row_block = bestb;
     set_row_block(bestb);
     if (best_us) *best_us = best;
-    // stencil schedule: the level-0 passes of one V-cycle step for every
-    // (largest time tile, blocks per SM); a candidate whose launch plan does
-    // not fit the reduction buffers is skipped
-    if (mixed && use_stencil<float>(c) && c.sl.size() > 1) {
-        const int opi = c.tl[0].op;
-        const StencilOp<float> A0 = st_op(c, 0, opi), A1 = st_op(c, 1, opi);
-        float* w[4] = {c.w_f[0].p, c.w_f[1].p, c.w_f[2].p, c.w_f[3].p};
-        for (int k = 1; k < 4; ++k) PTP_CUDA(cudaMemsetAsync(w[k], 0, cnt * sizeof(float), st));
-        const size_t cnt1 = (size_t)c.sl[1].n * c.N;
-        PTP_CUDA(cudaMemsetAsync(c.g_xf[1].p, 0, cnt1 * sizeof(float), st));
-        ColRed<float> cr = make_cr<float>(c);
-        const bool even = c.N % 2 == 0 && c.tl.size() > 1;
-        auto pass = [&]() {
-            launch_st_presid(A0, c.N, w[0], w[1], w[2], w[3], 0.7f, false, Skip{}, st);
-            launch_st_resid_restrict(A0, A1, c.N, w[0], w[1], c.g_bf[1].p, c.g_xf[1].p, 0.7f, Skip{}, st);
-            launch_st_interp_sweep(A0, c.sl[1].nx - 2, c.sl[1].ny - 2, c.N, c.g_xf[1].p, w[0], w[1], w[2], 0.7f, cr, 1,
-                                   Skip{}, st);
-            if (even) launch_st_presid(A0, c.N, w[0], w[1], mgb<float>(c, 1), nullptr, 0.f, true, Skip{}, st);
-        };
+    // stencil schedule: whole outer steps (every level of both hierarchies
+    // runs with the schedule) for every (largest time tile, blocks per SM),
+    // from a zero start with the stopping rule off; a candidate whose launch
+    // plan does not fit the reduction buffers is skipped
+    const bool hierarchy = c.coarse_ok || c.dft_level >= 0 || c.active_levels < (int)c.tl.size();
+    if (mixed && use_stencil<float>(c) && !c.tl.empty() && hierarchy) {
+        ptp_opts o = c.opts;
+        o.tol = 0.0;
+        const int64_t launches0 = c.launches;
+        solve_begin(c, o, nullptr, STEP_FORWARD);
         double best_st = 1e300;
         int bt = c.st_tt, bw = c.st_waves;
         for (int tt : {8, 16, 32, 64}) {
             for (int wv : {2, 3, 4, 6}) {
                 set_stencil_schedule(tt, wv);
                 try {
-                    for (int r = 0; r < 2; ++r) pass();
+                    enqueue_step(c, STEP_FORWARD);
                     PTP_CUDA(cudaEventRecord(a, st));
-                    for (int r = 0; r < 5; ++r) pass();
+                    for (int r = 0; r < 3; ++r) enqueue_step(c, STEP_FORWARD);
                     PTP_CUDA(cudaEventRecord(b, st));
                     PTP_CUDA(cudaEventSynchronize(b));
                 } catch (const Error& e) {
@@ -1023,6 +1024,7 @@ int autotune(Ctx& c, double* best_us) {
         c.st_tt = bt;
         c.st_waves = bw;
         apply_schedule(c);
+        c.launches = launches0;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -92,6 +92,7 @@ def _load():
         "ptp_apply_shifted_dev": (I, [P, I, P, P]),
         "ptp_apply_shifted_f32_dev": (I, [P, I, P, P]),
         "ptp_periodic_apply_dev": (I, [P, I, P, P]),
+        "ptp_periodic_residual_f32_dev": (I, [P, I, P, P, P]),
         "ptp_spatial_solve_dev": (I, [P, I, P, P, D, I, pI]),
         "ptp_spatial_solve_f32_dev": (I, [P, I, P, P, D, I, pI]),
         "ptp_periodic_solve_dev": (I, [P, ctypes.POINTER(Opts), P, P, I, pD]),
@@ -143,7 +144,7 @@ EXPORTED = [
     "ptp_set_sources", "ptp_set_time",
     "ptp_setup", "ptp_sizes", "ptp_info", "ptp_source", "ptp_source_dev", "ptp_residual", "ptp_residual_dev",
     "ptp_residual_noalloc_dev",
-    "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_spatial_solve_dev",
+    "ptp_apply_shifted_dev", "ptp_apply_shifted_f32_dev", "ptp_periodic_apply_dev", "ptp_periodic_residual_f32_dev", "ptp_spatial_solve_dev",
     "ptp_spatial_solve_f32_dev", "ptp_periodic_solve_dev", "ptp_solve", "ptp_solve_dev",
     "ptp_static_solve", "ptp_static_solve_dev", "ptp_newton_solve", "ptp_newton_solve_dev",
     "ptp_jacobian_apply_dev",
@@ -446,6 +447,11 @@ class Context:
         n = self._count(level)
         return self._check(lib.ptp_periodic_apply_dev(self._h, level, _dev_ptr(X, "float64", n),
                                                       _dev_ptr(Y, "float64", n)))
+
+    def periodic_residual_f32_dev(self, level, X, B, R):
+        n = self._count(level)
+        return self._check(lib.ptp_periodic_residual_f32_dev(self._h, level, _dev_ptr(X, "float32", n),
+                                                             _dev_ptr(B, "float32", n), _dev_ptr(R, "float32", n)))
 
     def spatial_solve_dev(self, level, B, X, tol, max_it):
         it = ctypes.c_int()

@@ -116,3 +116,33 @@ def test_fixed_point_with_the_fused_residual_reaches_the_oracle(precision, tol, 
     U, st, rc = c.solve(o)
     assert rc == ptp.PTP_OK
     assert np.linalg.norm(U - Uo) / np.linalg.norm(Uo) < bar
+
+
+@pytest.mark.parametrize("name,make", [("square33_N32", lambda: W.unit_square_problem(33, 32)),
+                                       ("square17_N6", lambda: W.unit_square_problem(17, 6)),
+                                       ("transformer65x33_N16", lambda: W.transformer_problem(65, 33, 16))])
+def test_periodic_residual_f32_against_the_oracle(name, make):
+    """ptp_periodic_residual_f32_dev at every time level: B - [(M + tau_l L)
+    X^n - M X^{n-1}] in float against the oracle's double operator, to float
+    rounding of the seven-point sums (relative 1e-5 of |B| + |P X|)."""
+    prob = make()
+    d = P.assemble(prob)
+    c, o = _ctx(prob, precision=ptp.PTP_MIXED)
+    rng = np.random.default_rng(11)
+    levels = c.sizes()[3]
+    for l in range(levels):
+        Nl = prob.N >> l
+        if Nl < 1 or prob.N % (1 << l):
+            break
+        tau = d.tau * (1 << l)
+        X = rng.normal(size=(d.n, Nl))
+        B = rng.normal(size=(d.n, Nl))
+        PX = (d.M + tau * d.L) @ X - d.M @ np.roll(X, 1, axis=1)
+        ref = B - PX
+        Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+        Bd = torch.tensor(B, dtype=torch.float32, device="cuda")
+        Rd = torch.empty_like(Xd)
+        c.periodic_residual_f32_dev(l, Xd, Bd, Rd)
+        scale = np.abs(B) + np.abs((d.M + tau * d.L) @ np.abs(X)) + np.abs(d.M @ np.abs(np.roll(X, 1, axis=1)))
+        err = np.abs(Rd.cpu().numpy() - ref)
+        assert np.all(err <= 1e-5 * scale + 1e-30), (l, float((err / scale).max()))
