@@ -49,7 +49,7 @@ struct MergedOp {
     KShape shape;                              // common kind; the largest dynamic shared memory
     std::vector<int> inst;                     // instance of each entry
     std::vector<const RecordedLaunch*> rec;    // its recorded launch
-    size_t off_args = 0, off_start = 0, off_gx = 0, off_gy = 0;
+    size_t off_args = 0, off_inst = 0, off_geo = 0;
     int blocks = 0;
 };
 
@@ -199,38 +199,37 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
                          [&](int x, int y) { return b->recs[x].ops.size() > b->recs[y].ops.size(); });
         for (int i : grp[g]) seqs[g] = merge(std::move(seqs[g]), i, b->recs[i].ops);
     }
-    // work-lists: argument structs, block offsets and virtual grids of every merged launch
+    // work-lists: argument structs, the instance of every block and the
+    // virtual grid of every instance, for every merged launch
     size_t bytes = 0;
     for (auto& seq : seqs)
     for (MergedOp& m : seq) {
         const size_t k = m.inst.size();
+        long total = 0;
+        for (size_t j = 0; j < k; ++j) total += (long)m.rec[j]->shape.gx * std::max(1, m.rec[j]->shape.gy);
+        PTP_REQUIRE(total < (1L << 31), "batched launch: too many blocks");
+        m.blocks = (int)total;
         m.off_args = bytes = align_up(bytes, 256);
         bytes += k * m.rec.front()->args.size();
-        m.off_start = bytes = align_up(bytes, 16);
-        bytes += (k + 1) * sizeof(int);
-        m.off_gx = bytes = align_up(bytes, 16);
-        bytes += k * sizeof(int);
-        m.off_gy = bytes = align_up(bytes, 16);
-        bytes += k * sizeof(int);
+        m.off_geo = bytes = align_up(bytes, 16);
+        bytes += k * sizeof(int4);
+        m.off_inst = bytes = align_up(bytes, 16);
+        bytes += (size_t)total * sizeof(int);
     }
     std::vector<unsigned char> host(std::max<size_t>(bytes, 1), 0);
     for (auto& seq : seqs)
     for (MergedOp& m : seq) {
         const size_t k = m.inst.size(), asz = m.rec.front()->args.size();
-        int* start = reinterpret_cast<int*>(host.data() + m.off_start);
-        int* gx = reinterpret_cast<int*>(host.data() + m.off_gx);
-        int* gy = reinterpret_cast<int*>(host.data() + m.off_gy);
-        long total = 0;
+        int4* geo = reinterpret_cast<int4*>(host.data() + m.off_geo);
+        int* inst_of = reinterpret_cast<int*>(host.data() + m.off_inst);
+        int start = 0;
         for (size_t j = 0; j < k; ++j) {
             std::memcpy(host.data() + m.off_args + j * asz, m.rec[j]->args.data(), asz);
-            start[j] = (int)total;
-            gx[j] = m.rec[j]->shape.gx;
-            gy[j] = std::max(1, m.rec[j]->shape.gy);
-            total += (long)gx[j] * gy[j];
+            const int gx = m.rec[j]->shape.gx, gy = std::max(1, m.rec[j]->shape.gy);
+            geo[j] = make_int4(start, gx, gy, 0);
+            for (int t = 0; t < gx * gy; ++t) inst_of[start + t] = (int)j;
+            start += gx * gy;
         }
-        PTP_REQUIRE(total < (1L << 31), "batched launch: too many blocks");
-        start[k] = (int)total;
-        m.blocks = (int)total;
     }
     if (bytes > 0) {
         PTP_CUDA(cudaMalloc((void**)&b->blob, bytes));
@@ -267,9 +266,8 @@ void enqueue_batched_step(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
         if (g > 0) PTP_CUDA(cudaStreamWaitEvent(st, b->events[K], 0));
         for (const MergedOp& m : b->merged[g]) {
             ptp::BatchMap map;
-            map.start = reinterpret_cast<const int*>(b->blob + m.off_start);
-            map.gx = reinterpret_cast<const int*>(b->blob + m.off_gx);
-            map.gy = reinterpret_cast<const int*>(b->blob + m.off_gy);
+            map.inst_of = reinterpret_cast<const int*>(b->blob + m.off_inst);
+            map.geo = reinterpret_cast<const int4*>(b->blob + m.off_geo);
             map.n = (int)m.inst.size();
             launches += m.fn(b->blob + m.off_args, map, m.blocks, m.shape, st);
         }

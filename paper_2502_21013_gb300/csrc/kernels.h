@@ -32,35 +32,30 @@ bool pdl_enabled();   // false if the environment sets PTP_NO_PDL
 // ---------------------------------------------------------------------------
 // Virtual grids.  Kernel bodies index blocks through a VGrid so that one
 // launch can serve many instances (the batched step): a single launch passes
-// the native grid; a batched launch gives instance i the blocks
-// [start[i], start[i+1]) of a 1-D grid and maps them onto its own gx x gy.
+// the native grid; a batched launch gives instance i a contiguous range of
+// the blocks of a 1-D grid and maps them onto its own gx x gy.
 // ---------------------------------------------------------------------------
 struct VGrid {
     int bx, by, gx, gy;
 };
 struct BatchMap {
-    const int* start;   // n + 1 block offsets
-    const int* gx;      // virtual grid of each instance
-    const int* gy;
+    const int* inst_of;   // instance of every block of the launch
+    const int4* geo;      // per instance: first block, gx, gy
     int n;
 };
 #ifdef __CUDACC__
 __device__ __forceinline__ VGrid native_grid() {
     return VGrid{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
 }
-// instance and virtual block of this block in a batched launch
+// instance and virtual block of this block in a batched launch (two
+// dependent loads: the block's instance, then that instance's geometry)
 __device__ __forceinline__ bool batch_block(const BatchMap& m, int& inst, VGrid& g) {
     const int b = (int)blockIdx.x;
-    int lo = 0, hi = m.n - 1;
-    while (lo < hi) {   // largest i with start[i] <= b
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(m.start + mid) <= b) lo = mid; else hi = mid - 1;
-    }
-    inst = lo;
-    const int local = b - __ldg(m.start + lo);
-    const int gx = __ldg(m.gx + lo), gy = __ldg(m.gy + lo);
-    if (local >= gx * gy) return false;
-    g = VGrid{local % gx, local / gx, gx, gy};
+    inst = __ldg(m.inst_of + b);
+    const int4 q = __ldg(m.geo + inst);
+    const int local = b - q.x;
+    if (local < 0 || local >= q.y * q.z) return false;
+    g = VGrid{local % q.y, local / q.y, q.y, q.z};
     return true;
 }
 #endif
