@@ -138,7 +138,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_pcg_xupdate_b(const XUpdateArgs<T
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) pcg_xupdate_body<T, VEC>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        pcg_xupdate_body<T, VEC>(a_, g);
+    }
 }
 
 int grid_of(size_t count) {

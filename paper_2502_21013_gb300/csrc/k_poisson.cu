@@ -122,7 +122,10 @@ __global__ void __launch_bounds__(kDstThreads) k_dst_b(const DstArgs* __restrict
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) dst_body<TI, TO, TWICE>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        dst_body<TI, TO, TWICE>(a_, g);
+    }
 }
 
 template <typename... KArgs, typename... Args>

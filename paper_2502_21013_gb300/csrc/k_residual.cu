@@ -187,14 +187,20 @@ __global__ void __launch_bounds__(kBlock) k_elem_flux_b(const ElemFluxArgs* __re
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) elem_flux_body(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        elem_flux_body(a_, g);
+    }
 }
 __global__ void __launch_bounds__(kBlock) k_node_residual(ResidualArgs a) { node_residual_body(a, native_grid()); }
 __global__ void __launch_bounds__(kBlock) k_node_residual_b(const ResidualArgs* __restrict__ ps, BatchMap m) {
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) node_residual_body(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        node_residual_body(a_, g);
+    }
 }
 
 // ---------------------------------------------------------------------------

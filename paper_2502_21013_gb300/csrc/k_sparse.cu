@@ -512,7 +512,10 @@ __device__ __forceinline__ void direction_body(const DirArgs<T>& a_, const VGrid
         pdl_enter();                                                                                \
         int i;                                                                                      \
         VGrid g;                                                                                    \
-        if (batch_block(m, i, g)) BODY<TARGS>(ps[i], g);                                            \
+        if (batch_block(m, i, g)) {                                                    \
+            const auto a_ = ps[i];                                                  \
+            BODY<TARGS>(a_, g);                                                     \
+        }                                            \
     }
 #define PTP_COMMA ,
 PTP_ROW_KERNELS(k_spmm, spmm_body, SpmmArgs<T>, typename T PTP_COMMA int VEC PTP_COMMA int MODE, T PTP_COMMA VEC PTP_COMMA MODE)
@@ -595,7 +598,10 @@ __global__ void __launch_bounds__(256) k_dense_apply_b(const DenseArgs<T>* __res
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) dense_apply_body<T>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        dense_apply_body<T>(a_, g);
+    }
 }
 
 template <typename T>
@@ -619,7 +625,10 @@ __global__ void k_time_prolong_add_b(const ProlongArgs<T>* __restrict__ ps, Batc
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) time_prolong_add_body<T>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        time_prolong_add_body<T>(a_, g);
+    }
 }
 
 template <typename T>
@@ -637,7 +646,10 @@ __global__ void k_add_to_double_b(const AddArgs<T>* __restrict__ ps, BatchMap m)
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) add_to_double_body<T>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        add_to_double_body<T>(a_, g);
+    }
 }
 
 template <typename T>

@@ -300,11 +300,7 @@ __device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGri
     };
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
-    // every lane computes (the column shuffles need the whole warp); halo
-    // lanes read an interior slot and store nothing
-    const int lnc = (L.ln >= 1 && L.ln <= L.sx - 2) ? L.ln : 1;
-    const bool from_left = L.lc > 0 && (threadIdx.x & 31) != 0;   // column col - 1 is in the lane to the left
-    const float* pre_base = xr + (size_t)L.lc * VEC - 1;         // the same from shared memory (lc > 0)
+    const float* pre_base = xr + (size_t)L.lc * VEC - 1;       // column col - 1 within a slot row (lc > 0)
     // this node's coefficients for the next row, loaded one row ahead
     A7 cn{}, mn{};
     float idn = 0.f;
@@ -323,30 +319,27 @@ __device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGri
         issue_q(i + kLA + 2);
         cp_wait<kLA>();
         __syncthreads();
-        const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
-        float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
-        nbrs<VEC>(xr, sS, sC, sN, lnc, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
-        // column col - 1 of the seven nodes: the lane to the left's last column,
-        // else shared memory (a node split across warps), else the tile's previous column
-        auto before = [&](int slot, int nd, float mine) -> float {
-            const float up = __shfl_up_sync(0xffffffffu, mine, 1);
-            if (from_left) return up;
-            return L.lc > 0 ? pre_base[((size_t)slot * L.sx + nd) * TT] : prev[slot * L.sx + nd];
-        };
-        float p_c = before(sC, lnc, xc[VEC - 1]), p_e = before(sC, lnc + 1, xe[VEC - 1]),
-              p_w = before(sC, lnc - 1, xw[VEC - 1]), p_n = before(sN, lnc, xn[VEC - 1]),
-              p_s = before(sS, lnc, xs[VEC - 1]), p_ne = before(sN, lnc + 1, xne[VEC - 1]),
-              p_sw = before(sS, lnc - 1, xsw[VEC - 1]);
-        float bv[VEC], r[VEC];
-        lds<VEC>(srow<VEC>(br, sN, lnc, L.sx, TT, L.lc), bv);
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-            const float ax = apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
-            const float mx = m.c * p_c + m.e * p_e + m.w * p_w + m.n * p_n + m.s * p_s + m.ne * p_ne + m.sw * p_sw;
-            r[v] = bv[v] - (ax - mx);
-            p_c = xc[v]; p_e = xe[v]; p_w = xw[v]; p_n = xn[v]; p_s = xs[v]; p_ne = xne[v]; p_sw = xsw[v];
-        }
         if (out_lane) {
+            const int sS = sl8(i), sC = sl8(i + 1), sN = sl8(i + 2);
+            float xc[VEC], xe[VEC], xw[VEC], xn[VEC], xs[VEC], xne[VEC], xsw[VEC];
+            nbrs<VEC>(xr, sS, sC, sN, L.ln, L.sx, TT, L.lc, xc, xe, xw, xn, xs, xne, xsw);
+            // column col - 1 of the seven nodes: from the lane to the left, or the tile's previous column
+            auto before = [&](int slot, int nd) -> float {
+                return L.lc > 0 ? pre_base[((size_t)slot * L.sx + nd) * TT] : prev[slot * L.sx + nd];
+            };
+            float p_c = before(sC, L.ln), p_e = before(sC, L.ln + 1), p_w = before(sC, L.ln - 1);
+            float p_n = before(sN, L.ln), p_s = before(sS, L.ln), p_ne = before(sN, L.ln + 1),
+                  p_sw = before(sS, L.ln - 1);
+            float bv[VEC], r[VEC];
+            lds<VEC>(bslot0 + sN * sstride, bv);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const float ax = apply7<VEC>(c, xc, xe, xw, xn, xs, xne, xsw, v);
+                const float mx = m.c * p_c + m.e * p_e + m.w * p_w + m.n * p_n + m.s * p_s + m.ne * p_ne +
+                                 m.sw * p_sw;
+                r[v] = bv[v] - (ax - mx);
+                p_c = xc[v]; p_e = xe[v]; p_w = xw[v]; p_n = xn[v]; p_s = xs[v]; p_ne = xne[v]; p_sw = xsw[v];
+            }
             if constexpr (MODE == 0) {
                 const long o = cx.off(b);
                 st_vec<float, VEC>(R + o, r);
@@ -787,7 +780,10 @@ __global__ void __launch_bounds__(256) k_st_copy_sweep_b(const StCopyArgs* __res
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) st_copy_sweep_body<VEC>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        st_copy_sweep_body<VEC>(a_, g);
+    }
 }
 template <int VEC, int MODE>
 __global__ void __launch_bounds__(kStBlock) k_st_presid(StPresidArgs p) {
@@ -798,7 +794,10 @@ __global__ void __launch_bounds__(kStBlock) k_st_presid_b(const StPresidArgs* __
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) st_presid_body<VEC, MODE>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        st_presid_body<VEC, MODE>(a_, g);
+    }
 }
 template <int VEC>
 __global__ void __launch_bounds__(kStBlock) k_st_resid_restrict(StRestrictArgs p) {
@@ -809,7 +808,10 @@ __global__ void __launch_bounds__(kStBlock) k_st_resid_restrict_b(const StRestri
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) st_resid_restrict_body<VEC>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        st_resid_restrict_body<VEC>(a_, g);
+    }
 }
 template <int VEC, int DOTS>
 __global__ void __launch_bounds__(kStBlock) k_st_interp_sweep(StInterpArgs p) {
@@ -820,7 +822,10 @@ __global__ void __launch_bounds__(kStBlock) k_st_interp_sweep_b(const StInterpAr
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) st_interp_sweep_body<VEC, DOTS>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        st_interp_sweep_body<VEC, DOTS>(a_, g);
+    }
 }
 template <int VEC>
 __global__ void __launch_bounds__(kStBlock) k_st_apply_dot(StApplyDotArgs p) {
@@ -831,7 +836,10 @@ __global__ void __launch_bounds__(kStBlock) k_st_apply_dot_b(const StApplyDotArg
     pdl_enter();
     int i;
     VGrid g;
-    if (batch_block(m, i, g)) st_apply_dot_body<VEC>(ps[i], g);
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        st_apply_dot_body<VEC>(a_, g);
+    }
 }
 
 // ---- plans: arguments and shape of one call ----
