@@ -421,12 +421,13 @@ def transformer_leg(args, local, dev, stream, world, hbm_peak):
 def batched_leg(args, local, dev, world):
     """Batched uneven instances (meshes drawn from {65,129,257,513}^2 nodes,
     N from {64..512}, J0 ~ U[20,80], s_sat ~ U[0.5,2]), mixed precision to
-    1e-8 from U = 0, every instance in one merged CUDA-graph launch per
-    fixed-point step.  Bounded sample: the first `batched_count` instances of
-    the seeded 64-instance draw (the whole draw is a separate workload,
-    --workload batched64).  Also timed: the same batch with every instance
-    as a graph branch of its own (its launches unmerged), over a fixed
-    number of steps, for the per-step cost of merging."""
+    1e-8 from U = 0, one CUDA-graph launch per fixed-point step in the
+    layout the batch's autotuner picks (merged programs or one branch per
+    instance).  Bounded sample: the first `batched_count` instances of the
+    seeded 64-instance draw (the whole draw is a separate workload,
+    --workload batched64).  Also timed over a fixed number of steps: both
+    layouts on this batch and on 64 small instances (17x17 nodes, N = 16),
+    where the steps are launch-bound."""
     import torch
     from paper_2502_21013_gb300 import ptp
     rank = int(os.environ.get("RANK", "0"))
@@ -468,6 +469,26 @@ def batched_leg(args, local, dev, world):
                           "launches_per_step": batch.plan_info()[0]}
     batch.close()
     del ctxs
+    small = []
+    sb = ptp.Batch(local)
+    for k in range(64):
+        c = ptp.Context(local)
+        ptp.load_problem(c, W.unit_square_problem(17, 16, amps=(20.0 + k,)))
+        c.setup(ptp.default_opts(precision=ptp.PTP_MIXED))
+        small.append(c)
+        sb.add(c)
+    per_step_small = {}
+    for mode, name in ((ptp.PTP_BATCH_MERGED, "merged"), (ptp.PTP_BATCH_BRANCHES, "branches")):
+        sb.set_mode(mode)
+        sb.solve(ptp.default_opts(precision=ptp.PTP_MIXED, tol=0.0, max_outer=2))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sb.solve(fixed)
+        torch.cuda.synchronize()
+        per_step_small[name] = {"ms_per_step": (time.perf_counter() - t) * 1e3 / fixed.max_outer,
+                                "launches_per_step": sb.plan_info()[0]}
+    sb.close()
+    del small
     torch.cuda.empty_cache()
     return {"workload": "batched_uneven", "value": reduce_scalar(dofs, "sum", dev, world) / el, "unit": UNIT,
             "sample": f"the first {len(probs)} of the 64 seeded instances", "instances": len(probs),
@@ -476,7 +497,8 @@ def batched_leg(args, local, dev, world):
             "outer_iterations": [s.outer_iterations for s in stats],
             "grids_and_steps": [f"{int(round(math.sqrt(p.n_nodes)))}^2 N={p.N}" for p in probs],
             "launches_per_step": lps, "merged_instances": merged, "merged_launches": nmerged,
-            "per_step_64": per_step, "gpu_launches": int(lps * steps),
+            "layout": "merged" if merged else "branches",
+            "per_step_64": per_step, "per_step_64_small_17x17_N16": per_step_small, "gpu_launches": int(lps * steps),
             "autotuned_schedules": {f"rows{b}_tile{t}_waves{w}": schedules.count((b, t, w))
                                     for (b, t, w) in sorted(set(schedules))}}
 

@@ -305,6 +305,7 @@ int ptp_autotune(ptp_ctx* ctx, int* block_threads, double* best_us);
    Same device only. */
 #define PTP_BATCH_MERGED   0
 #define PTP_BATCH_BRANCHES 1
+#define PTP_BATCH_AUTO     2   /* default: the faster of the two, timed */
 typedef struct ptp_batch ptp_batch;
 int  ptp_batch_create(ptp_batch** out, int device);
 void ptp_batch_destroy(ptp_batch* batch);
@@ -323,7 +324,12 @@ int  ptp_batch_size(const ptp_batch* batch);
 int  ptp_batch_solve(ptp_batch* batch, const ptp_opts* opts, ptp_stats* stats, int* n_converged);
 /* Copies instance i's current iterate (device U, [n_free][N]). */
 int  ptp_batch_result_dev(ptp_batch* batch, int i, double* U);
-/* PTP_BATCH_MERGED or PTP_BATCH_BRANCHES (takes effect at the next solve). */
+/* PTP_BATCH_MERGED, PTP_BATCH_BRANCHES or PTP_BATCH_AUTO (takes effect at
+   the next solve).  AUTO (the default) times a few steps of one branch per
+   instance, one merged program and four merged groups when the step is
+   captured, keeps the fastest, and restarts every instance from zero: merged
+   launches win when the instances are small (launch-bound steps), separate
+   branches when they are large enough to fill the GPU alone. */
 int  ptp_batch_set_mode(ptp_batch* batch, int mode);
 /* Merged mode: the instances are split into `groups` (1..64, default 4)
    groups of about equal space-time size, each merged into its own program;

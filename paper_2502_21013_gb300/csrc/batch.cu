@@ -112,8 +112,9 @@ struct ptp_batch {
     std::vector<int64_t> per_step;
     std::vector<cudaEvent_t> events;
     std::string err;
-    int mode = PTP_BATCH_MERGED;
-    int groups = 4;                 // merged programs that run concurrently
+    int mode = PTP_BATCH_AUTO;      // requested layout
+    int groups = 4;                 // merged programs that run concurrently (PTP_BATCH_MERGED)
+    int use_mode = PTP_BATCH_MERGED, use_groups = 4;   // layout of the captured step
     std::vector<cudaStream_t> gstreams;
     std::vector<cudaEvent_t> gevents;
     // the merged programs, one per group of instances
@@ -166,7 +167,7 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
     b->per_step.assign(K, 0);
     std::vector<int> mergeable;
     for (int i = 0; i < K; ++i) {
-        if (b->mode != PTP_BATCH_MERGED) {
+        if (b->use_mode != PTP_BATCH_MERGED) {
             b->branch.push_back(i);
             continue;
         }
@@ -180,7 +181,7 @@ void plan(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
     }
     // groups balanced by space-time size (largest first onto the lightest
     // group); inside a group the longest programs form the backbone
-    const int G = std::max(1, std::min(b->groups, (int)mergeable.size()));
+    const int G = std::max(1, std::min(b->use_groups, (int)mergeable.size()));
     std::vector<std::vector<int>> grp(G);
     {
         std::vector<int> order = mergeable;
@@ -278,6 +279,22 @@ void enqueue_batched_step(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
     b->step_launches = launches;
 }
 
+// plan and capture one step of every instance in the layout b->use_mode / use_groups
+void capture_step(ptp_batch* b, const std::vector<ptp::Ctx*>& cs) {
+    plan(b, cs);
+    cudaGraph_t g;
+    PTP_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        enqueue_batched_step(b, cs);
+    } catch (...) {
+        cudaStreamEndCapture(b->stream, &g);
+        throw;
+    }
+    PTP_CUDA(cudaStreamEndCapture(b->stream, &g));
+    PTP_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+    cudaGraphDestroy(g);
+}
+
 }  // namespace
 
 extern "C" {
@@ -331,7 +348,8 @@ int ptp_batch_size(const ptp_batch* b) { return b ? (int)b->items.size() : PTP_E
 
 int ptp_batch_set_mode(ptp_batch* b, int mode) {
     return batch_guard(b, [&]() {
-        PTP_REQUIRE(mode == PTP_BATCH_MERGED || mode == PTP_BATCH_BRANCHES, "ptp_batch_set_mode: bad mode");
+        PTP_REQUIRE(mode == PTP_BATCH_MERGED || mode == PTP_BATCH_BRANCHES || mode == PTP_BATCH_AUTO,
+                    "ptp_batch_set_mode: bad mode");
         if (mode != b->mode) drop_graph(b);
         b->mode = mode;
         return PTP_OK;
@@ -401,18 +419,48 @@ int ptp_batch_solve(ptp_batch* b, const ptp_opts* opts, ptp_stats* stats, int* n
                 PTP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
                 b->events.push_back(e);
             }
-            plan(b, cs);
-            cudaGraph_t g;
-            PTP_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            try {
-                enqueue_batched_step(b, cs);
-            } catch (...) {
-                cudaStreamEndCapture(b->stream, &g);
-                throw;
+            if (b->mode == PTP_BATCH_AUTO) {
+                // layout autotuner: a few steps of each candidate, the fastest kept;
+                // then every instance starts again from zero
+                struct Layout { int mode, groups; };
+                const Layout cands[3] = {{PTP_BATCH_BRANCHES, 1}, {PTP_BATCH_MERGED, 1}, {PTP_BATCH_MERGED, 4}};
+                cudaEvent_t e0, e1;
+                PTP_CUDA(cudaEventCreate(&e0));
+                PTP_CUDA(cudaEventCreate(&e1));
+                double best = 1e300;
+                Layout bl = cands[0];
+                for (const Layout& cd : cands) {
+                    if (cd.groups > 1 && K < 2 * cd.groups) continue;
+                    b->use_mode = cd.mode;
+                    b->use_groups = cd.groups;
+                    capture_step(b, cs);
+                    for (int i = 0; i < K; ++i) PTP_CUDA(cudaStreamSynchronize(cs[i]->stream));
+                    for (int r = 0; r < 2; ++r) PTP_CUDA(cudaGraphLaunch(b->exec, b->stream));
+                    PTP_CUDA(cudaEventRecord(e0, b->stream));
+                    for (int r = 0; r < 3; ++r) PTP_CUDA(cudaGraphLaunch(b->exec, b->stream));
+                    PTP_CUDA(cudaEventRecord(e1, b->stream));
+                    PTP_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    PTP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        bl = cd;
+                    }
+                    drop_graph(b);
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                b->use_mode = bl.mode;
+                b->use_groups = bl.groups;
+                for (int i = 0; i < K; ++i) {
+                    ptp::apply_schedule(*cs[i]);
+                    ptp::solve_begin(*cs[i], cs[i]->opts, nullptr, ptp::STEP_FORWARD);
+                }
+            } else {
+                b->use_mode = b->mode;
+                b->use_groups = b->groups;
             }
-            PTP_CUDA(cudaStreamEndCapture(b->stream, &g));
-            PTP_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
-            cudaGraphDestroy(g);
+            capture_step(b, cs);
             b->keys = keys;
         }
         // every context's stream must see its set-up work before the graph runs

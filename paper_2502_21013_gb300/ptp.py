@@ -21,7 +21,7 @@ PTP_OK, PTP_EINVAL, PTP_ECUDA, PTP_ENOTCONV, PTP_ENAN, PTP_ESTATE, PTP_ENOMEM = 
 PTP_FP64, PTP_MIXED = 0, 1
 PTP_PREC_JACOBI, PTP_PREC_GMG = 0, 1
 PTP_COARSE_VCYCLES, PTP_COARSE_DFT = 0, 1
-PTP_BATCH_MERGED, PTP_BATCH_BRANCHES = 0, 1
+PTP_BATCH_MERGED, PTP_BATCH_BRANCHES, PTP_BATCH_AUTO = 0, 1, 2
 
 
 class Opts(ctypes.Structure):

@@ -50,6 +50,7 @@ def _oracle_solution(i, prob):
     (ptp.PTP_FP64, 1e-13, 1e-10, ptp.PTP_BATCH_MERGED),
     (ptp.PTP_MIXED, 1e-11, 1e-8, ptp.PTP_BATCH_MERGED),
     (ptp.PTP_MIXED, 1e-11, 1e-8, ptp.PTP_BATCH_BRANCHES),
+    (ptp.PTP_MIXED, 1e-11, 1e-8, ptp.PTP_BATCH_AUTO),
 ])
 def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar, mode):
     """Every instance of the batch is bitwise the instance solved alone (the
@@ -77,8 +78,10 @@ def test_batch_equals_individual_solves_and_the_oracle(precision, tol, bar, mode
     lps, merged, nmerged = batch.plan_info()
     if mode == ptp.PTP_BATCH_MERGED:
         assert merged == len(probs) and nmerged == lps
-    else:
+    elif mode == ptp.PTP_BATCH_BRANCHES:
         assert merged == 0 and nmerged == 0
+    else:   # the timed choice: one of the layouts, every instance restarted from zero
+        assert merged in (0, len(probs))
     results = []
     for i, p in enumerate(probs):
         Ub = torch.empty((p.n_free, p.N), dtype=torch.float64, device="cuda")
@@ -134,6 +137,7 @@ def test_merged_launches_do_not_grow_with_the_instances():
     counts = []
     for copies in (1, 3):
         batch = ptp.Batch(0)
+        batch.set_mode(ptp.PTP_BATCH_MERGED)
         batch.set_groups(1)
         keep = []
         for _ in range(copies):
@@ -159,6 +163,7 @@ def test_groups_run_concurrently_and_keep_results():
     res = {}
     for groups in (1, 2, 4):
         batch = ptp.Batch(0)
+        batch.set_mode(ptp.PTP_BATCH_MERGED)
         batch.set_groups(groups)
         keep = []
         for mk in makes:
