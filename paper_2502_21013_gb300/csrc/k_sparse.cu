@@ -529,21 +529,23 @@ PTP_ROW_KERNELS(k_pcg_direction, direction_body, DirArgs<T>, typename T PTP_COMM
 #undef PTP_COMMA
 
 // Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600).
-// A block computes a 32 x 32 tile of Y (rows i, columns c; four rows per
-// thread) from the 32 rows of Ainv and the 32 columns of B it needs, copied
-// to shared memory kc values of k at a time (kc = n when it fits, so one
-// chunk in float).  Every copy of a chunk is in flight at once (cp.async,
-// zero-filled outside the matrices): this small product is bound by latency,
-// and one round trip per chunk replaces one per 32-wide panel.
-constexpr int kDT = 32;
+// A block computes an 8 x 32 tile of Y (one row and column per thread) from
+// the 8 rows of Ainv and the 32 columns of B it needs, copied to shared
+// memory kc values of k at a time (kc = n when it fits, so one chunk in
+// float).  Every copy of a chunk is in flight at once (cp.async, zero-filled
+// outside the matrices).  The product is small and bound by latency: small
+// tiles give many blocks, and two partial sums per thread halve the chain of
+// dependent FMAs.
+constexpr int kDT = 32;   // columns of a tile
+constexpr int kDR = 8;    // rows of a tile
 constexpr size_t kDenseSmem = 96 * 1024;
 template <typename T>
 int dense_chunk(int n) {   // k values per chunk
-    const int fit = (int)((kDenseSmem / sizeof(T) - kDT) / (2 * kDT));
+    const int fit = (int)((kDenseSmem / sizeof(T) - kDR) / (kDR + kDT));
     return std::max(1, std::min(n, fit));
 }
 template <typename T>
-size_t dense_smem(int kc) { return (size_t)(kDT * (kc + 1) + kc * kDT) * sizeof(T); }
+size_t dense_smem(int kc) { return (size_t)(kDR * (kc + 1) + kc * kDT) * sizeof(T); }
 
 template <typename T>
 __device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VGrid& g) {
@@ -554,14 +556,14 @@ __device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VG
     const T* __restrict__ B = p.B;
     T* __restrict__ Y = p.Y;
     extern __shared__ __align__(16) unsigned char dense_smem_raw[];
-    T* As = reinterpret_cast<T*>(dense_smem_raw);   // [32][kc + 1]
-    T* Bs = As + kDT * (kc + 1);                    // [kc][32]
-    const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row group (8 groups of 4 rows)
-    const int c0 = g.bx * kDT, i0 = g.by * kDT;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    T* As = reinterpret_cast<T*>(dense_smem_raw);   // [8][kc + 1]
+    T* Bs = As + kDR * (kc + 1);                    // [kc][32]
+    const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row of the tile
+    const int c0 = g.bx * kDT, i0 = g.by * kDR;
+    T acc0 = T(0), acc1 = T(0);
     for (int k0 = 0; k0 < n; k0 += kc) {
         const int kk = min(kc, n - k0);
-        for (int e = threadIdx.x; e < kDT * kc; e += blockDim.x) {
+        for (int e = threadIdx.x; e < kDR * kc; e += blockDim.x) {
             const int r = e / kc, q = e - r * kc;
             const bool ok = i0 + r < n && q < kk;
             cp_async<sizeof(T)>(As + r * (kc + 1) + q, ok ? A + (size_t)(i0 + r) * n + (k0 + q) : A, ok);
@@ -574,22 +576,18 @@ __device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VG
         cp_commit();
         cp_wait<0>();
         __syncthreads();
-        const T* ar = As + (ty * 4) * (kc + 1);
+        const T* ar = As + ty * (kc + 1);
+        int k = 0;
 #pragma unroll 4
-        for (int k = 0; k < kk; ++k) {
-            const T b = Bs[k * kDT + tx];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[r] += ar[r * (kc + 1) + k] * b;
+        for (; k + 1 < kk; k += 2) {
+            acc0 += ar[k] * Bs[k * kDT + tx];
+            acc1 += ar[k + 1] * Bs[(k + 1) * kDT + tx];
         }
+        if (k < kk) acc0 += ar[k] * Bs[k * kDT + tx];
         __syncthreads();
     }
-    const int c = c0 + tx;
-    if (c < N)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = i0 + ty * 4 + r;
-            if (i < n) Y[(size_t)i * N + c] = acc[r];
-        }
+    const int c = c0 + tx, i = i0 + ty;
+    if (c < N && i < n) Y[(size_t)i * N + c] = acc0 + acc1;
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_apply(DenseArgs<T> p) { dense_apply_body<T>(p, native_grid()); }
@@ -1020,7 +1018,7 @@ int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, c
     const DenseArgs<T> a{n, N, kc, Ainv, B, Y, sk};
     KShape sh;
     sh.gx = (N + kDT - 1) / kDT;
-    sh.gy = (n + kDT - 1) / kDT;
+    sh.gy = (n + kDR - 1) / kDR;
     sh.block = 256;
     sh.smem = dense_smem<T>(kc);
     if (record_launch(launch_dense_apply_batch<T>, a, sh)) return 1;
