@@ -117,7 +117,6 @@ struct OpPair {
     double cm = 1.0, cl = 0.0;
     DBuf<double> inv_d;  // dense inverse on the coarsest spatial level (row-major)
     DBuf<float> inv_f;
-    bool inv_f_ok = true;  // inv_f keeps its accuracy; else the float path applies inv_d
     // per spatial level, double: padded-ELL values cm M + cl L and its diagonal,
     // formed once so the double row kernels spend no FMA on the combination
     std::vector<DBuf<double>> comb, dcomb;

@@ -539,34 +539,34 @@ PTP_ROW_KERNELS(k_pcg_direction, direction_body, DirArgs<T>, typename T PTP_COMM
 constexpr int kDT = 32;   // columns of a tile
 constexpr int kDR = 8;    // rows of a tile
 constexpr size_t kDenseSmem = 96 * 1024;
-template <typename T, typename TA = T>
+template <typename T>
 int dense_chunk(int n) {   // k values per chunk
-    const int fit = (int)((kDenseSmem - kDR * sizeof(TA)) / (kDR * sizeof(TA) + kDT * sizeof(T)));
+    const int fit = (int)((kDenseSmem / sizeof(T) - kDR) / (kDR + kDT));
     return std::max(1, std::min(n, fit));
 }
-template <typename T, typename TA = T>
-size_t dense_smem(int kc) { return (size_t)kDR * (kc + 1) * sizeof(TA) + (size_t)kc * kDT * sizeof(T); }
+template <typename T>
+size_t dense_smem(int kc) { return (size_t)(kDR * (kc + 1) + kc * kDT) * sizeof(T); }
 
-template <typename T, typename TA>
-__device__ __forceinline__ void dense_apply_body(const DenseArgs<T, TA>& p, const VGrid& g) {
+template <typename T>
+__device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VGrid& g) {
     pdl_enter();
     if (skip_now(p.sk)) return;
     const int n = p.n, N = p.N, kc = p.kc;
-    const TA* __restrict__ A = p.A;
+    const T* __restrict__ A = p.A;
     const T* __restrict__ B = p.B;
     T* __restrict__ Y = p.Y;
     extern __shared__ __align__(16) unsigned char dense_smem_raw[];
-    TA* As = reinterpret_cast<TA*>(dense_smem_raw);                     // [8][kc + 1]
-    T* Bs = reinterpret_cast<T*>(As + kDR * (kc + 1));                 // [kc][32]
+    T* As = reinterpret_cast<T*>(dense_smem_raw);   // [8][kc + 1]
+    T* Bs = As + kDR * (kc + 1);                    // [kc][32]
     const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row of the tile
     const int c0 = g.bx * kDT, i0 = g.by * kDR;
-    TA acc0 = TA(0), acc1 = TA(0);
+    T acc0 = T(0), acc1 = T(0);
     for (int k0 = 0; k0 < n; k0 += kc) {
         const int kk = min(kc, n - k0);
         for (int e = threadIdx.x; e < kDR * kc; e += blockDim.x) {
             const int r = e / kc, q = e - r * kc;
             const bool ok = i0 + r < n && q < kk;
-            cp_async<sizeof(TA)>(As + r * (kc + 1) + q, ok ? A + (size_t)(i0 + r) * n + (k0 + q) : A, ok);
+            cp_async<sizeof(T)>(As + r * (kc + 1) + q, ok ? A + (size_t)(i0 + r) * n + (k0 + q) : A, ok);
         }
         for (int e = threadIdx.x; e < kc * kDT; e += blockDim.x) {
             const int r = e / kDT, q = e - r * kDT;
@@ -576,31 +576,29 @@ __device__ __forceinline__ void dense_apply_body(const DenseArgs<T, TA>& p, cons
         cp_commit();
         cp_wait<0>();
         __syncthreads();
-        const TA* ar = As + ty * (kc + 1);
+        const T* ar = As + ty * (kc + 1);
         int k = 0;
 #pragma unroll 4
         for (; k + 1 < kk; k += 2) {
-            acc0 += ar[k] * (TA)Bs[k * kDT + tx];
-            acc1 += ar[k + 1] * (TA)Bs[(k + 1) * kDT + tx];
+            acc0 += ar[k] * Bs[k * kDT + tx];
+            acc1 += ar[k + 1] * Bs[(k + 1) * kDT + tx];
         }
-        if (k < kk) acc0 += ar[k] * (TA)Bs[k * kDT + tx];
+        if (k < kk) acc0 += ar[k] * Bs[k * kDT + tx];
         __syncthreads();
     }
     const int c = c0 + tx, i = i0 + ty;
-    if (c < N && i < n) Y[(size_t)i * N + c] = (T)(acc0 + acc1);
+    if (c < N && i < n) Y[(size_t)i * N + c] = acc0 + acc1;
 }
-template <typename T, typename TA>
-__global__ void __launch_bounds__(256) k_dense_apply(DenseArgs<T, TA> p) {
-    dense_apply_body<T, TA>(p, native_grid());
-}
-template <typename T, typename TA>
-__global__ void __launch_bounds__(256) k_dense_apply_b(const DenseArgs<T, TA>* __restrict__ ps, BatchMap m) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply(DenseArgs<T> p) { dense_apply_body<T>(p, native_grid()); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply_b(const DenseArgs<T>* __restrict__ ps, BatchMap m) {
     pdl_enter();
     int i;
     VGrid g;
     if (batch_block(m, i, g)) {
         const auto a_ = ps[i];   // a local copy: no store of the body aliases it
-        dense_apply_body<T, TA>(a_, g);
+        dense_apply_body<T>(a_, g);
     }
 }
 
@@ -1006,36 +1004,27 @@ void grant_smem(void (*kernel)(KArgs...), size_t smem) {
     }
 }
 
-template <typename T, typename TA>
+template <typename T>
 int launch_dense_apply_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {
-    grant_smem(k_dense_apply_b<T, TA>, sh.smem);
-    launch_k_smem(k_dense_apply_b<T, TA>, dim3(blocks), dim3(256), sh.smem, s,
-                  static_cast<const DenseArgs<T, TA>*>(args), m);
-    return 1;
-}
-
-template <typename T, typename TA>
-int dense_go(int n, int N, const TA* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    const int kc = dense_chunk<T, TA>(n);
-    const DenseArgs<T, TA> a{n, N, kc, Ainv, B, Y, sk};
-    KShape sh;
-    sh.gx = (N + kDT - 1) / kDT;
-    sh.gy = (n + kDR - 1) / kDR;
-    sh.block = 256;
-    sh.smem = dense_smem<T, TA>(kc);
-    if (record_launch(launch_dense_apply_batch<T, TA>, a, sh)) return 1;
-    grant_smem(k_dense_apply<T, TA>, sh.smem);
-    launch_k_smem(k_dense_apply<T, TA>, dim3(sh.gx, sh.gy), dim3(256), sh.smem, s, a);
+    grant_smem(k_dense_apply_b<T>, sh.smem);
+    launch_k_smem(k_dense_apply_b<T>, dim3(blocks), dim3(256), sh.smem, s, static_cast<const DenseArgs<T>*>(args),
+                  m);
     return 1;
 }
 
 template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s) {
-    return dense_go<T, T>(n, N, Ainv, B, Y, sk, s);
-}
-
-int launch_dense_apply_mixed(int n, int N, const double* Ainv, const float* B, float* Y, Skip sk, cudaStream_t s) {
-    return dense_go<float, double>(n, N, Ainv, B, Y, sk, s);
+    const int kc = dense_chunk<T>(n);
+    const DenseArgs<T> a{n, N, kc, Ainv, B, Y, sk};
+    KShape sh;
+    sh.gx = (N + kDT - 1) / kDT;
+    sh.gy = (n + kDR - 1) / kDR;
+    sh.block = 256;
+    sh.smem = dense_smem<T>(kc);
+    if (record_launch(launch_dense_apply_batch<T>, a, sh)) return 1;
+    grant_smem(k_dense_apply<T>, sh.smem);
+    launch_k_smem(k_dense_apply<T>, dim3(sh.gx, sh.gy), dim3(256), sh.smem, s, a);
+    return 1;
 }
 
 template <typename T>

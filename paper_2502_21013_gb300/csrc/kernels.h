@@ -465,19 +465,16 @@ template <typename T>   // x = (tau_c L)^{-1} b, both [W x H] node order (one co
 int launch_dst_solve(const DstSolve& d, const T* b, T* x, Skip sk, cudaStream_t s);
 
 // dense coarse-level apply Y = Ainv B  (n x n, row-major)
-template <typename T, typename TA = T>   // TA: the inverse's type and the accumulation
+template <typename T>
 struct DenseArgs {
     int n, N, kc;   // kc: k values staged in shared memory per chunk
-    const TA* A;
+    const T* A;
     const T* B;
     T* Y;
     Skip sk;
 };
 template <typename T>
 int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, cudaStream_t s);
-// float columns through the double inverse, accumulated in double (coarsest
-// levels whose inverse loses its accuracy when rounded to float)
-int launch_dense_apply_mixed(int n, int N, const double* Ainv, const float* B, float* Y, Skip sk, cudaStream_t s);
 template <typename T>
 struct ProlongArgs {   // x^{2m}, x^{2m+1} += xc^m
     int rows, Nc;

@@ -5,7 +5,6 @@
 // homogeneous Dirichlet nodes removed, implicit Euler with tau = T/N.
 #include <algorithm>
 #include <cmath>
-#include <cstdint>
 #include <cstring>
 #include <map>
 
@@ -203,47 +202,6 @@ std::vector<double> dense_inverse(const HostCSR& M, const HostCSR& L, double cm,
 
 std::vector<float> to_float(const std::vector<double>& v) {
     return std::vector<float>(v.begin(), v.end());
-}
-
-// Whether the coarsest inverse keeps its use rounded to float: with F the
-// float-rounded inverse applied with float sums (as the float V-cycle does),
-// ||A F v - v|| / ||v|| for two pseudo-random v against 1e-2.  Rounding puts
-// an error of about 2^-24 |A^-1| |v| into F v, which A amplifies by its
-// condition number: operators beyond about 1e5 (coefficient jumps, as the
-// K_hat weights of the paper's transformer) fail and keep a double apply.
-static bool float_inverse_ok(const HostCSR& M, const HostCSR& L, double cm, double cl,
-                             const std::vector<double>& inv) {
-    const int n = M.rows;
-    std::vector<float> f(inv.begin(), inv.end());
-    std::vector<double> v(n), w(n);
-    uint64_t st = 0x243F6A8885A308D3ull;
-    double worst = 0.0;
-    for (int t = 0; t < 2; ++t) {
-        for (auto& x : v) {
-            st = st * 6364136223846793005ull + 1442695040888963407ull;
-            x = (double)(st >> 11) / 9007199254740992.0 - 0.5;
-        }
-        for (int i = 0; i < n; ++i) {
-            float a0 = 0.f, a1 = 0.f;
-            int j = 0;
-            for (; j + 1 < n; j += 2) {
-                a0 += f[(size_t)i * n + j] * (float)v[j];
-                a1 += f[(size_t)i * n + j + 1] * (float)v[j + 1];
-            }
-            if (j < n) a0 += f[(size_t)i * n + j] * (float)v[j];
-            w[i] = (double)(a0 + a1);
-        }
-        double e2 = 0.0, v2 = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double a = 0.0;
-            for (int k = M.ptr[i]; k < M.ptr[i + 1]; ++k) a += cm * M.val[k] * w[M.idx[k]];
-            for (int k = L.ptr[i]; k < L.ptr[i + 1]; ++k) a += cl * L.val[k] * w[L.idx[k]];
-            e2 += (a - v[i]) * (a - v[i]);
-            v2 += v[i] * v[i];
-        }
-        worst = std::max(worst, std::sqrt(e2 / v2));
-    }
-    return worst < 1e-2;
 }
 
 }  // namespace
@@ -813,7 +771,6 @@ void build_hierarchy(Ctx& c) {
             std::vector<double> inv = dense_inverse(cs.hM, cs.hL, p.cm, p.cl);
             p.inv_d.upload(inv, s);
             p.inv_f.upload(to_float(inv), s);
-            p.inv_f_ok = float_inverse_ok(cs.hM, cs.hL, p.cm, p.cl, inv);
         }
     }
 }

@@ -212,11 +212,9 @@ float* gmg_vcycle_stencil(Ctx& c, int opi, int N, const float* b0, float* xa, fl
     }
     {
         const int s = S - 1;
-        const OpPair& op = c.ops[opi];
-        if (op.inv_f.p && op.inv_f_ok) {
-            c.launches += launch_dense_apply<float>(c.sl[s].n, N, op.inv_f.p, b[s], cur[s], sk, st);
-        } else if (op.inv_d.p) {
-            c.launches += launch_dense_apply_mixed(c.sl[s].n, N, op.inv_d.p, b[s], cur[s], sk, st);
+        const float* inv = c.ops[opi].inv_f.p;
+        if (inv) {
+            c.launches += launch_dense_apply<float>(c.sl[s].n, N, inv, b[s], cur[s], sk, st);
         } else {
             Op<float> A = level_op<float>(c, s, opi);
             c.launches += launch_spmm<float>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
@@ -275,21 +273,9 @@ T* gmg_vcycle(Ctx& c, int opi, int N, const T* b0, T* xa, T* xb, Skip sk, bool f
         const int s = S - 1;
         const OpPair& p = c.ops[opi];
         const T* inv = nullptr;
-        if constexpr (sizeof(T) == 8) inv = p.inv_d.p; else inv = p.inv_f_ok ? p.inv_f.p : nullptr;
+        if constexpr (sizeof(T) == 8) inv = p.inv_d.p; else inv = p.inv_f.p;
         if (inv) {
             c.launches += launch_dense_apply<T>(c.sl[s].n, N, inv, b[s], cur[s], sk, st);
-        } else if constexpr (sizeof(T) == 4) {
-            if (p.inv_d.p) {
-                c.launches += launch_dense_apply_mixed(c.sl[s].n, N, p.inv_d.p, (const float*)b[s], (float*)cur[s], sk, st);
-            } else {
-                Op<T> A = level_op<T>(c, s, opi);
-                if (!(s == 0 && first_done))
-                    c.launches += launch_spmm<T>(SP_JACOBI, A, N, nullptr, b[s], cur[s], w, sk, st);
-                for (int k = 1; k < 4 * nu; ++k) {
-                    c.launches += launch_spmm<T>(SP_JACOBI, A, N, cur[s], b[s], oth[s], w, sk, st);
-                    std::swap(cur[s], oth[s]);
-                }
-            }
         } else {
             Op<T> A = level_op<T>(c, s, opi);
             if (!(s == 0 && first_done))
