@@ -133,3 +133,26 @@ def test_full_size_fp64_to_the_paper_tolerance():
     assert rc == ptp.PTP_OK and st.converged
     R = P.residual(prob, d, U)
     assert np.linalg.norm(R) <= 1.01e-4 * st.res0
+
+
+def test_full_size_mixed_with_the_dft_inner_solve():
+    """161x209, N = 64 in mixed precision.  With the float multigrid V-cycle
+    inside multigrid in time this grid diverges (the K_hat weights span 29 to
+    8e5, beyond what float sums keep); with the DFT in time as the inner
+    solve (double complex CG per mode, float right-hand side and
+    correction) the mixed solve converges: the oracle's residual of the
+    returned iterate meets the stopping rule and the iterate agrees with the
+    FP64 solve's to the tolerance's accuracy."""
+    prob = W.paper_transformer_problem(161, 209, 64)
+    d = P.assemble(prob)
+    opts = dict(tol=1e-8, max_outer=200, coarse_solver=ptp.PTP_COARSE_DFT, time_levels=1, dft_max_it=60)
+    c, o = make_ctx(prob, precision=ptp.PTP_MIXED, **opts)
+    U, st, rc = c.solve(o)
+    assert rc == ptp.PTP_OK and st.converged
+    F = P.source(prob, d)
+    R = P.residual(prob, d, U)
+    assert np.linalg.norm(R) <= 1.01e-8 * np.linalg.norm(F)
+    c64, o64 = make_ctx(prob, precision=ptp.PTP_FP64, **opts)
+    U64, st64, rc64 = c64.solve(o64)
+    assert rc64 == ptp.PTP_OK
+    assert rel(U, U64) < 1e-6
