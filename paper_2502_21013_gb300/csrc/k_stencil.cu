@@ -786,11 +786,11 @@ __global__ void __launch_bounds__(256) k_st_copy_sweep_b(const StCopyArgs* __res
     }
 }
 template <int VEC, int MODE>
-__global__ void __launch_bounds__(kStBlock) k_st_presid(StPresidArgs p) {
+__global__ void __launch_bounds__(kStBlock, 3) k_st_presid(StPresidArgs p) {
     st_presid_body<VEC, MODE>(p, native_grid());
 }
 template <int VEC, int MODE>
-__global__ void __launch_bounds__(kStBlock) k_st_presid_b(const StPresidArgs* __restrict__ ps, BatchMap m) {
+__global__ void __launch_bounds__(kStBlock, 3) k_st_presid_b(const StPresidArgs* __restrict__ ps, BatchMap m) {
     pdl_enter();
     int i;
     VGrid g;

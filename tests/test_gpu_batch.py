@@ -185,3 +185,27 @@ def test_groups_run_concurrently_and_keep_results():
         for a, b in zip(res[1][0], res[groups][0]):
             assert torch.equal(a, b)
     assert res[4][1] >= res[1][1]
+
+
+def test_auto_layout_merges_small_instances():
+    """The batch's layout autotuner on 32 small instances (17x17, N = 16),
+    whose steps are launch-bound: the merged program is the faster layout
+    (about 1.4x per step on a GB300) and is the one kept; the solve still
+    reaches the oracle's solution of an instance."""
+    probs = [W.unit_square_problem(17, 16, amps=(20.0 + 2 * k,)) for k in range(32)]
+    batch = ptp.Batch(0)
+    keep = []
+    for p in probs:
+        c = _ctx(p, precision=ptp.PTP_MIXED)
+        keep.append(c)
+        batch.add(c)
+    opts = ptp.default_opts(precision=ptp.PTP_MIXED, tol=1e-11, max_outer=20000)
+    stats, nconv, rc = batch.solve(opts)
+    assert rc == ptp.PTP_OK and nconv == len(probs)
+    lps, merged, _ = batch.plan_info()
+    assert merged == len(probs), (lps, merged)
+    U = torch.empty((probs[5].n_free, probs[5].N), dtype=torch.float64, device="cuda")
+    batch.result_dev(5, U)
+    d = P.assemble(probs[5])
+    ref = P.fixed_point(probs[5], d, tol=1e-13, max_it=50000)
+    assert np.linalg.norm(U.cpu().numpy() - ref.U) / np.linalg.norm(ref.U) < 1e-8
