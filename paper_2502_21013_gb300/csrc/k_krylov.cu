@@ -4,7 +4,7 @@
 // basis vectors, and a division by a device scalar.  The dot products are
 // deterministic: per-block partials, then the last block to finish (atomic
 // ticket, no waiting) sums them in block order.
-#include "dev_util.cuh"
+#include "dev_bodies.cuh"
 
 namespace ptp {
 
@@ -104,31 +104,6 @@ __global__ void k_sqrt_or_one(double* x) {
 // The last update of a batched PCG whose residual and residual norm are not
 // used again: x = xscale alpha p (assign) or x += xscale alpha p, with the
 // per-column alpha of the ColRed scalars (the same arithmetic as the full update).
-template <typename T, int VEC>
-__device__ __forceinline__ void pcg_xupdate_body(const XUpdateArgs<T>& a, const VGrid& g) {
-    pdl_enter();
-    if (skip_now(a.sk)) return;
-    const int N = a.N, NC = N / VEC, rpb = blockDim.x / NC;
-    const T xscale = a.xscale;
-    const T* __restrict__ p = a.p;
-    const T* __restrict__ alpha = a.alpha;
-    T* x = a.x;
-    PTP_ROW_LOOP_G(a.rows, NC, rpb, g) {
-        const size_t o = (size_t)row * N + col0;
-        T pv[VEC], xv[VEC];
-        ldg_vec<T, VEC>(p + o, pv);
-        if (a.assign) {
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) xv[v] = T(0);
-        } else {
-            ld_vec<T, VEC>(x + o, xv);
-        }
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) xv[v] += xscale * alpha[col0 + v] * pv[v];
-        st_vec<T, VEC>(x + o, xv);
-    }
-}
-
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kMaxBlock) k_pcg_xupdate(XUpdateArgs<T> a) {
     pcg_xupdate_body<T, VEC>(a, native_grid());

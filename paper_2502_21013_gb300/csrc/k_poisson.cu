@@ -24,94 +24,11 @@
 #include <map>
 #include <mutex>
 
-#include "dev_fft.cuh"
-#include "dev_util.cuh"
+#include "dev_bodies.cuh"
 
 namespace ptp {
 
 namespace {
-
-constexpr int kDstThreads = 256;
-
-// Loads transforms t1 = 2p and t2 = 2p + 1 (of ntr) as the odd extension, in
-// bit-reversed order, into sh (2m complex values).
-template <typename TI>
-__device__ __forceinline__ void dst_load(double2* sh, int p, int ntr, int n, int logM2, const TI* __restrict__ in,
-                                         long in_tr, long in_el) {
-    const int m = n + 1, M2 = 2 * m;
-    const int t1 = 2 * p, t2 = 2 * p + 1;
-    for (int idx = threadIdx.x; idx < M2; idx += blockDim.x) {
-        double2 v = make_double2(0.0, 0.0);
-        int j = 0;
-        double sgn = 1.0;
-        if (idx >= 1 && idx <= n) {
-            j = idx - 1;
-        } else if (idx > m) {
-            j = M2 - idx - 1;
-            sgn = -1.0;
-        } else {
-            j = -1;
-        }
-        if (j >= 0) {
-            v.x = sgn * (double)in[(long)t1 * in_tr + (long)j * in_el];
-            if (t2 < ntr) v.y = sgn * (double)in[(long)t2 * in_tr + (long)j * in_el];
-        }
-        sh[bit_reverse(idx, logM2)] = v;
-    }
-}
-
-// out = S in along each transform (two per block pass); with TWICE the
-// transform is scaled elementwise by scale[t][k] and transformed again
-// (S (scale * S in)), in one pass over shared memory.
-template <typename TI, typename TO, bool TWICE>
-__device__ __forceinline__ void dst_body(const DstArgs& p, const VGrid& g) {
-    pdl_enter();
-    if (skip_now(p.sk)) return;
-    const int ntr = p.ntr, n = p.n, logM2 = p.logM2;
-    const TI* __restrict__ in = static_cast<const TI*>(p.in);
-    TO* __restrict__ out = static_cast<TO*>(p.out);
-    const double* __restrict__ scale = p.scale;
-    const double2* __restrict__ Wt = p.Wt;
-    extern __shared__ double2 dsm[];
-    const int m = n + 1, M2 = 2 * m;
-    double2* sh = dsm;
-    double2* sh2 = dsm + M2;
-    for (int q = g.bx; 2 * q < ntr; q += g.gx) {
-        const int t1 = 2 * q, t2 = 2 * q + 1;
-        dst_load<TI>(sh, q, ntr, n, logM2, in, p.in_tr, p.in_el);
-        __syncthreads();
-        fft_stages<false>(sh, 1, M2, Wt);
-        if constexpr (TWICE) {
-            // S z_k of both transforms, scaled, as the new odd extension
-            for (int idx = threadIdx.x; idx < M2; idx += blockDim.x) {
-                double2 v = make_double2(0.0, 0.0);
-                int k = -1;
-                double sgn = 1.0;
-                if (idx >= 1 && idx <= n) {
-                    k = idx;
-                } else if (idx > m) {
-                    k = M2 - idx;
-                    sgn = -1.0;
-                }
-                if (k > 0) {
-                    const double2 Y = sh[k];
-                    v.x = sgn * (-0.5 * Y.y) * __ldg(scale + (long)t1 * n + (k - 1));
-                    if (t2 < ntr) v.y = sgn * (0.5 * Y.x) * __ldg(scale + (long)t2 * n + (k - 1));
-                }
-                sh2[bit_reverse(idx, logM2)] = v;
-            }
-            __syncthreads();
-            fft_stages<false>(sh2, 1, M2, Wt);
-        }
-        const double2* res = TWICE ? sh2 : sh;
-        for (int k = 1 + threadIdx.x; k <= n; k += blockDim.x) {
-            const double2 Y = res[k];
-            out[(long)t1 * p.out_tr + (long)(k - 1) * p.out_el] = (TO)(-0.5 * Y.y);
-            if (t2 < ntr) out[(long)t2 * p.out_tr + (long)(k - 1) * p.out_el] = (TO)(0.5 * Y.x);
-        }
-        __syncthreads();
-    }
-}
 
 template <typename TI, typename TO, bool TWICE>
 __global__ void __launch_bounds__(kDstThreads) k_dst(DstArgs p) {

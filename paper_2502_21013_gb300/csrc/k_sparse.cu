@@ -17,8 +17,7 @@
 #include <map>
 #include <mutex>
 
-#include "dev_async.cuh"
-#include "dev_util.cuh"
+#include "dev_bodies.cuh"
 
 namespace ptp {
 
@@ -528,67 +527,6 @@ PTP_ROW_KERNELS(k_pcg_direction, direction_body, DirArgs<T>, typename T PTP_COMM
 #undef PTP_ROW_KERNELS
 #undef PTP_COMMA
 
-// Y = Ainv B on the coarsest spatial level (dense, row-major Ainv, n <= 600).
-// A block computes an 8 x 32 tile of Y (one row and column per thread) from
-// the 8 rows of Ainv and the 32 columns of B it needs, copied to shared
-// memory kc values of k at a time (kc = n when it fits, so one chunk in
-// float).  Every copy of a chunk is in flight at once (cp.async, zero-filled
-// outside the matrices).  The product is small and bound by latency: small
-// tiles give many blocks, and two partial sums per thread halve the chain of
-// dependent FMAs.
-constexpr int kDT = 32;   // columns of a tile
-constexpr int kDR = 8;    // rows of a tile
-constexpr size_t kDenseSmem = 96 * 1024;
-template <typename T>
-int dense_chunk(int n) {   // k values per chunk
-    const int fit = (int)((kDenseSmem / sizeof(T) - kDR) / (kDR + kDT));
-    return std::max(1, std::min(n, fit));
-}
-template <typename T>
-size_t dense_smem(int kc) { return (size_t)(kDR * (kc + 1) + kc * kDT) * sizeof(T); }
-
-template <typename T>
-__device__ __forceinline__ void dense_apply_body(const DenseArgs<T>& p, const VGrid& g) {
-    pdl_enter();
-    if (skip_now(p.sk)) return;
-    const int n = p.n, N = p.N, kc = p.kc;
-    const T* __restrict__ A = p.A;
-    const T* __restrict__ B = p.B;
-    T* __restrict__ Y = p.Y;
-    extern __shared__ __align__(16) unsigned char dense_smem_raw[];
-    T* As = reinterpret_cast<T*>(dense_smem_raw);   // [8][kc + 1]
-    T* Bs = As + kDR * (kc + 1);                    // [kc][32]
-    const int tx = threadIdx.x % kDT, ty = threadIdx.x / kDT;   // column, row of the tile
-    const int c0 = g.bx * kDT, i0 = g.by * kDR;
-    T acc0 = T(0), acc1 = T(0);
-    for (int k0 = 0; k0 < n; k0 += kc) {
-        const int kk = min(kc, n - k0);
-        for (int e = threadIdx.x; e < kDR * kc; e += blockDim.x) {
-            const int r = e / kc, q = e - r * kc;
-            const bool ok = i0 + r < n && q < kk;
-            cp_async<sizeof(T)>(As + r * (kc + 1) + q, ok ? A + (size_t)(i0 + r) * n + (k0 + q) : A, ok);
-        }
-        for (int e = threadIdx.x; e < kc * kDT; e += blockDim.x) {
-            const int r = e / kDT, q = e - r * kDT;
-            const bool ok = r < kk && c0 + q < N;
-            cp_async<sizeof(T)>(Bs + r * kDT + q, ok ? B + (size_t)(k0 + r) * N + (c0 + q) : B, ok);
-        }
-        cp_commit();
-        cp_wait<0>();
-        __syncthreads();
-        const T* ar = As + ty * (kc + 1);
-        int k = 0;
-#pragma unroll 4
-        for (; k + 1 < kk; k += 2) {
-            acc0 += ar[k] * Bs[k * kDT + tx];
-            acc1 += ar[k + 1] * Bs[(k + 1) * kDT + tx];
-        }
-        if (k < kk) acc0 += ar[k] * Bs[k * kDT + tx];
-        __syncthreads();
-    }
-    const int c = c0 + tx, i = i0 + ty;
-    if (c < N && i < n) Y[(size_t)i * N + c] = acc0 + acc1;
-}
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_apply(DenseArgs<T> p) { dense_apply_body<T>(p, native_grid()); }
 template <typename T>
@@ -602,20 +540,6 @@ __global__ void __launch_bounds__(256) k_dense_apply_b(const DenseArgs<T>* __res
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void time_prolong_add_body(const ProlongArgs<T>& p, const VGrid& g) {
-    pdl_enter();
-    if (skip_now(p.sk)) return;
-    const int Nc = p.Nc;
-    const size_t total = (size_t)p.rows * Nc;
-    for (size_t q = (size_t)g.bx * blockDim.x + threadIdx.x; q < total; q += (size_t)g.gx * blockDim.x) {
-        const size_t i = q / Nc, m = q - i * Nc;
-        const T v = p.xc[q];
-        T* xr = p.x + i * (2 * (size_t)Nc) + 2 * m;
-        xr[0] += v;
-        xr[1] += v;
-    }
-}
 template <typename T>
 __global__ void k_time_prolong_add(ProlongArgs<T> p) { time_prolong_add_body<T>(p, native_grid()); }
 template <typename T>
