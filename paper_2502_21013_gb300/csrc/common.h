@@ -268,6 +268,13 @@ struct Ctx {
     double lambda_min = -1.0;
     double kappa_min = 0.0;      // tau lambda_min on the finest time level
     double rho_time = 0.0;       // model spectral radius of the chosen cycle
+    // fused program of the coarse time levels (one cooperative kernel)
+    int fz_level = -1;           // time level the program starts at (-1: none)
+    bool fz_on = false;          // used by the step being enqueued
+    int fz_nph = 0, fz_grid = 0;
+    size_t fz_smem = 0;
+    int64_t fz_key = -1;
+    DBuf<unsigned char> fz_blob; // phases, then the argument structs
 
     ~Ctx();
 };

@@ -184,7 +184,8 @@ int launch_pcg_xupdate(int rows, int N, T xscale, int assign, T* x, const T* p, 
     sh.gy = 1;
     sh.block = l.block;
     sh.vec = vec;
-    if (record_launch(launch_pcg_xupdate_batch<T>, a, sh)) return 1;
+    if (record_launch(launch_pcg_xupdate_batch<T>, a, sh, sizeof(T) == 4 ? body_id(BF_XUPDATE_F, vec, 0) : 0))
+        return 1;
     if (vec == 4) {
         if constexpr (sizeof(T) == 4) launch_k(k_pcg_xupdate<T, 4>, dim3(l.grid), dim3(l.block), s, a);
     } else if (vec == 2) {

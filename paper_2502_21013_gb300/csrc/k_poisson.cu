@@ -74,7 +74,11 @@ void dst_pass(const DstArgs& a, cudaStream_t s) {
     sh.gy = 1;
     sh.block = kDstThreads;
     sh.smem = (size_t)(TWICE ? 4 : 2) * (a.n + 1) * sizeof(double2);
-    if (record_launch(dst_batch<TI, TO, TWICE>, a, sh)) return;
+    int body = 0;
+    if constexpr (sizeof(TI) == 4 && sizeof(TO) == 8 && !TWICE) body = body_id(BF_DST_FD, 0, 0);
+    if constexpr (sizeof(TI) == 8 && sizeof(TO) == 8 && TWICE) body = body_id(BF_DST_DD2, 0, 0);
+    if constexpr (sizeof(TI) == 8 && sizeof(TO) == 4 && !TWICE) body = body_id(BF_DST_DF, 0, 0);
+    if (record_launch(dst_batch<TI, TO, TWICE>, a, sh, body)) return;
     dst_launch(k_dst<TI, TO, TWICE>, sh.gx, sh.smem, s, a);
 }
 

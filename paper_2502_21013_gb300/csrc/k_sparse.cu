@@ -945,7 +945,7 @@ int launch_dense_apply(int n, int N, const T* Ainv, const T* B, T* Y, Skip sk, c
     sh.gy = (n + kDR - 1) / kDR;
     sh.block = 256;
     sh.smem = dense_smem<T>(kc);
-    if (record_launch(launch_dense_apply_batch<T>, a, sh)) return 1;
+    if (record_launch(launch_dense_apply_batch<T>, a, sh, sizeof(T) == 4 ? body_id(BF_DENSE_F, 0, 0) : 0)) return 1;
     grant_smem(k_dense_apply<T>, sh.smem);
     launch_k_smem(k_dense_apply<T>, dim3(sh.gx, sh.gy), dim3(256), sh.smem, s, a);
     return 1;
@@ -964,7 +964,8 @@ int launch_time_prolong_add(int rows, int Nc, const T* xc, T* x, Skip sk, cudaSt
     sh.gx = flat_grid((size_t)rows * Nc);
     sh.gy = 1;
     sh.block = 256;
-    if (record_launch(launch_time_prolong_add_batch<T>, a, sh)) return 1;
+    if (record_launch(launch_time_prolong_add_batch<T>, a, sh, sizeof(T) == 4 ? body_id(BF_PROLONG_F, 0, 0) : 0))
+        return 1;
     launch_k(k_time_prolong_add<T>, dim3(sh.gx), 256, s, a);
     return 1;
 }

@@ -33,8 +33,9 @@
 #include <map>
 #include <mutex>
 
-#include "dev_async.cuh"
-#include "dev_util.cuh"
+#include <cooperative_groups.h>
+
+#include "dev_bodies.cuh"
 
 namespace ptp {
 
@@ -925,7 +926,7 @@ int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const flo
                      float omega, bool time_restrict, Skip sk, cudaStream_t s) {
     KShape ks;
     const StPresidArgs a = plan_st_presid(A, N, X, B, R, Z0, omega, time_restrict, sk, ks);
-    if (record_launch(launch_st_presid_batch, a, ks)) return 1;
+    if (record_launch(launch_st_presid_batch, a, ks, body_id(BF_ST_PRESID, ks.vec, ks.variant))) return 1;
     const dim3 grid(ks.gx, ks.gy);
     if (time_restrict) {
         if (ks.vec == 4) st_launch(k_st_presid<4, 1>, grid, ks.block, ks.smem, s, a);
@@ -940,7 +941,7 @@ int launch_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>&
                              const float* Bf, float* Bc, float* Xc, float omega, Skip sk, cudaStream_t s) {
     KShape ks;
     const StRestrictArgs a = plan_st_resid_restrict(Af, Ac, N, Xf, Bf, Bc, Xc, omega, sk, ks);
-    if (record_launch(launch_st_resid_restrict_batch, a, ks)) return 1;
+    if (record_launch(launch_st_resid_restrict_batch, a, ks, body_id(BF_ST_RESTRICT, ks.vec, 0))) return 1;
     PTP_ST_VEC(ks.vec, st_launch(k_st_resid_restrict<VEC>, dim3(ks.gx, ks.gy), ks.block, ks.smem, s, a));
     return 1;
 }
@@ -950,7 +951,7 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
                            cudaStream_t s) {
     KShape ks;
     const StInterpArgs a = plan_st_interp_sweep(A, Wc, Hc, N, Xc, X, B, Out, omega, cr, dots, sk, ks);
-    if (record_launch(launch_st_interp_sweep_batch, a, ks)) return 1;
+    if (record_launch(launch_st_interp_sweep_batch, a, ks, body_id(BF_ST_INTERP, ks.vec, ks.variant))) return 1;
     const dim3 grid(ks.gx, ks.gy);
     if (dots == 1) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 1>, grid, ks.block, ks.smem, s, a))
     else if (dots == 2) PTP_ST_VEC(ks.vec, st_launch(k_st_interp_sweep<VEC, 2>, grid, ks.block, ks.smem, s, a))
@@ -961,7 +962,7 @@ int launch_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int N, con
 int launch_st_apply_dot(const StencilOp<float>& A, int N, const float* P, ColRed<float> cr, Skip sk, cudaStream_t s) {
     KShape ks;
     const StApplyDotArgs a = plan_st_apply_dot(A, N, P, cr, sk, ks);
-    if (record_launch(launch_st_apply_dot_batch, a, ks)) return 1;
+    if (record_launch(launch_st_apply_dot_batch, a, ks, body_id(BF_ST_APPLYDOT, ks.vec, 0))) return 1;
     PTP_ST_VEC(ks.vec, st_launch(k_st_apply_dot<VEC>, dim3(ks.gx, ks.gy), ks.block, ks.smem, s, a));
     return 1;
 }
@@ -984,7 +985,7 @@ int launch_st_copy_sweep(const StencilOp<float>& A, int N, const float* B, float
     ks.gx = (int)std::max<size_t>(1, std::min((total + 255) / 256, (size_t)num_sms() * 8));
     ks.gy = 1;
     ks.block = 256;
-    if (record_launch(launch_st_copy_sweep_batch, a, ks)) return 1;
+    if (record_launch(launch_st_copy_sweep_batch, a, ks, body_id(BF_ST_COPY, ks.vec, 0))) return 1;
     PTP_ST_VEC(ks.vec, launch_k(k_st_copy_sweep<VEC>, dim3(ks.gx), dim3(256), s, a));
     return 1;
 }
@@ -1021,6 +1022,106 @@ int launch_st_interp_sweep_batch(const void* argv, BatchMap m, int blocks, const
 int launch_st_apply_dot_batch(const void* argv, BatchMap m, int blocks, const KShape& ks, cudaStream_t s) {
     const StApplyDotArgs* args = static_cast<const StApplyDotArgs*>(argv);
     PTP_ST_VEC(ks.vec, st_launch(k_st_apply_dot_b<VEC>, dim3(blocks), ks.block, ks.smem, s, args, m));
+    return 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// Fused program of the coarse time levels.  Below a time level with few
+// steps the V-cycle is a chain of small passes whose duration is launch and
+// pipeline latency, not work.  It runs as one cooperative kernel: every
+// phase is one recorded launch (body, virtual grid, argument struct); the
+// kernel's blocks walk the phase's virtual blocks, and a grid-wide barrier
+// separates the phases, as stream order separated the launches.  Every
+// virtual block computes what the block of the separate launch computed, so
+// the results are the same bit for bit.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename A>
+__device__ __forceinline__ A load_args(const void* p) {
+    return *static_cast<const A*>(p);
+}
+
+#define PTP_FUSED_BODIES(X)                                                                               \
+    X(body_id(BF_ST_COPY, 4, 0), st_copy_sweep_body<4>(load_args<StCopyArgs>(args), g))                  \
+    X(body_id(BF_ST_COPY, 2, 0), st_copy_sweep_body<2>(load_args<StCopyArgs>(args), g))                  \
+    X(body_id(BF_ST_PRESID, 4, 0), (st_presid_body<4, 0>(load_args<StPresidArgs>(args), g)))             \
+    X(body_id(BF_ST_PRESID, 2, 0), (st_presid_body<2, 0>(load_args<StPresidArgs>(args), g)))             \
+    X(body_id(BF_ST_PRESID, 4, 1), (st_presid_body<4, 1>(load_args<StPresidArgs>(args), g)))             \
+    X(body_id(BF_ST_PRESID, 2, 1), (st_presid_body<2, 1>(load_args<StPresidArgs>(args), g)))             \
+    X(body_id(BF_ST_RESTRICT, 4, 0), st_resid_restrict_body<4>(load_args<StRestrictArgs>(args), g))      \
+    X(body_id(BF_ST_RESTRICT, 2, 0), st_resid_restrict_body<2>(load_args<StRestrictArgs>(args), g))      \
+    X(body_id(BF_ST_INTERP, 4, 0), (st_interp_sweep_body<4, 0>(load_args<StInterpArgs>(args), g)))       \
+    X(body_id(BF_ST_INTERP, 2, 0), (st_interp_sweep_body<2, 0>(load_args<StInterpArgs>(args), g)))       \
+    X(body_id(BF_ST_INTERP, 4, 1), (st_interp_sweep_body<4, 1>(load_args<StInterpArgs>(args), g)))       \
+    X(body_id(BF_ST_INTERP, 2, 1), (st_interp_sweep_body<2, 1>(load_args<StInterpArgs>(args), g)))       \
+    X(body_id(BF_ST_INTERP, 4, 2), (st_interp_sweep_body<4, 2>(load_args<StInterpArgs>(args), g)))       \
+    X(body_id(BF_ST_INTERP, 2, 2), (st_interp_sweep_body<2, 2>(load_args<StInterpArgs>(args), g)))       \
+    X(body_id(BF_ST_APPLYDOT, 4, 0), st_apply_dot_body<4>(load_args<StApplyDotArgs>(args), g))           \
+    X(body_id(BF_ST_APPLYDOT, 2, 0), st_apply_dot_body<2>(load_args<StApplyDotArgs>(args), g))           \
+    X(body_id(BF_DENSE_F, 0, 0), dense_apply_body<float>(load_args<DenseArgs<float>>(args), g))          \
+    X(body_id(BF_XUPDATE_F, 4, 0), (pcg_xupdate_body<float, 4>(load_args<XUpdateArgs<float>>(args), g))) \
+    X(body_id(BF_XUPDATE_F, 2, 0), (pcg_xupdate_body<float, 2>(load_args<XUpdateArgs<float>>(args), g))) \
+    X(body_id(BF_PROLONG_F, 0, 0), time_prolong_add_body<float>(load_args<ProlongArgs<float>>(args), g)) \
+    X(body_id(BF_DST_FD, 0, 0), (dst_body<float, double, false>(load_args<DstArgs>(args), g)))           \
+    X(body_id(BF_DST_DD2, 0, 0), (dst_body<double, double, true>(load_args<DstArgs>(args), g)))          \
+    X(body_id(BF_DST_DF, 0, 0), (dst_body<double, float, false>(load_args<DstArgs>(args), g)))
+
+__device__ __forceinline__ void run_body(int body, const void* args, const VGrid& g) {
+#define PTP_CASE(ID, CALL) \
+    case ID:               \
+        CALL;              \
+        break;
+    switch (body) { PTP_FUSED_BODIES(PTP_CASE) }
+#undef PTP_CASE
+}
+
+__global__ void __launch_bounds__(kStBlock) k_fused_program(const FusedPhase* __restrict__ ph, int nph) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    for (int p = 0; p < nph; ++p) {
+        const FusedPhase P = ph[p];
+        const int nb = P.gx * P.gy;
+        for (int vb = blockIdx.x; vb < nb; vb += gridDim.x) {
+            run_body(P.body, P.args, VGrid{vb % P.gx, vb / P.gx, P.gx, P.gy});
+            __syncthreads();   // the next virtual block reuses the shared memory
+        }
+        grid.sync();
+    }
+}
+
+}  // namespace
+
+bool fused_body_supported(int body) {
+#define PTP_CASE(ID, CALL) \
+    case ID:               \
+        return true;
+    switch (body) { PTP_FUSED_BODIES(PTP_CASE) }
+#undef PTP_CASE
+    return false;
+}
+
+int fused_program_grid(size_t smem) {
+    if (smem > 48 * 1024)
+        PTP_CUDA(cudaFuncSetAttribute(k_fused_program, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_program, kStBlock, smem));
+    return per_sm * num_sms();
+}
+
+int launch_fused_program(const FusedPhase* phases, int nphases, int grid, size_t smem, cudaStream_t s) {
+    if (record_foreign()) return 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kStBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PTP_CUDA(cudaLaunchKernelEx(&cfg, k_fused_program, phases, nphases));
     return 1;
 }
 

@@ -75,6 +75,15 @@ struct KShape {
 // stream operation counts as foreign (and the instance is then not merged
 // with others).
 // ---------------------------------------------------------------------------
+// one phase of the fused program of the coarse time levels (k_stencil.cu)
+struct FusedPhase {
+    int body, gx, gy, pad;
+    const void* args;   // device copy of the argument struct
+};
+bool fused_body_supported(int body);
+int fused_program_grid(size_t smem);   // blocks that can be co-resident (cooperative launch)
+int launch_fused_program(const FusedPhase* phases, int nphases, int grid, size_t smem, cudaStream_t s);
+
 // batched form of a kernel kind: one launch over the instances of `args`
 // (device array of argument structs) with their virtual grids in m
 using BatchLaunch = int (*)(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s);
@@ -82,7 +91,17 @@ struct RecordedLaunch {
     BatchLaunch fn = nullptr;
     KShape shape;
     std::vector<unsigned char> args;
+    int body = 0;   // body id for the fused program of the coarse time levels (0: none)
 };
+// body ids: family * 100 + VEC * 10 + variant
+enum BodyFamily {
+    BF_ST_COPY = 1, BF_ST_PRESID = 2, BF_ST_RESTRICT = 3, BF_ST_INTERP = 4, BF_ST_APPLYDOT = 5,
+    BF_DENSE_F = 6, BF_XUPDATE_F = 7, BF_PROLONG_F = 8, BF_DST_FD = 9, BF_DST_DD2 = 10, BF_DST_DF = 11,
+};
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int body_id(int family, int vec, int variant) { return family * 100 + vec * 10 + variant; }
 struct Recorder {
     std::vector<RecordedLaunch> ops;
     int foreign = 0;
@@ -90,12 +109,13 @@ struct Recorder {
 Recorder*& active_recorder();   // this host thread's recorder (null: launch)
 
 template <typename A>
-inline bool record_launch(BatchLaunch fn, const A& a, const KShape& sh) {
+inline bool record_launch(BatchLaunch fn, const A& a, const KShape& sh, int body = 0) {
     Recorder* r = active_recorder();
     if (!r) return false;
     RecordedLaunch l;
     l.fn = fn;
     l.shape = sh;
+    l.body = body;
     l.args.resize(sizeof(A));
     std::memcpy(l.args.data(), &a, sizeof(A));
     r->ops.push_back(std::move(l));

@@ -553,6 +553,13 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
         coarse_solve<T>(c, sk);  // x_zero is implied: exact solve
         return;
     }
+    if constexpr (sizeof(T) == 4) {
+        if (c.fz_on && l == c.fz_level && x_zero && !full) {   // the recorded program of levels l..L-1
+            c.launches += launch_fused_program(reinterpret_cast<const FusedPhase*>(c.fz_blob.p), c.fz_nph, c.fz_grid,
+                                               c.fz_smem, st);
+            return;
+        }
+    }
     if (!full && l == c.active_levels - 1) {
         const int cyc = std::max(1, c.opts.coarse_cycles);
         for (int k = 0; k < cyc; ++k) mgt_vcycle<T>(c, l, x_zero && k == 0, sk, true);
@@ -942,9 +949,9 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
     };
-    const int ints[16] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+    const int ints[17] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
                           o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it,
-                          o.stencil, o.k1_fused, o.coarse_direct, c.st_tt, c.st_waves};
+                          o.stencil, o.k1_fused, o.coarse_direct, c.st_tt, c.st_waves, c.fz_on ? c.fz_level : -1};
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));
@@ -1145,6 +1152,7 @@ void solve_begin(Ctx& c, const ptp_opts& o, const double* X0, int kind) {
                     o.coarse_solver == c.opts.coarse_solver,
                 "precision / preconditioner / hierarchy options differ from ptp_setup");
     c.opts = o;
+    c.fz_on = false;
     if (kind != STEP_STATIC) resolve_time_smoother(c);
     cudaStream_t st = c.stream;
     double* X = adjoint ? c.Lam.p : c.U.p;
@@ -1206,12 +1214,82 @@ int solve_end(Ctx& c, ptp_stats* stats, int kind, int64_t step_launches, double 
     return conv ? PTP_OK : PTP_ENOTCONV;
 }
 
+// The fused program of the coarse time levels (k_stencil.cu): the launches
+// of the V-cycle from the first time level with at most kFuseSteps steps
+// down to the coarsest level and back, recorded once (from zero, as every
+// level below the finest starts) and replayed as one cooperative kernel.
+// Only on the float stencil path with the full hierarchy and an exact
+// coarsest level; anything without a fused body keeps the separate launches.
+constexpr int kFuseSteps = 16;
+static void prepare_fused(Ctx& c, int kind) {
+    c.fz_on = false;
+    const int L = (int)c.tl.size();
+    if (!c.opts.fuse_coarse || kind != STEP_FORWARD || !use_stencil<float>(c) || c.dft_level >= 0 ||
+        c.active_levels != L || L < 3 || c.opts.vcycles < 1)
+        return;
+    int l0 = -1;
+    for (int l = 1; l < L - 1; ++l)
+        if (c.tl[l].N <= kFuseSteps) { l0 = l; break; }
+    if (l0 < 0) return;
+    const int64_t key = step_key(c, c.opts) ^ ((int64_t)l0 << 40);
+    if (c.fz_level == l0 && c.fz_key == key && c.fz_blob.p) {
+        c.fz_on = true;
+        return;
+    }
+    c.fz_level = -1;
+    const int64_t launches0 = c.launches;
+    Recorder rec;
+    active_recorder() = &rec;
+    try {
+        Skip sk;
+        sk.done = c.flag.p;
+        mgt_vcycle<float>(c, l0, true, sk, false);
+    } catch (...) {
+        active_recorder() = nullptr;
+        throw;
+    }
+    active_recorder() = nullptr;
+    c.launches = launches0;
+    if (rec.foreign || rec.ops.empty()) return;
+    size_t smem = 0;
+    for (const RecordedLaunch& r : rec.ops) {
+        if (!fused_body_supported(r.body) || r.shape.block != 256) return;
+        smem = std::max(smem, r.shape.smem);
+    }
+    const int grid = fused_program_grid(smem);
+    if (grid < 1) return;
+    const size_t nph = rec.ops.size();
+    size_t bytes = nph * sizeof(FusedPhase);
+    std::vector<size_t> off(nph);
+    for (size_t k = 0; k < nph; ++k) {
+        bytes = (bytes + 15) / 16 * 16;
+        off[k] = bytes;
+        bytes += rec.ops[k].args.size();
+    }
+    c.fz_blob.alloc(bytes);
+    std::vector<unsigned char> host(bytes, 0);
+    FusedPhase* ph = reinterpret_cast<FusedPhase*>(host.data());
+    for (size_t k = 0; k < nph; ++k) {
+        const RecordedLaunch& r = rec.ops[k];
+        ph[k] = FusedPhase{r.body, r.shape.gx, std::max(1, r.shape.gy), 0, c.fz_blob.p + off[k]};
+        std::memcpy(host.data() + off[k], r.args.data(), r.args.size());
+    }
+    PTP_CUDA(cudaMemcpy(c.fz_blob.p, host.data(), bytes, cudaMemcpyHostToDevice));
+    c.fz_nph = (int)nph;
+    c.fz_grid = grid;
+    c.fz_smem = smem;
+    c.fz_level = l0;
+    c.fz_key = key;
+    c.fz_on = true;
+}
+
 // Fixed-point iteration of one kind from X0 (null: zero start) until its
 // stopping rule or max_outer; the graph of one step is re-captured when the
 // options change.
 static int run_fixed_point(Ctx& c, const ptp_opts& o, const double* X0, double* U, ptp_stats* stats, int kind) {
     const auto t0 = std::chrono::steady_clock::now();
     solve_begin(c, o, X0, kind);
+    prepare_fused(c, kind);
     double* X = kind == STEP_ADJOINT ? c.Lam.p : c.U.p;
     const int gi = kind;
     cudaStream_t st = c.stream;
@@ -1271,6 +1349,7 @@ static int run_fixed_point(Ctx& c, const ptp_opts& o, const double* X0, double* 
     cudaEventDestroy(e0); cudaEventDestroy(e1);
     cudaEventDestroy(chk[0]); cudaEventDestroy(chk[1]);
     const double wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    c.fz_on = false;
     const int rc = solve_end(c, stats, kind, step_launches, wall, ms);
     if (U) {
         PTP_CUDA(cudaMemcpyAsync(U, X, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -147,3 +147,25 @@ def test_periodic_residual_f32_against_the_oracle(name, make):
         scale = np.abs(B) + abs(d.M + tau * d.L) @ np.abs(X) + abs(d.M) @ np.abs(np.roll(X, 1, axis=1))
         err = np.abs(Rd.cpu().numpy() - ref)
         assert np.all(err <= 1e-5 * scale + 1e-30), (l, float((err / scale).max()))
+
+
+@pytest.mark.parametrize("name,make", [("square33_N32", lambda: W.unit_square_problem(33, 32)),
+                                       ("square65_N64", lambda: W.unit_square_problem(65, 64, amps=(70.0,))),
+                                       ("transformer65x33_N16", lambda: W.transformer_problem(65, 33, 16))])
+def test_fused_coarse_levels_are_bitwise_the_separate_launches(name, make):
+    """The time levels with at most 16 steps run as one cooperative kernel
+    (fuse_coarse = 1): every virtual block computes what the block of the
+    separate launch computed, so the fixed point's iterates and iteration
+    counts are identical, and the fused step issues fewer launches."""
+    prob = make()
+    out = []
+    for fuse in (0, 1):
+        c, o = _ctx(prob, precision=ptp.PTP_MIXED, tol=1e-10, max_outer=20000, fuse_coarse=fuse)
+        U = torch.zeros((prob.n_free, prob.N), dtype=torch.float64, device="cuda")
+        st, rc = c.solve_dev(U, o)
+        assert rc == ptp.PTP_OK
+        out.append((U.cpu().numpy(), st.outer_iterations, st.kernel_launches / (st.outer_iterations + 1)))
+    (u0, i0, l0), (u1, i1, l1) = out
+    assert i0 == i1
+    assert np.array_equal(u0, u1)
+    assert l1 < l0
