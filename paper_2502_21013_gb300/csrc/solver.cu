@@ -1224,7 +1224,8 @@ constexpr int kFuseSteps = 16;
 static void prepare_fused(Ctx& c, int kind) {
     c.fz_on = false;
     const int L = (int)c.tl.size();
-    if (!c.opts.fuse_coarse || kind != STEP_FORWARD || !use_stencil<float>(c) || c.dft_level >= 0 ||
+    if (!c.opts.fuse_coarse || c.opts.precision != PTP_MIXED || kind != STEP_FORWARD || !use_stencil<float>(c) ||
+        c.dft_level >= 0 ||
         c.active_levels != L || L < 3 || c.opts.vcycles < 1)
         return;
     int l0 = -1;
