@@ -147,12 +147,13 @@ typedef struct ptp_opts {
                             powers of two, the tau_c L solve of the coarsest
                             time level is direct (sine transforms, exact up
                             to rounding) instead of coarse_tol PCG; 0 = PCG */
-    int    fuse_coarse;  /* 1 (default): in PTP_MIXED fixed-point solves on
-                            the stencil path, the multigrid-in-time work of
-                            the time levels with at most 16 steps runs as one
-                            cooperative kernel (its launches are latency-
-                            bound); same results bit for bit.  0 = separate
-                            launches                                         */
+    int    fuse_coarse;  /* 1: in PTP_MIXED fixed-point solves on the
+                            stencil path, the multigrid-in-time work of the
+                            time levels with at most 16 steps runs as one
+                            cooperative kernel with a grid-wide barrier
+                            between its passes (same results bit for bit,
+                            half the launches).  0 (default): separate
+                            launches, which measured faster on a GB300       */
 } ptp_opts;
 
 /* Statistics of the last solve. */

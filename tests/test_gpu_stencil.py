@@ -153,8 +153,8 @@ def test_periodic_residual_f32_against_the_oracle(name, make):
                                        ("square65_N64", lambda: W.unit_square_problem(65, 64, amps=(70.0,))),
                                        ("transformer65x33_N16", lambda: W.transformer_problem(65, 33, 16))])
 def test_fused_coarse_levels_are_bitwise_the_separate_launches(name, make):
-    """The time levels with at most 16 steps run as one cooperative kernel
-    (fuse_coarse = 1): every virtual block computes what the block of the
+    """With fuse_coarse = 1 the time levels with at most 16 steps run as one
+    cooperative kernel: every virtual block computes what the block of the
     separate launch computed, so the fixed point's iterates and iteration
     counts are identical, and the fused step issues fewer launches."""
     prob = make()
