@@ -136,6 +136,7 @@ void ptp_default_opts(ptp_opts* o) {
     o->k1_fused = 0;
     o->coarse_direct = 1;
     o->fuse_coarse = 0;
+    o->fuse_update = 1;
 }
 
 const char* ptp_version(void) { return "ptp 0.1 (sm_103a)"; }

@@ -103,13 +103,13 @@ __device__ __forceinline__ void pcg_xupdate_body(const XUpdateArgs<T>& a, const 
     if (skip_now(a.sk)) return;
     const int N = a.N, NC = N / VEC, rpb = blockDim.x / NC;
     const T xscale = a.xscale;
-    const T* __restrict__ p = a.p;
-    const T* __restrict__ alpha = a.alpha;
+    const T* p = a.p;
+    const T* alpha = a.alpha;
     T* x = a.x;
     PTP_ROW_LOOP_G(a.rows, NC, rpb, g) {
         const size_t o = (size_t)row * N + col0;
         T pv[VEC], xv[VEC];
-        ldg_vec<T, VEC>(p + o, pv);
+        ld_vec<T, VEC>(p + o, pv);   // a plain load: p may be written earlier in the same fused program
         if (a.assign) {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) xv[v] = T(0);

@@ -112,9 +112,6 @@ enum Fin {
     FIN_C_RZ_NEXT = 13,   // s = r^T z:                  beta = s / rho, rho = s
 };
 
-// column scalar slots in ColRed::col (each N long; complex scalars of
-// unknown k at columns 2k (re) and 2k+1 (im))
-enum Slot { S_RHO = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_BB = 4 };
 
 // num / den for PCG scalars, evaluated in double; 0 when the column has
 // no (or a non-finite) search direction, so a column whose right-hand side

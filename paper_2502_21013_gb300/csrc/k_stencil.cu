@@ -302,6 +302,14 @@ __device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGri
     for (int q = 0; q < kLA + 2; ++q) issue_q(q);
     const bool out_lane = L.ln >= 1 && L.ln <= L.sx - 2 && a < W;
     const float* pre_base = xr + (size_t)L.lc * VEC - 1;       // column col - 1 within a slot row (lc > 0)
+    // fused last PCG update (time restriction only): per-column scale xscale alpha[n]
+    const bool upd = MODE == 1 && p.alpha != nullptr;
+    float sv[VEC], sprev = 0.f;
+    if (upd) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) sv[v] = p.xscale * p.alpha[L.col + v];
+        sprev = p.xscale * p.alpha[L.lc > 0 ? L.col - 1 : pcol];
+    }
     // this node's coefficients for the next row, loaded one row ahead
     A7 cn{}, mn{};
     float idn = 0.f;
@@ -331,6 +339,20 @@ __device__ __forceinline__ void st_presid_body(const StPresidArgs& p, const VGri
             float p_c = before(sC, L.ln), p_e = before(sC, L.ln + 1), p_w = before(sC, L.ln - 1);
             float p_n = before(sN, L.ln), p_s = before(sS, L.ln), p_ne = before(sN, L.ln + 1),
                   p_sw = before(sS, L.ln - 1);
+            if constexpr (MODE == 1) {
+                if (upd) {   // the rings hold p: x = (xscale alpha) p, as the PCG update forms it
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {   // 0 + s p: the update's rounding, signed zeros included
+                        xc[v] = 0.f + sv[v] * xc[v]; xe[v] = 0.f + sv[v] * xe[v]; xw[v] = 0.f + sv[v] * xw[v];
+                        xn[v] = 0.f + sv[v] * xn[v]; xs[v] = 0.f + sv[v] * xs[v];
+                        xne[v] = 0.f + sv[v] * xne[v]; xsw[v] = 0.f + sv[v] * xsw[v];
+                    }
+                    p_c = 0.f + sprev * p_c; p_e = 0.f + sprev * p_e; p_w = 0.f + sprev * p_w;
+                    p_n = 0.f + sprev * p_n; p_s = 0.f + sprev * p_s; p_ne = 0.f + sprev * p_ne;
+                    p_sw = 0.f + sprev * p_sw;
+                    st_vec<float, VEC>(p.Xw + cx.off(b), xc);
+                }
+            }
             float bv[VEC], r[VEC];
             lds<VEC>(bslot0 + sN * sstride, bv);
 #pragma unroll
@@ -849,15 +871,27 @@ StPresidArgs plan_st_presid(const StencilOp<float>& A, int N, const float* X, co
     const Shape sh = st_shape(N, {X, B, R, Z0}, time_restrict);
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
+    ks.smem = (2 * kNS * (size_t)sh.sx * sh.TT + kNS * (size_t)sh.sx) * sizeof(float);
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
     ks.block = sh.block;
-    ks.smem = (2 * kNS * (size_t)sh.sx * sh.TT + kNS * (size_t)sh.sx) * sizeof(float);
     ks.vec = sh.vec;
     ks.variant = time_restrict ? 1 : 0;
-    return StPresidArgs{A, N, sh.TT, sy, nseg, X, B, R, Z0, omega, sk};
+    StPresidArgs a;
+    a.A = A;
+    a.N = N;
+    a.TT = sh.TT;
+    a.sy = sy;
+    a.nseg = nseg;
+    a.X = X;
+    a.B = B;
+    a.R = R;
+    a.Z0 = Z0;
+    a.omega = omega;
+    a.sk = sk;
+    return a;
 }
 
 StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
@@ -868,12 +902,12 @@ StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilO
     PTP_REQUIRE(cxo >= 1, "stencil restriction: block too narrow");
     const int nseg = (Ac.W + cxo - 1) / cxo;
     const int nch = N / sh.TT;
+    ks.smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
     const int cy = std::max(1, strip_rows(Ac.H, nseg, nch) / 2);
     const int nstrip = (Ac.H + cy - 1) / cy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
     ks.block = sh.block;
-    ks.smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
     ks.vec = sh.vec;
     ks.variant = 0;
     return StRestrictArgs{Af, Ac, N, sh.TT, cy, nseg, Xf, Bf, Bc, Xc, omega, sk};
@@ -886,12 +920,12 @@ StInterpArgs plan_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int
     const Shape sh = st_shape(N, {Xc, X, B, Out}, false);
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
+    ks.smem = (2 * kNS * (size_t)sh.sx + kNS * (size_t)(sh.sx / 2 + 2)) * sh.TT * sizeof(float);
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
     ks.block = sh.block;
-    ks.smem = (2 * kNS * (size_t)sh.sx + kNS * (size_t)(sh.sx / 2 + 2)) * sh.TT * sizeof(float);
     ks.vec = sh.vec;
     ks.variant = dots;
     if (dots) {
@@ -907,12 +941,12 @@ StApplyDotArgs plan_st_apply_dot(const StencilOp<float>& A, int N, const float* 
     const Shape sh = st_shape(N, {P}, false);
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
+    ks.smem = kNS * (size_t)sh.sx * sh.TT * sizeof(float);
     const int sy = strip_rows(A.H, nseg, nch);
     const int nstrip = (A.H + sy - 1) / sy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
     ks.block = sh.block;
-    ks.smem = kNS * (size_t)sh.sx * sh.TT * sizeof(float);
     ks.vec = sh.vec;
     ks.variant = 0;
     const size_t need = (size_t)ks.gx * ks.gy * sh.TT;
@@ -922,6 +956,21 @@ StApplyDotArgs plan_st_apply_dot(const StencilOp<float>& A, int N, const float* 
 }
 
 // ---- single launches ----
+int launch_st_presid_restrict_update(const StencilOp<float>& A, int N, const float* p, const float* alpha,
+                                     float xscale, float* Xw, const float* B, float* Bc, Skip sk, cudaStream_t s) {
+    KShape ks;
+    StPresidArgs a = plan_st_presid(A, N, p, B, Bc, nullptr, 0.f, true, sk, ks);
+    PTP_REQUIRE(alpha && Xw && ((uintptr_t)Xw % (ks.vec * sizeof(float))) == 0, "fused update: bad arguments");
+    a.alpha = alpha;
+    a.xscale = xscale;
+    a.Xw = Xw;
+    if (record_launch(launch_st_presid_batch, a, ks, body_id(BF_ST_PRESID, ks.vec, ks.variant))) return 1;
+    const dim3 grid(ks.gx, ks.gy);
+    if (ks.vec == 4) st_launch(k_st_presid<4, 1>, grid, ks.block, ks.smem, s, a);
+    else st_launch(k_st_presid<2, 1>, grid, ks.block, ks.smem, s, a);
+    return 1;
+}
+
 int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
                      float omega, bool time_restrict, Skip sk, cudaStream_t s) {
     KShape ks;

@@ -286,6 +286,10 @@ struct Op {             // cm * v1 + cl * v2 on a CSR pattern
     const T* ev2 = nullptr;
 };
 
+// column scalar slots in ColRed::col (each N long; complex scalars of
+// unknown k at columns 2k (re) and 2k+1 (im))
+enum Slot { S_RHO = 0, S_ALPHA = 1, S_BETA = 2, S_RR = 3, S_BB = 4 };
+
 template <typename T>
 struct ColRed {         // per-column reduction workspace
     T* partials = nullptr;   // grid * N * 2
@@ -385,6 +389,12 @@ struct StPresidArgs {
     float* Z0;
     float omega;
     Skip sk;
+    // time restriction only: if alpha is set, X holds the PCG direction p and
+    // the iterate is x = (xscale alpha[n]) p (the last PCG update from zero),
+    // formed on the fly and written to Xw
+    const float* alpha = nullptr;
+    float xscale = 0.f;
+    float* Xw = nullptr;
 };
 struct StRestrictArgs {
     StencilOp<float> Af, Ac;
@@ -420,6 +430,9 @@ StPresidArgs plan_st_presid(const StencilOp<float>& A, int N, const float* X, co
                             float omega, bool time_restrict, Skip sk, KShape& sh);
 int launch_st_presid(const StencilOp<float>& A, int N, const float* X, const float* B, float* R, float* Z0,
                      float omega, bool time_restrict, Skip sk, cudaStream_t s);
+// the time restriction of B - P x with x = (xscale alpha[n]) p, x written to Xw
+int launch_st_presid_restrict_update(const StencilOp<float>& A, int N, const float* p, const float* alpha,
+                                     float xscale, float* Xw, const float* B, float* Bc, Skip sk, cudaStream_t s);
 // Bc = P^T (Bf - Af Xf); Xc = omega Dc^-1 Bc if Xc is set
 StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilOp<float>& Ac, int N, const float* Xf,
                                       const float* Bf, float* Bc, float* Xc, float omega, Skip sk, KShape& sh);

@@ -356,7 +356,16 @@ struct PCG {
         }
     }
 
-    void iterate(bool last) {
+    // Whether the last iteration from a zero start can leave x = xscale
+    // alpha p to its consumer (the time restriction forms it on the fly).
+    bool can_defer_update(int iters) const {
+        if constexpr (sizeof(T) == 4) return iters == 1 && assign_first && !cr.pdone && use_stencil<T>(c);
+        return false;
+    }
+
+    // defer: skip the final x update (only where can_defer_update holds);
+    // p and alpha() then define x
+    void iterate(bool last, bool defer = false) {
         cudaStream_t st = c.stream;
         const int assign = (assign_first && iter == 0) ? 1 : 0;
         if (last && !cr.pdone) {   // no tolerance: the final r and its norm are never read
@@ -364,7 +373,8 @@ struct PCG {
             if constexpr (sizeof(T) == 4) {
                 if (use_stencil<T>(c)) {   // q = A p is not needed: only p.(A p) for alpha
                     c.launches += launch_st_apply_dot(st_op(c, 0, opi), N, p, cr, sk2, st);
-                    c.launches += launch_pcg_xupdate<T>(A.rows, N, xscale, assign, x, p, cr, sk2, st);
+                    if (!(defer && assign))
+                        c.launches += launch_pcg_xupdate<T>(A.rows, N, xscale, assign, x, p, cr, sk2, st);
                     return;
                 }
             }
@@ -386,11 +396,24 @@ struct PCG {
         }
         c.launches += launch_pcg_direction<T>(A.rows, N, z, p, cr, sk2, st);
     }
+
+    const T* alpha() const { return cr.col + S_ALPHA * N; }
 };
 
-// one damped block-Jacobi sweep at time level l on x (in place)
+// x = xscale alpha[n] p left for the time restriction to form (bj_sweep)
+struct DeferredUpdate {
+    bool on = false;
+    const float* p = nullptr;
+    const float* alpha = nullptr;
+    float xscale = 0.f;
+};
+
+// One damped block-Jacobi sweep at time level l on x (in place).  With
+// `defer` set, a sweep from zero whose single PCG iteration would end with
+// x = omega_t alpha p leaves that update out and describes it in *defer
+// (on = false where it cannot).
 template <typename T>
-void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
+void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk, DeferredUpdate* defer = nullptr) {
     const TimeLevel& t = c.tl[l];
     T* r = wbuf<T>(c, 0);
     const size_t cnt = (size_t)c.n * t.N;
@@ -420,7 +443,19 @@ void bj_sweep(Ctx& c, int l, T* x, const T* b, bool x_zero, Skip sk) {
     }
     pcg.init(pcg.gmg);
     const int it = std::max(1, c.opts.pcg_iters);
-    for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
+    const bool dfr = defer && pcg.can_defer_update(it);
+    for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1, dfr);
+    if (defer) {
+        defer->on = false;
+        if constexpr (sizeof(T) == 4) {
+            if (dfr) {
+                defer->on = true;
+                defer->p = pcg.p;
+                defer->alpha = pcg.alpha();
+                defer->xscale = pcg.xscale;
+            }
+        }
+    }
 }
 
 DstSolve dst_of(Ctx& c) {
@@ -571,13 +606,21 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
         c.launches += launch_fill<T>((size_t)c.n * t.N, T(0), x, sk, st);
         zero = false;
     }
+    const bool st_restrict = use_stencil<T>(c) && sizeof(T) == 4 && t.N % 2 == 0;
+    DeferredUpdate du;
     for (int k = 0; k < pre; ++k) {
-        bj_sweep<T>(c, l, x, b, zero, sk);
+        // the last pre-sweep from zero hands x = omega_t alpha p to the restriction
+        const bool hand_over = st_restrict && c.opts.fuse_update && k == pre - 1;
+        bj_sweep<T>(c, l, x, b, zero, sk, hand_over ? &du : nullptr);
         zero = false;
     }
     bool restricted = false;
     if constexpr (sizeof(T) == 4) {
-        if (use_stencil<T>(c) && t.N % 2 == 0) {
+        if (st_restrict && du.on) {
+            c.launches += launch_st_presid_restrict_update(st_op(c, 0, t.op), t.N, du.p, du.alpha, du.xscale, x, b,
+                                                           mgb<T>(c, l + 1), sk, st);
+            restricted = true;
+        } else if (st_restrict) {
             c.launches += launch_st_presid(st_op(c, 0, t.op), t.N, x, b, mgb<T>(c, l + 1), nullptr, 0.f, true, sk, st);
             restricted = true;
         }
@@ -949,9 +992,10 @@ int64_t step_key(const Ctx& c, const ptp_opts& o) {
         const unsigned char* b = static_cast<const unsigned char*>(p);
         for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
     };
-    const int ints[17] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
+    const int ints[18] = {o.precision, o.pcg_iters, o.vcycles, o.pre_smooth, o.post_smooth, o.gmg_smooth,
                           o.coarse_max_it, c.row_block, o.coarse_cycles, o.coarse_solver, o.dft_max_it,
-                          o.stencil, o.k1_fused, o.coarse_direct, c.st_tt, c.st_waves, c.fz_on ? c.fz_level : -1};
+                          o.stencil, o.k1_fused, o.coarse_direct, c.st_tt, c.st_waves, c.fz_on ? c.fz_level : -1,
+                          o.fuse_update};
     const double dbls[3] = {o.omega_t, o.gmg_omega, o.coarse_tol};
     mix(ints, sizeof(ints));
     mix(dbls, sizeof(dbls));

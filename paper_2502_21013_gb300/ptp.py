@@ -36,6 +36,7 @@ class Opts(ctypes.Structure):
         ("init_static", ctypes.c_int), ("newton_eta", ctypes.c_double), ("krylov_dim", ctypes.c_int),
         ("stencil", ctypes.c_int), ("k1_fused", ctypes.c_int),
         ("coarse_direct", ctypes.c_int), ("fuse_coarse", ctypes.c_int),
+        ("fuse_update", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -169,3 +169,28 @@ def test_fused_coarse_levels_are_bitwise_the_separate_launches(name, make):
     assert i0 == i1
     assert np.array_equal(u0, u1)
     assert l1 < l0
+
+
+@pytest.mark.parametrize("name,make,extra", [
+    ("square33_N32", lambda: W.unit_square_problem(33, 32), {}),
+    ("square65_N12", lambda: W.unit_square_problem(65, 12, amps=(70.0,)), {"coarse_solver": 1}),
+    ("transformer65x33_N16", lambda: W.transformer_problem(65, 33, 16), {}),
+    ("square33_N32_fused", lambda: W.unit_square_problem(33, 32), {"fuse_coarse": 1}),
+])
+def test_update_handed_to_the_restriction_is_bitwise_the_update_kernel(name, make, extra):
+    """With fuse_update = 1 (default) the pre-sweep from zero leaves
+    x = omega_t alpha p to the time restriction, which forms and stores it:
+    the same float products as the update kernel, so iterates and iteration
+    counts are identical, with one launch fewer per restricted level."""
+    prob = make()
+    out = []
+    for fuse in (0, 1):
+        c, o = _ctx(prob, precision=ptp.PTP_MIXED, tol=1e-10, max_outer=20000, fuse_update=fuse, **extra)
+        U = torch.zeros((prob.n_free, prob.N), dtype=torch.float64, device="cuda")
+        st, rc = c.solve_dev(U, o)
+        assert rc == ptp.PTP_OK
+        out.append((U.cpu().numpy(), st.outer_iterations, st.kernel_launches / (st.outer_iterations + 1)))
+    (u0, i0, l0), (u1, i1, l1) = out
+    assert i0 == i1
+    assert np.array_equal(u0, u1)
+    assert l1 < l0
