@@ -154,12 +154,15 @@ typedef struct ptp_opts {
                             between its passes (same results bit for bit,
                             half the launches).  0 (default): separate
                             launches, which measured faster on a GB300       */
-    int    fuse_update;  /* 1 (default): on the stencil path, a pre-sweep
-                            from zero with one PCG iteration leaves its
-                            update x = omega_t alpha p to the time
-                            restriction that follows, which forms x on the
-                            fly and stores it (same results bit for bit, one
-                            pass over x fewer); 0 = separate update kernel */
+    int    fuse_update;  /* 1 (default): fewer passes over the iterates of
+                            the time levels, with the same results bit for
+                            bit.  On the stencil path a pre-sweep from zero
+                            with one PCG iteration leaves its update
+                            x = omega_t alpha p to the time restriction that
+                            follows, which forms x on the fly and stores it;
+                            and in a V(pre, 0) cycle (one per outer step)
+                            the prolongations of every level and the update
+                            of U run as one pass.  0 = separate kernels     */
 } ptp_opts;
 
 /* Statistics of the last solve. */

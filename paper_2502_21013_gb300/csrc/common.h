@@ -274,6 +274,9 @@ struct Ctx {
     int fz_nph = 0, fz_grid = 0;
     size_t fz_smem = 0;
     int64_t fz_key = -1;
+    // time levels 0 .. chain_depth - 1 of the V-cycle being enqueued leave
+    // their prolongation to one pass that also updates U (0: none)
+    int chain_depth = 0;
     DBuf<unsigned char> fz_blob; // phases, then the argument structs
 
     ~Ctx();

@@ -553,6 +553,54 @@ __global__ void k_time_prolong_add_b(const ProlongArgs<T>* __restrict__ ps, Batc
     }
 }
 
+// VEC consecutive columns n0.. of one node per thread.  The sum runs from
+// the coarsest level to the finest, the order of the level-by-level
+// prolongations, so U receives the same float value.
+template <typename T, int VEC>
+__device__ __forceinline__ void prolong_chain_add_body(const ChainAddArgs<T>& p, const VGrid& g) {
+    pdl_enter();
+    if (skip_now(p.sk)) return;
+    const double sc = p.scale ? *p.scale : 1.0;
+    const int N = p.N, NC = N / VEC, D = p.D;
+    const size_t total = (size_t)p.rows * NC;
+    for (size_t q = (size_t)g.bx * blockDim.x + threadIdx.x; q < total; q += (size_t)g.gx * blockDim.x) {
+        const size_t i = q / NC;
+        const int n0 = (int)(q - i * NC) * VEC;
+        T s[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) s[k] = T(0);
+#pragma unroll
+        for (int l = kMaxChain - 1; l >= 0; --l) {
+            if (l > D) continue;
+            const T* xl = p.x[l] + i * (size_t)(N >> l);
+            T v[VEC];
+            if (l == 0) {
+                ld_vec<T, VEC>(xl + n0, v);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) v[k] = xl[(n0 + k) >> l];
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) s[k] = l == D ? v[k] : v[k] + s[k];
+        }
+        double* u = p.U + i * (size_t)N + n0;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) u[k] += sc * (double)s[k];
+    }
+}
+template <typename T, int VEC>
+__global__ void k_prolong_chain_add(ChainAddArgs<T> p) { prolong_chain_add_body<T, VEC>(p, native_grid()); }
+template <typename T, int VEC>
+__global__ void k_prolong_chain_add_b(const ChainAddArgs<T>* __restrict__ ps, BatchMap m) {
+    pdl_enter();
+    int i;
+    VGrid g;
+    if (batch_block(m, i, g)) {
+        const auto a_ = ps[i];   // a local copy: no store of the body aliases it
+        prolong_chain_add_body<T, VEC>(a_, g);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void add_to_double_body(const AddArgs<T>& p, const VGrid& g) {
     pdl_enter();
@@ -1006,6 +1054,38 @@ int launch_add_to_double(size_t count, const T* d, double* U, const double* scal
     return 1;
 }
 
+template <typename T>
+int launch_prolong_chain_add_batch(const void* args, BatchMap m, int blocks, const KShape& sh, cudaStream_t s) {
+    const auto* a = static_cast<const ChainAddArgs<T>*>(args);
+    if (sh.vec == 4) launch_k(k_prolong_chain_add_b<T, 4>, dim3(blocks), dim3(256), s, a, m);
+    else launch_k(k_prolong_chain_add_b<T, 1>, dim3(blocks), dim3(256), s, a, m);
+    return 1;
+}
+
+template <typename T>
+int launch_prolong_chain_add(int rows, int N, int D, const T* const* x, double* U, const double* scale, Skip sk,
+                             cudaStream_t s) {
+    PTP_REQUIRE(D >= 0 && D < kMaxChain && (N >> D) << D == N, "prolongation chain: bad level count");
+    ChainAddArgs<T> a{};
+    a.rows = rows;
+    a.N = N;
+    a.D = D;
+    for (int l = 0; l <= D; ++l) a.x[l] = x[l];
+    a.U = U;
+    a.scale = scale;
+    a.sk = sk;
+    const bool v4 = N % 4 == 0 && ((uintptr_t)x[0] % (4 * sizeof(T))) == 0;
+    KShape sh;
+    sh.gx = flat_grid((size_t)rows * (N / (v4 ? 4 : 1)));
+    sh.gy = 1;
+    sh.block = 256;
+    sh.vec = v4 ? 4 : 1;
+    if (record_launch(launch_prolong_chain_add_batch<T>, a, sh)) return 1;
+    if (v4) launch_k(k_prolong_chain_add<T, 4>, dim3(sh.gx), 256, s, a);
+    else launch_k(k_prolong_chain_add<T, 1>, dim3(sh.gx), 256, s, a);
+    return 1;
+}
+
 template <typename TI, typename TO>
 int launch_cast_scaled(size_t count, const TI* x, TO* y, const double* mul, const double* div, cudaStream_t s) {
     launch_k(k_cast_scaled<TI, TO>, flat_grid(count), 256, s, count, x, y, mul, div);
@@ -1048,6 +1128,8 @@ int launch_norm2(size_t count, const T* x, double* partials, unsigned* counter, 
     template int launch_axpy<T>(size_t, T, const T*, T*, Skip, cudaStream_t);                              \
     template int launch_fill<T>(size_t, T, T*, Skip, cudaStream_t);                                        \
     template int launch_add_to_double<T>(size_t, const T*, double*, const double*, Skip, cudaStream_t);    \
+    template int launch_prolong_chain_add<T>(int, int, int, const T* const*, double*, const double*, Skip,    \
+                                             cudaStream_t);                                                   \
     template int launch_split2<T>(int, const T*, double*, double*, Skip, cudaStream_t);                    \
     template int launch_combine2<T>(int, const double*, const double*, T*, Skip, cudaStream_t);            \
     template int launch_norm2<T>(size_t, const T*, double*, unsigned*, double*, cudaStream_t);

@@ -723,11 +723,44 @@ Shape st_shape(int N, std::initializer_list<const void*> ptrs, bool need_even) {
     return s;
 }
 
-// rows per block strip: enough blocks for about g_st_waves per SM, 2..32 rows
-int strip_rows(int H, int nseg, int nch) {
-    const long want = (long)g_st_waves * num_sms();
-    long sy = ((long)H * nseg * nch) / std::max(1L, want);
-    return (int)std::max(2L, std::min(32L, sy));
+// Blocks of `kern` (with `smem` bytes of dynamic shared memory) that fit on
+// one SM at once: the least of the thread, shared-memory and register limits.
+int st_resident(const void* kern, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, size_t>, int> memo;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kern, smem);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    cudaFuncAttributes fa{};
+    PTP_CUDA(cudaFuncGetAttributes(&fa, kern));
+    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+    PTP_CUDA(cudaGetDevice(&dev));
+    PTP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    PTP_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    PTP_CUDA(cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    const size_t per_block = smem + fa.sharedSizeBytes + 1024;   // 1 KB of each block is reserved
+    int r = thr_sm / block;
+    r = std::min(r, (int)((size_t)smem_sm / per_block));
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;   // allocated per warp in units of 256
+    if (regs_warp > 0) r = std::min(r, regs_sm / (regs_warp * ((block + 31) / 32)));
+    r = std::max(1, r);
+    memo[key] = r;
+    return r;
+}
+
+// Rows per block strip.  The blocks of a pass (nseg segments x nch time
+// tiles x strips) should fill whole waves: w = min(g_st_waves, resident)
+// blocks per SM at once.  A pass with few segments and tiles gets one wave
+// of tall strips (every block of an SM starts and ends together, no tail);
+// a larger one gets the fewest waves of strips of at most 64 rows.
+int strip_rows(int H, int nseg, int nch, int resident) {
+    const long want = (long)std::max(1, std::min(g_st_waves, resident)) * num_sms();
+    const long per = std::max(1L, (long)nseg * nch);
+    const long waves = std::max(1L, (per * ((H + 63) / 64) + want - 1) / want);
+    const long nstrip = std::max(1L, std::min((long)H, waves * want / per));
+    const long sy = (H + nstrip - 1) / nstrip;
+    return (int)std::max(2L, sy);
 }
 
 }  // namespace
@@ -872,7 +905,8 @@ StPresidArgs plan_st_presid(const StencilOp<float>& A, int N, const float* X, co
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
     ks.smem = (2 * kNS * (size_t)sh.sx * sh.TT + kNS * (size_t)sh.sx) * sizeof(float);
-    const int sy = strip_rows(A.H, nseg, nch);
+    const void* kern = time_restrict ? (const void*)k_st_presid<4, 1> : (const void*)k_st_presid<4, 0>;
+    const int sy = strip_rows(A.H, nseg, nch, st_resident(kern, sh.block, ks.smem));
     const int nstrip = (A.H + sy - 1) / sy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
@@ -903,7 +937,9 @@ StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilO
     const int nseg = (Ac.W + cxo - 1) / cxo;
     const int nch = N / sh.TT;
     ks.smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
-    const int cy = std::max(1, strip_rows(Ac.H, nseg, nch) / 2);
+    // a strip of cy coarse rows walks 2 cy fine rows
+    const int res = st_resident((const void*)k_st_resid_restrict<4>, sh.block, ks.smem);
+    const int cy = std::max(1, strip_rows(Ac.H, nseg, nch, res));
     const int nstrip = (Ac.H + cy - 1) / cy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
@@ -921,7 +957,7 @@ StInterpArgs plan_st_interp_sweep(const StencilOp<float>& A, int Wc, int Hc, int
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
     ks.smem = (2 * kNS * (size_t)sh.sx + kNS * (size_t)(sh.sx / 2 + 2)) * sh.TT * sizeof(float);
-    const int sy = strip_rows(A.H, nseg, nch);
+    const int sy = strip_rows(A.H, nseg, nch, st_resident((const void*)k_st_interp_sweep<4, 1>, sh.block, ks.smem));
     const int nstrip = (A.H + sy - 1) / sy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;
@@ -942,7 +978,7 @@ StApplyDotArgs plan_st_apply_dot(const StencilOp<float>& A, int N, const float* 
     const int nseg = (A.W + sh.sx - 3) / (sh.sx - 2);
     const int nch = N / sh.TT;
     ks.smem = kNS * (size_t)sh.sx * sh.TT * sizeof(float);
-    const int sy = strip_rows(A.H, nseg, nch);
+    const int sy = strip_rows(A.H, nseg, nch, st_resident((const void*)k_st_apply_dot<4>, sh.block, ks.smem));
     const int nstrip = (A.H + sy - 1) / sy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;

@@ -515,6 +515,18 @@ struct ProlongArgs {   // x^{2m}, x^{2m+1} += xc^m
     T* x;
     Skip sk;
 };
+// U += (*scale) (x_0 + P (x_1 + P (x_2 + ... + P x_D))), P the injection
+// in time (x_l has N >> l columns): the prolongations of a V(pre, 0) cycle
+// from level D down to 0 and the update of U in one pass
+constexpr int kMaxChain = 16;
+template <typename T>
+struct ChainAddArgs {
+    int rows, N, D;
+    const T* x[kMaxChain];
+    double* U;
+    const double* scale;
+    Skip sk;
+};
 template <typename T>
 struct AddArgs {       // U += (*scale) d
     size_t count;
@@ -535,6 +547,9 @@ template <typename TI, typename TO>
 int launch_cast(size_t count, const TI* x, TO* y, Skip sk, cudaStream_t s);
 template <typename T>   // U += s d with s = *scale (scale may be null: s = 1)
 int launch_add_to_double(size_t count, const T* d, double* U, const double* scale, Skip sk, cudaStream_t s);
+template <typename T>   // ChainAddArgs: x[0..D] the time levels' iterates, D < kMaxChain
+int launch_prolong_chain_add(int rows, int N, int D, const T* const* x, double* U, const double* scale, Skip sk,
+                             cudaStream_t s);
 template <typename TI, typename TO>   // y = x * (*mul) / (*div)   (null pointers read as 1)
 int launch_cast_scaled(size_t count, const TI* x, TO* y, const double* mul, const double* div, cudaStream_t s);
 // coarsest level with two steps: split b into sum / difference columns, and combine

@@ -630,8 +630,27 @@ void mgt_vcycle(Ctx& c, int l, bool x_zero, Skip sk, bool full = false) {
         c.launches += launch_spmm<T>(SP_PRESID_RESTRICT, A, t.N, x, b, mgb<T>(c, l + 1), T(0), sk, st);
     }
     mgt_vcycle<T>(c, l + 1, true, sk, full);
-    c.launches += launch_time_prolong_add<T>(c.n, c.tl[l + 1].N, mgx<T>(c, l + 1), x, sk, st);
+    if (l >= c.chain_depth)   // else x stays the smoothed iterate; the chain pass adds the prolongations
+        c.launches += launch_time_prolong_add<T>(c.n, c.tl[l + 1].N, mgx<T>(c, l + 1), x, sk, st);
     for (int k = 0; k < post; ++k) bj_sweep<T>(c, l, x, b, false, sk);
+}
+
+// Levels of one V(pre, 0) cycle from zero whose final iterate is only read
+// by the prolongation to the level above: 0 .. D - 1, where level D is the
+// first whose cycle is not the plain recursion (the exact last level, the
+// DFT level, the fused coarse program, the coarse cycles) and x_D is final
+// when its cycle returns.  0 where post-smoothing or a second cycle reads
+// the finer iterates.
+static int prolong_chain_depth(const Ctx& c) {
+    if (c.opts.post_smooth != 0 || std::max(1, c.opts.vcycles) != 1) return 0;
+    int D = (int)c.tl.size() - 1;
+    if (c.dft_level >= 0) D = std::min(D, c.dft_level);
+    if (c.fz_on) D = std::min(D, c.fz_level);
+    if (c.active_levels < (int)c.tl.size()) D = std::min(D, c.active_levels - 1);
+    if (D < 1 || D >= kMaxChain) return 0;
+    for (int l = 0; l <= D; ++l)
+        if (c.tl[l].N != c.N >> l) return 0;
+    return D;
 }
 
 // One outer step of the fixed point (correction form of eq. iter1) on the
@@ -668,11 +687,20 @@ void outer_step(Ctx& c, Skip sk, int kind) {
         const int it = std::max(1, c.opts.pcg_iters);
         for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
     } else {
+        c.chain_depth = c.opts.fuse_update ? prolong_chain_depth(c) : 0;
         const int cyc = std::max(1, c.opts.vcycles);
         for (int v = 0; v < cyc; ++v) mgt_vcycle<T>(c, 0, v == 0, sk);
     }
+    const int D = c.chain_depth;
+    c.chain_depth = 0;
     const double* sc = sizeof(T) == 4 ? &c.status.p->bscale_used : nullptr;
-    c.launches += launch_add_to_double<T>((size_t)c.n * c.N, mgx<T>(c, 0), X, sc, sk, c.stream);
+    if (D > 0) {
+        const T* xs[kMaxChain];
+        for (int l = 0; l <= D; ++l) xs[l] = mgx<T>(c, l);
+        c.launches += launch_prolong_chain_add<T>(c.n, c.N, D, xs, X, sc, sk, c.stream);
+    } else {
+        c.launches += launch_add_to_double<T>((size_t)c.n * c.N, mgx<T>(c, 0), X, sc, sk, c.stream);
+    }
 }
 
 void final_residual(Ctx& c, int kind) {

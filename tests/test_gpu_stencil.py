@@ -176,16 +176,21 @@ def test_fused_coarse_levels_are_bitwise_the_separate_launches(name, make):
     ("square65_N12", lambda: W.unit_square_problem(65, 12, amps=(70.0,)), {"coarse_solver": 1}),
     ("transformer65x33_N16", lambda: W.transformer_problem(65, 33, 16), {}),
     ("square33_N32_fused", lambda: W.unit_square_problem(33, 32), {"fuse_coarse": 1}),
+    ("square33_N32_fp64", lambda: W.unit_square_problem(33, 32), {"precision": ptp.PTP_FP64, "tol": 1e-11}),
 ])
 def test_update_handed_to_the_restriction_is_bitwise_the_update_kernel(name, make, extra):
     """With fuse_update = 1 (default) the pre-sweep from zero leaves
-    x = omega_t alpha p to the time restriction, which forms and stores it:
-    the same float products as the update kernel, so iterates and iteration
-    counts are identical, with one launch fewer per restricted level."""
+    x = omega_t alpha p to the time restriction, which forms and stores it
+    (the same float products as the update kernel), and the prolongations of
+    the V(1, 0) cycle and the update of U run as one pass summing the levels
+    from the coarsest in the order of the level-by-level prolongations: the
+    iterates and iteration counts are identical, with fewer launches."""
     prob = make()
     out = []
     for fuse in (0, 1):
-        c, o = _ctx(prob, precision=ptp.PTP_MIXED, tol=1e-10, max_outer=20000, fuse_update=fuse, **extra)
+        kw = dict(precision=ptp.PTP_MIXED, tol=1e-10, max_outer=20000)
+        kw.update(extra)
+        c, o = _ctx(prob, fuse_update=fuse, **kw)
         U = torch.zeros((prob.n_free, prob.N), dtype=torch.float64, device="cuda")
         st, rc = c.solve_dev(U, o)
         assert rc == ptp.PTP_OK
