@@ -47,16 +47,7 @@ __global__ void __launch_bounds__(kDstThreads) k_dst_b(const DstArgs* __restrict
 
 template <typename... KArgs, typename... Args>
 void dst_launch(void (*kernel)(KArgs...), int blocks, size_t smem, cudaStream_t s, Args&&... args) {
-    static std::mutex mu;
-    static std::map<const void*, size_t> granted;   // dynamic shared memory granted per kernel
-    if (smem > 48 * 1024) {
-        std::lock_guard<std::mutex> lock(mu);
-        size_t& g = granted[(const void*)kernel];
-        if (smem > g) {
-            PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            g = smem;
-        }
-    }
+    ensure_dynamic_smem((const void*)kernel, smem);
     launch_k_smem(kernel, dim3(std::max(1, blocks)), dim3(kDstThreads), smem, s, std::forward<Args>(args)...);
 }
 

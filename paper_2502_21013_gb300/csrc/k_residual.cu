@@ -21,6 +21,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "dev_math.cuh"
 #include "kernels.h"
@@ -418,6 +421,30 @@ bool pdl_enabled() {
     return on == 1;
 }
 
+void ensure_dynamic_smem(const void* kernel, size_t smem) {
+    if (smem <= 48 * 1024) return;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> granted;
+    int dev = 0;
+    PTP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& g = granted[std::make_pair(dev, kernel)];
+    if (smem > g) {
+        PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        g = smem;
+    }
+}
+
+void launch_failed(cudaError_t e, const void* kernel, const cudaLaunchConfig_t& cfg) {
+    (void)cudaGetLastError();   // the refused launch also set the last-error state
+    const char* name = nullptr;
+    if (cudaFuncGetName(&name, kernel) != cudaSuccess || !name) name = "?";
+    throw Error(PTP_ECUDA, std::string("launch of ") + name + " (grid " + std::to_string(cfg.gridDim.x) + " x " +
+                               std::to_string(cfg.gridDim.y) + " x " + std::to_string(cfg.gridDim.z) + ", block " +
+                               std::to_string(cfg.blockDim.x) + ", dynamic shared memory " +
+                               std::to_string(cfg.dynamicSmemBytes) + " B): " + cudaGetErrorString(e));
+}
+
 int num_sms() {
     static int sms = 0;
     if (sms == 0) {
@@ -448,12 +475,7 @@ int launch_residual(const ResidualArgs& a, cudaStream_t s) {
         }
         if (blocks <= (long)a.partials_cap) {
             const int nstrip = (a.st_H + sy - 1) / sy;
-            static thread_local int smem_set = -1;
-            if (smem_set < 0) {
-                PTP_CUDA(cudaFuncSetAttribute(k_k1_structured, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kK1Smem));
-                smem_set = 1;
-            }
+            ensure_dynamic_smem((const void*)k_k1_structured, kK1Smem);
             launch_k_smem(k_k1_structured, dim3(nseg * nstrip, nch), dim3(kBlock), kK1Smem, s, a, sy, nseg);
             return 1;
         }

@@ -965,15 +965,7 @@ int launch_pcg_direction(int rows, int N, const T* z, T* p, ColRed<T> cr, Skip s
 // raises a kernel's dynamic shared memory limit to smem once per size
 template <typename... KArgs>
 void grant_smem(void (*kernel)(KArgs...), size_t smem) {
-    if (smem <= 48 * 1024) return;
-    static std::mutex mu;
-    static std::map<const void*, size_t> granted;
-    std::lock_guard<std::mutex> lock(mu);
-    size_t& g = granted[(const void*)kernel];
-    if (smem > g) {
-        PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        g = smem;
-    }
+    ensure_dynamic_smem((const void*)kernel, smem);
 }
 
 template <typename T>

@@ -777,16 +777,7 @@ int strip_rows(int H, int nseg, int nch, int resident) {
 // sizes depend on the columns of the level).
 template <typename... KArgs, typename... Args>
 static void st_launch(void (*kernel)(KArgs...), dim3 grid, int block, size_t smem, cudaStream_t s, Args&&... args) {
-    static std::mutex mu;
-    static std::map<const void*, size_t> granted;
-    if (smem > 48 * 1024) {
-        std::lock_guard<std::mutex> lock(mu);
-        size_t& g = granted[(const void*)kernel];
-        if (smem > g) {
-            PTP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            g = smem;
-        }
-    }
+    ensure_dynamic_smem((const void*)kernel, smem);
     launch_k_smem(kernel, grid, dim3(block), smem, s, std::forward<Args>(args)...);
 }
 
@@ -1187,8 +1178,7 @@ bool fused_body_supported(int body) {
 }
 
 int fused_program_grid(size_t smem) {
-    if (smem > 48 * 1024)
-        PTP_CUDA(cudaFuncSetAttribute(k_fused_program, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dynamic_smem((const void*)k_fused_program, smem);
     int per_sm = 0;
     PTP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_program, kStBlock, smem));
     return per_sm * num_sms();

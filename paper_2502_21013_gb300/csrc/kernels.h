@@ -130,6 +130,16 @@ inline bool record_foreign() {
 }
 
 
+// A launch the runtime refused: the error names the kernel and its shape
+// (and clears the runtime's last-error state, so later calls do not see it).
+[[noreturn]] void launch_failed(cudaError_t e, const void* kernel, const cudaLaunchConfig_t& cfg);
+
+// Raise `kernel`'s dynamic shared-memory limit on the current device to at
+// least `smem` bytes.  One record per (device, kernel) for the whole
+// process, so the limit only grows: launches of one kernel from different
+// call sites cannot lower it under one another.
+void ensure_dynamic_smem(const void* kernel, size_t smem);
+
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
     if (record_foreign()) return;
@@ -143,7 +153,8 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
     attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) launch_failed(e, (const void*)kernel, cfg);
 }
 
 // the same with dynamic shared memory
@@ -161,7 +172,8 @@ inline void launch_k_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_
     attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PTP_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) launch_failed(e, (const void*)kernel, cfg);
 }
 
 // ---------------------------------------------------------------------------

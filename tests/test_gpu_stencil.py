@@ -199,3 +199,28 @@ def test_update_handed_to_the_restriction_is_bitwise_the_update_kernel(name, mak
     assert i0 == i1
     assert np.array_equal(u0, u1)
     assert l1 < l0
+
+
+def test_shared_memory_limit_never_shrinks_in_a_fresh_process():
+    """The same stencil kernel is launched from several call sites with ring
+    sizes that differ per time level (the restriction after a sweep from
+    zero, and after a sweep from a nonzero iterate).  Its dynamic
+    shared-memory limit must only grow: a fresh process (nothing granted
+    yet) running a few mixed multigrid-in-time cycles, whose first cycle
+    takes one call site and later cycles the other, completes."""
+    import subprocess
+    import sys
+    script = (
+        "import sys; sys.path.insert(0, '.'); import numpy as np, torch, workloads as W\n"
+        "from paper_2502_21013_gb300 import ptp\n"
+        "p = W.config_plain_fp64(); c = ptp.Context(0); ptp.load_problem(c, p)\n"
+        "o = ptp.default_opts(precision=ptp.PTP_MIXED); c.setup(o)\n"
+        "n, N, _, _ = c.sizes()\n"
+        "B = torch.tensor(np.random.default_rng(4).normal(size=(n, N)), device='cuda')\n"
+        "X = torch.empty_like(B)\n"
+        "r = c.periodic_solve_dev(B, X, 8, o)\n"
+        "assert r < 1e-3, r\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", script], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and "ok" in out.stdout, out.stdout[-2000:] + out.stderr[-2000:]
