@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include <cooperative_groups.h>
 
@@ -749,18 +750,37 @@ int st_resident(const void* kern, int block, size_t smem) {
     return r;
 }
 
-// Rows per block strip.  The blocks of a pass (nseg segments x nch time
-// tiles x strips) should fill whole waves: w = min(g_st_waves, resident)
-// blocks per SM at once.  A pass with few segments and tiles gets one wave
-// of tall strips (every block of an SM starts and ends together, no tail);
-// a larger one gets the fewest waves of strips of at most 64 rows.
-int strip_rows(int H, int nseg, int nch, int resident) {
-    const long want = (long)std::max(1, std::min(g_st_waves, resident)) * num_sms();
+// Rows per block strip.  A pass has nseg segments x nch time tiles x
+// strips blocks, of which S = min(g_st_waves, resident) per SM run at once;
+// each block walks its strip plus `halo` rows.  The strip height minimises
+// waves x (rows + halo), waves = ceil(blocks / (S x SMs)): with few
+// segments and tiles that is one wave of tall strips (every block of an SM
+// starts and ends together), with many it is the fewest waves of shorter
+// strips.  Memoised (the search is over H heights).
+int strip_rows(int H, int nseg, int nch, int resident, double halo = 2.0, int min_rows = 2) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, long, long, double, int>, int> memo;
+    const long S = (long)std::max(1, std::min(g_st_waves, resident)) * num_sms();
     const long per = std::max(1L, (long)nseg * nch);
-    const long waves = std::max(1L, (per * ((H + 63) / 64) + want - 1) / want);
-    const long nstrip = std::max(1L, std::min((long)H, waves * want / per));
-    const long sy = (H + nstrip - 1) / nstrip;
-    return (int)std::max(2L, sy);
+    const auto key = std::make_tuple(H, per, S, halo, min_rows);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    double best = 1e300;
+    long rows_best = std::max(1, H);
+    for (long ns = 1; ns <= H; ++ns) {
+        const long rows = (H + ns - 1) / ns;
+        const long strips = (H + rows - 1) / rows;
+        const long waves = (per * strips + S - 1) / S;
+        const double t = (double)waves * ((double)rows + halo);
+        if (t < best - 1e-9) {
+            best = t;
+            rows_best = rows;
+        }
+    }
+    const int r = (int)std::max((long)min_rows, rows_best);
+    memo[key] = r;
+    return r;
 }
 
 }  // namespace
@@ -928,9 +948,9 @@ StRestrictArgs plan_st_resid_restrict(const StencilOp<float>& Af, const StencilO
     const int nseg = (Ac.W + cxo - 1) / cxo;
     const int nch = N / sh.TT;
     ks.smem = (2 * kNS + 3) * (size_t)sh.sx * sh.TT * sizeof(float);
-    // a strip of cy coarse rows walks 2 cy fine rows
+    // a strip of cy coarse rows walks 2 cy + 3 fine rows: 1.5 coarse rows of halo
     const int res = st_resident((const void*)k_st_resid_restrict<4>, sh.block, ks.smem);
-    const int cy = std::max(1, strip_rows(Ac.H, nseg, nch, res));
+    const int cy = strip_rows(Ac.H, nseg, nch, res, 1.5, 1);
     const int nstrip = (Ac.H + cy - 1) / cy;
     ks.gx = nseg * nstrip;
     ks.gy = nch;

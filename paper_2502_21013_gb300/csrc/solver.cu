@@ -681,18 +681,24 @@ void outer_step(Ctx& c, Skip sk, int kind) {
         a.st_no_mass = 1;
     }
     c.launches += launch_residual_law(a, law_data(c), c.stream);
+    int D = 0;   // levels whose prolongation the chain pass below adds
     if (kind == STEP_STATIC) {
         PCG<T> pcg(c, c.coarse_ops[0], c.N, mgb<T>(c, 0), mgx<T>(c, 0), T(1), 0.0, sk, true);
         pcg.init();
         const int it = std::max(1, c.opts.pcg_iters);
         for (int k = 0; k < it; ++k) pcg.iterate(k == it - 1);
     } else {
+        // set for this cycle only: other callers of the V-cycle (also after an
+        // exception here) see 0 and prolongate level by level
+        struct Reset {
+            int& v;
+            ~Reset() { v = 0; }
+        } reset{c.chain_depth};
         c.chain_depth = c.opts.fuse_update ? prolong_chain_depth(c) : 0;
+        D = c.chain_depth;
         const int cyc = std::max(1, c.opts.vcycles);
         for (int v = 0; v < cyc; ++v) mgt_vcycle<T>(c, 0, v == 0, sk);
     }
-    const int D = c.chain_depth;
-    c.chain_depth = 0;
     const double* sc = sizeof(T) == 4 ? &c.status.p->bscale_used : nullptr;
     if (D > 0) {
         const T* xs[kMaxChain];
