@@ -293,10 +293,12 @@ def k1_algorithmic_flops(info):
 
 def measure_stencil(ctx, info, stream, dev, reps=50):
     """Level-0 float periodic residual R = B - [(M + tau L) X^n - M X^{n-1}]
-    (the 7-point stencil pass of the block-Jacobi smoother), timed with CUDA
-    events on the context stream: algorithmic bytes (X, B in, R out, the two
-    stencils once: 64 B per node) per launch over the average launch time.
-    X, B and R together (200 MB on the bench workload) exceed L2."""
+    (the 7-point stencil pass that starts a block-Jacobi sweep from a nonzero
+    iterate; the V(1, 0) cycle from zero runs the same stencil code summed
+    over step pairs as its time restriction), timed with CUDA events on the
+    context stream: algorithmic bytes (X, B in, R out, the two stencils once:
+    64 B per node) per launch over the average launch time.  X, B and R
+    together (200 MB on the bench workload) exceed L2."""
     import torch
     n, N = info["n_free"], info["N"]
     X = torch.randn((n, N), dtype=torch.float32, device=dev)
